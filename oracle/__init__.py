@@ -1,0 +1,238 @@
+"""CPU oracle for the Cell2Fire fire-growth path (test infrastructure only).
+
+This package is the plain, slow, single-threaded restatement of the method
+(Pais et al., arXiv:1905.09317, Algorithm 1 with Secs. 3.1-3.7 and Eqs. 1-4)
+that the GPU library is checked against.  Only the test-suite, the smoke
+check and the CPU-baseline leg of the benchmark may import it; the product
+path never does.  It shares no code with the CUDA library.
+
+The arithmetic lives in ``c2f_oracle.c`` (plain C, binary64, contraction
+off); this module compiles it with gcc on first use and wraps it with
+ctypes.  ``burn_prob`` (the burn-probability count, Sec. 3.6 / 3.1 outputs)
+is a plain numpy sum over replica scars.
+
+Parity status: the FBP surface-spread equations (not printed in the paper)
+are "parity unpinned" against their publication; they are pinned only by
+closed-form properties.  Everything else is pinned (see tests/).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "c2f_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ROW_LEN = 18
+ROW_FIELDS = ("hros", "bros", "lb", "fros", "a", "e", "ux", "uy", "wsv", "wse")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (no contraction, no fast-math)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math",
+           "-fvisibility=hidden", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("seed", C.c_uint64),
+        ("hours", C.c_int32),
+        ("minutes_per_step", C.c_int32),
+        ("ignition_mode", C.c_int32),
+        ("ignition_cell", C.c_int32),
+        ("ros_sigma", C.c_double),
+        ("ros_threshold", C.c_double),
+        ("burnout_delta", C.c_double),
+        ("ellipse_mode", C.c_int32),
+        ("o1_curing_pct", C.c_double),
+        ("m1_pc", C.c_double),
+        ("const_ros", C.c_double),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(build())
+        d, f, i32, u32, u64, i64 = C.c_double, C.c_float, C.c_int32, C.c_uint32, C.c_uint64, C.c_int64
+        P = C.POINTER
+        lib.or_exp.restype = d; lib.or_exp.argtypes = [d]
+        lib.or_log.restype = d; lib.or_log.argtypes = [d]
+        lib.or_pow.restype = d; lib.or_pow.argtypes = [d, d]
+        lib.or_sincos_deg.restype = None; lib.or_sincos_deg.argtypes = [d, P(d), P(d)]
+        lib.or_expf.restype = f; lib.or_expf.argtypes = [f]
+        lib.or_logf.restype = f; lib.or_logf.argtypes = [f]
+        lib.or_cos_turnsf.restype = f; lib.or_cos_turnsf.argtypes = [f]
+        lib.or_philox4x32_10.restype = None
+        lib.or_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
+        lib.or_noise_factor.restype = f
+        lib.or_noise_factor.argtypes = [u64, u32, u32, u32, f]
+        lib.or_fbp_cell.restype = None
+        lib.or_fbp_cell.argtypes = [C.c_int, d, d, d, d, d, d, d, d, C.c_int, P(d)]
+        lib.or_create.restype = C.c_void_p
+        lib.or_create.argtypes = [i32, i32, d, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  i32, C.c_void_p, P(Params)]
+        lib.or_destroy.restype = None; lib.or_destroy.argtypes = [C.c_void_p]
+        lib.or_distances.restype = None; lib.or_distances.argtypes = [C.c_void_p, P(i64)]
+        lib.or_cell_row.restype = None; lib.or_cell_row.argtypes = [C.c_void_p, i32, i32, P(d)]
+        lib.or_base_inc.restype = None
+        lib.or_base_inc.argtypes = [C.c_void_p, i32, i32, P(i64), P(d)]
+        lib.or_ignition_cell.restype = i32; lib.or_ignition_cell.argtypes = [C.c_void_p, i32]
+        for name in ("or_run_replica", "or_run_replica_event"):
+            fn = getattr(lib, name)
+            fn.restype = C.c_int
+            fn.argtypes = [C.c_void_p, i32, C.c_void_p, C.c_void_p, P(i64), P(i32), P(i32)]
+        _lib = lib
+        return lib
+
+
+# ---------------------------------------------------------------- math pins
+def exp(x: float) -> float: return _load().or_exp(float(x))
+def log(x: float) -> float: return _load().or_log(float(x))
+def pow(x: float, y: float) -> float: return _load().or_pow(float(x), float(y))  # noqa: A001
+
+
+def sincos_deg(x: float):
+    s, c = C.c_double(), C.c_double()
+    _load().or_sincos_deg(float(x), C.byref(s), C.byref(c))
+    return s.value, c.value
+
+
+def expf(x) -> np.float32: return np.float32(_load().or_expf(float(np.float32(x))))
+def logf(x) -> np.float32: return np.float32(_load().or_logf(float(np.float32(x))))
+def cos_turnsf(u) -> np.float32: return np.float32(_load().or_cos_turnsf(float(np.float32(u))))
+
+
+def philox4x32_10(ctr, key):
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    _load().or_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def noise_factor(seed: int, replica: int, cell: int, hour: int, sigma: float) -> np.float32:
+    return np.float32(_load().or_noise_factor(int(seed), replica, cell, hour,
+                                              float(np.float32(sigma))))
+
+
+def fbp_cell(fuel, slope_pct, aspect_deg, ws, wd_from, ffmc, bui, m1_pc=50.0,
+             o1_curing=60.0, ellipse_mode=0) -> dict:
+    out = (C.c_double * ROW_LEN)()
+    _load().or_fbp_cell(int(fuel), float(slope_pct), float(aspect_deg), float(ws),
+                        float(wd_from), float(ffmc), float(bui), float(m1_pc),
+                        float(o1_curing), int(ellipse_mode), out)
+    row = list(out)
+    d = {k: row[i] for i, k in enumerate(ROW_FIELDS)}
+    d["ros8"] = np.array(row[10:18])
+    return d
+
+
+# ---------------------------------------------------------------- simulation
+def make_params(seed=0, hours=1, minutes_per_step=1, ignition_mode=0, ignition_cell=0,
+                ros_sigma=0.0, ros_threshold=0.0, burnout_delta=0.0, ellipse_mode=0,
+                o1_curing_pct=60.0, m1_pc=50.0, const_ros=0.0, **_ignored) -> Params:
+    return Params(int(seed), int(hours), int(minutes_per_step), int(ignition_mode),
+                  int(ignition_cell), float(ros_sigma), float(ros_threshold),
+                  float(burnout_delta), int(ellipse_mode), float(o1_curing_pct),
+                  float(m1_pc), float(const_ros))
+
+
+class Oracle:
+    """One landscape + weather stream + run parameters, simulated replica by replica."""
+
+    def __init__(self, fuel, slope=None, aspect=None, unburnable=None, cell_size=100.0,
+                 weather=None, **params):
+        self.lib = _load()
+        fuel = np.ascontiguousarray(fuel, dtype=np.uint8)
+        self.rows, self.cols = fuel.shape
+        self.n = self.rows * self.cols
+        self._fuel = fuel
+        self._slope = None if slope is None else np.ascontiguousarray(slope, dtype=np.float32)
+        self._aspect = None if aspect is None else np.ascontiguousarray(aspect, dtype=np.float32)
+        self._unb = None if unburnable is None else np.ascontiguousarray(unburnable, dtype=np.uint8)
+        w = np.ascontiguousarray(weather, dtype=np.float64).reshape(-1, 4)
+        self._weather = w
+        self.params = make_params(**params)
+        if w.shape[0] < self.params.hours:
+            raise ValueError("weather stream shorter than the simulated hours")
+        if 60 % self.params.minutes_per_step:
+            raise ValueError("minutes_per_step must divide 60")
+
+        def ptr(a):
+            return None if a is None else a.ctypes.data_as(C.c_void_p)
+        self._h = self.lib.or_create(self.rows, self.cols, float(cell_size), ptr(fuel),
+                                     ptr(self._slope), ptr(self._aspect), ptr(self._unb),
+                                     int(w.shape[0]), ptr(w), C.byref(self.params))
+        self.sph = 60 // self.params.minutes_per_step
+        self.steps = self.params.hours * self.sph
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.or_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def distances(self):
+        d = (C.c_int64 * 8)()
+        self.lib.or_distances(self._h, d)
+        return list(d)
+
+    def cell_row(self, cell: int, hour: int) -> dict:
+        out = (C.c_double * ROW_LEN)()
+        self.lib.or_cell_row(self._h, int(cell), int(hour), out)
+        row = list(out)
+        d = {k: row[i] for i, k in enumerate(ROW_FIELDS)}
+        d["ros8"] = np.array(row[10:18])
+        return d
+
+    def base_inc(self, cell: int, hour: int):
+        b = (C.c_int64 * 8)()
+        hr = C.c_double()
+        self.lib.or_base_inc(self._h, int(cell), int(hour), b, C.byref(hr))
+        return np.array(list(b), dtype=np.int64), hr.value
+
+    def ignition_cell(self, replica: int) -> int:
+        return int(self.lib.or_ignition_cell(self._h, int(replica)))
+
+    def _run(self, fn, replica):
+        scar = np.zeros(self.n, dtype=np.uint8)
+        ign = np.zeros(self.n, dtype=np.int32)
+        w, ni, ic = C.c_int64(), C.c_int32(), C.c_int32()
+        fn(self._h, int(replica), scar.ctypes.data_as(C.c_void_p),
+           ign.ctypes.data_as(C.c_void_p), C.byref(w), C.byref(ni), C.byref(ic))
+        return {"scar": scar.reshape(self.rows, self.cols),
+                "ign": ign.reshape(self.rows, self.cols),
+                "work": int(w.value), "n_ignited": int(ni.value), "ignition_cell": int(ic.value)}
+
+    def run_replica(self, replica: int) -> dict:
+        """Algorithm 1 stepped period by period (O1)."""
+        return self._run(self.lib.or_run_replica, replica)
+
+    def run_replica_event(self, replica: int) -> dict:
+        """Label-setting search over ignition steps (O2); equals O1."""
+        return self._run(self.lib.or_run_replica_event, replica)
+
+
+def burn_prob(scars) -> np.ndarray:
+    """count[c] = number of replicas whose scar contains c (uint32)."""
+    s = np.asarray(scars)
+    return s.astype(np.uint32).sum(axis=0, dtype=np.uint64).astype(np.uint32)

@@ -1,0 +1,120 @@
+"""Pins of the oracle's own elementary functions and Philox generator.
+
+The oracle computes every exp/log/sin/cos itself (so the GPU can reproduce
+it bit for bit); these tests pin those functions to high-precision values
+from mpmath (an independent arbitrary-precision library) and Philox to its
+published known-answer vectors.
+"""
+import math
+import os
+
+import mpmath
+import numpy as np
+import pytest
+
+import oracle
+from conftest import ROOT
+
+mpmath.mp.prec = 200
+ULP = 2.0 ** -52
+
+
+def _rel(a, b):
+    b = float(b)
+    return abs(a - b) / abs(b) if b != 0 else abs(a)
+
+
+def test_exp_accuracy():
+    xs = np.concatenate([np.linspace(-745.0, 709.7, 4001), np.linspace(-1, 1, 2001),
+                         [0.0, 1e-300, -1e-300, 0.5 * math.log(2), -0.5 * math.log(2)]])
+    worst = max(_rel(oracle.exp(x), mpmath.exp(mpmath.mpf(float(x)))) for x in xs
+                if float(mpmath.exp(mpmath.mpf(float(x)))) > 1e-300)
+    assert worst <= 2 * ULP
+    assert oracle.exp(0.0) == 1.0
+    assert oracle.exp(800.0) == math.inf and oracle.exp(-800.0) == 0.0
+
+
+def test_log_accuracy():
+    xs = np.concatenate([np.exp(np.linspace(-700, 700, 4001)), np.linspace(0.5, 2.0, 3001),
+                         [1.0, 2.0, 0.5, 1e-310, 5e-324, 1.7e308]])
+    for x in xs:
+        ref = mpmath.log(mpmath.mpf(float(x)))
+        got = oracle.log(float(x))
+        if ref == 0:
+            assert got == 0.0
+        else:
+            # relative error near 1 is bounded by the absolute error of log(m)
+            assert abs(got - float(ref)) <= 2 * ULP * max(abs(float(ref)), 1.0) * 1.0001
+    assert oracle.log(1.0) == 0.0
+    assert oracle.log(0.0) == -math.inf and math.isnan(oracle.log(-1.0))
+
+
+def test_pow_accuracy():
+    rng = np.random.default_rng(0)
+    for _ in range(3000):
+        x = float(rng.uniform(1e-6, 100.0)); y = float(rng.uniform(-5, 5))
+        ref = mpmath.power(mpmath.mpf(x), mpmath.mpf(y))
+        bound = (abs(y * math.log(x)) + 3.0) * ULP
+        assert _rel(oracle.pow(x, y), ref) <= bound
+    assert oracle.pow(0.0, 2.155) == 0.0 and oracle.pow(0.0, 0.0) == 1.0
+
+
+def test_sincos_deg_accuracy_and_exact_quadrants():
+    xs = np.concatenate([np.linspace(-1000, 1000, 8001), [45.0, 135.0, 30.0, 60.0, 1e-8]])
+    for x in xs:
+        s, c = oracle.sincos_deg(float(x))
+        rad = mpmath.mpf(float(x)) * mpmath.pi / 180
+        assert abs(s - float(mpmath.sin(rad))) <= 3 * ULP
+        assert abs(c - float(mpmath.cos(rad))) <= 3 * ULP
+    for k in range(-12, 13):
+        s, c = oracle.sincos_deg(90.0 * k)
+        exp_s = [0.0, 1.0, 0.0, -1.0][k % 4]
+        exp_c = [1.0, 0.0, -1.0, 0.0][k % 4]
+        assert s == exp_s and c == exp_c, (k, s, c)
+
+
+def test_binary32_functions():
+    f32ulp = 2.0 ** -23
+    for x in np.linspace(-87.0, 88.0, 3001, dtype=np.float32):
+        ref = mpmath.exp(mpmath.mpf(float(x)))
+        assert _rel(float(oracle.expf(x)), ref) <= 1.5 * f32ulp
+    assert oracle.expf(0.0) == np.float32(1.0)
+    for u in np.concatenate([np.linspace(2.0 ** -25, 1.0, 3001, dtype=np.float32),
+                             np.float32([1.0, 0.5, 2.0 ** -24])]):
+        ref = mpmath.log(mpmath.mpf(float(u)))
+        got = float(oracle.logf(u))
+        assert abs(got - float(ref)) <= 1.5 * f32ulp * max(abs(float(ref)), 1.0)
+    assert oracle.logf(1.0) == 0.0
+    for u in np.linspace(0.0, 1.0, 4001, dtype=np.float32):
+        ref = mpmath.cos(2 * mpmath.pi * mpmath.mpf(float(u)))
+        assert abs(float(oracle.cos_turnsf(u)) - float(ref)) <= 2.0 * f32ulp
+    for q in range(5):
+        assert oracle.cos_turnsf(q * 0.25) == [1.0, 0.0, -1.0, 0.0, 1.0][q]
+
+
+def _kat():
+    rows = []
+    with open(os.path.join(ROOT, "tests", "golden", "philox_kat.txt")) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].split()
+            if line:
+                v = [int(t, 16) for t in line]
+                rows.append((v[:4], v[4:6], v[6:10]))
+    return rows
+
+
+@pytest.mark.parametrize("ctr,key,out", _kat())
+def test_philox_known_answers(ctr, key, out):
+    assert oracle.philox4x32_10(ctr, key) == out
+
+
+def test_noise_factor_distribution():
+    """exp(sigma z) with z from Box-Muller: log f / sigma has mean 0, variance 1."""
+    sig = 0.1
+    z = np.array([math.log(float(oracle.noise_factor(1234, r, c, 0, sig))) / sig
+                  for r in range(40) for c in range(500)])
+    assert abs(z.mean()) < 0.03 and abs(z.std() - 1.0) < 0.03
+    assert oracle.noise_factor(1, 2, 3, 4, 0.0) == np.float32(1.0)
+    # one draw per (replica, cell, hour): changing any coordinate changes it
+    a = oracle.noise_factor(7, 1, 2, 3, sig)
+    assert a != oracle.noise_factor(7, 1, 2, 4, sig) and a != oracle.noise_factor(7, 2, 2, 3, sig)

@@ -1,0 +1,139 @@
+"""Pins of the oracle's step loop (Algorithm 1) and burn-probability count.
+
+- hand-enumerated ignition steps and work counts on 3x3 and 5x5 grids
+  (tests/golden, derived by hand from Secs. 3.1, 3.3, 3.4 and A5);
+- arrival time ceil(d / ROS) along rows;
+- exact symmetries: circle under the 8 symmetries of the square, rotating
+  and mirroring the wind rotates and mirrors the scar;
+- brute force: the label-setting search (O2) equals the stepped loop (O1)
+  on random small landscapes, including noise, thresholds and delta burn-out;
+- the threshold and delta rules of Sec. 3.1 and A5 (i).
+"""
+import numpy as np
+import pytest
+
+import c2f_synth as S
+import oracle
+from conftest import read_golden_grid
+
+
+def homog(rows, cols, wd=270.0, ws=0.0, hours=1, **params):
+    fuel = np.full((rows, cols), 1, dtype=np.uint8)
+    weather = S.constant_weather(hours, ws=ws, wd_from=wd)
+    p = dict(hours=hours, ignition_mode=0, ignition_cell=(rows // 2) * cols + cols // 2)
+    p.update(params)
+    return oracle.Oracle(fuel, weather=weather, **p)
+
+
+@pytest.mark.parametrize("name", ["hand_3x3.txt", "hand_5x5.txt"])
+@pytest.mark.parametrize("runner", ["run_replica", "run_replica_event"])
+def test_hand_enumeration(name, runner):
+    meta, grid = read_golden_grid(name)
+    g = np.array(grid)
+    o = homog(g.shape[0], g.shape[1], hours=int(meta["hours"]), const_ros=float(meta["const_ros"]))
+    r = getattr(o, runner)(0)
+    assert np.array_equal(r["ign"], g)
+    assert r["work"] == int(meta["work"])
+    assert r["n_ignited"] == g.size
+
+
+def test_arrival_time_is_distance_over_rate():
+    # 1 x 41 strip, constant ROS: cell at distance d ignites at ceil(100 d / ros) per hop
+    for ros in (7.0, 10.0, 33.0, 99.0):
+        o = homog(1, 41, hours=3, const_ros=ros)
+        r = o.run_replica(0)
+        hop = int(np.ceil(100.0 / ros))
+        ign = r["ign"][0]
+        for d in range(0, 21):
+            expect = d * hop if d * hop <= o.steps else -1
+            assert ign[20 + d] == expect and ign[20 - d] == expect
+
+
+def test_circle_is_invariant_under_square_symmetries():
+    o = homog(31, 31, ws=0.0, hours=4)
+    ign = o.run_replica(0)["ign"]
+    for k in range(4):
+        assert np.array_equal(np.rot90(ign, k), ign)
+        assert np.array_equal(np.fliplr(np.rot90(ign, k)), ign)
+
+
+def test_rotating_the_wind_rotates_the_scar():
+    east = homog(41, 41, wd=270.0, ws=25.0, hours=3).run_replica(0)["ign"]
+    north = homog(41, 41, wd=180.0, ws=25.0, hours=3).run_replica(0)["ign"]
+    west = homog(41, 41, wd=90.0, ws=25.0, hours=3).run_replica(0)["ign"]
+    assert np.array_equal(np.rot90(east), north)
+    assert np.array_equal(np.fliplr(east), west)
+    assert (east[:, 21:] >= 0).sum() > (east[:, :20] >= 0).sum()   # grows downwind
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_event_search_equals_stepped_loop(seed):
+    w = S.random_small_case(seed)
+    L = w.landscape
+    o = oracle.Oracle(L.fuel, L.slope, L.aspect, L.unburnable, weather=w.weather, **w.params)
+    if o.lib.or_ignition_cell(o._h, 0) < 0:
+        pytest.skip("no burnable cell")
+    for r in range(3):
+        a, b = o.run_replica(r), o.run_replica_event(r)
+        assert np.array_equal(a["ign"], b["ign"])
+        assert a["work"] == b["work"] and a["n_ignited"] == b["n_ignited"]
+
+
+def test_event_search_equals_stepped_loop_on_workload_sample():
+    w = S.config2(side=96, n_replicas=4, hours=6)
+    L = w.landscape
+    o = oracle.Oracle(L.fuel, L.slope, L.aspect, weather=w.weather, **w.params)
+    for r in range(4):
+        a, b = o.run_replica(r), o.run_replica_event(r)
+        assert np.array_equal(a["ign"], b["ign"]) and a["work"] == b["work"]
+
+
+def test_threshold_blocks_ignition():
+    o = homog(5, 5, const_ros=10.0, ros_threshold=10.0)   # needs ROS > 10
+    r = o.run_replica(0)
+    assert r["n_ignited"] == 1 and r["work"] == o.steps    # the centre keeps burning
+    o = homog(5, 5, const_ros=10.0, ros_threshold=9.99)
+    assert o.run_replica(0)["n_ignited"] == 25
+
+
+def test_delta_burnout():
+    o = homog(5, 5, const_ros=10.0, burnout_delta=20.0)
+    r = o.run_replica(0)
+    assert r["n_ignited"] == 1 and r["work"] == 1        # sends in step 1, burned after it
+
+
+def test_isolated_ignition_burns_out_after_one_step():
+    fuel = np.zeros((3, 3), dtype=np.uint8); fuel[1, 1] = 1
+    o = oracle.Oracle(fuel, weather=S.constant_weather(1), hours=1, ignition_cell=4)
+    r = o.run_replica(0)
+    assert r["work"] == 1 and r["n_ignited"] == 1
+
+
+def test_uniform_ignition_hits_only_burnable_cells():
+    w = S.config2(side=64, n_replicas=1, hours=1)
+    L = w.landscape
+    o = oracle.Oracle(L.fuel, L.slope, L.aspect, weather=w.weather, **w.params)
+    cells = [o.ignition_cell(r) for r in range(400)]
+    assert all(L.fuel.ravel()[c] != 0 for c in cells)
+    assert len(set(cells)) > 300
+
+
+def test_burn_prob_counts():
+    w = S.config2(side=64, n_replicas=6, hours=3)
+    L = w.landscape
+    o = oracle.Oracle(L.fuel, L.slope, L.aspect, weather=w.weather, **w.params)
+    scars = np.stack([o.run_replica(r)["scar"] for r in range(6)])
+    bp = oracle.burn_prob(scars)
+    assert bp.dtype == np.uint32 and bp.max() <= 6
+    assert np.array_equal(bp, scars.sum(0))
+    assert np.array_equal(oracle.burn_prob(scars[:1]), scars[0])
+
+
+def test_smaller_steps_change_the_scar_little():
+    """Sec. 3.1: a finer clock barely changes the final scar (sanity, not parity)."""
+    w = S.config1()
+    L = w.landscape
+    a = oracle.Oracle(L.fuel, weather=w.weather, **dict(w.params, minutes_per_step=1)).run_replica(0)
+    b = oracle.Oracle(L.fuel, weather=w.weather, **dict(w.params, minutes_per_step=2)).run_replica(0)
+    diff = (a["scar"] != b["scar"]).sum()
+    assert diff <= 0.1 * a["scar"].sum()
