@@ -1,0 +1,194 @@
+/*
+ * c2f.h -- C ABI of the GB300 Cell2Fire fire-growth library (libc2f.so).
+ *
+ * The library runs Monte-Carlo replicas of the cell-based fire-growth model
+ * of Pais et al., "Cell2Fire: A Cell Based Forest Fire Growth Model"
+ * (arXiv:1905.09317) on one NVIDIA GB300 (sm_103a):
+ *
+ *   Sim(ForestData, FTypes, Ignitions, Weather, TMax, Options)   (Alg. 1)
+ *     ForestData/FTypes  -> c2f_load_landscape   (Sec. 3.5 (i), (ii); Table 1)
+ *     Weather            -> c2f_set_weather      (Sec. 3.5 (iv); Table 2)
+ *     Ignitions, TMax, Options -> c2f_sim_params (Sec. 3.1 uncertainty (1),(2))
+ *     Step 0..2          -> c2f_simulate / c2f_simulate_batch / c2f_submit
+ *     Step 3 outputs     -> c2f_burn_prob, c2f_get_scars, c2f_get_counters
+ *                           (Sec. 3.6: burn grids, burn-probability maps)
+ *
+ * Conventions (all entry points):
+ *  - Every function returns int: C2F_OK (0) or a negative C2F_E* code; no
+ *    function aborts the process.  c2f_last_error() describes the last error
+ *    raised on a context (per context, per calling thread).
+ *  - Host arrays passed in are copied; the caller keeps ownership.  Output
+ *    arrays are caller-owned and written only on success (never partially).
+ *  - Device memory is owned by the context and freed by c2f_release /
+ *    c2f_destroy.  A context is used from one host thread at a time.
+ *  - Grids are row-major, row 0 = north, cell id = row * cols + col.
+ *  - Fuel codes (uint8, Table 1 style, 1 = C-1): 0 non-fuel, 1 C1, 2 C2,
+ *    3 C3, 4 C4, 5 C5, 6 C6, 7 C7, 8 D1, 9 M1, 10 M2, 11 O1a, 12 O1b, 13 S1,
+ *    14 S2, 15 S3.  Any other code is C2F_EINVAL.
+ */
+#ifndef C2F_H
+#define C2F_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define C2F_API __attribute__((visibility("default")))
+
+enum {
+  C2F_OK = 0,
+  C2F_EINVAL = -1,    /* bad argument: sizes, codes, parameters, ids          */
+  C2F_ENOMEM = -2,    /* device allocation failed or admission refused       */
+  C2F_ECUDA = -3,     /* a CUDA call failed (message in c2f_last_error)      */
+  C2F_ETIMEOUT = -4,  /* a bounded wait ran out                               */
+  C2F_ENOTFOUND = -5, /* unknown landscape or simulation id                   */
+  C2F_EBUSY = -6,     /* the simulation has not finished yet                  */
+  C2F_ECANCELED = -7  /* the simulation was cancelled                         */
+};
+
+/* output selection bits of c2f_sim_params.outputs */
+enum {
+  C2F_OUT_SCARS = 1u,     /* keep per-replica burn grids (always kept)          */
+  C2F_OUT_IGN_STEPS = 2u, /* keep per-replica ignition steps (int32 per cell)   */
+  C2F_OUT_COUNTERS = 8u   /* keep per-replica counters (always kept)            */
+};
+
+typedef struct c2f_ctx c2f_ctx;
+
+/* One hour of the weather stream (Sec. 3.5 (iv), Table 2): wind speed
+ * (km/h), wind direction the wind blows FROM (degrees clockwise from north),
+ * Fine Fuel Moisture Code and Buildup Index of the FWI System. */
+typedef struct {
+  double ws_kmh;
+  double wd_from_deg;
+  double ffmc;
+  double bui;
+} c2f_weather_hour;
+
+/* Simulation options (Alg. 1 "Options"; Sec. 3.1 sources of uncertainty). */
+typedef struct {
+  uint64_t seed;            /* key of the counter-based Philox4x32-10 draws            */
+  int32_t n_replicas;       /* Monte-Carlo replicas, >= 1                               */
+  int32_t hours;            /* TMax in weather hours, 1 .. n_hours of the weather       */
+  int32_t minutes_per_step; /* fire-period length; must divide 60 (Sec. 3.1: 1 min)     */
+  int32_t ignition_mode;    /* 0: fixed ignition_cell; 1: uniform over burnable cells   */
+  int32_t ignition_cell;    /* cell id for mode 0; must be burnable                     */
+  double ros_sigma;         /* lognormal sigma of the ROS perturbation, 0 .. 1          */
+  double ros_threshold;     /* receiver ignites iff ROS * f > threshold (Sec. 3.1)      */
+  double burnout_delta;     /* > 0: Burned when ROS * f < delta (A5 (i)); 0 = off       */
+  int32_t ellipse_mode;     /* 0: Eq. (1); 1: centre-offset ellipse ray (Sec. 3.7 fig.) */
+  double o1_curing_pct;     /* grass curing percent for O1a/O1b (default 60)            */
+  double m1_pc;             /* percent conifer for M1/M2 (default 50)                   */
+  double const_ros;         /* > 0: every burnable cell spreads at this rate (m/min) on
+                               all 8 axes instead of FBP (deterministic test hook)      */
+  uint32_t outputs;         /* C2F_OUT_* bits                                           */
+} c2f_sim_params;
+
+/* Fills *p with the defaults: seed 0, 1 replica, 1 hour, 1-minute steps,
+ * fixed ignition at cell 0, sigma 0, threshold 0, delta 0, Eq. (1),
+ * curing 60, PC 50, no constant ROS, scars + counters. */
+C2F_API void c2f_default_params(c2f_sim_params *p);
+
+/* Creates a context on CUDA device `device`.  The context owns a stream,
+ * all device buffers and the per-device constant tables.
+ * Errors: C2F_EINVAL (no such device), C2F_ECUDA. */
+C2F_API int c2f_create(c2f_ctx **out, int device);
+
+/* Makes the context issue its work on `stream` (a cudaStream_t of the same
+ * device, e.g. a PyTorch stream); NULL restores the context's own stream. */
+C2F_API int c2f_set_stream(c2f_ctx *ctx, void *stream);
+
+/* Frees everything the context owns.  NULL is accepted. */
+C2F_API void c2f_destroy(c2f_ctx *ctx);
+
+/* Text of the last error raised on ctx (empty string if none). */
+C2F_API const char *c2f_last_error(const c2f_ctx *ctx);
+
+/* Loads a landscape (Sec. 3.3 cell fields; Sec. 3.5 (i)): `fuel` codes
+ * (rows*cols), `slope_pct` (percent rise over run, NULL = flat),
+ * `aspect_deg` (downslope-facing azimuth clockwise from north, NULL = 0)
+ * and `unburnable` (NULL or 1 = Harvested / not available, Sec. 3.1).
+ * rows, cols >= 1, rows*cols < 2^31; cell_size_m > 0; slopes finite >= 0.
+ * Copies the arrays to the device.  Returns the id in *landscape_id. */
+C2F_API int c2f_load_landscape(c2f_ctx *ctx, int32_t rows, int32_t cols, double cell_size_m,
+                               const uint8_t *fuel, const float *slope_pct,
+                               const float *aspect_deg, const uint8_t *unburnable,
+                               int32_t *landscape_id);
+
+/* Sets the hourly weather stream of a landscape (n_hours rows, copied).
+ * FFMC must lie in [0, 101), BUI > 0, wind speed >= 0, all finite.
+ * Invalidates the cached rate-of-spread tables of the landscape. */
+C2F_API int c2f_set_weather(c2f_ctx *ctx, int32_t landscape_id, int32_t n_hours,
+                            const c2f_weather_hour *w);
+
+/* Builds (or rebuilds, when `force` != 0) the rate-of-spread table of a
+ * landscape for the FBP/ellipse options in *p (Sec. 3.7, Eqs. 1-4): per
+ * (hour, cell) the 8 directional ROS in 2^32 fixed point per fire period,
+ * and HROS.  c2f_simulate builds it on demand; this call lets a caller pay
+ * for it up front or time it.  Asynchronous on the context stream. */
+C2F_API int c2f_build_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p,
+                          int force);
+
+/* Exports one hour of the rate-of-spread table for checking: ros8
+ * (rows*cols*8 doubles, m/min, axis k = 45k degrees counter-clockwise from
+ * east), hros (rows*cols), base (rows*cols*8 int64: the per-period fixed-point
+ * increment before the perturbation).  Any output may be NULL. Synchronous. */
+C2F_API int c2f_get_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p,
+                        int32_t hour, double *ros8, double *hros, int64_t *base);
+
+/* Runs all replicas of one simulation (Alg. 1 Steps 0-2 per replica) and
+ * returns when they are finished.  The result stays on the device under
+ * *sim_id until c2f_release.  Errors: C2F_EINVAL, C2F_ENOMEM, C2F_ECUDA. */
+C2F_API int c2f_simulate(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p,
+                         int32_t *sim_id);
+
+/* Runs n simulations (possibly of different landscapes and replica counts)
+ * as one batch: one work list, one persistent kernel launch.  Results are
+ * identical to n separate c2f_simulate calls.  sim_ids has n entries. */
+C2F_API int c2f_simulate_batch(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
+                               const c2f_sim_params *params, int32_t *sim_ids);
+
+/* Burn-probability counts (Sec. 3.6 (i), Sec. 3.1 outputs): counts[c] = number
+ * of replicas in which cell c ignited, uint32, rows*cols entries, host memory. */
+C2F_API int c2f_burn_prob(c2f_ctx *ctx, int32_t sim_id, uint32_t *counts);
+
+/* Same into device memory (`counts_dev`, rows*cols uint32 on the context's
+ * device); asynchronous on the context stream. */
+C2F_API int c2f_burn_prob_device(c2f_ctx *ctx, int32_t sim_id, uint32_t *counts_dev);
+
+/* Per-replica burn grids (Sec. 3.6 (i)): scars[r*N + c] = 1 if cell c ignited
+ * in replica r (n_replicas*N bytes), and, if the simulation kept them,
+ * ignition steps ign_step[r*N + c] (-1 = never).  Either pointer may be NULL. */
+C2F_API int c2f_get_scars(c2f_ctx *ctx, int32_t sim_id, uint8_t *scars, int32_t *ign_step);
+
+/* Per-replica counters: work[r] = sum over fire periods of the number of
+ * burning cells (cell-updates), ignited[r] = cells ever ignited, ign_cell[r]
+ * = ignition cell.  Any pointer may be NULL. */
+C2F_API int c2f_get_counters(c2f_ctx *ctx, int32_t sim_id, int64_t *work, int32_t *ignited,
+                             int32_t *ign_cell);
+
+/* Initial burning-list capacity (entries per CTA) of the frontier kernel;
+ * 0 = automatic.  A replica that outgrows it is re-run with a larger one, so
+ * results never depend on this value (a tuning and test knob). */
+C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap);
+
+/* Kernel timing: with profiling on, the context brackets each launch of its
+ * kernel families with CUDA events on its stream.  c2f_kernel_times waits for
+ * the stream, writes per family the summed milliseconds and the launch count
+ * since the last call, and resets them.  Families (index): 0 ROS table (K1,
+ * with its hour prep), 1 ignition (K2), 2 frontier (K3), 3 burn probability
+ * (K4).  ms and launches hold C2F_KT_FAMILIES entries. */
+#define C2F_KT_FAMILIES 4
+C2F_API int c2f_profile(c2f_ctx *ctx, int enable);
+C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches);
+
+/* Frees a landscape (and its tables) or a simulation result. */
+C2F_API int c2f_release(c2f_ctx *ctx, int32_t id);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* C2F_H */

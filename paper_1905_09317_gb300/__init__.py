@@ -1,0 +1,230 @@
+"""GB300 (sm_103a) Monte-Carlo fire growth after Cell2Fire (Pais et al., arXiv:1905.09317).
+
+Thin ctypes binding over ``libc2f.so`` (C ABI in ``include/c2f.h``): argument
+marshalling only, every step of the fire-growth path runs in the library's
+CUDA kernels.  Importing this package does not load the library; the first
+call does, and it raises if the library has not been built (``build()``) or
+if no CUDA device is present -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB as LIB_PATH, build  # noqa: F401
+
+C2F_OK, C2F_EINVAL, C2F_ENOMEM, C2F_ECUDA, C2F_ETIMEOUT = 0, -1, -2, -3, -4
+C2F_ENOTFOUND, C2F_EBUSY, C2F_ECANCELED = -5, -6, -7
+OUT_SCARS, OUT_IGN_STEPS, OUT_COUNTERS = 1, 2, 8
+_ERR = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ENOTFOUND",
+        -6: "EBUSY", -7: "ECANCELED"}
+
+
+class C2FError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"c2f error {code} ({_ERR.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class WeatherHour(C.Structure):
+    _fields_ = [("ws_kmh", C.c_double), ("wd_from_deg", C.c_double),
+                ("ffmc", C.c_double), ("bui", C.c_double)]
+
+
+class SimParams(C.Structure):
+    _fields_ = [
+        ("seed", C.c_uint64), ("n_replicas", C.c_int32), ("hours", C.c_int32),
+        ("minutes_per_step", C.c_int32), ("ignition_mode", C.c_int32),
+        ("ignition_cell", C.c_int32), ("ros_sigma", C.c_double),
+        ("ros_threshold", C.c_double), ("burnout_delta", C.c_double),
+        ("ellipse_mode", C.c_int32), ("o1_curing_pct", C.c_double), ("m1_pc", C.c_double),
+        ("const_ros", C.c_double), ("outputs", C.c_uint32),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# (name, restype, argtypes)
+_P = C.POINTER
+_SIGS = [
+    ("c2f_default_params", None, [_P(SimParams)]),
+    ("c2f_create", C.c_int, [_P(C.c_void_p), C.c_int]),
+    ("c2f_set_stream", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("c2f_destroy", None, [C.c_void_p]),
+    ("c2f_last_error", C.c_char_p, [C.c_void_p]),
+    ("c2f_load_landscape", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, _P(C.c_int32)]),
+    ("c2f_set_weather", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
+    ("c2f_build_ros", C.c_int, [C.c_void_p, C.c_int32, _P(SimParams), C.c_int]),
+    ("c2f_get_ros", C.c_int, [C.c_void_p, C.c_int32, _P(SimParams), C.c_int32, C.c_void_p,
+                              C.c_void_p, C.c_void_p]),
+    ("c2f_simulate", C.c_int, [C.c_void_p, C.c_int32, _P(SimParams), _P(C.c_int32)]),
+    ("c2f_simulate_batch", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("c2f_burn_prob", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    ("c2f_burn_prob_device", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    ("c2f_get_scars", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    ("c2f_get_counters", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("c2f_set_list_capacity", C.c_int, [C.c_void_p, C.c_int64]),
+    ("c2f_profile", C.c_int, [C.c_void_p, C.c_int]),
+    ("c2f_kernel_times", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("c2f_release", C.c_int, [C.c_void_p, C.c_int32]),
+]
+KERNEL_FAMILIES = ("ros_table", "ignite", "frontier", "burn_prob")
+
+
+def exported_symbols():
+    """Names of the C ABI entry points the binding expects the library to export."""
+    return [s[0] for s in _SIGS]
+
+
+def load_library(path: str | None = None):
+    """dlopen libc2f.so and declare its signatures (no device call is made)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libc2f.so has not been built ({p}); run "
+                               "paper_1905_09317_gb300.build() -- there is no CPU fallback")
+        lib = C.CDLL(p)
+        for name, res, args in _SIGS:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def default_params(**kw) -> SimParams:
+    p = SimParams()
+    load_library().c2f_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+class Context:
+    """One c2f context on a CUDA device (owns a stream and all device memory)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load_library()
+        h = C.c_void_p()
+        rc = self.lib.c2f_create(C.byref(h), int(device))
+        if rc != C2F_OK:
+            raise C2FError(rc, f"c2f_create(device={device}) failed (no usable CUDA device?)")
+        self.h = h
+        self._keep = []
+
+    def _check(self, rc):
+        if rc != C2F_OK:
+            raise C2FError(rc, self.lib.c2f_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.c2f_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream_ptr: int | None):
+        self._check(self.lib.c2f_set_stream(self.h, C.c_void_p(stream_ptr) if stream_ptr else None))
+
+    # ---- inputs
+    def load_landscape(self, fuel, slope=None, aspect=None, unburnable=None, cell_size=100.0) -> int:
+        fuel = np.ascontiguousarray(fuel, dtype=np.uint8)
+        rows, cols = fuel.shape
+        s = None if slope is None else np.ascontiguousarray(slope, dtype=np.float32)
+        a = None if aspect is None else np.ascontiguousarray(aspect, dtype=np.float32)
+        u = None if unburnable is None else np.ascontiguousarray(unburnable, dtype=np.uint8)
+        lid = C.c_int32()
+        self._check(self.lib.c2f_load_landscape(self.h, rows, cols, float(cell_size), _ptr(fuel),
+                                                _ptr(s), _ptr(a), _ptr(u), C.byref(lid)))
+        return lid.value
+
+    def set_weather(self, landscape_id: int, weather) -> None:
+        w = np.ascontiguousarray(weather, dtype=np.float64).reshape(-1, 4)
+        self._check(self.lib.c2f_set_weather(self.h, int(landscape_id), w.shape[0], _ptr(w)))
+
+    def build_ros(self, landscape_id: int, params: SimParams, force=False) -> None:
+        self._check(self.lib.c2f_build_ros(self.h, int(landscape_id), C.byref(params), int(force)))
+
+    def get_ros(self, landscape_id: int, params: SimParams, hour: int, n_cells: int):
+        ros8 = np.empty((n_cells, 8), dtype=np.float64)
+        hros = np.empty(n_cells, dtype=np.float64)
+        base = np.empty((n_cells, 8), dtype=np.int64)
+        self._check(self.lib.c2f_get_ros(self.h, int(landscape_id), C.byref(params), int(hour),
+                                         _ptr(ros8), _ptr(hros), _ptr(base)))
+        return ros8, hros, base
+
+    # ---- runs
+    def simulate(self, landscape_id: int, params: SimParams) -> int:
+        sid = C.c_int32()
+        self._check(self.lib.c2f_simulate(self.h, int(landscape_id), C.byref(params), C.byref(sid)))
+        return sid.value
+
+    def simulate_batch(self, landscape_ids, params_list) -> list[int]:
+        n = len(landscape_ids)
+        ids = (C.c_int32 * n)(*landscape_ids)
+        ps = (SimParams * n)(*params_list)
+        out = (C.c_int32 * n)()
+        self._check(self.lib.c2f_simulate_batch(self.h, n, ids, ps, out))
+        return list(out)
+
+    # ---- outputs
+    def burn_prob(self, sim_id: int, n_cells: int) -> np.ndarray:
+        out = np.empty(n_cells, dtype=np.uint32)
+        self._check(self.lib.c2f_burn_prob(self.h, int(sim_id), _ptr(out)))
+        return out
+
+    def burn_prob_device(self, sim_id: int, dev_ptr: int) -> None:
+        self._check(self.lib.c2f_burn_prob_device(self.h, int(sim_id), C.c_void_p(dev_ptr)))
+
+    def get_scars(self, sim_id: int, n_replicas: int, n_cells: int, ign_steps=False):
+        scars = np.empty((n_replicas, n_cells), dtype=np.uint8)
+        ign = np.empty((n_replicas, n_cells), dtype=np.int32) if ign_steps else None
+        self._check(self.lib.c2f_get_scars(self.h, int(sim_id), _ptr(scars), _ptr(ign)))
+        return scars, ign
+
+    def get_counters(self, sim_id: int, n_replicas: int):
+        work = np.empty(n_replicas, dtype=np.int64)
+        ign = np.empty(n_replicas, dtype=np.int32)
+        cell = np.empty(n_replicas, dtype=np.int32)
+        self._check(self.lib.c2f_get_counters(self.h, int(sim_id), _ptr(work), _ptr(ign), _ptr(cell)))
+        return work, ign, cell
+
+    def set_list_capacity(self, cap: int) -> None:
+        self._check(self.lib.c2f_set_list_capacity(self.h, int(cap)))
+
+    def profile(self, enable: bool = True) -> None:
+        self._check(self.lib.c2f_profile(self.h, int(bool(enable))))
+
+    def kernel_times(self) -> dict:
+        ms = np.zeros(len(KERNEL_FAMILIES), dtype=np.float64)
+        n = np.zeros(len(KERNEL_FAMILIES), dtype=np.int64)
+        self._check(self.lib.c2f_kernel_times(self.h, _ptr(ms), _ptr(n)))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_FAMILIES)}
+
+    def release(self, id_: int) -> None:
+        self._check(self.lib.c2f_release(self.h, int(id_)))

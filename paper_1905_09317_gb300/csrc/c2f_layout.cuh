@@ -1,0 +1,98 @@
+// c2f_layout.cuh -- data layout shared by the kernels (c2f_kernels.cu) and the
+// host runtime (c2f_runtime.cu); no device code.
+#pragma once
+#include <cstdint>
+
+
+namespace c2f {
+
+struct MathConstants {
+  double inv_fact[24];   // 1/k!
+  double log_c[12];      // 1/(2n+1)
+  double sin_c[10];      // (-1)^n/(2n+1)!
+  double cos_c[10];      // (-1)^n/(2n)!
+  float inv_fact_f[12];
+  float log_cf[8];
+  float sin_cf[8];
+  float cos_cf[8];
+};
+
+enum FuelCode : int {
+  F_NONE = 0, F_C1, F_C2, F_C3, F_C4, F_C5, F_C6, F_C7, F_D1, F_M1, F_M2,
+  F_O1A, F_O1B, F_S1, F_S2, F_S3, F_NCODES
+};
+
+struct FuelCoef { double a, b, c, q, bui0; };
+
+struct HourPrep {
+  double ws, ff, isz, sin_w, cos_w;
+  double cf;              // O1 curing factor
+  double be[F_NCODES];    // build-up effect per fuel code
+  double rszf[F_NCODES];  // RSI at zero wind and slope per code (O1 includes curing)
+};
+
+struct CellPrep { double sf, sin_s, cos_s; };
+
+// One simulation inside a frontier launch (several for a batch).
+struct SimJob {
+  // landscape
+  int32_t rows, cols, wpr;        // wpr: 32-bit words per row of a bit plane
+  int32_t n_burnable;
+  const uint32_t *burnable;       // rows*wpr words, bit = burnable and not harvested
+  const int32_t *burnable_list;   // burnable cell ids in row-major order
+  // rate-of-spread table of this run
+  const int64_t *base;            // [hours][N][8] fixed-point per-period increments
+  const double *hros;             // [hours][N]
+  // run parameters
+  uint64_t seed;
+  float sigma;
+  int32_t ignition_mode, ignition_cell;
+  double thr, delta;
+  int32_t sph, hours;             // fire periods per hour, simulated hours
+  int64_t d_orth, d_diag;         // axis lengths in fixed point
+  int32_t n_replicas;
+  // per-replica outputs
+  uint32_t *ign_plane;            // [R][rows*wpr] scar bits
+  uint32_t *burned_plane;         // [R][rows*wpr]
+  int32_t *ign_step;              // [R][N] or nullptr
+  int64_t *work;                  // [R]
+  int32_t *n_ignited;             // [R]
+  int32_t *ign_cell;              // [R]
+  int32_t *status;                // [R] 0 ok, 1 list capacity exceeded, 2 internal error
+};
+
+struct FrontierArgs {
+  const SimJob *jobs;
+  int32_t n_jobs;
+  const int64_t *item_begin;      // [n_jobs + 1]: replicas of job j are items item_begin[j]..
+  const int64_t *item_list;       // nullptr: items 0..n_items-1; else explicit global items
+  int64_t n_items;
+  unsigned long long *counter;    // work-list cursor (zeroed before the launch)
+  int32_t cap;                    // burning-list capacity per slot
+  int32_t *ent_cell;              // [slots][cap]
+  uint8_t *ent_mask;              // [slots][cap] open axes
+  uint8_t *ent_next;              // [slots][cap] next event offset in the hour (0xFF none)
+  uint64_t *ent_cofs;             // [slots][cap] 8 per-axis crossing offsets (0xFF none)
+  int64_t *ent_P;                 // [slots][cap][8] progress at the start of the next hour
+};
+
+// K1 launch arguments: grid.y covers hours hour0 .. hour0 + gridDim.y - 1
+struct RosTableArgs {
+  const uint8_t *fuel;
+  const float *slope;
+  const uint32_t *burnable;
+  int32_t rows, cols, wpr;
+  const CellPrep *cell;
+  const HourPrep *hour;    // indexed by absolute hour
+  int32_t hour0;
+  double pcf, const_ros, dt2p32;
+  int32_t ellipse_mode;
+  int64_t *base;           // [hour][N][8] (absolute hour), or nullptr
+  double *hros;            // [hour][N], or nullptr
+  double *ros8;            // export: [N][8] of hour0 only, or nullptr
+};
+
+constexpr int kFrontierThreads = 256;
+constexpr uint8_t kNone = 0xFF;
+
+}  // namespace c2f

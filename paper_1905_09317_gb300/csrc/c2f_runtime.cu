@@ -1,0 +1,877 @@
+// c2f_runtime.cu -- host runtime behind the C ABI of include/c2f.h.
+//
+// A context owns one CUDA stream, the landscapes loaded on it (device copies
+// of the fuel, slope and aspect grids, the burnable bit plane and list, the
+// hoisted per-cell FBP terms, the weather stream and the cached rate-of-spread
+// tables) and the simulation results (per-replica scar planes, optional
+// ignition steps and counters).  Device memory comes from the stream-ordered
+// allocator (cudaMallocAsync) so that allocation never synchronises the
+// device.  The frontier kernel runs one CTA per replica over a work list; a
+// replica whose burning list outgrows the per-CTA capacity is re-run with a
+// larger capacity, so results never depend on that capacity.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/c2f.h"
+#include "c2f_layout.cuh"
+
+namespace c2f {
+__global__ void k_burnable_plane(const uint8_t *, const uint8_t *, int32_t, int32_t, int32_t,
+                                 uint32_t *, int32_t *);
+__global__ void k_scan_counts(const int32_t *, int64_t, int32_t *, int32_t *);
+__global__ void k_burnable_list(const uint32_t *, const int32_t *, int32_t, int32_t, int32_t,
+                                int32_t *);
+__global__ void k_cell_prep(const float *, const float *, int64_t, CellPrep *);
+__global__ void k_hour_prep(const double *, int32_t, double, HourPrep *);
+__global__ void k_ros_table(RosTableArgs);
+__global__ void k_ignite(const SimJob *, int32_t);
+__global__ void k_frontier(FrontierArgs);
+__global__ void k_burn_prob(const uint32_t *, int32_t, int32_t, int32_t, int32_t, int32_t,
+                            uint32_t *, int32_t);
+__global__ void k_scar_bytes(const uint32_t *, int32_t, int32_t, int32_t, int32_t, uint8_t *);
+cudaError_t upload_constants();
+}  // namespace c2f
+
+using namespace c2f;
+
+namespace {
+
+// ------------------------------------------------------------------ device buffers
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t st = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { reset(); }
+  void reset() {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+struct TableKey {
+  int32_t hours = 0, dt = 0, ellipse = 0;
+  double pc = 0, curing = 0, const_ros = 0;
+  bool operator==(const TableKey &o) const {
+    return dt == o.dt && ellipse == o.ellipse && pc == o.pc && curing == o.curing &&
+           const_ros == o.const_ros;
+  }
+};
+
+struct Landscape {
+  int32_t rows = 0, cols = 0, wpr = 0;
+  int64_t n = 0;
+  double cell_size = 0;
+  int32_t n_burnable = 0;
+  std::vector<uint8_t> burnable_host;  // for validation of fixed ignitions
+  DevBuf fuel, slope, aspect, burnable, burnable_list, cell_prep;
+  bool has_slope = false;
+  int32_t n_hours = 0;
+  std::vector<double> weather;          // n_hours x 4
+  DevBuf weather_dev, hour_prep;
+  bool table_valid = false;
+  TableKey key;
+  DevBuf base, hros;
+};
+
+struct Sim {
+  int32_t landscape = -1;
+  c2f_sim_params p{};
+  int32_t rows = 0, cols = 0, wpr = 0;
+  int64_t n = 0;
+  DevBuf ign_plane, burned_plane, ign_step, work, n_ignited, ign_cell, status;
+};
+
+struct DeviceInit {
+  std::once_flag once;
+  cudaError_t err = cudaSuccess;
+};
+
+DeviceInit g_devinit[64];
+
+}  // namespace
+
+struct c2f_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+  int32_t next_id = 1;
+  std::unordered_map<int32_t, std::unique_ptr<Landscape>> lands;
+  std::unordered_map<int32_t, std::unique_ptr<Sim>> sims;
+  // frontier scratch
+  DevBuf ent_cell, ent_mask, ent_next, ent_cofs, ent_P, counter;
+  int64_t scratch_slots = 0, scratch_cap = 0;
+  int frontier_blocks_per_sm = 0;
+  int64_t cap_override = 0;
+  // kernel timing
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[C2F_KT_FAMILIES];
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+int fail(c2f_ctx *ctx, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->last_error = buf;
+  return code;
+}
+
+int cuda_fail(c2f_ctx *ctx, cudaError_t e, const char *what) {
+  cudaGetLastError();
+  const int code = (e == cudaErrorMemoryAllocation) ? C2F_ENOMEM : C2F_ECUDA;
+  return fail(ctx, code, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+#define CKL(what)                                             \
+  do {                                                        \
+    cudaError_t e_ = cudaGetLastError();                      \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what);   \
+  } while (0)
+
+int dalloc(c2f_ctx *ctx, DevBuf &b, size_t bytes) {
+  b.reset();
+  b.st = ctx->stream;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocAsync(&b.p, bytes, ctx->stream);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return cuda_fail(ctx, e, "cudaMallocAsync");
+  }
+  b.bytes = bytes;
+  return C2F_OK;
+}
+
+int ensure_device_constants(c2f_ctx *ctx) {
+  if (ctx->device < 0 || ctx->device >= 64) return fail(ctx, C2F_EINVAL, "device index out of range");
+  DeviceInit &d = g_devinit[ctx->device];
+  std::call_once(d.once, [&] { d.err = upload_constants(); });
+  if (d.err != cudaSuccess) return cuda_fail(ctx, d.err, "uploading constant tables");
+  return C2F_OK;
+}
+
+cudaEvent_t get_event(c2f_ctx *ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return e;
+}
+
+// brackets the launches of one kernel family with events when profiling
+struct ProfScope {
+  c2f_ctx *ctx;
+  int fam;
+  cudaEvent_t a = nullptr;
+  ProfScope(c2f_ctx *c, int f) : ctx(c), fam(f) {
+    if (ctx->profiling && (a = get_event(ctx))) cudaEventRecord(a, ctx->stream);
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = get_event(ctx);
+    if (!b) { ctx->event_pool.push_back(a); return; }
+    cudaEventRecord(b, ctx->stream);
+    ctx->prof_events[fam].emplace_back(a, b);
+  }
+};
+
+unsigned grid1(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+int validate_params(c2f_ctx *ctx, const Landscape &L, const c2f_sim_params *p) {
+  if (!p) return fail(ctx, C2F_EINVAL, "params is NULL");
+  if (p->n_replicas < 1) return fail(ctx, C2F_EINVAL, "n_replicas must be >= 1");
+  if (p->minutes_per_step < 1 || 60 % p->minutes_per_step)
+    return fail(ctx, C2F_EINVAL, "minutes_per_step must divide 60");
+  if (p->hours < 1) return fail(ctx, C2F_EINVAL, "hours must be >= 1");
+  if (p->hours > L.n_hours)
+    return fail(ctx, C2F_EINVAL, "hours (%d) exceeds the weather stream (%d hours)", p->hours,
+                L.n_hours);
+  if ((int64_t)p->hours * (60 / p->minutes_per_step) > 2000000000LL)
+    return fail(ctx, C2F_EINVAL, "too many fire periods");
+  if (!(p->ros_sigma >= 0.0 && p->ros_sigma <= 1.0))
+    return fail(ctx, C2F_EINVAL, "ros_sigma must lie in [0, 1]");
+  if (!std::isfinite(p->ros_threshold) || !std::isfinite(p->burnout_delta) ||
+      p->burnout_delta < 0.0)
+    return fail(ctx, C2F_EINVAL, "threshold / burnout_delta must be finite, delta >= 0");
+  if (p->ellipse_mode != 0 && p->ellipse_mode != 1)
+    return fail(ctx, C2F_EINVAL, "ellipse_mode must be 0 or 1");
+  if (!(p->o1_curing_pct >= 0.0 && p->o1_curing_pct <= 100.0))
+    return fail(ctx, C2F_EINVAL, "o1_curing_pct must lie in [0, 100]");
+  if (!(p->m1_pc >= 0.0 && p->m1_pc <= 100.0)) return fail(ctx, C2F_EINVAL, "m1_pc must lie in [0, 100]");
+  if (!(p->const_ros >= 0.0 && p->const_ros < 1e9)) return fail(ctx, C2F_EINVAL, "const_ros out of range");
+  if (p->ignition_mode == 0) {
+    if (p->ignition_cell < 0 || p->ignition_cell >= L.n)
+      return fail(ctx, C2F_EINVAL, "ignition_cell out of range");
+    if (!L.burnable_host[p->ignition_cell])
+      return fail(ctx, C2F_EINVAL, "ignition_cell is not burnable");
+  } else if (p->ignition_mode == 1) {
+    if (L.n_burnable == 0) return fail(ctx, C2F_EINVAL, "landscape has no burnable cell");
+  } else {
+    return fail(ctx, C2F_EINVAL, "ignition_mode must be 0 or 1");
+  }
+  return C2F_OK;
+}
+
+TableKey key_of(const c2f_sim_params *p) {
+  TableKey k;
+  k.hours = p->hours;
+  k.dt = p->minutes_per_step;
+  k.ellipse = p->ellipse_mode;
+  k.pc = p->m1_pc;
+  k.curing = p->o1_curing_pct;
+  k.const_ros = p->const_ros;
+  return k;
+}
+
+// K1 for hours [0, hours) into the landscape's table (a1: hour prep first)
+int build_table(c2f_ctx *ctx, Landscape &L, const c2f_sim_params *p) {
+  int rc;
+  const int32_t H = p->hours;
+  if ((rc = dalloc(ctx, L.hour_prep, sizeof(HourPrep) * (size_t)L.n_hours))) return rc;
+  if ((rc = dalloc(ctx, L.base, sizeof(int64_t) * 8 * (size_t)L.n * H))) return rc;
+  if ((rc = dalloc(ctx, L.hros, sizeof(double) * (size_t)L.n * H))) return rc;
+  ProfScope prof(ctx, 0);
+  k_hour_prep<<<grid1(L.n_hours, 64), 64, 0, ctx->stream>>>(
+      L.weather_dev.as<double>(), L.n_hours, p->o1_curing_pct, L.hour_prep.as<HourPrep>());
+  CKL("k_hour_prep");
+  L.table_valid = false;
+  RosTableArgs a{};
+  a.fuel = L.fuel.as<uint8_t>();
+  a.slope = L.has_slope ? L.slope.as<float>() : nullptr;
+  a.burnable = L.burnable.as<uint32_t>();
+  a.rows = L.rows; a.cols = L.cols; a.wpr = L.wpr;
+  a.cell = L.cell_prep.as<CellPrep>();
+  a.hour = L.hour_prep.as<HourPrep>();
+  a.hour0 = 0;
+  a.pcf = p->m1_pc / 100.0;
+  a.const_ros = p->const_ros;
+  a.dt2p32 = (double)p->minutes_per_step * 4294967296.0;
+  a.ellipse_mode = p->ellipse_mode;
+  a.base = L.base.as<int64_t>();
+  a.hros = L.hros.as<double>();
+  a.ros8 = nullptr;
+  dim3 grid(grid1(L.n, 128), (unsigned)H);
+  k_ros_table<<<grid, 128, 0, ctx->stream>>>(a);
+  CKL("k_ros_table");
+  L.key = key_of(p);
+  L.table_valid = true;
+  return C2F_OK;
+}
+
+int ensure_table(c2f_ctx *ctx, Landscape &L, const c2f_sim_params *p, bool force) {
+  const TableKey k = key_of(p);
+  if (!force && L.table_valid && L.key == k && L.key.hours >= k.hours) return C2F_OK;
+  return build_table(ctx, L, p);
+}
+
+Landscape *find_land(c2f_ctx *ctx, int32_t id) {
+  auto it = ctx->lands.find(id);
+  return it == ctx->lands.end() ? nullptr : it->second.get();
+}
+
+Sim *find_sim(c2f_ctx *ctx, int32_t id) {
+  auto it = ctx->sims.find(id);
+  return it == ctx->sims.end() ? nullptr : it->second.get();
+}
+
+int64_t default_cap(const c2f_ctx *ctx, const Landscape &L) {
+  if (ctx->cap_override > 0) return std::min<int64_t>(L.n, ctx->cap_override);
+  const int64_t c = std::max<int64_t>(4096, 8 * (int64_t)(L.rows + L.cols));
+  return std::min<int64_t>(L.n, c);
+}
+
+int ensure_scratch(c2f_ctx *ctx, int64_t slots, int64_t cap) {
+  if (slots <= ctx->scratch_slots && cap <= ctx->scratch_cap && ctx->ent_cell.p) return C2F_OK;
+  slots = std::max(slots, ctx->scratch_slots);
+  cap = std::max(cap, ctx->scratch_cap);
+  int rc;
+  const size_t sc = (size_t)slots * cap;
+  if ((rc = dalloc(ctx, ctx->ent_cell, sc * 4))) return rc;
+  if ((rc = dalloc(ctx, ctx->ent_mask, sc))) return rc;
+  if ((rc = dalloc(ctx, ctx->ent_next, sc))) return rc;
+  if ((rc = dalloc(ctx, ctx->ent_cofs, sc * 8))) return rc;
+  if ((rc = dalloc(ctx, ctx->ent_P, sc * 64))) return rc;
+  if (!ctx->counter.p && (rc = dalloc(ctx, ctx->counter, 64))) return rc;
+  ctx->scratch_slots = slots;
+  ctx->scratch_cap = cap;
+  return C2F_OK;
+}
+
+int alloc_sim(c2f_ctx *ctx, const Landscape &L, Sim &s) {
+  int rc;
+  const int64_t R = s.p.n_replicas;
+  const size_t pw = (size_t)L.rows * L.wpr;
+  if ((rc = dalloc(ctx, s.ign_plane, pw * 4 * R))) return rc;
+  if ((rc = dalloc(ctx, s.burned_plane, pw * 4 * R))) return rc;
+  if (s.p.outputs & C2F_OUT_IGN_STEPS) {
+    if ((rc = dalloc(ctx, s.ign_step, (size_t)L.n * 4 * R))) return rc;
+    CK(cudaMemsetAsync(s.ign_step.p, 0xFF, (size_t)L.n * 4 * R, ctx->stream));
+  }
+  if ((rc = dalloc(ctx, s.work, 8 * R))) return rc;
+  if ((rc = dalloc(ctx, s.n_ignited, 4 * R))) return rc;
+  if ((rc = dalloc(ctx, s.ign_cell, 4 * R))) return rc;
+  if ((rc = dalloc(ctx, s.status, 4 * R))) return rc;
+  CK(cudaMemsetAsync(s.ign_plane.p, 0, pw * 4 * R, ctx->stream));
+  CK(cudaMemsetAsync(s.burned_plane.p, 0, pw * 4 * R, ctx->stream));
+  CK(cudaMemsetAsync(s.status.p, 0, 4 * R, ctx->stream));
+  s.rows = L.rows; s.cols = L.cols; s.wpr = L.wpr; s.n = L.n;
+  return C2F_OK;
+}
+
+SimJob job_of(const Landscape &L, const Sim &s) {
+  SimJob j{};
+  j.rows = L.rows; j.cols = L.cols; j.wpr = L.wpr;
+  j.n_burnable = L.n_burnable;
+  j.burnable = L.burnable.as<uint32_t>();
+  j.burnable_list = L.burnable_list.as<int32_t>();
+  j.base = L.base.as<int64_t>();
+  j.hros = L.hros.as<double>();
+  j.seed = s.p.seed;
+  j.sigma = (float)s.p.ros_sigma;
+  j.ignition_mode = s.p.ignition_mode;
+  j.ignition_cell = s.p.ignition_cell;
+  j.thr = s.p.ros_threshold;
+  j.delta = s.p.burnout_delta;
+  j.sph = 60 / s.p.minutes_per_step;
+  j.hours = s.p.hours;
+  j.d_orth = (int64_t)std::llrint(L.cell_size * 4294967296.0);
+  j.d_diag = (int64_t)std::llrint((L.cell_size * std::sqrt(2.0)) * 4294967296.0);
+  j.n_replicas = s.p.n_replicas;
+  j.ign_plane = s.ign_plane.as<uint32_t>();
+  j.burned_plane = s.burned_plane.as<uint32_t>();
+  j.ign_step = s.ign_step.as<int32_t>();
+  j.work = s.work.as<int64_t>();
+  j.n_ignited = s.n_ignited.as<int32_t>();
+  j.ign_cell = s.ign_cell.as<int32_t>();
+  j.status = s.status.as<int32_t>();
+  return j;
+}
+
+// one persistent frontier launch over the replicas of `jobs`; failed
+// (capacity) replicas are reset and re-run with a larger capacity
+int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim *> &sims) {
+  int rc;
+  const int32_t nj = (int32_t)sims.size();
+  std::vector<SimJob> jobs(nj);
+  std::vector<int64_t> begin(nj + 1, 0);
+  int64_t cap = 0;
+  int64_t max_n = 0;
+  for (int32_t i = 0; i < nj; ++i) {
+    jobs[i] = job_of(*lands[i], *sims[i]);
+    begin[i + 1] = begin[i] + sims[i]->p.n_replicas;
+    cap = std::max(cap, default_cap(ctx, *lands[i]));
+    max_n = std::max(max_n, lands[i]->n);
+  }
+  const int64_t n_items = begin[nj];
+  DevBuf djobs, dbegin, dlist;
+  if ((rc = dalloc(ctx, djobs, sizeof(SimJob) * nj))) return rc;
+  if ((rc = dalloc(ctx, dbegin, sizeof(int64_t) * (nj + 1)))) return rc;
+  CK(cudaMemcpyAsync(djobs.p, jobs.data(), sizeof(SimJob) * nj, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(dbegin.p, begin.data(), sizeof(int64_t) * (nj + 1), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  {
+    ProfScope prof(ctx, 1);
+    for (int32_t i = 0; i < nj; ++i) {
+      k_ignite<<<grid1(sims[i]->p.n_replicas, 128), 128, 0, ctx->stream>>>(djobs.as<SimJob>(), i);
+      CKL("k_ignite");
+    }
+  }
+  std::vector<int64_t> items;  // empty: all
+  for (int attempt = 0;; ++attempt) {
+    const int64_t todo = items.empty() ? n_items : (int64_t)items.size();
+    const int64_t max_slots = (int64_t)ctx->sm_count * ctx->frontier_blocks_per_sm;
+    int64_t slots = std::min<int64_t>(todo, max_slots);
+    if (attempt > 0) slots = std::min<int64_t>(slots, std::max<int64_t>(1, ctx->sm_count));
+    if ((rc = ensure_scratch(ctx, slots, cap))) return rc;
+    FrontierArgs A{};
+    A.jobs = djobs.as<SimJob>();
+    A.n_jobs = nj;
+    A.item_begin = dbegin.as<int64_t>();
+    A.item_list = nullptr;
+    if (!items.empty()) {
+      if ((rc = dalloc(ctx, dlist, sizeof(int64_t) * items.size()))) return rc;
+      CK(cudaMemcpyAsync(dlist.p, items.data(), sizeof(int64_t) * items.size(),
+                         cudaMemcpyHostToDevice, ctx->stream));
+      A.item_list = dlist.as<int64_t>();
+    }
+    A.n_items = todo;
+    A.counter = ctx->counter.as<unsigned long long>();
+    A.cap = (int32_t)cap;
+    A.ent_cell = ctx->ent_cell.as<int32_t>();
+    A.ent_mask = ctx->ent_mask.as<uint8_t>();
+    A.ent_next = ctx->ent_next.as<uint8_t>();
+    A.ent_cofs = ctx->ent_cofs.as<uint64_t>();
+    A.ent_P = ctx->ent_P.as<int64_t>();
+    CK(cudaMemsetAsync(ctx->counter.p, 0, 8, ctx->stream));
+    {
+      ProfScope prof(ctx, 2);
+      k_frontier<<<(unsigned)slots, kFrontierThreads, 0, ctx->stream>>>(A);
+      CKL("k_frontier");
+    }
+    // gather failed replicas
+    std::vector<int64_t> failed;
+    for (int32_t i = 0; i < nj; ++i) {
+      const int32_t R = sims[i]->p.n_replicas;
+      std::vector<int32_t> st(R);
+      CK(cudaMemcpyAsync(st.data(), sims[i]->status.p, 4 * (size_t)R, cudaMemcpyDeviceToHost,
+                         ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      for (int32_t r = 0; r < R; ++r) {
+        if (st[r] == 2) return fail(ctx, C2F_ECUDA, "internal frontier error (replica %d)", r);
+        if (st[r]) failed.push_back(begin[i] + r);
+      }
+    }
+    if (failed.empty()) return C2F_OK;
+    if (cap >= max_n) return fail(ctx, C2F_ECUDA, "frontier list overflow at full capacity");
+    cap = std::min<int64_t>(max_n, cap * 4);
+    // reset the failed replicas' state before the re-run
+    for (int64_t it : failed) {
+      int32_t i = (int32_t)(std::upper_bound(begin.begin(), begin.end(), it) - begin.begin() - 1);
+      const int64_t r = it - begin[i];
+      Sim &s = *sims[i];
+      const size_t pw = (size_t)s.rows * s.wpr;
+      CK(cudaMemsetAsync(s.ign_plane.as<uint32_t>() + r * pw, 0, pw * 4, ctx->stream));
+      CK(cudaMemsetAsync(s.burned_plane.as<uint32_t>() + r * pw, 0, pw * 4, ctx->stream));
+      CK(cudaMemsetAsync(s.status.as<int32_t>() + r, 0, 4, ctx->stream));
+      if (s.ign_step.p)
+        CK(cudaMemsetAsync(s.ign_step.as<int32_t>() + r * s.n, 0xFF, (size_t)s.n * 4, ctx->stream));
+    }
+    items = failed;
+  }
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+C2F_API void c2f_default_params(c2f_sim_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->n_replicas = 1;
+  p->hours = 1;
+  p->minutes_per_step = 1;
+  p->o1_curing_pct = 60.0;
+  p->m1_pc = 50.0;
+  p->outputs = C2F_OUT_SCARS | C2F_OUT_COUNTERS;
+}
+
+C2F_API int c2f_create(c2f_ctx **out, int device) {
+  if (!out) return C2F_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return C2F_EINVAL;
+  }
+  std::unique_ptr<c2f_ctx> ctx(new c2f_ctx());
+  ctx->device = device;
+  c2f_ctx *c = ctx.get();
+  {
+    c2f_ctx *ctx = c;  // for CK
+    CK(cudaSetDevice(device));
+    CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+    CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    c->stream = c->own_stream;
+    int rc = ensure_device_constants(c);
+    if (rc) return rc;
+    int bps = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_frontier, kFrontierThreads, 0));
+    c->frontier_blocks_per_sm = std::max(1, bps);
+  }
+  *out = ctx.release();
+  return C2F_OK;
+}
+
+C2F_API int c2f_set_stream(c2f_ctx *ctx, void *stream) {
+  if (!ctx) return C2F_EINVAL;
+  ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+  return C2F_OK;
+}
+
+C2F_API void c2f_destroy(c2f_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  ctx->sims.clear();
+  ctx->lands.clear();
+  ctx->ent_cell.reset(); ctx->ent_mask.reset(); ctx->ent_next.reset();
+  ctx->ent_cofs.reset(); ctx->ent_P.reset(); ctx->counter.reset();
+  cudaStreamSynchronize(ctx->stream);
+  for (int f = 0; f < C2F_KT_FAMILIES; ++f)
+    for (auto &pr : ctx->prof_events[f]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  delete ctx;
+}
+
+C2F_API const char *c2f_last_error(const c2f_ctx *ctx) {
+  return ctx ? ctx->last_error.c_str() : "";
+}
+
+C2F_API int c2f_load_landscape(c2f_ctx *ctx, int32_t rows, int32_t cols, double cell_size_m,
+                               const uint8_t *fuel, const float *slope_pct,
+                               const float *aspect_deg, const uint8_t *unburnable,
+                               int32_t *landscape_id) {
+  if (!ctx) return C2F_EINVAL;
+  if (!fuel || !landscape_id) return fail(ctx, C2F_EINVAL, "fuel and landscape_id are required");
+  if (rows < 1 || cols < 1 || (int64_t)rows * cols >= (1LL << 31))
+    return fail(ctx, C2F_EINVAL, "rows*cols must lie in [1, 2^31)");
+  if (!(cell_size_m > 0.0 && cell_size_m <= 1e6)) return fail(ctx, C2F_EINVAL, "cell_size_m out of range");
+  const int64_t n = (int64_t)rows * cols;
+  for (int64_t i = 0; i < n; ++i)
+    if (fuel[i] >= F_NCODES) return fail(ctx, C2F_EINVAL, "fuel code %d at cell %lld is not in the table",
+                                         (int)fuel[i], (long long)i);
+  if (slope_pct)
+    for (int64_t i = 0; i < n; ++i)
+      if (!(slope_pct[i] >= 0.0f && slope_pct[i] < 1e6f))
+        return fail(ctx, C2F_EINVAL, "slope at cell %lld is not a finite value >= 0", (long long)i);
+  if (aspect_deg)
+    for (int64_t i = 0; i < n; ++i)
+      if (!std::isfinite(aspect_deg[i]) || std::fabs(aspect_deg[i]) > 1e6f)
+        return fail(ctx, C2F_EINVAL, "aspect at cell %lld is not finite", (long long)i);
+  CK(cudaSetDevice(ctx->device));
+  std::unique_ptr<Landscape> L(new Landscape());
+  L->rows = rows; L->cols = cols; L->n = n; L->cell_size = cell_size_m;
+  L->wpr = (cols + 31) / 32;
+  L->burnable_host.resize(n);
+  for (int64_t i = 0; i < n; ++i) L->burnable_host[i] = (fuel[i] != 0 && !(unburnable && unburnable[i])) ? 1 : 0;
+  int rc;
+  if ((rc = dalloc(ctx, L->fuel, n))) return rc;
+  CK(cudaMemcpyAsync(L->fuel.p, fuel, n, cudaMemcpyHostToDevice, ctx->stream));
+  L->has_slope = slope_pct != nullptr;
+  if (slope_pct) {
+    if ((rc = dalloc(ctx, L->slope, n * 4))) return rc;
+    CK(cudaMemcpyAsync(L->slope.p, slope_pct, n * 4, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  if (aspect_deg) {
+    if ((rc = dalloc(ctx, L->aspect, n * 4))) return rc;
+    CK(cudaMemcpyAsync(L->aspect.p, aspect_deg, n * 4, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  DevBuf unb;
+  if (unburnable) {
+    if ((rc = dalloc(ctx, unb, n))) return rc;
+    CK(cudaMemcpyAsync(unb.p, unburnable, n, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  const int64_t words = (int64_t)rows * L->wpr;
+  DevBuf wcount, woffs, total;
+  if ((rc = dalloc(ctx, L->burnable, words * 4))) return rc;
+  if ((rc = dalloc(ctx, wcount, words * 4))) return rc;
+  if ((rc = dalloc(ctx, woffs, words * 4))) return rc;
+  if ((rc = dalloc(ctx, total, 4))) return rc;
+  k_burnable_plane<<<grid1(words, 256), 256, 0, ctx->stream>>>(
+      L->fuel.as<uint8_t>(), unb.as<uint8_t>(), rows, cols, L->wpr, L->burnable.as<uint32_t>(),
+      wcount.as<int32_t>());
+  CKL("k_burnable_plane");
+  k_scan_counts<<<1, 1024, 0, ctx->stream>>>(wcount.as<int32_t>(), words, woffs.as<int32_t>(),
+                                              total.as<int32_t>());
+  CKL("k_scan_counts");
+  int32_t nb = 0;
+  CK(cudaMemcpyAsync(&nb, total.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  L->n_burnable = nb;
+  if ((rc = dalloc(ctx, L->burnable_list, (size_t)std::max(nb, 1) * 4))) return rc;
+  k_burnable_list<<<grid1(words, 256), 256, 0, ctx->stream>>>(
+      L->burnable.as<uint32_t>(), woffs.as<int32_t>(), rows, cols, L->wpr,
+      L->burnable_list.as<int32_t>());
+  CKL("k_burnable_list");
+  if ((rc = dalloc(ctx, L->cell_prep, sizeof(CellPrep) * n))) return rc;
+  k_cell_prep<<<grid1(n, 256), 256, 0, ctx->stream>>>(L->slope.as<float>(), L->aspect.as<float>(), n,
+                                                     L->cell_prep.as<CellPrep>());
+  CKL("k_cell_prep");
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int32_t id = ctx->next_id++;
+  ctx->lands[id] = std::move(L);
+  *landscape_id = id;
+  return C2F_OK;
+}
+
+C2F_API int c2f_set_weather(c2f_ctx *ctx, int32_t landscape_id, int32_t n_hours,
+                            const c2f_weather_hour *w) {
+  if (!ctx) return C2F_EINVAL;
+  Landscape *L = find_land(ctx, landscape_id);
+  if (!L) return fail(ctx, C2F_ENOTFOUND, "unknown landscape %d", landscape_id);
+  if (n_hours < 1 || n_hours > 65535 || !w) return fail(ctx, C2F_EINVAL, "n_hours must lie in [1, 65535]");
+  for (int32_t h = 0; h < n_hours; ++h) {
+    const c2f_weather_hour &x = w[h];
+    if (!std::isfinite(x.ws_kmh) || x.ws_kmh < 0 || x.ws_kmh > 1000 || !std::isfinite(x.wd_from_deg) ||
+        std::fabs(x.wd_from_deg) > 1e6 || !(x.ffmc >= 0.0 && x.ffmc < 101.0) ||
+        !(x.bui > 0.0 && x.bui < 1e6))
+      return fail(ctx, C2F_EINVAL, "weather hour %d out of range", h);
+  }
+  CK(cudaSetDevice(ctx->device));
+  L->n_hours = n_hours;
+  L->weather.assign(n_hours * 4, 0.0);
+  for (int32_t h = 0; h < n_hours; ++h) {
+    L->weather[h * 4 + 0] = w[h].ws_kmh;
+    L->weather[h * 4 + 1] = w[h].wd_from_deg;
+    L->weather[h * 4 + 2] = w[h].ffmc;
+    L->weather[h * 4 + 3] = w[h].bui;
+  }
+  int rc;
+  if ((rc = dalloc(ctx, L->weather_dev, sizeof(double) * 4 * n_hours))) return rc;
+  CK(cudaMemcpyAsync(L->weather_dev.p, L->weather.data(), sizeof(double) * 4 * n_hours,
+                     cudaMemcpyHostToDevice, ctx->stream));
+  L->table_valid = false;
+  return C2F_OK;
+}
+
+C2F_API int c2f_build_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p, int force) {
+  if (!ctx) return C2F_EINVAL;
+  Landscape *L = find_land(ctx, landscape_id);
+  if (!L) return fail(ctx, C2F_ENOTFOUND, "unknown landscape %d", landscape_id);
+  if (L->n_hours < 1) return fail(ctx, C2F_EINVAL, "landscape has no weather");
+  int rc = validate_params(ctx, *L, p);
+  if (rc) return rc;
+  CK(cudaSetDevice(ctx->device));
+  return ensure_table(ctx, *L, p, force != 0);
+}
+
+C2F_API int c2f_get_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p, int32_t hour,
+                        double *ros8, double *hros, int64_t *base) {
+  if (!ctx) return C2F_EINVAL;
+  Landscape *L = find_land(ctx, landscape_id);
+  if (!L) return fail(ctx, C2F_ENOTFOUND, "unknown landscape %d", landscape_id);
+  if (L->n_hours < 1) return fail(ctx, C2F_EINVAL, "landscape has no weather");
+  int rc = validate_params(ctx, *L, p);
+  if (rc) return rc;
+  if (hour < 0 || hour >= p->hours) return fail(ctx, C2F_EINVAL, "hour out of range");
+  CK(cudaSetDevice(ctx->device));
+  if ((rc = ensure_table(ctx, *L, p, false))) return rc;
+  const size_t n = (size_t)L->n;
+  if (base)
+    CK(cudaMemcpyAsync(base, L->base.as<int64_t>() + (size_t)hour * n * 8, n * 64,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+  if (hros)
+    CK(cudaMemcpyAsync(hros, L->hros.as<double>() + (size_t)hour * n, n * 8, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  if (ros8) {
+    DevBuf tmp;
+    if ((rc = dalloc(ctx, tmp, n * 64))) return rc;
+    RosTableArgs a{};
+    a.fuel = L->fuel.as<uint8_t>();
+    a.slope = L->has_slope ? L->slope.as<float>() : nullptr;
+    a.burnable = L->burnable.as<uint32_t>();
+    a.rows = L->rows; a.cols = L->cols; a.wpr = L->wpr;
+    a.cell = L->cell_prep.as<CellPrep>();
+    a.hour = L->hour_prep.as<HourPrep>();
+    a.hour0 = hour;
+    a.pcf = p->m1_pc / 100.0;
+    a.const_ros = p->const_ros;
+    a.dt2p32 = (double)p->minutes_per_step * 4294967296.0;
+    a.ellipse_mode = p->ellipse_mode;
+    a.ros8 = tmp.as<double>();
+    k_ros_table<<<dim3(grid1(n, 128), 1), 128, 0, ctx->stream>>>(a);
+    CKL("k_ros_table(export)");
+    CK(cudaMemcpyAsync(ros8, tmp.p, n * 64, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return C2F_OK;
+}
+
+static int simulate_many(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_sim_params *params,
+                         int32_t *sim_ids) {
+  if (!ctx) return C2F_EINVAL;
+  if (n < 1 || !ids || !params || !sim_ids) return fail(ctx, C2F_EINVAL, "bad batch arguments");
+  CK(cudaSetDevice(ctx->device));
+  std::vector<Landscape *> lands(n);
+  for (int32_t i = 0; i < n; ++i) {
+    lands[i] = find_land(ctx, ids[i]);
+    if (!lands[i]) return fail(ctx, C2F_ENOTFOUND, "unknown landscape %d", ids[i]);
+    if (lands[i]->n_hours < 1) return fail(ctx, C2F_EINVAL, "landscape %d has no weather", ids[i]);
+    int rc = validate_params(ctx, *lands[i], &params[i]);
+    if (rc) return rc;
+  }
+  int rc;
+  for (int32_t i = 0; i < n; ++i) {
+    // jobs on one landscape must agree on the table options
+    for (int32_t k = 0; k < i; ++k)
+      if (ids[k] == ids[i] && !(key_of(&params[k]) == key_of(&params[i])))
+        return fail(ctx, C2F_EINVAL, "batch entries %d and %d share a landscape with different ROS options", k, i);
+    TableKey want = key_of(&params[i]);
+    for (int32_t k = 0; k < n; ++k)
+      if (ids[k] == ids[i]) want.hours = std::max(want.hours, params[k].hours);
+    c2f_sim_params q = params[i];
+    q.hours = want.hours;
+    if ((rc = ensure_table(ctx, *lands[i], &q, false))) return rc;
+  }
+  std::vector<std::unique_ptr<Sim>> owned(n);
+  std::vector<Sim *> sims(n);
+  for (int32_t i = 0; i < n; ++i) {
+    owned[i].reset(new Sim());
+    owned[i]->landscape = ids[i];
+    owned[i]->p = params[i];
+    if ((rc = alloc_sim(ctx, *lands[i], *owned[i]))) return rc;
+    sims[i] = owned[i].get();
+  }
+  if ((rc = run_frontier(ctx, lands, sims))) return rc;
+  for (int32_t i = 0; i < n; ++i) {
+    const int32_t id = ctx->next_id++;
+    ctx->sims[id] = std::move(owned[i]);
+    sim_ids[i] = id;
+  }
+  return C2F_OK;
+}
+
+C2F_API int c2f_simulate(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p,
+                         int32_t *sim_id) {
+  return simulate_many(ctx, 1, &landscape_id, p, sim_id);
+}
+
+C2F_API int c2f_simulate_batch(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
+                               const c2f_sim_params *params, int32_t *sim_ids) {
+  return simulate_many(ctx, n, landscape_ids, params, sim_ids);
+}
+
+static int burn_prob_into(c2f_ctx *ctx, Sim &s, uint32_t *dst) {
+  const int32_t R = s.p.n_replicas;
+  const int64_t words = (int64_t)s.rows * s.wpr;
+  const int64_t target = (int64_t)ctx->sm_count * 4 * 256;
+  int32_t chunks = (int32_t)std::min<int64_t>(R, std::max<int64_t>(1, target / std::max<int64_t>(words, 1)));
+  int32_t per = (R + chunks - 1) / chunks;
+  if (per > 65535) { per = 65535; chunks = (R + per - 1) / per; }
+  chunks = (R + per - 1) / per;
+  ProfScope prof(ctx, 3);
+  if (chunks > 1) CK(cudaMemsetAsync(dst, 0, (size_t)s.n * 4, ctx->stream));
+  k_burn_prob<<<dim3(grid1(words, 256), (unsigned)chunks), 256, 0, ctx->stream>>>(
+      s.ign_plane.as<uint32_t>(), R, s.rows, s.cols, s.wpr, per, dst, chunks > 1 ? 1 : 0);
+  CKL("k_burn_prob");
+  return C2F_OK;
+}
+
+C2F_API int c2f_burn_prob(c2f_ctx *ctx, int32_t sim_id, uint32_t *counts) {
+  if (!ctx) return C2F_EINVAL;
+  Sim *s = find_sim(ctx, sim_id);
+  if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  if (!counts) return fail(ctx, C2F_EINVAL, "counts is NULL");
+  CK(cudaSetDevice(ctx->device));
+  DevBuf tmp;
+  int rc;
+  if ((rc = dalloc(ctx, tmp, (size_t)s->n * 4))) return rc;
+  if ((rc = burn_prob_into(ctx, *s, tmp.as<uint32_t>()))) return rc;
+  CK(cudaMemcpyAsync(counts, tmp.p, (size_t)s->n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return C2F_OK;
+}
+
+C2F_API int c2f_burn_prob_device(c2f_ctx *ctx, int32_t sim_id, uint32_t *counts_dev) {
+  if (!ctx) return C2F_EINVAL;
+  Sim *s = find_sim(ctx, sim_id);
+  if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  if (!counts_dev) return fail(ctx, C2F_EINVAL, "counts_dev is NULL");
+  CK(cudaSetDevice(ctx->device));
+  return burn_prob_into(ctx, *s, counts_dev);
+}
+
+C2F_API int c2f_get_scars(c2f_ctx *ctx, int32_t sim_id, uint8_t *scars, int32_t *ign_step) {
+  if (!ctx) return C2F_EINVAL;
+  Sim *s = find_sim(ctx, sim_id);
+  if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  if (ign_step && !s->ign_step.p)
+    return fail(ctx, C2F_EINVAL, "simulation did not keep ignition steps (C2F_OUT_IGN_STEPS)");
+  CK(cudaSetDevice(ctx->device));
+  const int32_t R = s->p.n_replicas;
+  const size_t total = (size_t)s->n * R;
+  if (scars) {
+    DevBuf tmp;
+    int rc;
+    if ((rc = dalloc(ctx, tmp, total))) return rc;
+    k_scar_bytes<<<grid1((int64_t)total, 256), 256, 0, ctx->stream>>>(
+        s->ign_plane.as<uint32_t>(), R, s->rows, s->cols, s->wpr, tmp.as<uint8_t>());
+    CKL("k_scar_bytes");
+    CK(cudaMemcpyAsync(scars, tmp.p, total, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if (ign_step) {
+    CK(cudaMemcpyAsync(ign_step, s->ign_step.p, total * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return C2F_OK;
+}
+
+C2F_API int c2f_get_counters(c2f_ctx *ctx, int32_t sim_id, int64_t *work, int32_t *ignited,
+                             int32_t *ign_cell) {
+  if (!ctx) return C2F_EINVAL;
+  Sim *s = find_sim(ctx, sim_id);
+  if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  CK(cudaSetDevice(ctx->device));
+  const size_t R = (size_t)s->p.n_replicas;
+  if (work) CK(cudaMemcpyAsync(work, s->work.p, R * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  if (ignited) CK(cudaMemcpyAsync(ignited, s->n_ignited.p, R * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  if (ign_cell) CK(cudaMemcpyAsync(ign_cell, s->ign_cell.p, R * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return C2F_OK;
+}
+
+C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap) {
+  if (!ctx) return C2F_EINVAL;
+  if (cap < 0 || cap > (1LL << 31)) return fail(ctx, C2F_EINVAL, "capacity out of range");
+  ctx->cap_override = cap;
+  return C2F_OK;
+}
+
+C2F_API int c2f_profile(c2f_ctx *ctx, int enable) {
+  if (!ctx) return C2F_EINVAL;
+  ctx->profiling = enable != 0;
+  return C2F_OK;
+}
+
+C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches) {
+  if (!ctx) return C2F_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int f = 0; f < C2F_KT_FAMILIES; ++f) {
+    double tot = 0.0;
+    for (auto &pr : ctx->prof_events[f]) {
+      float t = 0.0f;
+      if (cudaEventElapsedTime(&t, pr.first, pr.second) == cudaSuccess) tot += t;
+      else cudaGetLastError();
+      ctx->event_pool.push_back(pr.first);
+      ctx->event_pool.push_back(pr.second);
+    }
+    if (ms) ms[f] = tot;
+    if (launches) launches[f] = (int64_t)ctx->prof_events[f].size();
+    ctx->prof_events[f].clear();
+  }
+  return C2F_OK;
+}
+
+C2F_API int c2f_release(c2f_ctx *ctx, int32_t id) {
+  if (!ctx) return C2F_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  if (ctx->sims.erase(id)) return C2F_OK;
+  if (ctx->lands.erase(id)) return C2F_OK;
+  return fail(ctx, C2F_ENOTFOUND, "unknown id %d", id);
+}
+
+}  // extern "C"
