@@ -147,7 +147,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     c2f.build()
-    w = S.config2()
+    w = S.config2(n_replicas=args.replicas)
     L = w.landscape
     n = L.fuel.size
     R = w.params["n_replicas"]
@@ -208,7 +208,7 @@ def run_ours(args, rank, world, local_rank):
 
     # e2e: host buffers through the C ABI, copies inside the timed region
     e2e = None
-    if rank == 0 or world > 1:
+    if not args.no_e2e:
         host_counts = np.empty(n, dtype=np.uint32)
         h2d = L.fuel.nbytes + L.slope.nbytes + L.aspect.nbytes + w.weather.nbytes
         e2e_steps = max(1, min(args.steps, 3))
@@ -336,7 +336,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=256)
+    ap.add_argument("--replicas", type=int, default=1000,
+                    help="replicas per GPU (the workload has 1000; fewer only for profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1000)
     ap.add_argument("--ref-sample", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -253,7 +253,13 @@ struct FrontierShared {
   int32_t out_base;
 };
 
-__global__ void __launch_bounds__(kFrontierThreads) k_frontier(FrontierArgs A) {
+// One CTA per replica (work list of (simulation, replica) items).  The
+// replica's Burning/Burned bit planes live in shared memory when they fit
+// (SMEM = true; the scar plane is copied out at the end) and otherwise in
+// global memory (the scar plane in place, the Burned plane in per-CTA scratch).
+template <bool SMEM>
+__device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
+  extern __shared__ __align__(16) uint32_t s_planes[];
   __shared__ FrontierShared S;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int T = kFrontierThreads;
@@ -281,8 +287,18 @@ __global__ void __launch_bounds__(kFrontierThreads) k_frontier(FrontierArgs A) {
     const int32_t rows = J.rows, cols = J.cols, wpr = J.wpr;
     const int64_t n = (int64_t)rows * cols;
     const size_t pw = (size_t)rows * wpr;
-    uint32_t *ign = J.ign_plane + (size_t)r * pw;
-    uint32_t *brn = J.burned_plane + (size_t)r * pw;
+    uint32_t *ign;
+    uint32_t *brn;
+    if constexpr (SMEM) {
+      ign = s_planes;
+      brn = s_planes + A.pw_max;
+      for (size_t i = tid; i < pw; i += T) { ign[i] = 0u; brn[i] = 0u; }
+    } else {
+      ign = J.ign_plane + (size_t)r * pw;
+      brn = A.brn_scratch + slot * (size_t)A.pw_max;
+      for (size_t i = tid; i < pw; i += T) brn[i] = 0u;
+    }
+    __syncthreads();
     int32_t *istep = J.ign_step ? J.ign_step + (size_t)r * n : nullptr;
     const int32_t sph = J.sph, H = J.hours;
 
@@ -527,6 +543,10 @@ __global__ void __launch_bounds__(kFrontierThreads) k_frontier(FrontierArgs A) {
       }
       __syncthreads();
     }
+    if constexpr (SMEM) {   // scar plane out
+      uint32_t *dst = J.ign_plane + (size_t)r * pw;
+      for (size_t i = tid; i < pw; i += T) dst[i] = ign[i];
+    }
     if (tid == 0) {
       J.work[r] = S.W;
       J.n_ignited[r] = S.nign;
@@ -534,6 +554,14 @@ __global__ void __launch_bounds__(kFrontierThreads) k_frontier(FrontierArgs A) {
     }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(kFrontierThreads, 3) k_frontier_smem(FrontierArgs A) {
+  frontier_body<true>(A);
+}
+
+__global__ void __launch_bounds__(kFrontierThreads, 3) k_frontier_gmem(FrontierArgs A) {
+  frontier_body<false>(A);
 }
 
 // ------------------------------------------------------------------ K4

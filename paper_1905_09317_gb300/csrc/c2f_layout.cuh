@@ -53,7 +53,6 @@ struct SimJob {
   int32_t n_replicas;
   // per-replica outputs
   uint32_t *ign_plane;            // [R][rows*wpr] scar bits
-  uint32_t *burned_plane;         // [R][rows*wpr]
   int32_t *ign_step;              // [R][N] or nullptr
   int64_t *work;                  // [R]
   int32_t *n_ignited;             // [R]
@@ -74,6 +73,8 @@ struct FrontierArgs {
   uint8_t *ent_next;              // [slots][cap] next event offset in the hour (0xFF none)
   uint64_t *ent_cofs;             // [slots][cap] 8 per-axis crossing offsets (0xFF none)
   int64_t *ent_P;                 // [slots][cap][8] progress at the start of the next hour
+  int64_t pw_max;                 // words per bit plane of the largest landscape
+  uint32_t *brn_scratch;          // [slots][pw_max] Burned planes (global-plane variant)
 };
 
 // K1 launch arguments: grid.y covers hours hour0 .. hour0 + gridDim.y - 1

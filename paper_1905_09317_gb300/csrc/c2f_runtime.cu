@@ -35,7 +35,8 @@ __global__ void k_cell_prep(const float *, const float *, int64_t, CellPrep *);
 __global__ void k_hour_prep(const double *, int32_t, double, HourPrep *);
 __global__ void k_ros_table(RosTableArgs);
 __global__ void k_ignite(const SimJob *, int32_t);
-__global__ void k_frontier(FrontierArgs);
+__global__ void k_frontier_smem(FrontierArgs);
+__global__ void k_frontier_gmem(FrontierArgs);
 __global__ void k_burn_prob(const uint32_t *, int32_t, int32_t, int32_t, int32_t, int32_t,
                             uint32_t *, int32_t);
 __global__ void k_scar_bytes(const uint32_t *, int32_t, int32_t, int32_t, int32_t, uint8_t *);
@@ -93,7 +94,7 @@ struct Sim {
   c2f_sim_params p{};
   int32_t rows = 0, cols = 0, wpr = 0;
   int64_t n = 0;
-  DevBuf ign_plane, burned_plane, ign_step, work, n_ignited, ign_cell, status;
+  DevBuf ign_plane, ign_step, work, n_ignited, ign_cell, status;
 };
 
 struct DeviceInit {
@@ -115,9 +116,10 @@ struct c2f_ctx {
   std::unordered_map<int32_t, std::unique_ptr<Landscape>> lands;
   std::unordered_map<int32_t, std::unique_ptr<Sim>> sims;
   // frontier scratch
-  DevBuf ent_cell, ent_mask, ent_next, ent_cofs, ent_P, counter;
-  int64_t scratch_slots = 0, scratch_cap = 0;
-  int frontier_blocks_per_sm = 0;
+  DevBuf ent_cell, ent_mask, ent_next, ent_cofs, ent_P, counter, brn_scratch;
+  int64_t scratch_slots = 0, scratch_cap = 0, brn_words = 0;
+  int smem_optin = 0;
+  int64_t smem_plane_limit = 112 * 1024;   // planes staged in shared memory up to this size
   int64_t cap_override = 0;
   // kernel timing
   bool profiling = false;
@@ -331,7 +333,6 @@ int alloc_sim(c2f_ctx *ctx, const Landscape &L, Sim &s) {
   const int64_t R = s.p.n_replicas;
   const size_t pw = (size_t)L.rows * L.wpr;
   if ((rc = dalloc(ctx, s.ign_plane, pw * 4 * R))) return rc;
-  if ((rc = dalloc(ctx, s.burned_plane, pw * 4 * R))) return rc;
   if (s.p.outputs & C2F_OUT_IGN_STEPS) {
     if ((rc = dalloc(ctx, s.ign_step, (size_t)L.n * 4 * R))) return rc;
     CK(cudaMemsetAsync(s.ign_step.p, 0xFF, (size_t)L.n * 4 * R, ctx->stream));
@@ -341,7 +342,6 @@ int alloc_sim(c2f_ctx *ctx, const Landscape &L, Sim &s) {
   if ((rc = dalloc(ctx, s.ign_cell, 4 * R))) return rc;
   if ((rc = dalloc(ctx, s.status, 4 * R))) return rc;
   CK(cudaMemsetAsync(s.ign_plane.p, 0, pw * 4 * R, ctx->stream));
-  CK(cudaMemsetAsync(s.burned_plane.p, 0, pw * 4 * R, ctx->stream));
   CK(cudaMemsetAsync(s.status.p, 0, 4 * R, ctx->stream));
   s.rows = L.rows; s.cols = L.cols; s.wpr = L.wpr; s.n = L.n;
   return C2F_OK;
@@ -367,7 +367,6 @@ SimJob job_of(const Landscape &L, const Sim &s) {
   j.d_diag = (int64_t)std::llrint((L.cell_size * std::sqrt(2.0)) * 4294967296.0);
   j.n_replicas = s.p.n_replicas;
   j.ign_plane = s.ign_plane.as<uint32_t>();
-  j.burned_plane = s.burned_plane.as<uint32_t>();
   j.ign_step = s.ign_step.as<int32_t>();
   j.work = s.work.as<int64_t>();
   j.n_ignited = s.n_ignited.as<int32_t>();
@@ -405,13 +404,28 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
       CKL("k_ignite");
     }
   }
+  int64_t pw_max = 0;
+  for (int32_t i = 0; i < nj; ++i) pw_max = std::max<int64_t>(pw_max, (int64_t)lands[i]->rows * lands[i]->wpr);
+  const size_t plane_bytes = (size_t)pw_max * 4 * 2;
+  const bool use_smem = (int64_t)plane_bytes <= ctx->smem_plane_limit &&
+                        (int64_t)plane_bytes <= (int64_t)ctx->smem_optin - 4096;
+  auto kern = use_smem ? k_frontier_smem : k_frontier_gmem;
+  const size_t dyn_smem = use_smem ? plane_bytes : 0;
+  if (use_smem) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem));
+  int bps = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kFrontierThreads, dyn_smem));
+  bps = std::max(bps, 1);
   std::vector<int64_t> items;  // empty: all
   for (int attempt = 0;; ++attempt) {
     const int64_t todo = items.empty() ? n_items : (int64_t)items.size();
-    const int64_t max_slots = (int64_t)ctx->sm_count * ctx->frontier_blocks_per_sm;
+    const int64_t max_slots = (int64_t)ctx->sm_count * bps;
     int64_t slots = std::min<int64_t>(todo, max_slots);
     if (attempt > 0) slots = std::min<int64_t>(slots, std::max<int64_t>(1, ctx->sm_count));
     if ((rc = ensure_scratch(ctx, slots, cap))) return rc;
+    if (!use_smem && (slots * pw_max > ctx->brn_words)) {
+      if ((rc = dalloc(ctx, ctx->brn_scratch, (size_t)slots * pw_max * 4))) return rc;
+      ctx->brn_words = slots * pw_max;
+    }
     FrontierArgs A{};
     A.jobs = djobs.as<SimJob>();
     A.n_jobs = nj;
@@ -431,10 +445,12 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
     A.ent_next = ctx->ent_next.as<uint8_t>();
     A.ent_cofs = ctx->ent_cofs.as<uint64_t>();
     A.ent_P = ctx->ent_P.as<int64_t>();
+    A.pw_max = pw_max;
+    A.brn_scratch = use_smem ? nullptr : ctx->brn_scratch.as<uint32_t>();
     CK(cudaMemsetAsync(ctx->counter.p, 0, 8, ctx->stream));
     {
       ProfScope prof(ctx, 2);
-      k_frontier<<<(unsigned)slots, kFrontierThreads, 0, ctx->stream>>>(A);
+      kern<<<(unsigned)slots, kFrontierThreads, dyn_smem, ctx->stream>>>(A);
       CKL("k_frontier");
     }
     // gather failed replicas
@@ -460,7 +476,6 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
       Sim &s = *sims[i];
       const size_t pw = (size_t)s.rows * s.wpr;
       CK(cudaMemsetAsync(s.ign_plane.as<uint32_t>() + r * pw, 0, pw * 4, ctx->stream));
-      CK(cudaMemsetAsync(s.burned_plane.as<uint32_t>() + r * pw, 0, pw * 4, ctx->stream));
       CK(cudaMemsetAsync(s.status.as<int32_t>() + r, 0, 4, ctx->stream));
       if (s.ign_step.p)
         CK(cudaMemsetAsync(s.ign_step.as<int32_t>() + r * s.n, 0xFF, (size_t)s.n * 4, ctx->stream));
@@ -504,9 +519,7 @@ C2F_API int c2f_create(c2f_ctx **out, int device) {
     c->stream = c->own_stream;
     int rc = ensure_device_constants(c);
     if (rc) return rc;
-    int bps = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_frontier, kFrontierThreads, 0));
-    c->frontier_blocks_per_sm = std::max(1, bps);
+    CK(cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
   }
   *out = ctx.release();
   return C2F_OK;
@@ -525,7 +538,7 @@ C2F_API void c2f_destroy(c2f_ctx *ctx) {
   ctx->sims.clear();
   ctx->lands.clear();
   ctx->ent_cell.reset(); ctx->ent_mask.reset(); ctx->ent_next.reset();
-  ctx->ent_cofs.reset(); ctx->ent_P.reset(); ctx->counter.reset();
+  ctx->ent_cofs.reset(); ctx->ent_P.reset(); ctx->counter.reset(); ctx->brn_scratch.reset();
   cudaStreamSynchronize(ctx->stream);
   for (int f = 0; f < C2F_KT_FAMILIES; ++f)
     for (auto &pr : ctx->prof_events[f]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
