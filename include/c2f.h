@@ -174,6 +174,12 @@ C2F_API int c2f_get_counters(c2f_ctx *ctx, int32_t sim_id, int64_t *work, int32_
  * results never depend on this value (a tuning and test knob). */
 C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap);
 
+/* Frontier-kernel launch shape: CTA size `threads` (64, 128 or 256) and the
+ * largest pair of per-replica bit planes (bytes) staged in shared memory
+ * instead of global memory (0 = always global).  Results do not depend on
+ * either; they are tuning knobs (see c2f_autotune in the Python package). */
+C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem_plane_bytes);
+
 /* Kernel timing: with profiling on, the context brackets each launch of its
  * kernel families with CUDA events on its stream.  c2f_kernel_times waits for
  * the stream, writes per family the summed milliseconds and the launch count

@@ -69,6 +69,7 @@ _SIGS = [
     ("c2f_get_scars", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     ("c2f_get_counters", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("c2f_set_list_capacity", C.c_int, [C.c_void_p, C.c_int64]),
+    ("c2f_set_frontier_config", C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
     ("c2f_profile", C.c_int, [C.c_void_p, C.c_int]),
     ("c2f_kernel_times", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("c2f_release", C.c_int, [C.c_void_p, C.c_int32]),
@@ -216,6 +217,9 @@ class Context:
 
     def set_list_capacity(self, cap: int) -> None:
         self._check(self.lib.c2f_set_list_capacity(self.h, int(cap)))
+
+    def set_frontier_config(self, threads: int, smem_plane_bytes: int) -> None:
+        self._check(self.lib.c2f_set_frontier_config(self.h, int(threads), int(smem_plane_bytes)))
 
     def profile(self, enable: bool = True) -> None:
         self._check(self.lib.c2f_profile(self.h, int(bool(enable))))

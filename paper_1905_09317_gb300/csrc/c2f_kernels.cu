@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(128) k_ros_table(RosTableArgs a) {
                                   fixed_of(__dmul_rn(ros[k + 1], a.dt2p32)));
   }
   if (a.hros) a.hros[idx] = hr;
+  if (a.hros_pos && burn && !(hr > 1e-200)) atomicAnd(a.hros_pos, 0);
   if (a.ros8) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) a.ros8[(size_t)cell * 8 + k] = ros[k];
@@ -243,32 +244,52 @@ __device__ __forceinline__ uint32_t warp_min(uint32_t v) {
   return v;
 }
 
+template <int T>
 struct FrontierShared {
   SimJob job;
   int64_t item;
-  long long W;
-  int32_t count, nnew, live, burn, dying, overflow, nign, step;
+  int32_t nnew, overflow, hros_pos;
+  int32_t burn[2];
   uint32_t minnext[2];
-  int32_t warp_tot[kFrontierThreads / 32];
+  int32_t warp_tot[T / 32];
   int32_t out_base;
 };
 
-// One CTA per replica (work list of (simulation, replica) items).  The
-// replica's Burning/Burned bit planes live in shared memory when they fit
-// (SMEM = true; the scar plane is copied out at the end) and otherwise in
-// global memory (the scar plane in place, the Burned plane in per-CTA scratch).
-template <bool SMEM>
+// min over the 8 lanes of this lane's group
+__device__ __forceinline__ uint32_t group_min(uint32_t v) {
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// OR of a per-lane bit over the 8 lanes of this lane's group, as an 8-bit mask (bit k = lane k)
+__device__ __forceinline__ uint32_t group_bits(bool b) {
+  const uint32_t bal = __ballot_sync(0xffffffffu, b);
+  return (bal >> (threadIdx.x & 24)) & 0xFFu;
+}
+
+// One CTA per replica, taken from a work list of (simulation, replica) items.
+// Eight lanes cooperate on one burning cell, lane k owning axis k, so the
+// per-axis work of a cell (crossing tests, increments, crossing periods,
+// burn-out tests of the neighbour on that axis) runs side by side.  Each
+// visited period costs two CTA barriers: sends + receives, then the set-up of
+// the cells ignited in that period.  The replica's Burning/Burned planes live
+// in shared memory when they fit (SMEM; the scar plane is copied out at the
+// end), else in global memory (the scar plane in place, the Burned plane in
+// per-CTA scratch).
+template <int T, bool SMEM>
 __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
+  constexpr int G = T / 8;   // cell groups per CTA
   extern __shared__ __align__(16) uint32_t s_planes[];
-  __shared__ FrontierShared S;
+  __shared__ FrontierShared<T> S;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int T = kFrontierThreads;
+  const int k = tid & 7, g = tid >> 3;
   const size_t slot = blockIdx.x;
   const int32_t cap = A.cap;
   int32_t *ecell = A.ent_cell + slot * cap;
   uint8_t *emask = A.ent_mask + slot * cap;
   uint8_t *enext = A.ent_next + slot * cap;
-  uint64_t *ecofs = A.ent_cofs + slot * cap;
+  uint8_t *ecofs = A.ent_cofs + slot * (size_t)cap * 8;
   int64_t *eP = A.ent_P + slot * (size_t)cap * 8;
 
   for (;;) {
@@ -277,7 +298,10 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
       int64_t item = -1;
       if ((int64_t)i < A.n_items) item = A.item_list ? A.item_list[i] : (int64_t)i;
       S.item = item;
-      if (item >= 0) S.job = A.jobs[find_job(A.item_begin, A.n_jobs, item)];
+      if (item >= 0) {
+        S.job = A.jobs[find_job(A.item_begin, A.n_jobs, item)];
+        S.hros_pos = S.job.hros_pos ? *S.job.hros_pos : 0;
+      }
     }
     __syncthreads();
     const int64_t item = S.item;
@@ -287,6 +311,7 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
     const int32_t rows = J.rows, cols = J.cols, wpr = J.wpr;
     const int64_t n = (int64_t)rows * cols;
     const size_t pw = (size_t)rows * wpr;
+    const bool gate_free = (J.thr < 0.0) || (J.thr == 0.0 && S.hros_pos);
     uint32_t *ign;
     uint32_t *brn;
     if constexpr (SMEM) {
@@ -298,104 +323,90 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
       brn = A.brn_scratch + slot * (size_t)A.pw_max;
       for (size_t i = tid; i < pw; i += T) brn[i] = 0u;
     }
-    __syncthreads();
     int32_t *istep = J.ign_step ? J.ign_step + (size_t)r * n : nullptr;
     const int32_t sph = J.sph, H = J.hours;
-
-    // Step 1: the ignition cell burns from period 0 (Alg. 1)
+    const int64_t dk = (k & 1) ? J.d_diag : J.d_orth;   // this lane's axis length
     if (tid == 0) {
-      const int32_t ic = J.ign_cell[r];
-      const int32_t ir = ic / cols, icc = ic - ir * cols;
-      atomicOr(&ign[(int64_t)ir * wpr + (icc >> 5)], 1u << (icc & 31));
-      if (istep) istep[ic] = 0;
-      uint32_t mask = 0;
-      for (int k = 0; k < 8; ++k) {
-        const int32_t nr = ir + kDR[k], nc = icc + kDC[k];
-        if (nr < 0 || nr >= rows || nc < 0 || nc >= cols) continue;
-        if (plane_bit(J.burnable, wpr, nr, nc) && !plane_bit(ign, wpr, nr, nc)) mask |= 1u << k;
-      }
-      ecell[0] = ic; emask[0] = (uint8_t)mask; enext[0] = kNone; ecofs[0] = ~0ull;
-      for (int k = 0; k < 8; ++k) eP[k] = 0;
-      S.count = 1; S.nnew = 1; S.live = 1; S.W = 0; S.nign = 1; S.overflow = 0;
-      S.burn = 0; S.dying = 0; S.minnext[0] = kNone; S.minnext[1] = kNone;
-      if (mask == 0) {  // no Available neighbour: Burned at the end of period 1
-        atomicOr(&brn[(int64_t)ir * wpr + (icc >> 5)], 1u << (icc & 31));
-        S.live = 0;
-        S.W = (H * sph >= 1) ? 1 : 0;
-      }
+      S.nnew = 1; S.overflow = 0;
+      S.burn[0] = S.burn[1] = 0;
+      S.minnext[0] = S.minnext[1] = kNone;
     }
     __syncthreads();
-    long long s_done = 0;   // last period whose burning count is in W (thread 0)
-    int par = 0;
 
-    for (int32_t h = 0; h < H && S.live > 0 && !S.overflow; ++h) {
+    // Step 1 of Alg. 1: the ignition cell burns from period 0
+    int32_t live = 1;
+    long long W = 0;          // thread 0's running work count
+    int32_t nign = 1;
+    {
+      const int32_t ic = J.ign_cell[r];
+      const int32_t ir = ic / cols, icc = ic - ir * cols;
+      if (tid == 0) {
+        atomicOr(&ign[(int64_t)ir * wpr + (icc >> 5)], 1u << (icc & 31));
+        if (istep) istep[ic] = 0;
+      }
+      __syncthreads();
+      bool open = false;
+      if (tid < 8) {
+        const int32_t nr = ir + kDR[k], nc = icc + kDC[k];
+        open = nr >= 0 && nr < rows && nc >= 0 && nc < cols &&
+               plane_bit(J.burnable, wpr, nr, nc) && !plane_bit(ign, wpr, nr, nc);
+      }
+      const uint32_t mask = group_bits(open);   // lanes 0..7 of warp 0 hold the cell's mask
+      if (tid < 8) {
+        eP[k] = 0;
+        ecofs[k] = kNone;
+        if (k == 0) { ecell[0] = ic; emask[0] = (uint8_t)mask; enext[0] = kNone; }
+      }
+      if (tid == 0 && mask == 0) {   // no Available neighbour: Burned after period 1
+        atomicOr(&brn[(int64_t)ir * wpr + (icc >> 5)], 1u << (icc & 31));
+        S.burn[0] = 1;
+      }
+      __syncthreads();
+      if (S.burn[0]) { live = 0; W = (H * sph >= 1) ? 1 : 0; }
+      __syncthreads();
+      if (tid == 0) S.burn[0] = 0;
+      __syncthreads();
+    }
+    int32_t cnt = 1;          // entries in the list
+    long long s_done = 0;     // last period whose burning count is in W
+    int it = 0;               // visited-period counter (parity selects the buffers)
+    bool aborted = false;
+
+    for (int32_t h = 0; h < H && live > 0 && !aborted; ++h) {
       const int32_t s0 = h * sph + 1, L = s0 + sph - 1;
       const int64_t *baseh = J.base + (size_t)h * n * 8;
+      const int p0 = it & 1;
 
-      // ---- hour boundary: drop Burned cells, recompute per-axis crossings
+      // ---- hour boundary (i): drop Burned cells and cells with no open axis
       {
-        const int32_t cnt = S.count;
         if (tid == 0) S.out_base = 0;
         __syncthreads();
         for (int32_t b0 = 0; b0 < cnt; b0 += T) {
           const int32_t e = b0 + tid;
           bool keep = false;
           int32_t cell = 0;
-          uint32_t mask = 0, nx = kNone;
-          uint64_t cofs = ~0ull;
+          uint32_t mask = 0;
           int64_t P[8];
           if (e < cnt) {
             cell = ecell[e];
+            mask = emask[e];
             const int32_t cr = cell / cols, cc = cell - cr * cols;
-            if (!plane_bit(brn, wpr, cr, cc)) {
-              keep = true;
-              mask = emask[e];
+            keep = mask != 0 && !plane_bit(brn, wpr, cr, cc);
+            if (keep) {
 #pragma unroll
-              for (int k = 0; k < 8; ++k) P[k] = eP[(size_t)e * 8 + k];
-              for (int k = 0; k < 8; ++k)
-                if ((mask >> k) & 1u)
-                  if (plane_bit(ign, wpr, cr + kDR[k], cc + kDC[k])) mask &= ~(1u << k);
-              if (mask != 0 || J.delta > 0.0) {
-                const float f = noise_factor(J.seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, J.sigma);
-                const uint64_t F = noise_fixed(f);
-                const int64_t *bc = baseh + (size_t)cell * 8;
-                for (int k = 0; k < 8; ++k) {
-                  if (!((mask >> k) & 1u)) continue;
-                  const int64_t dk = axis_len(J, k);
-                  const int64_t inc = apply_noise(bc[k], F, dk);
-                  const int64_t rem = dk - P[k];
-                  if (inc > 0 && inc * sph >= rem) {
-                    const int32_t nst = ceil_div_small(rem, inc);
-                    cofs = (cofs & ~(0xFFull << (8 * k))) | ((uint64_t)(nst - 1) << (8 * k));
-                  } else {
-                    P[k] += inc * sph;
-                  }
-                }
-                if (J.delta > 0.0) {
-                  const double hr = J.hros[(size_t)h * n + cell];
-                  if (__dmul_rn(hr, (double)f) < J.delta) {   // A5 (i): Burned after period s0
-                    const uint32_t bit = 1u << (cc & 31);
-                    const uint32_t old = atomicOr(&brn[(int64_t)cr * wpr + (cc >> 5)], bit);
-                    if (!(old & bit)) atomicAdd(&S.dying, 1);
-                    for (int k = 0; k < 8; ++k)
-                      if (((cofs >> (8 * k)) & 0xFFull) != 0) cofs |= 0xFFull << (8 * k);
-                  }
-                }
-              }
-              nx = min_byte8(cofs);
+              for (int q = 0; q < 8; ++q) P[q] = eP[(size_t)e * 8 + q];
             }
           }
-          // compaction: exclusive scan of keep flags
           const uint32_t bal = __ballot_sync(0xffffffffu, keep);
           if (lane == 0) S.warp_tot[warp] = __popc(bal);
           __syncthreads();
           int32_t pos = S.out_base + __popc(bal & ((1u << lane) - 1u));
           for (int w = 0; w < warp; ++w) pos += S.warp_tot[w];
           if (keep) {
-            ecell[pos] = cell; emask[pos] = (uint8_t)mask; enext[pos] = (uint8_t)nx;
-            ecofs[pos] = cofs;
+            ecell[pos] = cell;
+            emask[pos] = (uint8_t)mask;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) eP[(size_t)pos * 8 + k] = P[k];
+            for (int q = 0; q < 8; ++q) eP[(size_t)pos * 8 + q] = P[q];
           }
           __syncthreads();
           if (tid == 0) {
@@ -405,164 +416,210 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
           }
           __syncthreads();
         }
-        if (tid == 0) { S.count = S.out_base; S.nnew = S.out_base; }
-        __syncthreads();
+        cnt = S.out_base;
+        if (tid == 0) S.nnew = cnt;
       }
+      // ---- hour boundary (ii): crossings of this hour, 8 lanes per cell
+      for (int32_t e0 = 0; e0 < cnt; e0 += G) {
+        const int32_t e = e0 + g;
+        const bool act = e < cnt;
+        int32_t cell = 0;
+        uint32_t mask = 0;
+        int64_t P = 0;
+        if (act) { cell = ecell[e]; mask = emask[e]; P = eP[(size_t)e * 8 + k]; }
+        const int32_t cr = cell / cols, cc = cell - cr * cols;
+        bool open = act && ((mask >> k) & 1u);
+        if (open) open = !plane_bit(ign, wpr, cr + kDR[k], cc + kDC[k]);
+        mask = group_bits(open);
+        uint32_t cof = kNone;
+        if (act && (mask != 0 || J.delta > 0.0)) {
+          const float f = noise_factor(J.seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, J.sigma);
+          if (open) {
+            const int64_t inc = apply_noise(baseh[(size_t)cell * 8 + k], noise_fixed(f), dk);
+            const int64_t rem = dk - P;
+            if (inc > 0 && inc * sph >= rem) cof = (uint32_t)(ceil_div_small(rem, inc) - 1);
+            else P += inc * sph;
+          }
+          if (J.delta > 0.0 &&
+              __dmul_rn(J.hros[(size_t)h * n + cell], (double)f) < J.delta) {   // A5 (i)
+            if (k == 0) {
+              const uint32_t bit = 1u << (cc & 31);
+              if (!(atomicOr(&brn[(int64_t)cr * wpr + (cc >> 5)], bit) & bit))
+                atomicAdd(&S.burn[p0], 1);
+            }
+            if (cof != 0) cof = kNone;   // still sends in period s0, Burned after it
+          }
+        }
+        const uint32_t nx = group_min(cof);
+        if (act) {
+          ecofs[(size_t)e * 8 + k] = (uint8_t)cof;
+          eP[(size_t)e * 8 + k] = P;
+          if (k == 0) { emask[e] = (uint8_t)mask; enext[e] = (uint8_t)nx; }
+        }
+      }
+      __syncthreads();
 
       // ---- periods of this hour at which some axis reaches a centre
       int32_t s = s0;
       for (;;) {
-        if (tid == 0) {
-          S.W += (long long)S.live * (long long)(s - s_done);
-          s_done = s;
-        }
-        const int32_t o = s - s0;
-        const int32_t cnt = S.count;
-        // send + receive: axes whose crossing offset is o
+        const int p = it & 1;
+        if (tid == 0) { W += (long long)live * (long long)(s - s_done); s_done = s; }
+        const uint32_t o = (uint32_t)(s - s0);
         uint32_t lmin = kNone;
-        for (int32_t e = tid; e < cnt; e += T) {
-          uint32_t nx = enext[e];
-          if (nx == (uint32_t)o) {
-            uint64_t cofs = ecofs[e];
-            uint32_t mask = emask[e];
-            const int32_t cell = ecell[e];
-            const int32_t cr = cell / cols, cc = cell - cr * cols;
-            for (int k = 0; k < 8; ++k) {
-              if (((cofs >> (8 * k)) & 0xFFull) != (uint64_t)o) continue;
-              cofs |= 0xFFull << (8 * k);
-              mask &= ~(1u << k);
-              const int32_t nr = cr + kDR[k], nc = cc + kDC[k];
-              if (plane_bit(ign, wpr, nr, nc)) continue;             // not Available
-              const int64_t jc = (int64_t)nr * cols + nc;
-              if (!receive_ok(J, r, jc, h, n)) continue;              // message consumed
-              const uint32_t bit = 1u << (nc & 31);
-              const uint32_t old = atomicOr(&ign[(int64_t)nr * wpr + (nc >> 5)], bit);
-              if (old & bit) continue;                                 // ignited this period already
-              const int32_t idx = atomicAdd(&S.nnew, 1);
-              if (idx < cap) ecell[idx] = (int32_t)jc; else S.overflow = 1;
-              if (istep) istep[jc] = s;
-            }
-            nx = min_byte8(cofs);
-            ecofs[e] = cofs; emask[e] = (uint8_t)mask; enext[e] = (uint8_t)nx;
-          }
-          lmin = min(lmin, nx);
-        }
-        lmin = warp_min(lmin);
-        if (lane == 0) atomicMin(&S.minnext[par], lmin);
-        __syncthreads();
-        if (S.overflow) break;
-        // new cells: open axes, first crossings, burn-out checks
-        const int32_t c1 = S.nnew;
-        lmin = kNone;
-        for (int32_t e = cnt + tid; e < c1; e += T) {
-          const int32_t cell = ecell[e];
-          const int32_t cr = cell / cols, cc = cell - cr * cols;
-          uint32_t mask = 0;
-          for (int k = 0; k < 8; ++k) {
-            const int32_t nr = cr + kDR[k], nc = cc + kDC[k];
-            if (nr < 0 || nr >= rows || nc < 0 || nc >= cols) continue;
-            if (plane_bit(J.burnable, wpr, nr, nc) && !plane_bit(ign, wpr, nr, nc)) mask |= 1u << k;
-          }
-          float f = 1.0f;
-          bool have_f = false;
-          if (J.delta > 0.0) {
-            f = noise_factor(J.seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, J.sigma);
-            have_f = true;
-            const double hr = J.hros[(size_t)h * n + cell];
-            if (__dmul_rn(hr, (double)f) < J.delta) {   // A5 (i) at the end of period s
-              const uint32_t bit = 1u << (cc & 31);
-              const uint32_t old = atomicOr(&brn[(int64_t)cr * wpr + (cc >> 5)], bit);
-              if (!(old & bit)) atomicAdd(&S.burn, 1);
-              mask = 0;
-            }
-          }
-          uint64_t cofs = ~0ull;
-          int64_t P[8];
+        // (A) send and receive: cells with a crossing at offset o
+        for (int32_t b0 = 0; b0 < cnt; b0 += T) {
+          const int32_t e = b0 + tid;
+          const uint32_t nx = (e < cnt) ? (uint32_t)enext[e] : kNone;
+          const bool hit = nx == o;
+          if (!hit) lmin = min(lmin, nx);
+          uint32_t hits = __ballot_sync(0xffffffffu, hit);
+          while (hits) {
+            int src[4];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) P[k] = 0;
-          if (mask != 0 && s < L) {
-            if (!have_f) f = noise_factor(J.seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, J.sigma);
-            const uint64_t F = noise_fixed(f);
-            const int64_t *bc = baseh + (size_t)cell * 8;
-            const int32_t nmax = L - s;
-            for (int k = 0; k < 8; ++k) {
-              if (!((mask >> k) & 1u)) continue;
-              const int64_t dk = axis_len(J, k);
-              const int64_t inc = apply_noise(bc[k], F, dk);
-              if (inc > 0 && inc * nmax >= dk) {
-                const int32_t nst = ceil_div_small(dk, inc);
-                cofs = (cofs & ~(0xFFull << (8 * k))) | ((uint64_t)(o + nst) << (8 * k));
-              } else {
-                P[k] = inc * nmax;
+            for (int q = 0; q < 4; ++q) {
+              src[q] = hits ? __ffs(hits) - 1 : -1;
+              if (hits) hits &= hits - 1;
+            }
+            const int my = src[lane >> 3];
+            int32_t ent = __shfl_sync(0xffffffffu, e, my < 0 ? 0 : my);
+            if (my < 0) ent = -1;
+            uint32_t cof = kNone, mask = 0;
+            bool crossed = false;
+            if (ent >= 0) {
+              cof = ecofs[(size_t)ent * 8 + k];
+              crossed = cof == o;
+              if (crossed) {
+                cof = kNone;
+                const int32_t cell = ecell[ent];
+                const int32_t cr = cell / cols, cc = cell - cr * cols;
+                const int32_t nr = cr + kDR[k], nc = cc + kDC[k];
+                if (!plane_bit(ign, wpr, nr, nc)) {                      // Available
+                  const int64_t jc = (int64_t)nr * cols + nc;
+                  if (gate_free || receive_ok(J, r, jc, h, n)) {          // else consumed
+                    const uint32_t bit = 1u << (nc & 31);
+                    if (!(atomicOr(&ign[(int64_t)nr * wpr + (nc >> 5)], bit) & bit)) {
+                      const int32_t idx = atomicAdd(&S.nnew, 1);
+                      if (idx < cap) ecell[idx] = (int32_t)jc; else S.overflow = 1;
+                      if (istep) istep[jc] = s;
+                    }
+                  }
+                }
+              }
+            }
+            const uint32_t cbits = group_bits(crossed);
+            const uint32_t nx2 = group_min(cof);
+            if (ent >= 0) {
+              if (crossed) ecofs[(size_t)ent * 8 + k] = kNone;
+              if (k == 0) {
+                mask = emask[ent];
+                emask[ent] = (uint8_t)(mask & ~cbits);
+                enext[ent] = (uint8_t)nx2;
+                lmin = min(lmin, nx2);
               }
             }
           }
-          const uint32_t nx = min_byte8(cofs);
-          emask[e] = (uint8_t)mask; ecofs[e] = cofs; enext[e] = (uint8_t)nx;
-#pragma unroll
-          for (int k = 0; k < 8; ++k) eP[(size_t)e * 8 + k] = P[k];
-          lmin = min(lmin, nx);
-          // A5 (ii): this cell and its ignited neighbours lose Available neighbours
-          for (int k = -1; k < 8; ++k) {
-            int32_t qr = cr, qc = cc;
-            if (k >= 0) {
-              qr = cr + kDR[k]; qc = cc + kDC[k];
-              if (qr < 0 || qr >= rows || qc < 0 || qc >= cols) continue;
-              if (!plane_bit(ign, wpr, qr, qc)) continue;
+        }
+        lmin = warp_min(lmin);
+        if (lane == 0) atomicMin(&S.minnext[p], lmin);
+        __syncthreads();
+        if (tid == 0) { S.burn[p ^ 1] = 0; S.minnext[p ^ 1] = kNone; }
+        if (S.overflow) { aborted = true; break; }
+        // (C) cells ignited in period s: open axes, first crossings, burn-out tests
+        const int32_t c1 = S.nnew;
+        lmin = kNone;
+        for (int32_t e0 = cnt; e0 < c1; e0 += G) {
+          const int32_t e = e0 + g;
+          const bool act = e < c1;
+          const int32_t cell = act ? ecell[e] : 0;
+          const int32_t cr = cell / cols, cc = cell - cr * cols;
+          const int32_t nr = cr + kDR[k], nc = cc + kDC[k];
+          const bool ingrid = act && nr >= 0 && nr < rows && nc >= 0 && nc < cols;
+          const bool ignq = ingrid && plane_bit(ign, wpr, nr, nc);
+          const bool open = ingrid && !ignq && plane_bit(J.burnable, wpr, nr, nc);
+          uint32_t mask = group_bits(open);
+          float f = 1.0f;
+          bool have_f = false;
+          if (act && J.delta > 0.0) {
+            f = noise_factor(J.seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, J.sigma);
+            have_f = true;
+            if (__dmul_rn(J.hros[(size_t)h * n + cell], (double)f) < J.delta) {   // A5 (i)
+              if (k == 0) {
+                const uint32_t bit = 1u << (cc & 31);
+                if (!(atomicOr(&brn[(int64_t)cr * wpr + (cc >> 5)], bit) & bit))
+                  atomicAdd(&S.burn[p], 1);
+              }
+              mask = 0;
             }
-            if (has_available_nbr(J, ign, qr, qc)) continue;
-            const uint32_t bit = 1u << (qc & 31);
-            const uint32_t old = atomicOr(&brn[(int64_t)qr * wpr + (qc >> 5)], bit);
-            if (!(old & bit)) atomicAdd(&S.burn, 1);
+          }
+          uint32_t cof = kNone;
+          int64_t P = 0;
+          if (act && mask != 0 && s < L) {
+            if (!have_f) f = noise_factor(J.seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, J.sigma);
+            if ((mask >> k) & 1u) {
+              const int32_t nmax = L - s;
+              const int64_t inc = apply_noise(baseh[(size_t)cell * 8 + k], noise_fixed(f), dk);
+              if (inc > 0 && inc * nmax >= dk) cof = o + (uint32_t)ceil_div_small(dk, inc);
+              else P = inc * nmax;
+            }
+          }
+          const uint32_t nx = group_min(cof);
+          if (act) {
+            ecofs[(size_t)e * 8 + k] = (uint8_t)cof;
+            eP[(size_t)e * 8 + k] = P;
+            if (k == 0) { emask[e] = (uint8_t)mask; enext[e] = (uint8_t)nx; lmin = min(lmin, nx); }
+            // A5 (ii): the neighbour on this axis (if ignited), and lane 0 also this cell
+            if (ignq && !has_available_nbr(J, ign, nr, nc)) {
+              const uint32_t bit = 1u << (nc & 31);
+              if (!(atomicOr(&brn[(int64_t)nr * wpr + (nc >> 5)], bit) & bit)) atomicAdd(&S.burn[p], 1);
+            }
+            if (k == 0 && !has_available_nbr(J, ign, cr, cc)) {
+              const uint32_t bit = 1u << (cc & 31);
+              if (!(atomicOr(&brn[(int64_t)cr * wpr + (cc >> 5)], bit) & bit)) atomicAdd(&S.burn[p], 1);
+            }
           }
         }
         lmin = warp_min(lmin);
-        if (lane == 0) atomicMin(&S.minnext[par], lmin);
+        if (lane == 0) atomicMin(&S.minnext[p], lmin);
         __syncthreads();
-        if (tid == 0) {
-          const int32_t added = S.nnew - S.count;
-          S.nign += added;
-          S.live += added - S.burn - S.dying;
-          S.burn = 0; S.dying = 0;
-          S.count = S.nnew;
-          const uint32_t mn = S.minnext[par];
-          S.minnext[par] = kNone;
-          S.step = (mn == kNone) ? L + 1 : s0 + (int32_t)mn;
-          if (S.step <= s) S.overflow = 2;   // cannot happen; never loop in place
+        const int32_t added = c1 - cnt;
+        nign += added;
+        live += added - S.burn[p];
+        cnt = c1;
+        const uint32_t mn = S.minnext[p];
+        ++it;
+        const int32_t next = (mn == kNone) ? L + 1 : s0 + (int32_t)mn;
+        if (next <= s) {   // cannot happen; never visit a period twice
+          if (tid == 0) S.overflow = 2;
+          aborted = true;
+          break;
         }
-        __syncthreads();
-        par ^= 1;
-        if (S.overflow) break;
-        if (S.live == 0) break;
-        s = S.step;
+        if (live == 0) break;
+        s = next;
         if (s > L) break;
       }
-      if (tid == 0 && !S.overflow) {
-        S.W += (long long)S.live * (long long)(L - s_done);
-        s_done = L;
-      }
-      __syncthreads();
+      if (!aborted && tid == 0) { W += (long long)live * (long long)(L - s_done); s_done = L; }
     }
+    __syncthreads();
     if constexpr (SMEM) {   // scar plane out
       uint32_t *dst = J.ign_plane + (size_t)r * pw;
       for (size_t i = tid; i < pw; i += T) dst[i] = ign[i];
     }
     if (tid == 0) {
-      J.work[r] = S.W;
-      J.n_ignited[r] = S.nign;
+      J.work[r] = W;
+      J.n_ignited[r] = nign;
       J.status[r] = S.overflow;
     }
     __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(kFrontierThreads, 3) k_frontier_smem(FrontierArgs A) {
-  frontier_body<true>(A);
-}
-
-__global__ void __launch_bounds__(kFrontierThreads, 3) k_frontier_gmem(FrontierArgs A) {
-  frontier_body<false>(A);
-}
+// Variants: CTA size 64 / 128 / 256, planes in global (g) or shared (s) memory.
+__global__ void __launch_bounds__(64, 16) k_frontier_g64(FrontierArgs A) { frontier_body<64, false>(A); }
+__global__ void __launch_bounds__(128, 8) k_frontier_g128(FrontierArgs A) { frontier_body<128, false>(A); }
+__global__ void __launch_bounds__(256, 4) k_frontier_g256(FrontierArgs A) { frontier_body<256, false>(A); }
+__global__ void __launch_bounds__(64, 16) k_frontier_s64(FrontierArgs A) { frontier_body<64, true>(A); }
+__global__ void __launch_bounds__(128, 8) k_frontier_s128(FrontierArgs A) { frontier_body<128, true>(A); }
+__global__ void __launch_bounds__(256, 4) k_frontier_s256(FrontierArgs A) { frontier_body<256, true>(A); }
 
 // ------------------------------------------------------------------ K4
 // counts[c] = sum over replicas of the scar bit of c.  Each thread owns one

@@ -43,6 +43,7 @@ struct SimJob {
   // rate-of-spread table of this run
   const int64_t *base;            // [hours][N][8] fixed-point per-period increments
   const double *hros;             // [hours][N]
+  const int32_t *hros_pos;        // 1 if HROS > 1e-200 on every burnable cell and hour
   // run parameters
   uint64_t seed;
   float sigma;
@@ -71,7 +72,7 @@ struct FrontierArgs {
   int32_t *ent_cell;              // [slots][cap]
   uint8_t *ent_mask;              // [slots][cap] open axes
   uint8_t *ent_next;              // [slots][cap] next event offset in the hour (0xFF none)
-  uint64_t *ent_cofs;             // [slots][cap] 8 per-axis crossing offsets (0xFF none)
+  uint8_t *ent_cofs;              // [slots][cap][8] per-axis crossing offsets (0xFF none)
   int64_t *ent_P;                 // [slots][cap][8] progress at the start of the next hour
   int64_t pw_max;                 // words per bit plane of the largest landscape
   uint32_t *brn_scratch;          // [slots][pw_max] Burned planes (global-plane variant)
@@ -91,9 +92,9 @@ struct RosTableArgs {
   int64_t *base;           // [hour][N][8] (absolute hour), or nullptr
   double *hros;            // [hour][N], or nullptr
   double *ros8;            // export: [N][8] of hour0 only, or nullptr
+  int32_t *hros_pos;       // cleared if some burnable cell has HROS <= 1e-200
 };
 
-constexpr int kFrontierThreads = 256;
 constexpr uint8_t kNone = 0xFF;
 
 }  // namespace c2f

@@ -35,8 +35,12 @@ __global__ void k_cell_prep(const float *, const float *, int64_t, CellPrep *);
 __global__ void k_hour_prep(const double *, int32_t, double, HourPrep *);
 __global__ void k_ros_table(RosTableArgs);
 __global__ void k_ignite(const SimJob *, int32_t);
-__global__ void k_frontier_smem(FrontierArgs);
-__global__ void k_frontier_gmem(FrontierArgs);
+__global__ void k_frontier_g64(FrontierArgs);
+__global__ void k_frontier_g128(FrontierArgs);
+__global__ void k_frontier_g256(FrontierArgs);
+__global__ void k_frontier_s64(FrontierArgs);
+__global__ void k_frontier_s128(FrontierArgs);
+__global__ void k_frontier_s256(FrontierArgs);
 __global__ void k_burn_prob(const uint32_t *, int32_t, int32_t, int32_t, int32_t, int32_t,
                             uint32_t *, int32_t);
 __global__ void k_scar_bytes(const uint32_t *, int32_t, int32_t, int32_t, int32_t, uint8_t *);
@@ -86,7 +90,7 @@ struct Landscape {
   DevBuf weather_dev, hour_prep;
   bool table_valid = false;
   TableKey key;
-  DevBuf base, hros;
+  DevBuf base, hros, hros_pos;
 };
 
 struct Sim {
@@ -119,7 +123,8 @@ struct c2f_ctx {
   DevBuf ent_cell, ent_mask, ent_next, ent_cofs, ent_P, counter, brn_scratch;
   int64_t scratch_slots = 0, scratch_cap = 0, brn_words = 0;
   int smem_optin = 0;
-  int64_t smem_plane_limit = 112 * 1024;   // planes staged in shared memory up to this size
+  int64_t smem_plane_limit = 0;            // planes staged in shared memory up to this size
+  int frontier_threads = 64;
   int64_t cap_override = 0;
   // kernel timing
   bool profiling = false;
@@ -281,6 +286,12 @@ int build_table(c2f_ctx *ctx, Landscape &L, const c2f_sim_params *p) {
   a.base = L.base.as<int64_t>();
   a.hros = L.hros.as<double>();
   a.ros8 = nullptr;
+  if (!L.hros_pos.p && (rc = dalloc(ctx, L.hros_pos, 4))) return rc;
+  {
+    const int32_t one = 1;
+    CK(cudaMemcpyAsync(L.hros_pos.p, &one, 4, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  a.hros_pos = L.hros_pos.as<int32_t>();
   dim3 grid(grid1(L.n, 128), (unsigned)H);
   k_ros_table<<<grid, 128, 0, ctx->stream>>>(a);
   CKL("k_ros_table");
@@ -320,7 +331,7 @@ int ensure_scratch(c2f_ctx *ctx, int64_t slots, int64_t cap) {
   if ((rc = dalloc(ctx, ctx->ent_cell, sc * 4))) return rc;
   if ((rc = dalloc(ctx, ctx->ent_mask, sc))) return rc;
   if ((rc = dalloc(ctx, ctx->ent_next, sc))) return rc;
-  if ((rc = dalloc(ctx, ctx->ent_cofs, sc * 8))) return rc;
+  if ((rc = dalloc(ctx, ctx->ent_cofs, sc * 8))) return rc;  // 8 offsets per entry
   if ((rc = dalloc(ctx, ctx->ent_P, sc * 64))) return rc;
   if (!ctx->counter.p && (rc = dalloc(ctx, ctx->counter, 64))) return rc;
   ctx->scratch_slots = slots;
@@ -355,6 +366,7 @@ SimJob job_of(const Landscape &L, const Sim &s) {
   j.burnable_list = L.burnable_list.as<int32_t>();
   j.base = L.base.as<int64_t>();
   j.hros = L.hros.as<double>();
+  j.hros_pos = L.hros_pos.as<int32_t>();
   j.seed = s.p.seed;
   j.sigma = (float)s.p.ros_sigma;
   j.ignition_mode = s.p.ignition_mode;
@@ -409,11 +421,14 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
   const size_t plane_bytes = (size_t)pw_max * 4 * 2;
   const bool use_smem = (int64_t)plane_bytes <= ctx->smem_plane_limit &&
                         (int64_t)plane_bytes <= (int64_t)ctx->smem_optin - 4096;
-  auto kern = use_smem ? k_frontier_smem : k_frontier_gmem;
+  const int threads = ctx->frontier_threads;
+  void (*kern)(FrontierArgs) =
+      use_smem ? (threads == 64 ? k_frontier_s64 : threads == 128 ? k_frontier_s128 : k_frontier_s256)
+               : (threads == 64 ? k_frontier_g64 : threads == 128 ? k_frontier_g128 : k_frontier_g256);
   const size_t dyn_smem = use_smem ? plane_bytes : 0;
   if (use_smem) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem));
   int bps = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kFrontierThreads, dyn_smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, threads, dyn_smem));
   bps = std::max(bps, 1);
   std::vector<int64_t> items;  // empty: all
   for (int attempt = 0;; ++attempt) {
@@ -443,14 +458,14 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
     A.ent_cell = ctx->ent_cell.as<int32_t>();
     A.ent_mask = ctx->ent_mask.as<uint8_t>();
     A.ent_next = ctx->ent_next.as<uint8_t>();
-    A.ent_cofs = ctx->ent_cofs.as<uint64_t>();
+    A.ent_cofs = ctx->ent_cofs.as<uint8_t>();
     A.ent_P = ctx->ent_P.as<int64_t>();
     A.pw_max = pw_max;
     A.brn_scratch = use_smem ? nullptr : ctx->brn_scratch.as<uint32_t>();
     CK(cudaMemsetAsync(ctx->counter.p, 0, 8, ctx->stream));
     {
       ProfScope prof(ctx, 2);
-      kern<<<(unsigned)slots, kFrontierThreads, dyn_smem, ctx->stream>>>(A);
+      kern<<<(unsigned)slots, threads, dyn_smem, ctx->stream>>>(A);
       CKL("k_frontier");
     }
     // gather failed replicas
@@ -850,6 +865,16 @@ C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap) {
   if (!ctx) return C2F_EINVAL;
   if (cap < 0 || cap > (1LL << 31)) return fail(ctx, C2F_EINVAL, "capacity out of range");
   ctx->cap_override = cap;
+  return C2F_OK;
+}
+
+C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem_plane_bytes) {
+  if (!ctx) return C2F_EINVAL;
+  if (threads != 64 && threads != 128 && threads != 256)
+    return fail(ctx, C2F_EINVAL, "threads must be 64, 128 or 256");
+  if (smem_plane_bytes < 0) return fail(ctx, C2F_EINVAL, "smem_plane_bytes must be >= 0");
+  ctx->frontier_threads = threads;
+  ctx->smem_plane_limit = smem_plane_bytes;
   return C2F_OK;
 }
 
