@@ -218,15 +218,33 @@ __device__ inline bool receive_ok(const SimJob &J, int32_t r, int64_t j, int32_t
   return __dmul_rn(hr, (double)f) > J.thr;
 }
 
-__device__ inline bool has_available_nbr(const SimJob &J, const uint32_t *ign, int32_t r,
-                                         int32_t c) {
+// true if some neighbour of (r, c) is still Available (bit set in the
+// Available plane: burnable, not harvested, not ignited)
+__device__ inline bool has_available_nbr(const uint32_t *avail, int32_t wpr, int32_t rows,
+                                         int32_t cols, int32_t r, int32_t c) {
+  uint32_t words[3][2];
+  const int32_t c0 = c > 0 ? c - 1 : 0, c1 = c + 1 < cols ? c + 1 : cols - 1;
+  const int32_t w0 = c0 >> 5, w1 = c1 >> 5;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int32_t nr = r + kDR[k], nc = c + kDC[k];
-    if (nr < 0 || nr >= J.rows || nc < 0 || nc >= J.cols) continue;
-    if (plane_bit(J.burnable, J.wpr, nr, nc) && !plane_bit(ign, J.wpr, nr, nc)) return true;
+  for (int d = 0; d < 3; ++d) {
+    const int32_t rr = r - 1 + d;
+    const bool ok = rr >= 0 && rr < rows;
+    words[d][0] = ok ? avail[(int64_t)rr * wpr + w0] : 0u;
+    words[d][1] = ok ? avail[(int64_t)rr * wpr + w1] : 0u;
   }
-  return false;
+  bool any = false;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int dc = -1; dc <= 1; ++dc) {
+      if (d == 1 && dc == 0) continue;
+      const int32_t cc = c + dc;
+      if (cc < 0 || cc >= cols) continue;
+      const uint32_t w = ((cc >> 5) == w0) ? words[d][0] : words[d][1];
+      any |= ((w >> (cc & 31)) & 1u) != 0;
+    }
+  }
+  return any;
 }
 
 __device__ __forceinline__ int64_t find_job(const int64_t *begin, int32_t n, int64_t item) {
@@ -273,10 +291,11 @@ __device__ __forceinline__ uint32_t group_bits(bool b) {
 // per-axis work of a cell (crossing tests, increments, crossing periods,
 // burn-out tests of the neighbour on that axis) runs side by side.  Each
 // visited period costs two CTA barriers: sends + receives, then the set-up of
-// the cells ignited in that period.  The replica's Burning/Burned planes live
-// in shared memory when they fit (SMEM; the scar plane is copied out at the
-// end), else in global memory (the scar plane in place, the Burned plane in
-// per-CTA scratch).
+// the cells ignited in that period.  The replica's state is one Available
+// bit plane (burnable and not yet ignited; an ignition is one atomicAnd that
+// also tells the single winner) held in shared memory when it fits (SMEM) and
+// in per-CTA global scratch otherwise, plus a Burned plane in global scratch;
+// the scar plane is written out at the end.
 template <int T, bool SMEM>
 __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
   constexpr int G = T / 8;   // cell groups per CTA
@@ -312,17 +331,12 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
     const int64_t n = (int64_t)rows * cols;
     const size_t pw = (size_t)rows * wpr;
     const bool gate_free = (J.thr < 0.0) || (J.thr == 0.0 && S.hros_pos);
-    uint32_t *ign;
-    uint32_t *brn;
-    if constexpr (SMEM) {
-      ign = s_planes;
-      brn = s_planes + A.pw_max;
-      for (size_t i = tid; i < pw; i += T) { ign[i] = 0u; brn[i] = 0u; }
-    } else {
-      ign = J.ign_plane + (size_t)r * pw;
-      brn = A.brn_scratch + slot * (size_t)A.pw_max;
-      for (size_t i = tid; i < pw; i += T) brn[i] = 0u;
-    }
+    // Available plane (burnable, not harvested, not yet ignited) and Burned plane
+    uint32_t *av;
+    if constexpr (SMEM) av = s_planes;
+    else av = A.avail_scratch + slot * (size_t)A.pw_max;
+    uint32_t *brn = A.brn_scratch + slot * (size_t)A.pw_max;
+    for (size_t i = tid; i < pw; i += T) { av[i] = __ldg(&J.burnable[i]); brn[i] = 0u; }
     int32_t *istep = J.ign_step ? J.ign_step + (size_t)r * n : nullptr;
     const int32_t sph = J.sph, H = J.hours;
     const int64_t dk = (k & 1) ? J.d_diag : J.d_orth;   // this lane's axis length
@@ -341,15 +355,14 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
       const int32_t ic = J.ign_cell[r];
       const int32_t ir = ic / cols, icc = ic - ir * cols;
       if (tid == 0) {
-        atomicOr(&ign[(int64_t)ir * wpr + (icc >> 5)], 1u << (icc & 31));
+        atomicAnd(&av[(int64_t)ir * wpr + (icc >> 5)], ~(1u << (icc & 31)));
         if (istep) istep[ic] = 0;
       }
       __syncthreads();
       bool open = false;
       if (tid < 8) {
         const int32_t nr = ir + kDR[k], nc = icc + kDC[k];
-        open = nr >= 0 && nr < rows && nc >= 0 && nc < cols &&
-               plane_bit(J.burnable, wpr, nr, nc) && !plane_bit(ign, wpr, nr, nc);
+        open = nr >= 0 && nr < rows && nc >= 0 && nc < cols && plane_bit(av, wpr, nr, nc);
       }
       const uint32_t mask = group_bits(open);   // lanes 0..7 of warp 0 hold the cell's mask
       if (tid < 8) {
@@ -429,7 +442,7 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
         if (act) { cell = ecell[e]; mask = emask[e]; P = eP[(size_t)e * 8 + k]; }
         const int32_t cr = cell / cols, cc = cell - cr * cols;
         bool open = act && ((mask >> k) & 1u);
-        if (open) open = !plane_bit(ign, wpr, cr + kDR[k], cc + kDC[k]);
+        if (open) open = plane_bit(av, wpr, cr + kDR[k], cc + kDC[k]);
         mask = group_bits(open);
         uint32_t cof = kNone;
         if (act && (mask != 0 || J.delta > 0.0)) {
@@ -493,11 +506,11 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
                 const int32_t cell = ecell[ent];
                 const int32_t cr = cell / cols, cc = cell - cr * cols;
                 const int32_t nr = cr + kDR[k], nc = cc + kDC[k];
-                if (!plane_bit(ign, wpr, nr, nc)) {                      // Available
+                if (plane_bit(av, wpr, nr, nc)) {                        // Available
                   const int64_t jc = (int64_t)nr * cols + nc;
                   if (gate_free || receive_ok(J, r, jc, h, n)) {          // else consumed
                     const uint32_t bit = 1u << (nc & 31);
-                    if (!(atomicOr(&ign[(int64_t)nr * wpr + (nc >> 5)], bit) & bit)) {
+                    if (atomicAnd(&av[(int64_t)nr * wpr + (nc >> 5)], ~bit) & bit) {
                       const int32_t idx = atomicAdd(&S.nnew, 1);
                       if (idx < cap) ecell[idx] = (int32_t)jc; else S.overflow = 1;
                       if (istep) istep[jc] = s;
@@ -534,8 +547,9 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
           const int32_t cr = cell / cols, cc = cell - cr * cols;
           const int32_t nr = cr + kDR[k], nc = cc + kDC[k];
           const bool ingrid = act && nr >= 0 && nr < rows && nc >= 0 && nc < cols;
-          const bool ignq = ingrid && plane_bit(ign, wpr, nr, nc);
-          const bool open = ingrid && !ignq && plane_bit(J.burnable, wpr, nr, nc);
+          const int64_t bk = act ? baseh[(size_t)cell * 8 + k] : 0;   // issue the table load early
+          const bool open = ingrid && plane_bit(av, wpr, nr, nc);
+          const bool ignq = ingrid && !open && (__ldg(&J.burnable[(int64_t)nr * wpr + (nc >> 5)]) >> (nc & 31)) & 1u;
           uint32_t mask = group_bits(open);
           float f = 1.0f;
           bool have_f = false;
@@ -557,7 +571,7 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
             if (!have_f) f = noise_factor(J.seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, J.sigma);
             if ((mask >> k) & 1u) {
               const int32_t nmax = L - s;
-              const int64_t inc = apply_noise(baseh[(size_t)cell * 8 + k], noise_fixed(f), dk);
+              const int64_t inc = apply_noise(bk, noise_fixed(f), dk);
               if (inc > 0 && inc * nmax >= dk) cof = o + (uint32_t)ceil_div_small(dk, inc);
               else P = inc * nmax;
             }
@@ -568,11 +582,11 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
             eP[(size_t)e * 8 + k] = P;
             if (k == 0) { emask[e] = (uint8_t)mask; enext[e] = (uint8_t)nx; lmin = min(lmin, nx); }
             // A5 (ii): the neighbour on this axis (if ignited), and lane 0 also this cell
-            if (ignq && !has_available_nbr(J, ign, nr, nc)) {
+            if (ignq && !has_available_nbr(av, wpr, rows, cols, nr, nc)) {
               const uint32_t bit = 1u << (nc & 31);
               if (!(atomicOr(&brn[(int64_t)nr * wpr + (nc >> 5)], bit) & bit)) atomicAdd(&S.burn[p], 1);
             }
-            if (k == 0 && !has_available_nbr(J, ign, cr, cc)) {
+            if (k == 0 && !has_available_nbr(av, wpr, rows, cols, cr, cc)) {
               const uint32_t bit = 1u << (cc & 31);
               if (!(atomicOr(&brn[(int64_t)cr * wpr + (cc >> 5)], bit) & bit)) atomicAdd(&S.burn[p], 1);
             }
@@ -600,9 +614,9 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
       if (!aborted && tid == 0) { W += (long long)live * (long long)(L - s_done); s_done = L; }
     }
     __syncthreads();
-    if constexpr (SMEM) {   // scar plane out
+    {   // scar plane: burnable cells that are no longer Available
       uint32_t *dst = J.ign_plane + (size_t)r * pw;
-      for (size_t i = tid; i < pw; i += T) dst[i] = ign[i];
+      for (size_t i = tid; i < pw; i += T) dst[i] = __ldg(&J.burnable[i]) & ~av[i];
     }
     if (tid == 0) {
       J.work[r] = W;

@@ -75,7 +75,8 @@ struct FrontierArgs {
   uint8_t *ent_cofs;              // [slots][cap][8] per-axis crossing offsets (0xFF none)
   int64_t *ent_P;                 // [slots][cap][8] progress at the start of the next hour
   int64_t pw_max;                 // words per bit plane of the largest landscape
-  uint32_t *brn_scratch;          // [slots][pw_max] Burned planes (global-plane variant)
+  uint32_t *brn_scratch;          // [slots][pw_max] Burned planes
+  uint32_t *avail_scratch;        // [slots][pw_max] Available planes (global-plane variant)
 };
 
 // K1 launch arguments: grid.y covers hours hour0 .. hour0 + gridDim.y - 1

@@ -120,11 +120,11 @@ struct c2f_ctx {
   std::unordered_map<int32_t, std::unique_ptr<Landscape>> lands;
   std::unordered_map<int32_t, std::unique_ptr<Sim>> sims;
   // frontier scratch
-  DevBuf ent_cell, ent_mask, ent_next, ent_cofs, ent_P, counter, brn_scratch;
-  int64_t scratch_slots = 0, scratch_cap = 0, brn_words = 0;
+  DevBuf ent_cell, ent_mask, ent_next, ent_cofs, ent_P, counter, brn_scratch, avail_scratch;
+  int64_t scratch_slots = 0, scratch_cap = 0, brn_words = 0, avail_words = 0;
   int smem_optin = 0;
-  int64_t smem_plane_limit = 0;            // planes staged in shared memory up to this size
-  int frontier_threads = 64;
+  int64_t smem_plane_limit = 48 * 1024;    // Available plane staged in shared memory up to this size
+  int frontier_threads = 128;
   int64_t cap_override = 0;
   // kernel timing
   bool profiling = false;
@@ -352,7 +352,6 @@ int alloc_sim(c2f_ctx *ctx, const Landscape &L, Sim &s) {
   if ((rc = dalloc(ctx, s.n_ignited, 4 * R))) return rc;
   if ((rc = dalloc(ctx, s.ign_cell, 4 * R))) return rc;
   if ((rc = dalloc(ctx, s.status, 4 * R))) return rc;
-  CK(cudaMemsetAsync(s.ign_plane.p, 0, pw * 4 * R, ctx->stream));
   CK(cudaMemsetAsync(s.status.p, 0, 4 * R, ctx->stream));
   s.rows = L.rows; s.cols = L.cols; s.wpr = L.wpr; s.n = L.n;
   return C2F_OK;
@@ -418,7 +417,7 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
   }
   int64_t pw_max = 0;
   for (int32_t i = 0; i < nj; ++i) pw_max = std::max<int64_t>(pw_max, (int64_t)lands[i]->rows * lands[i]->wpr);
-  const size_t plane_bytes = (size_t)pw_max * 4 * 2;
+  const size_t plane_bytes = (size_t)pw_max * 4;
   const bool use_smem = (int64_t)plane_bytes <= ctx->smem_plane_limit &&
                         (int64_t)plane_bytes <= (int64_t)ctx->smem_optin - 4096;
   const int threads = ctx->frontier_threads;
@@ -437,9 +436,13 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
     int64_t slots = std::min<int64_t>(todo, max_slots);
     if (attempt > 0) slots = std::min<int64_t>(slots, std::max<int64_t>(1, ctx->sm_count));
     if ((rc = ensure_scratch(ctx, slots, cap))) return rc;
-    if (!use_smem && (slots * pw_max > ctx->brn_words)) {
+    if (slots * pw_max > ctx->brn_words) {
       if ((rc = dalloc(ctx, ctx->brn_scratch, (size_t)slots * pw_max * 4))) return rc;
       ctx->brn_words = slots * pw_max;
+    }
+    if (!use_smem && slots * pw_max > ctx->avail_words) {
+      if ((rc = dalloc(ctx, ctx->avail_scratch, (size_t)slots * pw_max * 4))) return rc;
+      ctx->avail_words = slots * pw_max;
     }
     FrontierArgs A{};
     A.jobs = djobs.as<SimJob>();
@@ -461,7 +464,8 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
     A.ent_cofs = ctx->ent_cofs.as<uint8_t>();
     A.ent_P = ctx->ent_P.as<int64_t>();
     A.pw_max = pw_max;
-    A.brn_scratch = use_smem ? nullptr : ctx->brn_scratch.as<uint32_t>();
+    A.brn_scratch = ctx->brn_scratch.as<uint32_t>();
+    A.avail_scratch = use_smem ? nullptr : ctx->avail_scratch.as<uint32_t>();
     CK(cudaMemsetAsync(ctx->counter.p, 0, 8, ctx->stream));
     {
       ProfScope prof(ctx, 2);
@@ -490,7 +494,6 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
       const int64_t r = it - begin[i];
       Sim &s = *sims[i];
       const size_t pw = (size_t)s.rows * s.wpr;
-      CK(cudaMemsetAsync(s.ign_plane.as<uint32_t>() + r * pw, 0, pw * 4, ctx->stream));
       CK(cudaMemsetAsync(s.status.as<int32_t>() + r, 0, 4, ctx->stream));
       if (s.ign_step.p)
         CK(cudaMemsetAsync(s.ign_step.as<int32_t>() + r * s.n, 0xFF, (size_t)s.n * 4, ctx->stream));
@@ -554,6 +557,7 @@ C2F_API void c2f_destroy(c2f_ctx *ctx) {
   ctx->lands.clear();
   ctx->ent_cell.reset(); ctx->ent_mask.reset(); ctx->ent_next.reset();
   ctx->ent_cofs.reset(); ctx->ent_P.reset(); ctx->counter.reset(); ctx->brn_scratch.reset();
+  ctx->avail_scratch.reset();
   cudaStreamSynchronize(ctx->stream);
   for (int f = 0; f < C2F_KT_FAMILIES; ++f)
     for (auto &pr : ctx->prof_events[f]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
