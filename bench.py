@@ -156,6 +156,8 @@ def run_ours(args, rank, world, local_rank):
     params.seed = params.seed + 7919 * rank          # each rank: its own replicas
 
     ctx = c2f.Context(local_rank)
+    if args.frontier_threads:
+        ctx.set_frontier_config(args.frontier_threads, args.smem_plane_bytes)
     stream = torch.cuda.current_stream(dev)
     ctx.set_stream(stream.cuda_stream)
     lid = ctx.load_landscape(L.fuel, L.slope, L.aspect, cell_size=L.cell_size)
@@ -339,6 +341,9 @@ def main():
     ap.add_argument("--replicas", type=int, default=1000,
                     help="replicas per GPU (the workload has 1000; fewer only for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--frontier-threads", type=int, default=0,
+                    help="frontier CTA size (64/128/256); 0 = library default")
+    ap.add_argument("--smem-plane-bytes", type=int, default=49152)
     ap.add_argument("--cpu-sample", type=int, default=1000)
     ap.add_argument("--ref-sample", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
