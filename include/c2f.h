@@ -110,7 +110,7 @@ C2F_API const char *c2f_last_error(const c2f_ctx *ctx);
  * (rows*cols), `slope_pct` (percent rise over run, NULL = flat),
  * `aspect_deg` (downslope-facing azimuth clockwise from north, NULL = 0)
  * and `unburnable` (NULL or 1 = Harvested / not available, Sec. 3.1).
- * rows, cols >= 1, rows*cols < 2^31; cell_size_m > 0; slopes finite >= 0.
+ * 1 <= rows, cols <= 65535; cell_size_m > 0; slopes finite >= 0.
  * Copies the arrays to the device.  Returns the id in *landscape_id. */
 C2F_API int c2f_load_landscape(c2f_ctx *ctx, int32_t rows, int32_t cols, double cell_size_m,
                                const uint8_t *fuel, const float *slope_pct,
@@ -174,10 +174,10 @@ C2F_API int c2f_get_counters(c2f_ctx *ctx, int32_t sim_id, int64_t *work, int32_
  * results never depend on this value (a tuning and test knob). */
 C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap);
 
-/* Frontier-kernel launch shape: CTA size `threads` (64, 128 or 256) and the
- * largest pair of per-replica bit planes (bytes) staged in shared memory
- * instead of global memory (0 = always global).  Results do not depend on
- * either; they are tuning knobs (see c2f_autotune in the Python package). */
+/* Frontier-kernel launch shape: CTA size `threads` (32, 64 or 128; each warp
+ * simulates one replica) and the largest per-replica Available bit plane
+ * (bytes) staged in shared memory instead of global memory (0 = always
+ * global).  Results do not depend on either; they are tuning knobs. */
 C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem_plane_bytes);
 
 /* Kernel timing: with profiling on, the context brackets each launch of its

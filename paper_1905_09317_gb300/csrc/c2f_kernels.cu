@@ -182,7 +182,7 @@ __global__ void k_ignite(const SimJob *jobs, int32_t job) {
 
 // ------------------------------------------------------------------ K3
 __device__ __forceinline__ bool plane_bit(const uint32_t *p, int32_t wpr, int32_t r, int32_t c) {
-  return (p[(int64_t)r * wpr + (c >> 5)] >> (c & 31)) & 1u;
+  return (p[r * wpr + (c >> 5)] >> (c & 31)) & 1u;
 }
 
 __device__ __forceinline__ uint32_t min_byte8(uint64_t v) {
@@ -229,8 +229,8 @@ __device__ inline bool has_available_nbr(const uint32_t *avail, int32_t wpr, int
   for (int d = 0; d < 3; ++d) {
     const int32_t rr = r - 1 + d;
     const bool ok = rr >= 0 && rr < rows;
-    words[d][0] = ok ? avail[(int64_t)rr * wpr + w0] : 0u;
-    words[d][1] = ok ? avail[(int64_t)rr * wpr + w1] : 0u;
+    words[d][0] = ok ? avail[rr * wpr + w0] : 0u;
+    words[d][1] = ok ? avail[rr * wpr + w1] : 0u;
   }
   bool any = false;
 #pragma unroll
@@ -262,17 +262,6 @@ __device__ __forceinline__ uint32_t warp_min(uint32_t v) {
   return v;
 }
 
-template <int T>
-struct FrontierShared {
-  SimJob job;
-  int64_t item;
-  int32_t nnew, overflow, hros_pos;
-  int32_t burn[2];
-  uint32_t minnext[2];
-  int32_t warp_tot[T / 32];
-  int32_t out_base;
-};
-
 // min over the 8 lanes of this lane's group
 __device__ __forceinline__ uint32_t group_min(uint32_t v) {
 #pragma unroll
@@ -280,185 +269,170 @@ __device__ __forceinline__ uint32_t group_min(uint32_t v) {
   return v;
 }
 
-// OR of a per-lane bit over the 8 lanes of this lane's group, as an 8-bit mask (bit k = lane k)
+// a per-lane flag over the 8 lanes of this lane's group, as an 8-bit mask (bit k = lane k)
 __device__ __forceinline__ uint32_t group_bits(bool b) {
   const uint32_t bal = __ballot_sync(0xffffffffu, b);
   return (bal >> (threadIdx.x & 24)) & 0xFFu;
 }
 
-// One CTA per replica, taken from a work list of (simulation, replica) items.
-// Eight lanes cooperate on one burning cell, lane k owning axis k, so the
-// per-axis work of a cell (crossing tests, increments, crossing periods,
-// burn-out tests of the neighbour on that axis) runs side by side.  Each
-// visited period costs two CTA barriers: sends + receives, then the set-up of
-// the cells ignited in that period.  The replica's state is one Available
-// bit plane (burnable and not yet ignited; an ignition is one atomicAnd that
-// also tells the single winner) held in shared memory when it fits (SMEM) and
-// in per-CTA global scratch otherwise, plus a Burned plane in global scratch;
-// the scar plane is written out at the end.
-template <int T, bool SMEM>
-__device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
-  constexpr int G = T / 8;   // cell groups per CTA
+__device__ __forceinline__ uint32_t rc_pack(int32_t r, int32_t c) {
+  return ((uint32_t)r << 16) | (uint32_t)c;
+}
+
+// One warp per replica; replicas come from a work list of (simulation,
+// replica) items that every warp pulls from.  The four 8-lane groups of the
+// warp each take one burning cell at a time, lane k owning axis k, so the
+// per-axis work of a cell (crossing tests, increments, crossing periods, the
+// burn-out test of the neighbour on that axis) runs side by side.  There is
+// no CTA barrier: the warp's own counters stay in registers, appends to the
+// burning list are placed by ballot + popc, and phases are ordered with
+// __syncwarp.  State per replica: one Available bit plane (burnable, not
+// harvested, not yet ignited -- an ignition is one atomicAnd, whose old value
+// also picks the single winner), in shared memory when it fits (SMEM) and in
+// per-warp global scratch otherwise, and a Burned plane in global scratch;
+// the scar plane (burnable and no longer Available) is written at the end.
+template <int WPC, bool SMEM>
+__device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
   extern __shared__ __align__(16) uint32_t s_planes[];
-  __shared__ FrontierShared<T> S;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int k = tid & 7, g = tid >> 3;
-  const size_t slot = blockIdx.x;
+  __shared__ SimJob s_job[WPC];
+  constexpr uint32_t FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int k = lane & 7, grp = lane >> 3;
+  const uint32_t lt = (1u << lane) - 1u;
+  const size_t slot = (size_t)blockIdx.x * WPC + wib;
   const int32_t cap = A.cap;
-  int32_t *ecell = A.ent_cell + slot * cap;
+  uint32_t *erc = reinterpret_cast<uint32_t *>(A.ent_cell) + slot * cap;   // row << 16 | col
   uint8_t *emask = A.ent_mask + slot * cap;
   uint8_t *enext = A.ent_next + slot * cap;
   uint8_t *ecofs = A.ent_cofs + slot * (size_t)cap * 8;
   int64_t *eP = A.ent_P + slot * (size_t)cap * 8;
+  uint32_t *av;
+  if constexpr (SMEM) av = s_planes + (size_t)wib * A.pw_max;
+  else av = A.avail_scratch + slot * (size_t)A.pw_max;
+  uint32_t *brn = A.brn_scratch + slot * (size_t)A.pw_max;
+  SimJob &J = s_job[wib];
 
   for (;;) {
-    if (tid == 0) {
+    long long item = -1;
+    int32_t jidx = 0;
+    if (lane == 0) {
       const unsigned long long i = atomicAdd(A.counter, 1ull);
-      int64_t item = -1;
-      if ((int64_t)i < A.n_items) item = A.item_list ? A.item_list[i] : (int64_t)i;
-      S.item = item;
-      if (item >= 0) {
-        S.job = A.jobs[find_job(A.item_begin, A.n_jobs, item)];
-        S.hros_pos = S.job.hros_pos ? *S.job.hros_pos : 0;
+      if ((int64_t)i < A.n_items) {
+        item = A.item_list ? A.item_list[i] : (long long)i;
+        jidx = (int32_t)find_job(A.item_begin, A.n_jobs, item);
+        J = A.jobs[jidx];
       }
     }
-    __syncthreads();
-    const int64_t item = S.item;
+    item = __shfl_sync(FULL, item, 0);
+    jidx = __shfl_sync(FULL, jidx, 0);
+    __syncwarp();
     if (item < 0) return;
-    const SimJob &J = S.job;
-    const int32_t r = (int32_t)(item - A.item_begin[find_job(A.item_begin, A.n_jobs, item)]);
+    const int32_t r = (int32_t)(item - A.item_begin[jidx]);
     const int32_t rows = J.rows, cols = J.cols, wpr = J.wpr;
     const int64_t n = (int64_t)rows * cols;
-    const size_t pw = (size_t)rows * wpr;
-    const bool gate_free = (J.thr < 0.0) || (J.thr == 0.0 && S.hros_pos);
-    // Available plane (burnable, not harvested, not yet ignited) and Burned plane
-    uint32_t *av;
-    if constexpr (SMEM) av = s_planes;
-    else av = A.avail_scratch + slot * (size_t)A.pw_max;
-    uint32_t *brn = A.brn_scratch + slot * (size_t)A.pw_max;
-    for (size_t i = tid; i < pw; i += T) { av[i] = __ldg(&J.burnable[i]); brn[i] = 0u; }
-    int32_t *istep = J.ign_step ? J.ign_step + (size_t)r * n : nullptr;
+    const int32_t pw = rows * wpr;
     const int32_t sph = J.sph, H = J.hours;
+    const bool gate_free = (J.thr < 0.0) || (J.thr == 0.0 && J.hros_pos && *J.hros_pos);
+    const double delta = J.delta;
+    const uint64_t seed = J.seed;
+    const float sigma = J.sigma;
+    const uint32_t *burnable = J.burnable;
+    int32_t *istep = J.ign_step ? J.ign_step + (size_t)r * n : nullptr;
     const int64_t dk = (k & 1) ? J.d_diag : J.d_orth;   // this lane's axis length
-    if (tid == 0) {
-      S.nnew = 1; S.overflow = 0;
-      S.burn[0] = S.burn[1] = 0;
-      S.minnext[0] = S.minnext[1] = kNone;
-    }
-    __syncthreads();
+    for (int32_t i = lane; i < pw; i += 32) { av[i] = __ldg(&burnable[i]); brn[i] = 0u; }
+    __syncwarp();
 
     // Step 1 of Alg. 1: the ignition cell burns from period 0
-    int32_t live = 1;
-    long long W = 0;          // thread 0's running work count
-    int32_t nign = 1;
+    int32_t live = 1, nign = 1, cnt = 1, status = 0;
+    long long W = 0, s_done = 0;
     {
       const int32_t ic = J.ign_cell[r];
       const int32_t ir = ic / cols, icc = ic - ir * cols;
-      if (tid == 0) {
-        atomicAnd(&av[(int64_t)ir * wpr + (icc >> 5)], ~(1u << (icc & 31)));
+      if (lane == 0) {
+        atomicAnd(&av[ir * wpr + (icc >> 5)], ~(1u << (icc & 31)));
         if (istep) istep[ic] = 0;
       }
-      __syncthreads();
+      __syncwarp();
       bool open = false;
-      if (tid < 8) {
+      if (lane < 8) {
         const int32_t nr = ir + kDR[k], nc = icc + kDC[k];
         open = nr >= 0 && nr < rows && nc >= 0 && nc < cols && plane_bit(av, wpr, nr, nc);
       }
-      const uint32_t mask = group_bits(open);   // lanes 0..7 of warp 0 hold the cell's mask
-      if (tid < 8) {
-        eP[k] = 0;
-        ecofs[k] = kNone;
-        if (k == 0) { ecell[0] = ic; emask[0] = (uint8_t)mask; enext[0] = kNone; }
+      const uint32_t mask0 = __ballot_sync(FULL, open) & 0xFFu;
+      if (lane < 8) { eP[k] = 0; ecofs[k] = kNone; }
+      if (lane == 0) { erc[0] = rc_pack(ir, icc); emask[0] = (uint8_t)mask0; enext[0] = kNone; }
+      if (mask0 == 0) {   // no Available neighbour: Burned at the end of period 1
+        if (lane == 0) atomicOr(&brn[ir * wpr + (icc >> 5)], 1u << (icc & 31));
+        live = 0;
+        W = (H * sph >= 1) ? 1 : 0;
       }
-      if (tid == 0 && mask == 0) {   // no Available neighbour: Burned after period 1
-        atomicOr(&brn[(int64_t)ir * wpr + (icc >> 5)], 1u << (icc & 31));
-        S.burn[0] = 1;
-      }
-      __syncthreads();
-      if (S.burn[0]) { live = 0; W = (H * sph >= 1) ? 1 : 0; }
-      __syncthreads();
-      if (tid == 0) S.burn[0] = 0;
-      __syncthreads();
+      __syncwarp();
     }
-    int32_t cnt = 1;          // entries in the list
-    long long s_done = 0;     // last period whose burning count is in W
-    int it = 0;               // visited-period counter (parity selects the buffers)
-    bool aborted = false;
 
-    for (int32_t h = 0; h < H && live > 0 && !aborted; ++h) {
+    for (int32_t h = 0; h < H && live > 0 && status == 0; ++h) {
       const int32_t s0 = h * sph + 1, L = s0 + sph - 1;
       const int64_t *baseh = J.base + (size_t)h * n * 8;
-      const int p0 = it & 1;
+      const double *hrosh = J.hros + (size_t)h * n;
+      int32_t burned = 0;   // cells Burned at the end of the period being visited
 
       // ---- hour boundary (i): drop Burned cells and cells with no open axis
       {
-        if (tid == 0) S.out_base = 0;
-        __syncthreads();
-        for (int32_t b0 = 0; b0 < cnt; b0 += T) {
-          const int32_t e = b0 + tid;
+        int32_t out = 0;
+        for (int32_t b0 = 0; b0 < cnt; b0 += 32) {
+          const int32_t e = b0 + lane;
           bool keep = false;
-          int32_t cell = 0;
-          uint32_t mask = 0;
+          uint32_t rc = 0, m = 0;
           int64_t P[8];
           if (e < cnt) {
-            cell = ecell[e];
-            mask = emask[e];
-            const int32_t cr = cell / cols, cc = cell - cr * cols;
-            keep = mask != 0 && !plane_bit(brn, wpr, cr, cc);
+            rc = erc[e];
+            m = emask[e];
+            keep = m != 0 && !plane_bit(brn, wpr, (int32_t)(rc >> 16), (int32_t)(rc & 0xFFFFu));
             if (keep) {
 #pragma unroll
               for (int q = 0; q < 8; ++q) P[q] = eP[(size_t)e * 8 + q];
             }
           }
-          const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-          if (lane == 0) S.warp_tot[warp] = __popc(bal);
-          __syncthreads();
-          int32_t pos = S.out_base + __popc(bal & ((1u << lane) - 1u));
-          for (int w = 0; w < warp; ++w) pos += S.warp_tot[w];
+          const uint32_t bal = __ballot_sync(FULL, keep);
+          const int32_t pos = out + __popc(bal & lt);
+          __syncwarp();
           if (keep) {
-            ecell[pos] = cell;
-            emask[pos] = (uint8_t)mask;
+            erc[pos] = rc;
+            emask[pos] = (uint8_t)m;
 #pragma unroll
             for (int q = 0; q < 8; ++q) eP[(size_t)pos * 8 + q] = P[q];
           }
-          __syncthreads();
-          if (tid == 0) {
-            int32_t tot = 0;
-            for (int w = 0; w < T / 32; ++w) tot += S.warp_tot[w];
-            S.out_base += tot;
-          }
-          __syncthreads();
+          out += __popc(bal);
+          __syncwarp();
         }
-        cnt = S.out_base;
-        if (tid == 0) S.nnew = cnt;
+        cnt = out;
       }
-      // ---- hour boundary (ii): crossings of this hour, 8 lanes per cell
-      for (int32_t e0 = 0; e0 < cnt; e0 += G) {
-        const int32_t e = e0 + g;
+      // ---- hour boundary (ii): crossing periods of this hour, a group per cell
+      for (int32_t b0 = 0; b0 < cnt; b0 += 4) {
+        const int32_t e = b0 + grp;
         const bool act = e < cnt;
-        int32_t cell = 0;
-        uint32_t mask = 0;
+        uint32_t rc = 0, m = 0;
         int64_t P = 0;
-        if (act) { cell = ecell[e]; mask = emask[e]; P = eP[(size_t)e * 8 + k]; }
-        const int32_t cr = cell / cols, cc = cell - cr * cols;
-        bool open = act && ((mask >> k) & 1u);
+        if (act) { rc = erc[e]; m = emask[e]; P = eP[(size_t)e * 8 + k]; }
+        const int32_t cr = (int32_t)(rc >> 16), cc = (int32_t)(rc & 0xFFFFu);
+        const int64_t cell = (int64_t)cr * cols + cc;
+        bool open = act && ((m >> k) & 1u);
         if (open) open = plane_bit(av, wpr, cr + kDR[k], cc + kDC[k]);
-        mask = group_bits(open);
+        const int64_t bk = open ? baseh[cell * 8 + k] : 0;
+        const uint32_t mask = group_bits(open);
         uint32_t cof = kNone;
-        if (act && (mask != 0 || J.delta > 0.0)) {
-          const float f = noise_factor(J.seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, J.sigma);
+        bool dying = false;
+        if (act && (mask != 0 || delta > 0.0)) {
+          const float f = noise_factor(seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, sigma);
           if (open) {
-            const int64_t inc = apply_noise(baseh[(size_t)cell * 8 + k], noise_fixed(f), dk);
+            const int64_t inc = apply_noise(bk, noise_fixed(f), dk);
             const int64_t rem = dk - P;
             if (inc > 0 && inc * sph >= rem) cof = (uint32_t)(ceil_div_small(rem, inc) - 1);
             else P += inc * sph;
           }
-          if (J.delta > 0.0 &&
-              __dmul_rn(J.hros[(size_t)h * n + cell], (double)f) < J.delta) {   // A5 (i)
+          if (delta > 0.0 && __dmul_rn(hrosh[cell], (double)f) < delta) {   // A5 (i)
             if (k == 0) {
               const uint32_t bit = 1u << (cc & 31);
-              if (!(atomicOr(&brn[(int64_t)cr * wpr + (cc >> 5)], bit) & bit))
-                atomicAdd(&S.burn[p0], 1);
+              dying = !(atomicOr(&brn[cr * wpr + (cc >> 5)], bit) & bit);
             }
             if (cof != 0) cof = kNone;   // still sends in period s0, Burned after it
           }
@@ -469,23 +443,26 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
           eP[(size_t)e * 8 + k] = P;
           if (k == 0) { emask[e] = (uint8_t)mask; enext[e] = (uint8_t)nx; }
         }
+        burned += __popc(__ballot_sync(FULL, dying));
       }
-      __syncthreads();
+      __syncwarp();
 
       // ---- periods of this hour at which some axis reaches a centre
       int32_t s = s0;
       for (;;) {
-        const int p = it & 1;
-        if (tid == 0) { W += (long long)live * (long long)(s - s_done); s_done = s; }
+        W += (long long)live * (long long)(s - s_done);
+        s_done = s;
         const uint32_t o = (uint32_t)(s - s0);
         uint32_t lmin = kNone;
+        int32_t nnew = cnt;
+        bool ovf = false;
         // (A) send and receive: cells with a crossing at offset o
-        for (int32_t b0 = 0; b0 < cnt; b0 += T) {
-          const int32_t e = b0 + tid;
-          const uint32_t nx = (e < cnt) ? (uint32_t)enext[e] : kNone;
-          const bool hit = nx == o;
-          if (!hit) lmin = min(lmin, nx);
-          uint32_t hits = __ballot_sync(0xffffffffu, hit);
+        for (int32_t b0 = 0; b0 < cnt; b0 += 32) {
+          const int32_t e = b0 + lane;
+          const uint32_t nxe = (e < cnt) ? (uint32_t)enext[e] : kNone;
+          const bool hit = nxe == o;
+          if (!hit) lmin = min(lmin, nxe);
+          uint32_t hits = __ballot_sync(FULL, hit);
           while (hits) {
             int src[4];
 #pragma unroll
@@ -493,82 +470,75 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
               src[q] = hits ? __ffs(hits) - 1 : -1;
               if (hits) hits &= hits - 1;
             }
-            const int my = src[lane >> 3];
-            int32_t ent = __shfl_sync(0xffffffffu, e, my < 0 ? 0 : my);
+            const int my = src[grp];
+            int32_t ent = __shfl_sync(FULL, e, my < 0 ? 0 : my);
             if (my < 0) ent = -1;
-            uint32_t cof = kNone, mask = 0;
-            bool crossed = false;
+            uint32_t cof = kNone, wrc = 0;
+            int64_t jc = 0;
+            bool crossed = false, won = false;
             if (ent >= 0) {
               cof = ecofs[(size_t)ent * 8 + k];
               crossed = cof == o;
               if (crossed) {
                 cof = kNone;
-                const int32_t cell = ecell[ent];
-                const int32_t cr = cell / cols, cc = cell - cr * cols;
-                const int32_t nr = cr + kDR[k], nc = cc + kDC[k];
-                if (plane_bit(av, wpr, nr, nc)) {                        // Available
-                  const int64_t jc = (int64_t)nr * cols + nc;
-                  if (gate_free || receive_ok(J, r, jc, h, n)) {          // else consumed
+                const uint32_t rc = erc[ent];
+                const int32_t nr = (int32_t)(rc >> 16) + kDR[k], nc = (int32_t)(rc & 0xFFFFu) + kDC[k];
+                if (plane_bit(av, wpr, nr, nc)) {                         // Available
+                  jc = (int64_t)nr * cols + nc;
+                  if (gate_free || receive_ok(J, r, jc, h, n)) {           // else consumed
                     const uint32_t bit = 1u << (nc & 31);
-                    if (atomicAnd(&av[(int64_t)nr * wpr + (nc >> 5)], ~bit) & bit) {
-                      const int32_t idx = atomicAdd(&S.nnew, 1);
-                      if (idx < cap) ecell[idx] = (int32_t)jc; else S.overflow = 1;
-                      if (istep) istep[jc] = s;
-                    }
+                    won = (atomicAnd(&av[nr * wpr + (nc >> 5)], ~bit) & bit) != 0;
+                    wrc = rc_pack(nr, nc);
                   }
                 }
               }
             }
+            const uint32_t wins = __ballot_sync(FULL, won);
+            if (won) {
+              const int32_t idx = nnew + __popc(wins & lt);
+              if (idx < cap) erc[idx] = wrc; else ovf = true;
+              if (istep) istep[jc] = s;
+            }
+            nnew += __popc(wins);
             const uint32_t cbits = group_bits(crossed);
             const uint32_t nx2 = group_min(cof);
             if (ent >= 0) {
               if (crossed) ecofs[(size_t)ent * 8 + k] = kNone;
               if (k == 0) {
-                mask = emask[ent];
-                emask[ent] = (uint8_t)(mask & ~cbits);
+                emask[ent] = (uint8_t)(emask[ent] & ~cbits);
                 enext[ent] = (uint8_t)nx2;
                 lmin = min(lmin, nx2);
               }
             }
           }
         }
-        lmin = warp_min(lmin);
-        if (lane == 0) atomicMin(&S.minnext[p], lmin);
-        __syncthreads();
-        if (tid == 0) { S.burn[p ^ 1] = 0; S.minnext[p ^ 1] = kNone; }
-        if (S.overflow) { aborted = true; break; }
+        if (__any_sync(FULL, ovf)) { status = 1; break; }
+        __syncwarp();
         // (C) cells ignited in period s: open axes, first crossings, burn-out tests
-        const int32_t c1 = S.nnew;
-        lmin = kNone;
-        for (int32_t e0 = cnt; e0 < c1; e0 += G) {
-          const int32_t e = e0 + g;
-          const bool act = e < c1;
-          const int32_t cell = act ? ecell[e] : 0;
-          const int32_t cr = cell / cols, cc = cell - cr * cols;
+        for (int32_t b0 = cnt; b0 < nnew; b0 += 4) {
+          const int32_t e = b0 + grp;
+          const bool act = e < nnew;
+          const uint32_t rc = act ? erc[e] : 0u;
+          const int32_t cr = (int32_t)(rc >> 16), cc = (int32_t)(rc & 0xFFFFu);
+          const int64_t cell = (int64_t)cr * cols + cc;
           const int32_t nr = cr + kDR[k], nc = cc + kDC[k];
           const bool ingrid = act && nr >= 0 && nr < rows && nc >= 0 && nc < cols;
-          const int64_t bk = act ? baseh[(size_t)cell * 8 + k] : 0;   // issue the table load early
+          const int64_t bk = act ? baseh[cell * 8 + k] : 0;   // issue the table load early
           const bool open = ingrid && plane_bit(av, wpr, nr, nc);
-          const bool ignq = ingrid && !open && (__ldg(&J.burnable[(int64_t)nr * wpr + (nc >> 5)]) >> (nc & 31)) & 1u;
-          uint32_t mask = group_bits(open);
+          const bool ignq = ingrid && !open && ((__ldg(&burnable[nr * wpr + (nc >> 5)]) >> (nc & 31)) & 1u);
+          const uint32_t omask = group_bits(open);
+          uint32_t mask = omask;
           float f = 1.0f;
-          bool have_f = false;
-          if (act && J.delta > 0.0) {
-            f = noise_factor(J.seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, J.sigma);
+          bool have_f = false, dies = false;
+          if (act && delta > 0.0) {
+            f = noise_factor(seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, sigma);
             have_f = true;
-            if (__dmul_rn(J.hros[(size_t)h * n + cell], (double)f) < J.delta) {   // A5 (i)
-              if (k == 0) {
-                const uint32_t bit = 1u << (cc & 31);
-                if (!(atomicOr(&brn[(int64_t)cr * wpr + (cc >> 5)], bit) & bit))
-                  atomicAdd(&S.burn[p], 1);
-              }
-              mask = 0;
-            }
+            if (__dmul_rn(hrosh[cell], (double)f) < delta) { dies = true; mask = 0; }   // A5 (i)
           }
           uint32_t cof = kNone;
           int64_t P = 0;
           if (act && mask != 0 && s < L) {
-            if (!have_f) f = noise_factor(J.seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, J.sigma);
+            if (!have_f) f = noise_factor(seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, sigma);
             if ((mask >> k) & 1u) {
               const int32_t nmax = L - s;
               const int64_t inc = apply_noise(bk, noise_fixed(f), dk);
@@ -577,63 +547,63 @@ __device__ __forceinline__ void frontier_body(const FrontierArgs &A) {
             }
           }
           const uint32_t nx = group_min(cof);
+          bool newly = false;
           if (act) {
             ecofs[(size_t)e * 8 + k] = (uint8_t)cof;
             eP[(size_t)e * 8 + k] = P;
-            if (k == 0) { emask[e] = (uint8_t)mask; enext[e] = (uint8_t)nx; lmin = min(lmin, nx); }
-            // A5 (ii): the neighbour on this axis (if ignited), and lane 0 also this cell
+            if (k == 0) {
+              emask[e] = (uint8_t)mask;
+              enext[e] = (uint8_t)nx;
+              lmin = min(lmin, nx);
+              if (omask == 0 || dies) {   // this cell: A5 (ii) no Available neighbour, or (i)
+                const uint32_t bit = 1u << (cc & 31);
+                newly = !(atomicOr(&brn[cr * wpr + (cc >> 5)], bit) & bit);
+              }
+            }
+            // A5 (ii) for the ignited neighbour on this lane's axis
             if (ignq && !has_available_nbr(av, wpr, rows, cols, nr, nc)) {
               const uint32_t bit = 1u << (nc & 31);
-              if (!(atomicOr(&brn[(int64_t)nr * wpr + (nc >> 5)], bit) & bit)) atomicAdd(&S.burn[p], 1);
-            }
-            if (k == 0 && !has_available_nbr(av, wpr, rows, cols, cr, cc)) {
-              const uint32_t bit = 1u << (cc & 31);
-              if (!(atomicOr(&brn[(int64_t)cr * wpr + (cc >> 5)], bit) & bit)) atomicAdd(&S.burn[p], 1);
+              if (!(atomicOr(&brn[nr * wpr + (nc >> 5)], bit) & bit)) newly = true;
             }
           }
+          burned += __popc(__ballot_sync(FULL, newly));
         }
         lmin = warp_min(lmin);
-        if (lane == 0) atomicMin(&S.minnext[p], lmin);
-        __syncthreads();
-        const int32_t added = c1 - cnt;
+        __syncwarp();
+        const int32_t added = nnew - cnt;
         nign += added;
-        live += added - S.burn[p];
-        cnt = c1;
-        const uint32_t mn = S.minnext[p];
-        ++it;
-        const int32_t next = (mn == kNone) ? L + 1 : s0 + (int32_t)mn;
-        if (next <= s) {   // cannot happen; never visit a period twice
-          if (tid == 0) S.overflow = 2;
-          aborted = true;
-          break;
-        }
+        live += added - burned;
+        burned = 0;
+        cnt = nnew;
+        const int32_t next = (lmin == kNone) ? L + 1 : s0 + (int32_t)lmin;
+        if (next <= s) { status = 2; break; }   // cannot happen; never visit a period twice
         if (live == 0) break;
         s = next;
         if (s > L) break;
       }
-      if (!aborted && tid == 0) { W += (long long)live * (long long)(L - s_done); s_done = L; }
+      if (status == 0) { W += (long long)live * (long long)(L - s_done); s_done = L; }
     }
-    __syncthreads();
     {   // scar plane: burnable cells that are no longer Available
       uint32_t *dst = J.ign_plane + (size_t)r * pw;
-      for (size_t i = tid; i < pw; i += T) dst[i] = __ldg(&J.burnable[i]) & ~av[i];
+      for (int32_t i = lane; i < pw; i += 32) dst[i] = __ldg(&burnable[i]) & ~av[i];
     }
-    if (tid == 0) {
+    if (lane == 0) {
       J.work[r] = W;
       J.n_ignited[r] = nign;
-      J.status[r] = S.overflow;
+      J.status[r] = status;
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
-// Variants: CTA size 64 / 128 / 256, planes in global (g) or shared (s) memory.
-__global__ void __launch_bounds__(64, 16) k_frontier_g64(FrontierArgs A) { frontier_body<64, false>(A); }
-__global__ void __launch_bounds__(128, 8) k_frontier_g128(FrontierArgs A) { frontier_body<128, false>(A); }
-__global__ void __launch_bounds__(256, 4) k_frontier_g256(FrontierArgs A) { frontier_body<256, false>(A); }
-__global__ void __launch_bounds__(64, 16) k_frontier_s64(FrontierArgs A) { frontier_body<64, true>(A); }
-__global__ void __launch_bounds__(128, 8) k_frontier_s128(FrontierArgs A) { frontier_body<128, true>(A); }
-__global__ void __launch_bounds__(256, 4) k_frontier_s256(FrontierArgs A) { frontier_body<256, true>(A); }
+// Variants: warps per CTA (1, 2, 4) with the Available plane in global
+// memory (g) or shared memory (s).
+__global__ void __launch_bounds__(32) k_frontier_g1(FrontierArgs A) { frontier_warp<1, false>(A); }
+__global__ void __launch_bounds__(64) k_frontier_g2(FrontierArgs A) { frontier_warp<2, false>(A); }
+__global__ void __launch_bounds__(128) k_frontier_g4(FrontierArgs A) { frontier_warp<4, false>(A); }
+__global__ void __launch_bounds__(32) k_frontier_s1(FrontierArgs A) { frontier_warp<1, true>(A); }
+__global__ void __launch_bounds__(64) k_frontier_s2(FrontierArgs A) { frontier_warp<2, true>(A); }
+__global__ void __launch_bounds__(128) k_frontier_s4(FrontierArgs A) { frontier_warp<4, true>(A); }
 
 // ------------------------------------------------------------------ K4
 // counts[c] = sum over replicas of the scar bit of c.  Each thread owns one

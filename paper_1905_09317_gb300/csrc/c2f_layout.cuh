@@ -69,7 +69,7 @@ struct FrontierArgs {
   int64_t n_items;
   unsigned long long *counter;    // work-list cursor (zeroed before the launch)
   int32_t cap;                    // burning-list capacity per slot
-  int32_t *ent_cell;              // [slots][cap]
+  int32_t *ent_cell;              // [slots][cap] cell as row << 16 | col
   uint8_t *ent_mask;              // [slots][cap] open axes
   uint8_t *ent_next;              // [slots][cap] next event offset in the hour (0xFF none)
   uint8_t *ent_cofs;              // [slots][cap][8] per-axis crossing offsets (0xFF none)

@@ -35,12 +35,12 @@ __global__ void k_cell_prep(const float *, const float *, int64_t, CellPrep *);
 __global__ void k_hour_prep(const double *, int32_t, double, HourPrep *);
 __global__ void k_ros_table(RosTableArgs);
 __global__ void k_ignite(const SimJob *, int32_t);
-__global__ void k_frontier_g64(FrontierArgs);
-__global__ void k_frontier_g128(FrontierArgs);
-__global__ void k_frontier_g256(FrontierArgs);
-__global__ void k_frontier_s64(FrontierArgs);
-__global__ void k_frontier_s128(FrontierArgs);
-__global__ void k_frontier_s256(FrontierArgs);
+__global__ void k_frontier_g1(FrontierArgs);
+__global__ void k_frontier_g2(FrontierArgs);
+__global__ void k_frontier_g4(FrontierArgs);
+__global__ void k_frontier_s1(FrontierArgs);
+__global__ void k_frontier_s2(FrontierArgs);
+__global__ void k_frontier_s4(FrontierArgs);
 __global__ void k_burn_prob(const uint32_t *, int32_t, int32_t, int32_t, int32_t, int32_t,
                             uint32_t *, int32_t);
 __global__ void k_scar_bytes(const uint32_t *, int32_t, int32_t, int32_t, int32_t, uint8_t *);
@@ -123,7 +123,7 @@ struct c2f_ctx {
   DevBuf ent_cell, ent_mask, ent_next, ent_cofs, ent_P, counter, brn_scratch, avail_scratch;
   int64_t scratch_slots = 0, scratch_cap = 0, brn_words = 0, avail_words = 0;
   int smem_optin = 0;
-  int64_t smem_plane_limit = 48 * 1024;    // Available plane staged in shared memory up to this size
+  int64_t smem_plane_limit = 0;            // Available plane staged in shared memory up to this size
   int frontier_threads = 128;
   int64_t cap_override = 0;
   // kernel timing
@@ -420,11 +420,12 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
   const size_t plane_bytes = (size_t)pw_max * 4;
   const bool use_smem = (int64_t)plane_bytes <= ctx->smem_plane_limit &&
                         (int64_t)plane_bytes <= (int64_t)ctx->smem_optin - 4096;
-  const int threads = ctx->frontier_threads;
+  const int threads = ctx->frontier_threads;   // 32, 64 or 128: one replica per warp
+  const int wpc = threads / 32;
   void (*kern)(FrontierArgs) =
-      use_smem ? (threads == 64 ? k_frontier_s64 : threads == 128 ? k_frontier_s128 : k_frontier_s256)
-               : (threads == 64 ? k_frontier_g64 : threads == 128 ? k_frontier_g128 : k_frontier_g256);
-  const size_t dyn_smem = use_smem ? plane_bytes : 0;
+      use_smem ? (wpc == 1 ? k_frontier_s1 : wpc == 2 ? k_frontier_s2 : k_frontier_s4)
+               : (wpc == 1 ? k_frontier_g1 : wpc == 2 ? k_frontier_g2 : k_frontier_g4);
+  const size_t dyn_smem = use_smem ? plane_bytes * wpc : 0;
   if (use_smem) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem));
   int bps = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, threads, dyn_smem));
@@ -432,9 +433,10 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
   std::vector<int64_t> items;  // empty: all
   for (int attempt = 0;; ++attempt) {
     const int64_t todo = items.empty() ? n_items : (int64_t)items.size();
-    const int64_t max_slots = (int64_t)ctx->sm_count * bps;
-    int64_t slots = std::min<int64_t>(todo, max_slots);
-    if (attempt > 0) slots = std::min<int64_t>(slots, std::max<int64_t>(1, ctx->sm_count));
+    const int64_t max_ctas = (int64_t)ctx->sm_count * bps;
+    int64_t ctas = std::min<int64_t>((todo + wpc - 1) / wpc, max_ctas);
+    if (attempt > 0) ctas = std::min<int64_t>(ctas, std::max<int64_t>(1, ctx->sm_count));
+    const int64_t slots = ctas * wpc;   // one warp per slot
     if ((rc = ensure_scratch(ctx, slots, cap))) return rc;
     if (slots * pw_max > ctx->brn_words) {
       if ((rc = dalloc(ctx, ctx->brn_scratch, (size_t)slots * pw_max * 4))) return rc;
@@ -469,7 +471,7 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
     CK(cudaMemsetAsync(ctx->counter.p, 0, 8, ctx->stream));
     {
       ProfScope prof(ctx, 2);
-      kern<<<(unsigned)slots, threads, dyn_smem, ctx->stream>>>(A);
+      kern<<<(unsigned)ctas, threads, dyn_smem, ctx->stream>>>(A);
       CKL("k_frontier");
     }
     // gather failed replicas
@@ -576,8 +578,8 @@ C2F_API int c2f_load_landscape(c2f_ctx *ctx, int32_t rows, int32_t cols, double 
                                int32_t *landscape_id) {
   if (!ctx) return C2F_EINVAL;
   if (!fuel || !landscape_id) return fail(ctx, C2F_EINVAL, "fuel and landscape_id are required");
-  if (rows < 1 || cols < 1 || (int64_t)rows * cols >= (1LL << 31))
-    return fail(ctx, C2F_EINVAL, "rows*cols must lie in [1, 2^31)");
+  if (rows < 1 || cols < 1 || rows > 65535 || cols > 65535 || (int64_t)rows * cols >= (1LL << 31))
+    return fail(ctx, C2F_EINVAL, "rows and cols must lie in [1, 65535] and rows*cols < 2^31");
   if (!(cell_size_m > 0.0 && cell_size_m <= 1e6)) return fail(ctx, C2F_EINVAL, "cell_size_m out of range");
   const int64_t n = (int64_t)rows * cols;
   for (int64_t i = 0; i < n; ++i)
@@ -874,8 +876,8 @@ C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap) {
 
 C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem_plane_bytes) {
   if (!ctx) return C2F_EINVAL;
-  if (threads != 64 && threads != 128 && threads != 256)
-    return fail(ctx, C2F_EINVAL, "threads must be 64, 128 or 256");
+  if (threads != 32 && threads != 64 && threads != 128)
+    return fail(ctx, C2F_EINVAL, "threads must be 32, 64 or 128 (one replica per warp)");
   if (smem_plane_bytes < 0) return fail(ctx, C2F_EINVAL, "smem_plane_bytes must be >= 0");
   ctx->frontier_threads = threads;
   ctx->smem_plane_limit = smem_plane_bytes;
