@@ -547,7 +547,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
             }
           }
           const uint32_t nx = group_min(cof);
-          bool newly = false;
+          uint32_t newly = 0;   // cells this lane turned Burned (its own cell, its axis neighbour)
           if (act) {
             ecofs[(size_t)e * 8 + k] = (uint8_t)cof;
             eP[(size_t)e * 8 + k] = P;
@@ -557,16 +557,16 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
               lmin = min(lmin, nx);
               if (omask == 0 || dies) {   // this cell: A5 (ii) no Available neighbour, or (i)
                 const uint32_t bit = 1u << (cc & 31);
-                newly = !(atomicOr(&brn[cr * wpr + (cc >> 5)], bit) & bit);
+                newly += (atomicOr(&brn[cr * wpr + (cc >> 5)], bit) & bit) ? 0u : 1u;
               }
             }
             // A5 (ii) for the ignited neighbour on this lane's axis
             if (ignq && !has_available_nbr(av, wpr, rows, cols, nr, nc)) {
               const uint32_t bit = 1u << (nc & 31);
-              if (!(atomicOr(&brn[nr * wpr + (nc >> 5)], bit) & bit)) newly = true;
+              newly += (atomicOr(&brn[nr * wpr + (nc >> 5)], bit) & bit) ? 0u : 1u;
             }
           }
-          burned += __popc(__ballot_sync(FULL, newly));
+          burned += (int32_t)__reduce_add_sync(FULL, newly);
         }
         lmin = warp_min(lmin);
         __syncwarp();
