@@ -124,10 +124,66 @@ __global__ void k_hour_prep(const double *__restrict__ weather, int32_t hours, d
 
 // ------------------------------------------------------------------ K1
 
+// Cells grouped by (fuel code, slope > 0) so that the lanes of a warp take the
+// same branches of the FBP code (set-up, once per landscape): a per-bucket
+// count, an exclusive scan, then a scatter; the order inside a bucket is
+// immaterial because every cell writes its own table row.
+__device__ __forceinline__ int order_bucket(const uint8_t *fuel, const float *slope,
+                                            const uint32_t *burnable, int32_t cols, int32_t wpr,
+                                            int64_t cell) {
+  const int32_t row = (int32_t)(cell / cols), col = (int32_t)(cell % cols);
+  const bool burn = (burnable[(int64_t)row * wpr + (col >> 5)] >> (col & 31)) & 1u;
+  if (!burn) return 0;
+  const bool sloped = slope && slope[cell] > 0.0f;
+  return 2 * (int)fuel[cell] + (sloped ? 1 : 0);
+}
+
+__global__ void k_order_count(const uint8_t *fuel, const float *slope, const uint32_t *burnable,
+                              int32_t rows, int32_t cols, int32_t wpr, int32_t *counts) {
+  __shared__ int32_t h[kOrderBuckets];
+  if (threadIdx.x < kOrderBuckets) h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell < (int64_t)rows * cols)
+    atomicAdd(&h[order_bucket(fuel, slope, burnable, cols, wpr, cell)], 1);
+  __syncthreads();
+  if (threadIdx.x < kOrderBuckets && h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_order_scan(int32_t *counts_to_cursor) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int32_t run = 0;
+    for (int b = 0; b < kOrderBuckets; ++b) {
+      const int32_t c = counts_to_cursor[b];
+      counts_to_cursor[b] = run;
+      run += c;
+    }
+  }
+}
+
+__global__ void k_order_scatter(const uint8_t *fuel, const float *slope, const uint32_t *burnable,
+                                int32_t rows, int32_t cols, int32_t wpr, int32_t *cursor,
+                                int32_t *order) {
+  __shared__ int32_t h[kOrderBuckets], base[kOrderBuckets];
+  if (threadIdx.x < kOrderBuckets) h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int b = -1, local = 0;
+  if (cell < (int64_t)rows * cols) {
+    b = order_bucket(fuel, slope, burnable, cols, wpr, cell);
+    local = atomicAdd(&h[b], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < kOrderBuckets && h[threadIdx.x]) base[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], h[threadIdx.x]);
+  __syncthreads();
+  if (b >= 0) order[base[b] + local] = (int32_t)cell;
+}
+
 __global__ void __launch_bounds__(128) k_ros_table(RosTableArgs a) {
   const int64_t n = (int64_t)a.rows * a.cols;
-  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= n) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int64_t cell = a.order ? (int64_t)a.order[t] : t;
   const int h = a.hour0 + blockIdx.y;
   const int32_t row = (int32_t)(cell / a.cols), col = (int32_t)(cell % a.cols);
   const bool burn = (a.burnable[(int64_t)row * a.wpr + (col >> 5)] >> (col & 31)) & 1u;

@@ -94,7 +94,10 @@ struct RosTableArgs {
   double *hros;            // [hour][N], or nullptr
   double *ros8;            // export: [N][8] of hour0 only, or nullptr
   int32_t *hros_pos;       // cleared if some burnable cell has HROS <= 1e-200
+  const int32_t *order;    // cells grouped by (fuel code, sloped); nullptr = identity
 };
+
+constexpr int kOrderBuckets = 2 * 16;   // (fuel code, slope > 0); code 0 = not burnable
 
 constexpr uint8_t kNone = 0xFF;
 

@@ -67,9 +67,12 @@ __device__ __forceinline__ double scale2(double p, int k) {
 }
 
 __device__ inline double dexp(double x) {
-  if (x != x) return x;
-  if (x > 709.78) return __longlong_as_double(0x7ff0000000000000LL);
-  if (x < -745.2) return 0.0;
+  // |x| < 704 (integer test of the high word) skips the range checks below
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x40860000) {
+    if (x != x) return x;
+    if (x > 709.78) return __longlong_as_double(0x7ff0000000000000LL);
+    if (x < -745.2) return 0.0;
+  }
   const double kd = rint(__dmul_rn(x, kInvLn2));
   const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(kd, kLn2Hi)), __dmul_rn(kd, kLn2Lo));
   double p = g_mc.inv_fact[13];
@@ -79,12 +82,15 @@ __device__ inline double dexp(double x) {
 }
 
 __device__ inline double dlog(double x) {
-  if (x != x) return x;
-  if (x < 0.0) return __longlong_as_double(0x7ff8000000000000LL);
-  if (x == 0.0) return __longlong_as_double((long long)0xfff0000000000000ULL);
-  if (__double_as_longlong(x) == 0x7ff0000000000000LL) return x;
   int e = 0;
-  if (x < 0x1p-1022) { x = __dmul_rn(x, 0x1p54); e = -54; }
+  const int hx = __double2hiint(x);
+  if (hx < 0x00100000 || hx >= 0x7ff00000) {   // not a positive normal finite number
+    if (x != x) return x;
+    if (x < 0.0) return __longlong_as_double(0x7ff8000000000000LL);
+    if (x == 0.0) return __longlong_as_double((long long)0xfff0000000000000ULL);
+    if (__double_as_longlong(x) == 0x7ff0000000000000LL) return x;
+    if (x < 0x1p-1022) { x = __dmul_rn(x, 0x1p54); e = -54; }
+  }
   unsigned long long b = (unsigned long long)__double_as_longlong(x);
   e += (int)((b >> 52) & 0x7ff) - 1023;
   b = (b & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL;
@@ -103,6 +109,8 @@ __device__ inline double dlog(double x) {
 }
 
 __device__ inline double dpow(double x, double y) {
+  const long long bx = __double_as_longlong(x);
+  if (bx > 0 && bx < 0x7ff0000000000000LL) return dexp(__dmul_rn(y, dlog(x)));   // 0 < x < inf
   if (x > 0.0) return dexp(__dmul_rn(y, dlog(x)));
   if (x == 0.0) return (y > 0.0) ? 0.0 : ((y == 0.0) ? 1.0 : __longlong_as_double(0x7ff0000000000000LL));
   return __longlong_as_double(0x7ff8000000000000LL);

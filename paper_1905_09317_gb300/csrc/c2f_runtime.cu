@@ -34,6 +34,11 @@ __global__ void k_burnable_list(const uint32_t *, const int32_t *, int32_t, int3
 __global__ void k_cell_prep(const float *, const float *, int64_t, CellPrep *);
 __global__ void k_hour_prep(const double *, int32_t, double, HourPrep *);
 __global__ void k_ros_table(RosTableArgs);
+__global__ void k_order_count(const uint8_t *, const float *, const uint32_t *, int32_t, int32_t,
+                              int32_t, int32_t *);
+__global__ void k_order_scan(int32_t *);
+__global__ void k_order_scatter(const uint8_t *, const float *, const uint32_t *, int32_t, int32_t,
+                                int32_t, int32_t *, int32_t *);
 __global__ void k_ignite(const SimJob *, int32_t);
 __global__ void k_frontier_g1(FrontierArgs);
 __global__ void k_frontier_g2(FrontierArgs);
@@ -83,7 +88,7 @@ struct Landscape {
   double cell_size = 0;
   int32_t n_burnable = 0;
   std::vector<uint8_t> burnable_host;  // for validation of fixed ignitions
-  DevBuf fuel, slope, aspect, burnable, burnable_list, cell_prep;
+  DevBuf fuel, slope, aspect, burnable, burnable_list, cell_prep, order;
   bool has_slope = false;
   int32_t n_hours = 0;
   std::vector<double> weather;          // n_hours x 4
@@ -292,6 +297,7 @@ int build_table(c2f_ctx *ctx, Landscape &L, const c2f_sim_params *p) {
     CK(cudaMemcpyAsync(L.hros_pos.p, &one, 4, cudaMemcpyHostToDevice, ctx->stream));
   }
   a.hros_pos = L.hros_pos.as<int32_t>();
+  a.order = L.order.as<int32_t>();
   dim3 grid(grid1(L.n, 128), (unsigned)H);
   k_ros_table<<<grid, 128, 0, ctx->stream>>>(a);
   CKL("k_ros_table");
@@ -638,6 +644,21 @@ C2F_API int c2f_load_landscape(c2f_ctx *ctx, int32_t rows, int32_t cols, double 
       L->burnable.as<uint32_t>(), woffs.as<int32_t>(), rows, cols, L->wpr,
       L->burnable_list.as<int32_t>());
   CKL("k_burnable_list");
+  {   // cells grouped by (fuel, sloped) for the ROS-table kernel
+    DevBuf cursor;
+    if ((rc = dalloc(ctx, L->order, (size_t)n * 4))) return rc;
+    if ((rc = dalloc(ctx, cursor, kOrderBuckets * 4))) return rc;
+    CK(cudaMemsetAsync(cursor.p, 0, kOrderBuckets * 4, ctx->stream));
+    k_order_count<<<grid1(n, 256), 256, 0, ctx->stream>>>(L->fuel.as<uint8_t>(), L->slope.as<float>(),
+        L->burnable.as<uint32_t>(), rows, cols, L->wpr, cursor.as<int32_t>());
+    CKL("k_order_count");
+    k_order_scan<<<1, 32, 0, ctx->stream>>>(cursor.as<int32_t>());
+    CKL("k_order_scan");
+    k_order_scatter<<<grid1(n, 256), 256, 0, ctx->stream>>>(L->fuel.as<uint8_t>(), L->slope.as<float>(),
+        L->burnable.as<uint32_t>(), rows, cols, L->wpr, cursor.as<int32_t>(), L->order.as<int32_t>());
+    CKL("k_order_scatter");
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
   if ((rc = dalloc(ctx, L->cell_prep, sizeof(CellPrep) * n))) return rc;
   k_cell_prep<<<grid1(n, 256), 256, 0, ctx->stream>>>(L->slope.as<float>(), L->aspect.as<float>(), n,
                                                      L->cell_prep.as<CellPrep>());
