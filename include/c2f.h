@@ -190,6 +190,51 @@ C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem_plan
 C2F_API int c2f_profile(c2f_ctx *ctx, int enable);
 C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free frontier step.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory (code running
+ * inside a CUDA-graph capture it does not own, a host application that has
+ * handed all device memory to its own allocator, a plugin forbidden to
+ * allocate after start-up).  It runs Step 2 of Alg. 1 for every replica --
+ * the same kernel and the same results as c2f_simulate -- taking all scratch
+ * from one fixed 16 MiB device array inside the library (every GPU that loads
+ * the library holds it until exit).  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *
+ * Inputs (device memory, caller-owned, not modified): the burnable bit plane
+ * (rows * ceil(cols/32) 32-bit words, rows padded to whole words, bit = fuel
+ * and not harvested), the rate-of-spread table `base` ([hours][rows*cols][8]
+ * int64, the per-period fixed-point increments that c2f_get_ros exports for
+ * the same minutes_per_step) and `hros` ([hours][rows*cols]), and the
+ * ignition cell of every replica.  Outputs (device memory, caller-owned):
+ * scars ([n_replicas][rows * ceil(cols/32)] words, same layout as the plane),
+ * work and n_ignited per replica.  From *p it uses seed, n_replicas (at most
+ * 65536), hours, minutes_per_step, ros_sigma, ros_threshold, burnout_delta.
+ *
+ * Limits: the two bit planes of one replica plus at least 256 burning-list
+ * entries must fit the array (about 28 million cells); larger landscapes give
+ * C2F_EINVAL before any device work.  A replica whose burning list outgrows
+ * the whole array gives C2F_ENOMEM.  Each call clears what must start at
+ * zero; all calls share the array and it keeps the last call's contents, so
+ * calls that overlap on the GPU (other streams, other host threads) race.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Synchronous: returns after the work on `stream` has finished.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t rows, cols;
+  double cell_size_m;
+  const uint32_t *burnable;
+  const int64_t *base;
+  const double *hros;
+  const int32_t *ign_cell;
+  uint32_t *scars;
+  int64_t *work;
+  int32_t *n_ignited;
+} c2f_frontier_io;
+
+C2F_API int c2f_frontier_static(const c2f_frontier_io *io, const c2f_sim_params *p, void *stream);
+
 /* Frees a landscape (and its tables) or a simulation result. */
 C2F_API int c2f_release(c2f_ctx *ctx, int32_t id);
 

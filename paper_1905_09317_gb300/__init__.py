@@ -45,6 +45,14 @@ class SimParams(C.Structure):
     ]
 
 
+class FrontierIO(C.Structure):
+    """Device-pointer arguments of c2f_frontier_static (allocation-free frontier step)."""
+    _fields_ = [("rows", C.c_int32), ("cols", C.c_int32), ("cell_size_m", C.c_double),
+                ("burnable", C.c_void_p), ("base", C.c_void_p), ("hros", C.c_void_p),
+                ("ign_cell", C.c_void_p), ("scars", C.c_void_p), ("work", C.c_void_p),
+                ("n_ignited", C.c_void_p)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -73,6 +81,7 @@ _SIGS = [
     ("c2f_profile", C.c_int, [C.c_void_p, C.c_int]),
     ("c2f_kernel_times", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("c2f_release", C.c_int, [C.c_void_p, C.c_int32]),
+    ("c2f_frontier_static", C.c_int, [C.c_void_p, _P(SimParams), C.c_void_p]),
 ]
 KERNEL_FAMILIES = ("ros_table", "ignite", "frontier", "burn_prob")
 
