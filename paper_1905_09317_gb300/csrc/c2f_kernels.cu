@@ -347,7 +347,11 @@ __device__ __forceinline__ uint32_t rc_pack(int32_t r, int32_t c) {
 // also picks the single winner), in shared memory when it fits (SMEM) and in
 // per-warp global scratch otherwise, and a Burned plane in global scratch;
 // the scar plane (burnable and no longer Available) is written at the end.
-template <int WPC, bool SMEM>
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+template <int WPC, bool SMEM, bool LSMEM>
 __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
   extern __shared__ __align__(16) uint32_t s_planes[];
   __shared__ SimJob s_job[WPC];
@@ -357,13 +361,25 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
   const uint32_t lt = (1u << lane) - 1u;
   const size_t slot = (size_t)blockIdx.x * WPC + wib;
   const int32_t cap = A.cap;
-  uint32_t *erc = reinterpret_cast<uint32_t *>(A.ent_cell) + slot * cap;   // row << 16 | col
-  uint8_t *emask = A.ent_mask + slot * cap;
-  uint8_t *enext = A.ent_next + slot * cap;
-  uint8_t *ecofs = A.ent_cofs + slot * (size_t)cap * 8;
+  // per-warp shared memory: [Available plane (SMEM)][list arrays (LSMEM)]
+  uint32_t *my_smem = s_planes + (size_t)wib * A.smem_warp_words;
+  uint32_t *erc;     // row << 16 | col
+  uint8_t *emask, *enext, *ecofs;
+  if constexpr (LSMEM) {
+    uint32_t *ls = my_smem + (SMEM ? A.pw_max : 0);
+    erc = ls;
+    ecofs = reinterpret_cast<uint8_t *>(ls + cap);
+    emask = reinterpret_cast<uint8_t *>(ls + 3 * (size_t)cap);
+    enext = emask + cap;
+  } else {
+    erc = reinterpret_cast<uint32_t *>(A.ent_cell) + slot * cap;
+    emask = A.ent_mask + slot * cap;
+    enext = A.ent_next + slot * cap;
+    ecofs = A.ent_cofs + slot * (size_t)cap * 8;
+  }
   int64_t *eP = A.ent_P + slot * (size_t)cap * 8;
   uint32_t *av;
-  if constexpr (SMEM) av = s_planes + (size_t)wib * A.pw_max;
+  if constexpr (SMEM) av = my_smem;
   else av = A.avail_scratch + slot * (size_t)A.pw_max;
   uint32_t *brn = A.brn_scratch + slot * (size_t)A.pw_max;
   SimJob &J = s_job[wib];
@@ -462,44 +478,68 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         }
         cnt = out;
       }
-      // ---- hour boundary (ii): crossing periods of this hour, a group per cell
-      for (int32_t b0 = 0; b0 < cnt; b0 += 4) {
-        const int32_t e = b0 + grp;
-        const bool act = e < cnt;
-        uint32_t rc = 0, m = 0;
-        int64_t P = 0;
-        if (act) { rc = erc[e]; m = emask[e]; P = eP[(size_t)e * 8 + k]; }
-        const int32_t cr = (int32_t)(rc >> 16), cc = (int32_t)(rc & 0xFFFFu);
-        const int64_t cell = (int64_t)cr * cols + cc;
-        bool open = act && ((m >> k) & 1u);
-        if (open) open = plane_bit(av, wpr, cr + kDR[k], cc + kDC[k]);
-        const int64_t bk = open ? baseh[cell * 8 + k] : 0;
-        const uint32_t mask = group_bits(open);
-        uint32_t cof = kNone;
-        bool dying = false;
-        if (act && (mask != 0 || delta > 0.0)) {
-          const float f = noise_factor(seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, sigma);
-          if (open) {
-            const int64_t inc = apply_noise(bk, noise_fixed(f), dk);
-            const int64_t rem = dk - P;
-            if (inc > 0 && inc * sph >= rem) cof = (uint32_t)(ceil_div_small(rem, inc) - 1);
-            else P += inc * sph;
-          }
-          if (delta > 0.0 && __dmul_rn(hrosh[cell], (double)f) < delta) {   // A5 (i)
-            if (k == 0) {
-              const uint32_t bit = 1u << (cc & 31);
-              dying = !(atomicOr(&brn[cr * wpr + (cc >> 5)], bit) & bit);
+      // ---- hour boundary (ii): crossing periods of this hour, a group per cell,
+      // four cells per group in flight
+      for (int32_t b0 = 0; b0 < cnt; b0 += 16) {
+        uint32_t rcu[4], mu[4], masku[4];
+        int64_t Pu[4], bku[4];
+        bool actu[4], openu[4];
+        float fu[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int32_t e = b0 + 4 * u + grp;
+          actu[u] = e < cnt;
+          rcu[u] = actu[u] ? erc[e] : 0u;
+          mu[u] = actu[u] ? emask[e] : 0u;
+          Pu[u] = actu[u] ? eP[(size_t)e * 8 + k] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int32_t cr = (int32_t)(rcu[u] >> 16), cc = (int32_t)(rcu[u] & 0xFFFFu);
+          bool open = actu[u] && ((mu[u] >> k) & 1u);
+          if (open) open = plane_bit(av, wpr, cr + kDR[k], cc + kDC[k]);
+          openu[u] = open;
+          bku[u] = open ? baseh[((int64_t)cr * cols + cc) * 8 + k] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) masku[u] = group_bits(openu[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t cell = (int64_t)(rcu[u] >> 16) * cols + (rcu[u] & 0xFFFFu);
+          fu[u] = (actu[u] && (masku[u] != 0 || delta > 0.0))
+                      ? noise_factor(seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, sigma) : 1.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int32_t e = b0 + 4 * u + grp;
+          const int32_t cr = (int32_t)(rcu[u] >> 16), cc = (int32_t)(rcu[u] & 0xFFFFu);
+          const int64_t cell = (int64_t)cr * cols + cc;
+          uint32_t cof = kNone;
+          int64_t P = Pu[u];
+          bool dying = false;
+          if (actu[u] && (masku[u] != 0 || delta > 0.0)) {
+            if (openu[u]) {
+              const int64_t inc = apply_noise(bku[u], noise_fixed(fu[u]), dk);
+              const int64_t rem = dk - P;
+              if (inc > 0 && inc * sph >= rem) cof = (uint32_t)(ceil_div_small(rem, inc) - 1);
+              else P += inc * sph;
             }
-            if (cof != 0) cof = kNone;   // still sends in period s0, Burned after it
+            if (delta > 0.0 && __dmul_rn(hrosh[cell], (double)fu[u]) < delta) {   // A5 (i)
+              if (k == 0) {
+                const uint32_t bit = 1u << (cc & 31);
+                dying = !(atomicOr(&brn[cr * wpr + (cc >> 5)], bit) & bit);
+              }
+              if (cof != 0) cof = kNone;   // still sends in period s0, Burned after it
+            }
           }
+          const uint32_t nx = group_min(cof);
+          if (actu[u]) {
+            ecofs[(size_t)e * 8 + k] = (uint8_t)cof;
+            eP[(size_t)e * 8 + k] = P;
+            if (k == 0) { emask[e] = (uint8_t)masku[u]; enext[e] = (uint8_t)nx; }
+          }
+          burned += __popc(__ballot_sync(FULL, dying));
         }
-        const uint32_t nx = group_min(cof);
-        if (act) {
-          ecofs[(size_t)e * 8 + k] = (uint8_t)cof;
-          eP[(size_t)e * 8 + k] = P;
-          if (k == 0) { emask[e] = (uint8_t)mask; enext[e] = (uint8_t)nx; }
-        }
-        burned += __popc(__ballot_sync(FULL, dying));
       }
       __syncwarp();
 
@@ -554,6 +594,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
               const int32_t idx = nnew + __popc(wins & lt);
               if (idx < cap) erc[idx] = wrc; else ovf = true;
               if (istep) istep[jc] = s;
+              prefetch_l2(baseh + jc * 8);   // the new cell's table row, read when it is set up
             }
             nnew += __popc(wins);
             const uint32_t cbits = group_bits(crossed);
@@ -654,12 +695,21 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
 
 // Variants: warps per CTA (1, 2, 4) with the Available plane in global
 // memory (g) or shared memory (s).
-__global__ void __launch_bounds__(32) k_frontier_g1(FrontierArgs A) { frontier_warp<1, false>(A); }
-__global__ void __launch_bounds__(64) k_frontier_g2(FrontierArgs A) { frontier_warp<2, false>(A); }
-__global__ void __launch_bounds__(128) k_frontier_g4(FrontierArgs A) { frontier_warp<4, false>(A); }
-__global__ void __launch_bounds__(32) k_frontier_s1(FrontierArgs A) { frontier_warp<1, true>(A); }
-__global__ void __launch_bounds__(64) k_frontier_s2(FrontierArgs A) { frontier_warp<2, true>(A); }
-__global__ void __launch_bounds__(128) k_frontier_s4(FrontierArgs A) { frontier_warp<4, true>(A); }
+// Variants: warps per CTA (1, 2, 4); the Available plane in global (g) or
+// shared (s) memory; the burning-list arrays in global memory or, for the
+// "l" variants, in shared memory.
+__global__ void __launch_bounds__(32) k_frontier_g1(FrontierArgs A) { frontier_warp<1, false, false>(A); }
+__global__ void __launch_bounds__(64) k_frontier_g2(FrontierArgs A) { frontier_warp<2, false, false>(A); }
+__global__ void __launch_bounds__(128) k_frontier_g4(FrontierArgs A) { frontier_warp<4, false, false>(A); }
+__global__ void __launch_bounds__(32) k_frontier_s1(FrontierArgs A) { frontier_warp<1, true, false>(A); }
+__global__ void __launch_bounds__(64) k_frontier_s2(FrontierArgs A) { frontier_warp<2, true, false>(A); }
+__global__ void __launch_bounds__(128) k_frontier_s4(FrontierArgs A) { frontier_warp<4, true, false>(A); }
+__global__ void __launch_bounds__(32) k_frontier_gl1(FrontierArgs A) { frontier_warp<1, false, true>(A); }
+__global__ void __launch_bounds__(64) k_frontier_gl2(FrontierArgs A) { frontier_warp<2, false, true>(A); }
+__global__ void __launch_bounds__(128) k_frontier_gl4(FrontierArgs A) { frontier_warp<4, false, true>(A); }
+__global__ void __launch_bounds__(32) k_frontier_sl1(FrontierArgs A) { frontier_warp<1, true, true>(A); }
+__global__ void __launch_bounds__(64) k_frontier_sl2(FrontierArgs A) { frontier_warp<2, true, true>(A); }
+__global__ void __launch_bounds__(128) k_frontier_sl4(FrontierArgs A) { frontier_warp<4, true, true>(A); }
 
 // ------------------------------------------------------------------ K4
 // counts[c] = sum over replicas of the scar bit of c.  Each thread owns one

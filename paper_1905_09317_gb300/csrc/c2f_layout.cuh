@@ -77,6 +77,7 @@ struct FrontierArgs {
   int64_t pw_max;                 // words per bit plane of the largest landscape
   uint32_t *brn_scratch;          // [slots][pw_max] Burned planes
   uint32_t *avail_scratch;        // [slots][pw_max] Available planes (global-plane variant)
+  int64_t smem_warp_words;        // 32-bit words of dynamic shared memory per warp
 };
 
 // K1 launch arguments: grid.y covers hours hour0 .. hour0 + gridDim.y - 1

@@ -46,6 +46,12 @@ __global__ void k_frontier_g4(FrontierArgs);
 __global__ void k_frontier_s1(FrontierArgs);
 __global__ void k_frontier_s2(FrontierArgs);
 __global__ void k_frontier_s4(FrontierArgs);
+__global__ void k_frontier_gl1(FrontierArgs);
+__global__ void k_frontier_gl2(FrontierArgs);
+__global__ void k_frontier_gl4(FrontierArgs);
+__global__ void k_frontier_sl1(FrontierArgs);
+__global__ void k_frontier_sl2(FrontierArgs);
+__global__ void k_frontier_sl4(FrontierArgs);
 __global__ void k_burn_prob(const uint32_t *, int32_t, int32_t, int32_t, int32_t, int32_t,
                             uint32_t *, int32_t);
 __global__ void k_scar_bytes(const uint32_t *, int32_t, int32_t, int32_t, int32_t, uint8_t *);
@@ -130,6 +136,7 @@ struct c2f_ctx {
   int smem_optin = 0;
   int64_t smem_plane_limit = 0;            // Available plane staged in shared memory up to this size
   int frontier_threads = 128;
+  bool list_smem = true;                   // burning-list arrays in shared memory when they fit
   int64_t cap_override = 0;
   // kernel timing
   bool profiling = false;
@@ -324,7 +331,7 @@ Sim *find_sim(c2f_ctx *ctx, int32_t id) {
 
 int64_t default_cap(const c2f_ctx *ctx, const Landscape &L) {
   if (ctx->cap_override > 0) return std::min<int64_t>(L.n, ctx->cap_override);
-  const int64_t c = std::max<int64_t>(4096, 8 * (int64_t)(L.rows + L.cols));
+  const int64_t c = std::max<int64_t>(1024, 2 * (int64_t)(L.rows + L.cols));
   return std::min<int64_t>(L.n, c);
 }
 
@@ -424,21 +431,32 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
   int64_t pw_max = 0;
   for (int32_t i = 0; i < nj; ++i) pw_max = std::max<int64_t>(pw_max, (int64_t)lands[i]->rows * lands[i]->wpr);
   const size_t plane_bytes = (size_t)pw_max * 4;
-  const bool use_smem = (int64_t)plane_bytes <= ctx->smem_plane_limit &&
-                        (int64_t)plane_bytes <= (int64_t)ctx->smem_optin - 4096;
   const int threads = ctx->frontier_threads;   // 32, 64 or 128: one replica per warp
   const int wpc = threads / 32;
-  void (*kern)(FrontierArgs) =
-      use_smem ? (wpc == 1 ? k_frontier_s1 : wpc == 2 ? k_frontier_s2 : k_frontier_s4)
-               : (wpc == 1 ? k_frontier_g1 : wpc == 2 ? k_frontier_g2 : k_frontier_g4);
-  const size_t dyn_smem = use_smem ? plane_bytes * wpc : 0;
-  if (use_smem) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem));
-  int bps = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, threads, dyn_smem));
-  bps = std::max(bps, 1);
   std::vector<int64_t> items;  // empty: all
   for (int attempt = 0;; ++attempt) {
     const int64_t todo = items.empty() ? n_items : (int64_t)items.size();
+    // launch shape: Available plane and/or list arrays in shared memory when they fit
+    cap = (cap + 3) & ~int64_t(3);
+    const bool use_smem = (int64_t)plane_bytes <= ctx->smem_plane_limit;
+    const int64_t list_bytes = cap * 14;
+    const int64_t budget = (int64_t)ctx->smem_optin - 2048;
+    const bool use_lsmem = ctx->list_smem &&
+                           ((use_smem ? (int64_t)plane_bytes : 0) + list_bytes) * wpc <= budget;
+    const int64_t warp_words = (use_smem ? pw_max : 0) + (use_lsmem ? cap * 7 / 2 : 0);
+    void (*kern)(FrontierArgs);
+    if (use_lsmem)
+      kern = use_smem ? (wpc == 1 ? k_frontier_sl1 : wpc == 2 ? k_frontier_sl2 : k_frontier_sl4)
+                      : (wpc == 1 ? k_frontier_gl1 : wpc == 2 ? k_frontier_gl2 : k_frontier_gl4);
+    else
+      kern = use_smem ? (wpc == 1 ? k_frontier_s1 : wpc == 2 ? k_frontier_s2 : k_frontier_s4)
+                      : (wpc == 1 ? k_frontier_g1 : wpc == 2 ? k_frontier_g2 : k_frontier_g4);
+    const size_t dyn_smem = (size_t)warp_words * 4 * wpc;
+    if (dyn_smem > 0)
+      CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem));
+    int bps = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, threads, dyn_smem));
+    bps = std::max(bps, 1);
     const int64_t max_ctas = (int64_t)ctx->sm_count * bps;
     int64_t ctas = std::min<int64_t>((todo + wpc - 1) / wpc, max_ctas);
     if (attempt > 0) ctas = std::min<int64_t>(ctas, std::max<int64_t>(1, ctx->sm_count));
@@ -474,6 +492,7 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
     A.pw_max = pw_max;
     A.brn_scratch = ctx->brn_scratch.as<uint32_t>();
     A.avail_scratch = use_smem ? nullptr : ctx->avail_scratch.as<uint32_t>();
+    A.smem_warp_words = warp_words;
     CK(cudaMemsetAsync(ctx->counter.p, 0, 8, ctx->stream));
     {
       ProfScope prof(ctx, 2);
