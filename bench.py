@@ -343,7 +343,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--frontier-threads", type=int, default=0,
                     help="frontier CTA size (64/128/256); 0 = library default")
-    ap.add_argument("--smem-plane-bytes", type=int, default=49152)
+    ap.add_argument("--smem-plane-bytes", type=int, default=1, help="0 = frontier state in global memory")
     ap.add_argument("--cpu-sample", type=int, default=1000)
     ap.add_argument("--ref-sample", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -175,10 +175,11 @@ C2F_API int c2f_get_counters(c2f_ctx *ctx, int32_t sim_id, int64_t *work, int32_
 C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap);
 
 /* Frontier-kernel launch shape: CTA size `threads` (32, 64 or 128; each warp
- * simulates one replica) and the largest per-replica Available bit plane
- * (bytes) staged in shared memory instead of global memory (0 = always
- * global).  Results do not depend on either; they are tuning knobs. */
-C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem_plane_bytes);
+ * simulates one replica) and whether a window of each replica's bit planes
+ * and its burning list are staged in shared memory (`smem` != 0, the default)
+ * or kept in global memory (0).  Results do not depend on either; they are
+ * tuning knobs. */
+C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem);
 
 /* Kernel timing: with profiling on, the context brackets each launch of its
  * kernel families with CUDA events on its stream.  c2f_kernel_times waits for

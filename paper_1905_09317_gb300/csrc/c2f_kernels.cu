@@ -274,35 +274,6 @@ __device__ inline bool receive_ok(const SimJob &J, int32_t r, int64_t j, int32_t
   return __dmul_rn(hr, (double)f) > J.thr;
 }
 
-// true if some neighbour of (r, c) is still Available (bit set in the
-// Available plane: burnable, not harvested, not ignited)
-__device__ inline bool has_available_nbr(const uint32_t *avail, int32_t wpr, int32_t rows,
-                                         int32_t cols, int32_t r, int32_t c) {
-  uint32_t words[3][2];
-  const int32_t c0 = c > 0 ? c - 1 : 0, c1 = c + 1 < cols ? c + 1 : cols - 1;
-  const int32_t w0 = c0 >> 5, w1 = c1 >> 5;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int32_t rr = r - 1 + d;
-    const bool ok = rr >= 0 && rr < rows;
-    words[d][0] = ok ? avail[rr * wpr + w0] : 0u;
-    words[d][1] = ok ? avail[rr * wpr + w1] : 0u;
-  }
-  bool any = false;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-#pragma unroll
-    for (int dc = -1; dc <= 1; ++dc) {
-      if (d == 1 && dc == 0) continue;
-      const int32_t cc = c + dc;
-      if (cc < 0 || cc >= cols) continue;
-      const uint32_t w = ((cc >> 5) == w0) ? words[d][0] : words[d][1];
-      any |= ((w >> (cc & 31)) & 1u) != 0;
-    }
-  }
-  return any;
-}
-
 __device__ __forceinline__ int64_t find_job(const int64_t *begin, int32_t n, int64_t item) {
   int32_t lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -351,9 +322,83 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-template <int WPC, bool SMEM, bool LSMEM>
+// The replica's Available and Burned bit planes.  With WIN, a window of
+// kWinRows x (32 kWinWords) cells around the ignition cell lives in shared
+// memory and the rest of the grid in global memory; without it, all in global
+// memory.  Accessors hand out a pointer to the 32-bit word holding (r, c).
+template <bool WIN>
+struct Planes {
+  uint32_t *sav, *sbr;   // shared-memory windows
+  uint32_t *gav, *gbr;   // full planes, global memory
+  int32_t r0, w0, wpr;
+  __device__ __forceinline__ bool in_win(int32_t r, int32_t w) const {
+    if constexpr (WIN) return (uint32_t)(r - r0) < (uint32_t)kWinRows && (uint32_t)(w - w0) < (uint32_t)kWinWords;
+    else return false;
+  }
+  __device__ __forceinline__ uint32_t *avw(int32_t r, int32_t c) const {
+    const int32_t w = c >> 5;
+    if (in_win(r, w)) return sav + (r - r0) * kWinWords + (w - w0);
+    return gav + r * wpr + w;
+  }
+  __device__ __forceinline__ uint32_t *brw(int32_t r, int32_t c) const {
+    const int32_t w = c >> 5;
+    if (in_win(r, w)) return sbr + (r - r0) * kWinWords + (w - w0);
+    return gbr + r * wpr + w;
+  }
+  __device__ __forceinline__ bool avail(int32_t r, int32_t c) const { return (*avw(r, c) >> (c & 31)) & 1u; }
+  __device__ __forceinline__ bool burned(int32_t r, int32_t c) const { return (*brw(r, c) >> (c & 31)) & 1u; }
+  // ignition: clears the Available bit; true for the one caller that cleared it
+  __device__ __forceinline__ bool take(int32_t r, int32_t c) const {
+    const uint32_t bit = 1u << (c & 31);
+    return (atomicAnd(avw(r, c), ~bit) & bit) != 0;
+  }
+  // burn-out: sets the Burned bit; true for the one caller that set it
+  __device__ __forceinline__ bool burn(int32_t r, int32_t c) const {
+    const uint32_t bit = 1u << (c & 31);
+    return (atomicOr(brw(r, c), bit) & bit) == 0;
+  }
+  // some neighbour of (r, c) is still Available
+  __device__ __forceinline__ bool any_avail_nbr(int32_t rows, int32_t cols, int32_t r, int32_t c) const {
+    uint32_t words[3][2];
+    const int32_t c0 = c > 0 ? c - 1 : 0, c1 = c + 1 < cols ? c + 1 : cols - 1;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int32_t rr = r - 1 + d;
+      const bool ok = rr >= 0 && rr < rows;
+      words[d][0] = ok ? *avw(rr, c0) : 0u;
+      words[d][1] = ok ? *avw(rr, c1) : 0u;
+    }
+    bool any = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int dc = -1; dc <= 1; ++dc) {
+        if (d == 1 && dc == 0) continue;
+        const int32_t cc = c + dc;
+        if (cc < 0 || cc >= cols) continue;
+        const uint32_t w = ((cc >> 5) == (c0 >> 5)) ? words[d][0] : words[d][1];
+        any |= ((w >> (cc & 31)) & 1u) != 0;
+      }
+    }
+    return any;
+  }
+};
+
+// One warp per replica; replicas come from a work list of (simulation,
+// replica) items that every warp pulls from.  The four 8-lane groups of the
+// warp each take one burning cell at a time, lane k owning axis k, so the
+// per-axis work of a cell (crossing tests, increments, crossing periods, the
+// burn-out test of the neighbour on that axis) runs side by side.  There is
+// no CTA barrier: the warp's counters stay in registers, appends to the
+// burning list are placed by ballot + popc, and phases are ordered with
+// __syncwarp.  Per replica: an Available plane (burnable, not harvested, not
+// yet ignited -- an ignition is one atomicAnd, whose old value also picks the
+// single winner) and a Burned plane; with WIN their window around the
+// ignition cell and the burning-list arrays sit in shared memory.  The scar
+// plane (burnable and no longer Available) is written at the end.
+template <int WPC, bool WIN>
 __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
-  extern __shared__ __align__(16) uint32_t s_planes[];
+  extern __shared__ __align__(16) uint32_t s_dyn[];
   __shared__ SimJob s_job[WPC];
   constexpr uint32_t FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -361,27 +406,28 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
   const uint32_t lt = (1u << lane) - 1u;
   const size_t slot = (size_t)blockIdx.x * WPC + wib;
   const int32_t cap = A.cap;
-  // per-warp shared memory: [Available plane (SMEM)][list arrays (LSMEM)]
-  uint32_t *my_smem = s_planes + (size_t)wib * A.smem_warp_words;
+  uint32_t *my = s_dyn + (size_t)wib * A.smem_warp_words;   // [Available win][Burned win][lists]
   uint32_t *erc;     // row << 16 | col
   uint8_t *emask, *enext, *ecofs;
-  if constexpr (LSMEM) {
-    uint32_t *ls = my_smem + (SMEM ? A.pw_max : 0);
+  Planes<WIN> pl;
+  pl.gav = A.avail_scratch + slot * (size_t)A.pw_max;
+  pl.gbr = A.brn_scratch + slot * (size_t)A.pw_max;
+  if constexpr (WIN) {
+    pl.sav = my;
+    pl.sbr = my + kWinRows * kWinWords;
+    uint32_t *ls = my + 2 * kWinRows * kWinWords;
     erc = ls;
     ecofs = reinterpret_cast<uint8_t *>(ls + cap);
     emask = reinterpret_cast<uint8_t *>(ls + 3 * (size_t)cap);
     enext = emask + cap;
   } else {
+    pl.sav = pl.sbr = nullptr;
     erc = reinterpret_cast<uint32_t *>(A.ent_cell) + slot * cap;
     emask = A.ent_mask + slot * cap;
     enext = A.ent_next + slot * cap;
     ecofs = A.ent_cofs + slot * (size_t)cap * 8;
   }
   int64_t *eP = A.ent_P + slot * (size_t)cap * 8;
-  uint32_t *av;
-  if constexpr (SMEM) av = my_smem;
-  else av = A.avail_scratch + slot * (size_t)A.pw_max;
-  uint32_t *brn = A.brn_scratch + slot * (size_t)A.pw_max;
   SimJob &J = s_job[wib];
 
   for (;;) {
@@ -411,30 +457,43 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
     const uint32_t *burnable = J.burnable;
     int32_t *istep = J.ign_step ? J.ign_step + (size_t)r * n : nullptr;
     const int64_t dk = (k & 1) ? J.d_diag : J.d_orth;   // this lane's axis length
-    for (int32_t i = lane; i < pw; i += 32) { av[i] = __ldg(&burnable[i]); brn[i] = 0u; }
+    const int32_t ic = J.ign_cell[r];
+    const int32_t ir = ic / cols, icc = ic - ir * cols;
+    pl.wpr = wpr;
+    bool need_global = true;
+    if constexpr (WIN) {   // window centred on the ignition cell, clamped to the grid
+      pl.r0 = min(max(ir - kWinRows / 2, 0), max(rows - kWinRows, 0));
+      pl.w0 = min(max((icc >> 5) - kWinWords / 2, 0), max(wpr - kWinWords, 0));
+      need_global = rows > kWinRows || wpr > kWinWords;
+      for (int32_t i = lane; i < kWinRows * kWinWords; i += 32) {
+        const int32_t rr = pl.r0 + i / kWinWords, ww = pl.w0 + i % kWinWords;
+        pl.sav[i] = (rr < rows && ww < wpr) ? __ldg(&burnable[rr * wpr + ww]) : 0u;
+        pl.sbr[i] = 0u;
+      }
+    }
+    if (need_global)
+      for (int32_t i = lane; i < pw; i += 32) { pl.gav[i] = __ldg(&burnable[i]); pl.gbr[i] = 0u; }
     __syncwarp();
 
     // Step 1 of Alg. 1: the ignition cell burns from period 0
     int32_t live = 1, nign = 1, cnt = 1, status = 0;
     long long W = 0, s_done = 0;
     {
-      const int32_t ic = J.ign_cell[r];
-      const int32_t ir = ic / cols, icc = ic - ir * cols;
       if (lane == 0) {
-        atomicAnd(&av[ir * wpr + (icc >> 5)], ~(1u << (icc & 31)));
+        pl.take(ir, icc);
         if (istep) istep[ic] = 0;
       }
       __syncwarp();
       bool open = false;
       if (lane < 8) {
         const int32_t nr = ir + kDR[k], nc = icc + kDC[k];
-        open = nr >= 0 && nr < rows && nc >= 0 && nc < cols && plane_bit(av, wpr, nr, nc);
+        open = nr >= 0 && nr < rows && nc >= 0 && nc < cols && pl.avail(nr, nc);
       }
       const uint32_t mask0 = __ballot_sync(FULL, open) & 0xFFu;
       if (lane < 8) { eP[k] = 0; ecofs[k] = kNone; }
       if (lane == 0) { erc[0] = rc_pack(ir, icc); emask[0] = (uint8_t)mask0; enext[0] = kNone; }
       if (mask0 == 0) {   // no Available neighbour: Burned at the end of period 1
-        if (lane == 0) atomicOr(&brn[ir * wpr + (icc >> 5)], 1u << (icc & 31));
+        if (lane == 0) pl.burn(ir, icc);
         live = 0;
         W = (H * sph >= 1) ? 1 : 0;
       }
@@ -447,7 +506,8 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       const double *hrosh = J.hros + (size_t)h * n;
       int32_t burned = 0;   // cells Burned at the end of the period being visited
 
-      // ---- hour boundary (i): drop Burned cells and cells with no open axis
+      // ---- hour boundary (i): drop Burned cells and cells with no open axis;
+      // prefetch the kept cells' table rows for (ii)
       {
         int32_t out = 0;
         for (int32_t b0 = 0; b0 < cnt; b0 += 32) {
@@ -458,8 +518,10 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           if (e < cnt) {
             rc = erc[e];
             m = emask[e];
-            keep = m != 0 && !plane_bit(brn, wpr, (int32_t)(rc >> 16), (int32_t)(rc & 0xFFFFu));
+            const int32_t cr = (int32_t)(rc >> 16), cc = (int32_t)(rc & 0xFFFFu);
+            keep = m != 0 && !pl.burned(cr, cc);
             if (keep) {
+              prefetch_l2(baseh + ((int64_t)cr * cols + cc) * 8);
 #pragma unroll
               for (int q = 0; q < 8; ++q) P[q] = eP[(size_t)e * 8 + q];
             }
@@ -497,7 +559,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         for (int u = 0; u < 4; ++u) {
           const int32_t cr = (int32_t)(rcu[u] >> 16), cc = (int32_t)(rcu[u] & 0xFFFFu);
           bool open = actu[u] && ((mu[u] >> k) & 1u);
-          if (open) open = plane_bit(av, wpr, cr + kDR[k], cc + kDC[k]);
+          if (open) open = pl.avail(cr + kDR[k], cc + kDC[k]);
           openu[u] = open;
           bku[u] = open ? baseh[((int64_t)cr * cols + cc) * 8 + k] : 0;
         }
@@ -525,10 +587,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
               else P += inc * sph;
             }
             if (delta > 0.0 && __dmul_rn(hrosh[cell], (double)fu[u]) < delta) {   // A5 (i)
-              if (k == 0) {
-                const uint32_t bit = 1u << (cc & 31);
-                dying = !(atomicOr(&brn[cr * wpr + (cc >> 5)], bit) & bit);
-              }
+              if (k == 0) dying = pl.burn(cr, cc);
               if (cof != 0) cof = kNone;   // still sends in period s0, Burned after it
             }
           }
@@ -566,9 +625,9 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
               src[q] = hits ? __ffs(hits) - 1 : -1;
               if (hits) hits &= hits - 1;
             }
-            const int my = src[grp];
-            int32_t ent = __shfl_sync(FULL, e, my < 0 ? 0 : my);
-            if (my < 0) ent = -1;
+            const int my_src = src[grp];
+            int32_t ent = __shfl_sync(FULL, e, my_src < 0 ? 0 : my_src);
+            if (my_src < 0) ent = -1;
             uint32_t cof = kNone, wrc = 0;
             int64_t jc = 0;
             bool crossed = false, won = false;
@@ -579,11 +638,10 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
                 cof = kNone;
                 const uint32_t rc = erc[ent];
                 const int32_t nr = (int32_t)(rc >> 16) + kDR[k], nc = (int32_t)(rc & 0xFFFFu) + kDC[k];
-                if (plane_bit(av, wpr, nr, nc)) {                         // Available
+                if (pl.avail(nr, nc)) {                                    // Available
                   jc = (int64_t)nr * cols + nc;
                   if (gate_free || receive_ok(J, r, jc, h, n)) {           // else consumed
-                    const uint32_t bit = 1u << (nc & 31);
-                    won = (atomicAnd(&av[nr * wpr + (nc >> 5)], ~bit) & bit) != 0;
+                    won = pl.take(nr, nc);
                     wrc = rc_pack(nr, nc);
                   }
                 }
@@ -621,7 +679,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           const int32_t nr = cr + kDR[k], nc = cc + kDC[k];
           const bool ingrid = act && nr >= 0 && nr < rows && nc >= 0 && nc < cols;
           const int64_t bk = act ? baseh[cell * 8 + k] : 0;   // issue the table load early
-          const bool open = ingrid && plane_bit(av, wpr, nr, nc);
+          const bool open = ingrid && pl.avail(nr, nc);
           const bool ignq = ingrid && !open && ((__ldg(&burnable[nr * wpr + (nc >> 5)]) >> (nc & 31)) & 1u);
           const uint32_t omask = group_bits(open);
           uint32_t mask = omask;
@@ -652,16 +710,11 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
               emask[e] = (uint8_t)mask;
               enext[e] = (uint8_t)nx;
               lmin = min(lmin, nx);
-              if (omask == 0 || dies) {   // this cell: A5 (ii) no Available neighbour, or (i)
-                const uint32_t bit = 1u << (cc & 31);
-                newly += (atomicOr(&brn[cr * wpr + (cc >> 5)], bit) & bit) ? 0u : 1u;
-              }
+              if (omask == 0 || dies)   // this cell: A5 (ii) no Available neighbour, or (i)
+                newly += pl.burn(cr, cc) ? 1u : 0u;
             }
             // A5 (ii) for the ignited neighbour on this lane's axis
-            if (ignq && !has_available_nbr(av, wpr, rows, cols, nr, nc)) {
-              const uint32_t bit = 1u << (nc & 31);
-              newly += (atomicOr(&brn[nr * wpr + (nc >> 5)], bit) & bit) ? 0u : 1u;
-            }
+            if (ignq && !pl.any_avail_nbr(rows, cols, nr, nc)) newly += pl.burn(nr, nc) ? 1u : 0u;
           }
           burned += (int32_t)__reduce_add_sync(FULL, newly);
         }
@@ -682,7 +735,13 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
     }
     {   // scar plane: burnable cells that are no longer Available
       uint32_t *dst = J.ign_plane + (size_t)r * pw;
-      for (int32_t i = lane; i < pw; i += 32) dst[i] = __ldg(&burnable[i]) & ~av[i];
+      for (int32_t i = lane; i < pw; i += 32) {
+        const int32_t rr = i / wpr, ww = i - rr * wpr;
+        uint32_t a;
+        if (pl.in_win(rr, ww)) a = pl.sav[(rr - pl.r0) * kWinWords + (ww - pl.w0)];
+        else a = pl.gav[i];
+        dst[i] = __ldg(&burnable[i]) & ~a;
+      }
     }
     if (lane == 0) {
       J.work[r] = W;
@@ -693,23 +752,14 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
   }
 }
 
-// Variants: warps per CTA (1, 2, 4) with the Available plane in global
-// memory (g) or shared memory (s).
-// Variants: warps per CTA (1, 2, 4); the Available plane in global (g) or
-// shared (s) memory; the burning-list arrays in global memory or, for the
-// "l" variants, in shared memory.
-__global__ void __launch_bounds__(32) k_frontier_g1(FrontierArgs A) { frontier_warp<1, false, false>(A); }
-__global__ void __launch_bounds__(64) k_frontier_g2(FrontierArgs A) { frontier_warp<2, false, false>(A); }
-__global__ void __launch_bounds__(128) k_frontier_g4(FrontierArgs A) { frontier_warp<4, false, false>(A); }
-__global__ void __launch_bounds__(32) k_frontier_s1(FrontierArgs A) { frontier_warp<1, true, false>(A); }
-__global__ void __launch_bounds__(64) k_frontier_s2(FrontierArgs A) { frontier_warp<2, true, false>(A); }
-__global__ void __launch_bounds__(128) k_frontier_s4(FrontierArgs A) { frontier_warp<4, true, false>(A); }
-__global__ void __launch_bounds__(32) k_frontier_gl1(FrontierArgs A) { frontier_warp<1, false, true>(A); }
-__global__ void __launch_bounds__(64) k_frontier_gl2(FrontierArgs A) { frontier_warp<2, false, true>(A); }
-__global__ void __launch_bounds__(128) k_frontier_gl4(FrontierArgs A) { frontier_warp<4, false, true>(A); }
-__global__ void __launch_bounds__(32) k_frontier_sl1(FrontierArgs A) { frontier_warp<1, true, true>(A); }
-__global__ void __launch_bounds__(64) k_frontier_sl2(FrontierArgs A) { frontier_warp<2, true, true>(A); }
-__global__ void __launch_bounds__(128) k_frontier_sl4(FrontierArgs A) { frontier_warp<4, true, true>(A); }
+// Variants: warps per CTA (1, 2, 4); planes windowed and lists in shared
+// memory (w), or everything in global memory (g).
+__global__ void __launch_bounds__(32) k_frontier_g1(FrontierArgs A) { frontier_warp<1, false>(A); }
+__global__ void __launch_bounds__(64) k_frontier_g2(FrontierArgs A) { frontier_warp<2, false>(A); }
+__global__ void __launch_bounds__(128) k_frontier_g4(FrontierArgs A) { frontier_warp<4, false>(A); }
+__global__ void __launch_bounds__(32) k_frontier_w1(FrontierArgs A) { frontier_warp<1, true>(A); }
+__global__ void __launch_bounds__(64) k_frontier_w2(FrontierArgs A) { frontier_warp<2, true>(A); }
+__global__ void __launch_bounds__(128) k_frontier_w4(FrontierArgs A) { frontier_warp<4, true>(A); }
 
 // ------------------------------------------------------------------ K4
 // counts[c] = sum over replicas of the scar bit of c.  Each thread owns one

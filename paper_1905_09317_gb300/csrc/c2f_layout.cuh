@@ -101,5 +101,8 @@ struct RosTableArgs {
 constexpr int kOrderBuckets = 2 * 16;   // (fuel code, slope > 0); code 0 = not burnable
 
 constexpr uint8_t kNone = 0xFF;
+// shared-memory window of the per-replica bit planes: kWinRows x (32 kWinWords) cells
+constexpr int kWinRows = 256;
+constexpr int kWinWords = 8;
 
 }  // namespace c2f

@@ -43,15 +43,9 @@ __global__ void k_ignite(const SimJob *, int32_t);
 __global__ void k_frontier_g1(FrontierArgs);
 __global__ void k_frontier_g2(FrontierArgs);
 __global__ void k_frontier_g4(FrontierArgs);
-__global__ void k_frontier_s1(FrontierArgs);
-__global__ void k_frontier_s2(FrontierArgs);
-__global__ void k_frontier_s4(FrontierArgs);
-__global__ void k_frontier_gl1(FrontierArgs);
-__global__ void k_frontier_gl2(FrontierArgs);
-__global__ void k_frontier_gl4(FrontierArgs);
-__global__ void k_frontier_sl1(FrontierArgs);
-__global__ void k_frontier_sl2(FrontierArgs);
-__global__ void k_frontier_sl4(FrontierArgs);
+__global__ void k_frontier_w1(FrontierArgs);
+__global__ void k_frontier_w2(FrontierArgs);
+__global__ void k_frontier_w4(FrontierArgs);
 __global__ void k_burn_prob(const uint32_t *, int32_t, int32_t, int32_t, int32_t, int32_t,
                             uint32_t *, int32_t);
 __global__ void k_scar_bytes(const uint32_t *, int32_t, int32_t, int32_t, int32_t, uint8_t *);
@@ -134,9 +128,8 @@ struct c2f_ctx {
   DevBuf ent_cell, ent_mask, ent_next, ent_cofs, ent_P, counter, brn_scratch, avail_scratch;
   int64_t scratch_slots = 0, scratch_cap = 0, brn_words = 0, avail_words = 0;
   int smem_optin = 0;
-  int64_t smem_plane_limit = 0;            // Available plane staged in shared memory up to this size
   int frontier_threads = 128;
-  bool list_smem = true;                   // burning-list arrays in shared memory when they fit
+  bool window_smem = true;                 // plane windows + lists in shared memory when they fit
   int64_t cap_override = 0;
   // kernel timing
   bool profiling = false;
@@ -430,27 +423,21 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
   }
   int64_t pw_max = 0;
   for (int32_t i = 0; i < nj; ++i) pw_max = std::max<int64_t>(pw_max, (int64_t)lands[i]->rows * lands[i]->wpr);
-  const size_t plane_bytes = (size_t)pw_max * 4;
   const int threads = ctx->frontier_threads;   // 32, 64 or 128: one replica per warp
   const int wpc = threads / 32;
   std::vector<int64_t> items;  // empty: all
   for (int attempt = 0;; ++attempt) {
     const int64_t todo = items.empty() ? n_items : (int64_t)items.size();
-    // launch shape: Available plane and/or list arrays in shared memory when they fit
+    // launch shape: plane windows and list arrays in shared memory when the
+    // list fits beside them, else everything in global memory
     cap = (cap + 3) & ~int64_t(3);
-    const bool use_smem = (int64_t)plane_bytes <= ctx->smem_plane_limit;
-    const int64_t list_bytes = cap * 14;
     const int64_t budget = (int64_t)ctx->smem_optin - 2048;
-    const bool use_lsmem = ctx->list_smem &&
-                           ((use_smem ? (int64_t)plane_bytes : 0) + list_bytes) * wpc <= budget;
-    const int64_t warp_words = (use_smem ? pw_max : 0) + (use_lsmem ? cap * 7 / 2 : 0);
-    void (*kern)(FrontierArgs);
-    if (use_lsmem)
-      kern = use_smem ? (wpc == 1 ? k_frontier_sl1 : wpc == 2 ? k_frontier_sl2 : k_frontier_sl4)
-                      : (wpc == 1 ? k_frontier_gl1 : wpc == 2 ? k_frontier_gl2 : k_frontier_gl4);
-    else
-      kern = use_smem ? (wpc == 1 ? k_frontier_s1 : wpc == 2 ? k_frontier_s2 : k_frontier_s4)
-                      : (wpc == 1 ? k_frontier_g1 : wpc == 2 ? k_frontier_g2 : k_frontier_g4);
+    const int64_t win_words = 2 * (int64_t)kWinRows * kWinWords + cap * 7 / 2;
+    const bool use_win = ctx->window_smem && win_words * 4 * wpc <= budget;
+    const int64_t warp_words = use_win ? win_words : 0;
+    void (*kern)(FrontierArgs) =
+        use_win ? (wpc == 1 ? k_frontier_w1 : wpc == 2 ? k_frontier_w2 : k_frontier_w4)
+                : (wpc == 1 ? k_frontier_g1 : wpc == 2 ? k_frontier_g2 : k_frontier_g4);
     const size_t dyn_smem = (size_t)warp_words * 4 * wpc;
     if (dyn_smem > 0)
       CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem));
@@ -466,7 +453,7 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
       if ((rc = dalloc(ctx, ctx->brn_scratch, (size_t)slots * pw_max * 4))) return rc;
       ctx->brn_words = slots * pw_max;
     }
-    if (!use_smem && slots * pw_max > ctx->avail_words) {
+    if (slots * pw_max > ctx->avail_words) {
       if ((rc = dalloc(ctx, ctx->avail_scratch, (size_t)slots * pw_max * 4))) return rc;
       ctx->avail_words = slots * pw_max;
     }
@@ -491,7 +478,7 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
     A.ent_P = ctx->ent_P.as<int64_t>();
     A.pw_max = pw_max;
     A.brn_scratch = ctx->brn_scratch.as<uint32_t>();
-    A.avail_scratch = use_smem ? nullptr : ctx->avail_scratch.as<uint32_t>();
+    A.avail_scratch = ctx->avail_scratch.as<uint32_t>();
     A.smem_warp_words = warp_words;
     CK(cudaMemsetAsync(ctx->counter.p, 0, 8, ctx->stream));
     {
@@ -914,13 +901,13 @@ C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap) {
   return C2F_OK;
 }
 
-C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem_plane_bytes) {
+C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem) {
   if (!ctx) return C2F_EINVAL;
   if (threads != 32 && threads != 64 && threads != 128)
     return fail(ctx, C2F_EINVAL, "threads must be 32, 64 or 128 (one replica per warp)");
-  if (smem_plane_bytes < 0) return fail(ctx, C2F_EINVAL, "smem_plane_bytes must be >= 0");
+  if (smem < 0) return fail(ctx, C2F_EINVAL, "smem must be >= 0");
   ctx->frontier_threads = threads;
-  ctx->smem_plane_limit = smem_plane_bytes;
+  ctx->window_smem = smem != 0;
   return C2F_OK;
 }
 
