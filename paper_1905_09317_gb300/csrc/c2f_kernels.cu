@@ -428,6 +428,8 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
     ecofs = A.ent_cofs + slot * (size_t)cap * 8;
   }
   int64_t *eP = A.ent_P + slot * (size_t)cap * 8;
+  __shared__ int32_t s_hits[WPC][64];
+  int32_t *hitbuf = s_hits[wib];
   SimJob &J = s_job[wib];
 
   for (;;) {
@@ -467,12 +469,17 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       need_global = rows > kWinRows || wpr > kWinWords;
       for (int32_t i = lane; i < kWinRows * kWinWords; i += 32) {
         const int32_t rr = pl.r0 + i / kWinWords, ww = pl.w0 + i % kWinWords;
-        pl.sav[i] = (rr < rows && ww < wpr) ? __ldg(&burnable[rr * wpr + ww]) : 0u;
-        pl.sbr[i] = 0u;
+        const uint32_t b = (rr < rows && ww < wpr) ? __ldg(&burnable[rr * wpr + ww]) : 0u;
+        pl.sav[i] = b;
+        pl.sbr[i] = ~b;   // cells that never burn count as Burned already
       }
     }
     if (need_global)
-      for (int32_t i = lane; i < pw; i += 32) { pl.gav[i] = __ldg(&burnable[i]); pl.gbr[i] = 0u; }
+      for (int32_t i = lane; i < pw; i += 32) {
+        const uint32_t b = __ldg(&burnable[i]);
+        pl.gav[i] = b;
+        pl.gbr[i] = ~b;
+      }
     __syncwarp();
 
     // Step 1 of Alg. 1: the ignition cell burns from period 0
@@ -611,39 +618,51 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         uint32_t lmin = kNone;
         int32_t nnew = cnt;
         bool ovf = false;
-        // (A) send and receive: cells with a crossing at offset o
-        for (int32_t b0 = 0; b0 < cnt; b0 += 32) {
-          const int32_t e = b0 + lane;
-          const uint32_t nxe = (e < cnt) ? (uint32_t)enext[e] : kNone;
-          const bool hit = nxe == o;
-          if (!hit) lmin = min(lmin, nxe);
-          uint32_t hits = __ballot_sync(FULL, hit);
-          while (hits) {
-            int src[4];
+        // (A) send and receive: cells with a crossing at offset o.  Hits are
+        // gathered across the whole list, then each lane takes one hit cell:
+        // its 8 crossing offsets in one load, every axis crossing at o handled
+        // in turn (targets tested, ignited, appended by ballot + popc).
+        int32_t hbase = 0;   // hits gathered so far in the buffer
+        for (int32_t b0 = 0; b0 < cnt || hbase > 0; b0 += 32) {
+          if (b0 < cnt) {
+            const int32_t e = b0 + lane;
+            const uint32_t nxe = (e < cnt) ? (uint32_t)enext[e] : kNone;
+            const bool hit = nxe == o;
+            if (!hit) lmin = min(lmin, nxe);
+            const uint32_t hits = __ballot_sync(FULL, hit);
+            if (hit) hitbuf[hbase + __popc(hits & lt)] = e;
+            hbase += __popc(hits);
+            __syncwarp();
+            if (hbase < 32 && b0 + 32 < cnt) continue;   // gather a full round first
+          }
+          const int32_t take_n = min(hbase, 32);
+          const int32_t ent = lane < take_n ? hitbuf[lane] : -1;
+          uint64_t cof8 = ~0ull;
+          uint32_t rc = 0;
+          if (ent >= 0) {
+            cof8 = *reinterpret_cast<const uint64_t *>(ecofs + (size_t)ent * 8);
+            rc = erc[ent];
+          }
+          // crossing axes of this lane's cell as an 8-bit mask
+          uint32_t cm = 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              src[q] = hits ? __ffs(hits) - 1 : -1;
-              if (hits) hits &= hits - 1;
-            }
-            const int my_src = src[grp];
-            int32_t ent = __shfl_sync(FULL, e, my_src < 0 ? 0 : my_src);
-            if (my_src < 0) ent = -1;
-            uint32_t cof = kNone, wrc = 0;
+          for (int q = 0; q < 8; ++q) cm |= (((cof8 >> (8 * q)) & 0xFFull) == o ? 1u : 0u) << q;
+          const int32_t cr = (int32_t)(rc >> 16), cc = (int32_t)(rc & 0xFFFFu);
+          uint32_t todo = cm;
+          const int rounds = (int)__reduce_max_sync(FULL, (uint32_t)__popc(cm));
+          for (int it2 = 0; it2 < rounds; ++it2) {
+            bool won = false;
+            uint32_t wrc = 0;
             int64_t jc = 0;
-            bool crossed = false, won = false;
-            if (ent >= 0) {
-              cof = ecofs[(size_t)ent * 8 + k];
-              crossed = cof == o;
-              if (crossed) {
-                cof = kNone;
-                const uint32_t rc = erc[ent];
-                const int32_t nr = (int32_t)(rc >> 16) + kDR[k], nc = (int32_t)(rc & 0xFFFFu) + kDC[k];
-                if (pl.avail(nr, nc)) {                                    // Available
-                  jc = (int64_t)nr * cols + nc;
-                  if (gate_free || receive_ok(J, r, jc, h, n)) {           // else consumed
-                    won = pl.take(nr, nc);
-                    wrc = rc_pack(nr, nc);
-                  }
+            if (todo) {
+              const int q = __ffs(todo) - 1;
+              todo &= todo - 1;
+              const int32_t nr = cr + kDR[q], nc = cc + kDC[q];
+              if (pl.avail(nr, nc)) {                                      // Available
+                jc = (int64_t)nr * cols + nc;
+                if (gate_free || receive_ok(J, r, jc, h, n)) {             // else consumed
+                  won = pl.take(nr, nc);
+                  wrc = rc_pack(nr, nc);
                 }
               }
             }
@@ -655,17 +674,25 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
               prefetch_l2(baseh + jc * 8);   // the new cell's table row, read when it is set up
             }
             nnew += __popc(wins);
-            const uint32_t cbits = group_bits(crossed);
-            const uint32_t nx2 = group_min(cof);
-            if (ent >= 0) {
-              if (crossed) ecofs[(size_t)ent * 8 + k] = kNone;
-              if (k == 0) {
-                emask[ent] = (uint8_t)(emask[ent] & ~cbits);
-                enext[ent] = (uint8_t)nx2;
-                lmin = min(lmin, nx2);
-              }
-            }
           }
+          if (ent >= 0) {
+            uint64_t nc8 = cof8;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              if ((cm >> q) & 1u) nc8 |= 0xFFull << (8 * q);
+            *reinterpret_cast<uint64_t *>(ecofs + (size_t)ent * 8) = nc8;
+            const uint32_t nx2 = min_byte8(nc8);
+            emask[ent] = (uint8_t)(emask[ent] & ~cm);
+            enext[ent] = (uint8_t)nx2;
+            lmin = min(lmin, nx2);
+          }
+          // drop the processed round from the buffer
+          __syncwarp();
+          const int32_t rest = hbase - take_n;
+          if (lane < rest) hitbuf[lane] = hitbuf[take_n + lane];
+          __syncwarp();
+          hbase = rest;
+          if (b0 >= cnt && hbase == 0) break;
         }
         if (__any_sync(FULL, ovf)) { status = 1; break; }
         __syncwarp();
@@ -680,7 +707,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           const bool ingrid = act && nr >= 0 && nr < rows && nc >= 0 && nc < cols;
           const int64_t bk = act ? baseh[cell * 8 + k] : 0;   // issue the table load early
           const bool open = ingrid && pl.avail(nr, nc);
-          const bool ignq = ingrid && !open && ((__ldg(&burnable[nr * wpr + (nc >> 5)]) >> (nc & 31)) & 1u);
+          const bool ignq = ingrid && !open;   // ignited, or never burnable (pre-marked Burned)
           const uint32_t omask = group_bits(open);
           uint32_t mask = omask;
           float f = 1.0f;
