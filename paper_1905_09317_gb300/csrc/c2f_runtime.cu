@@ -127,8 +127,8 @@ struct c2f_ctx {
   // frontier scratch
   DevBuf ent_cell, ent_mask, ent_next, ent_cofs, ent_P, counter, brn_scratch, avail_scratch;
   int64_t scratch_slots = 0, scratch_cap = 0, brn_words = 0, avail_words = 0;
-  int smem_optin = 0;
-  int frontier_threads = 128;
+  int smem_optin = 0, smem_per_sm = 0;
+  int frontier_threads = 32;
   bool window_smem = true;                 // plane windows + lists in shared memory when they fit
   int64_t cap_override = 0;
   // kernel timing
@@ -428,12 +428,22 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
   std::vector<int64_t> items;  // empty: all
   for (int attempt = 0;; ++attempt) {
     const int64_t todo = items.empty() ? n_items : (int64_t)items.size();
-    // launch shape: plane windows and list arrays in shared memory when the
-    // list fits beside them, else everything in global memory
+    // launch shape: plane windows and list arrays in shared memory, with the
+    // list capacity sized so that every replica of the launch is resident at
+    // once (first attempt); a replica that outgrows it re-runs with a larger
+    // list in global memory
     cap = (cap + 3) & ~int64_t(3);
+    int64_t win_cap = cap;
+    if (attempt == 0) {
+      const int64_t warps_per_sm = std::max<int64_t>(1, (todo + ctx->sm_count - 1) / ctx->sm_count);
+      const int64_t per_warp = ((int64_t)ctx->smem_per_sm - 1024 * warps_per_sm / wpc) / warps_per_sm;
+      const int64_t room = (per_warp - 2 * (int64_t)kWinRows * kWinWords * 4 - 512) / 14;
+      win_cap = std::min<int64_t>(cap, std::max<int64_t>(256, room & ~int64_t(63)));
+    }
     const int64_t budget = (int64_t)ctx->smem_optin - 2048;
-    const int64_t win_words = 2 * (int64_t)kWinRows * kWinWords + cap * 7 / 2;
-    const bool use_win = ctx->window_smem && win_words * 4 * wpc <= budget;
+    const int64_t win_words = 2 * (int64_t)kWinRows * kWinWords + win_cap * 7 / 2;
+    const bool use_win = ctx->window_smem && attempt == 0 && win_words * 4 * wpc <= budget;
+    if (use_win) cap = win_cap;
     const int64_t warp_words = use_win ? win_words : 0;
     void (*kern)(FrontierArgs) =
         use_win ? (wpc == 1 ? k_frontier_w1 : wpc == 2 ? k_frontier_w2 : k_frontier_w4)
@@ -501,7 +511,7 @@ int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim 
     }
     if (failed.empty()) return C2F_OK;
     if (cap >= max_n) return fail(ctx, C2F_ECUDA, "frontier list overflow at full capacity");
-    cap = std::min<int64_t>(max_n, cap * 4);
+    cap = std::min<int64_t>(max_n, std::max<int64_t>(cap * 4, default_cap(ctx, *lands[0])));
     // reset the failed replicas' state before the re-run
     for (int64_t it : failed) {
       int32_t i = (int32_t)(std::upper_bound(begin.begin(), begin.end(), it) - begin.begin() - 1);
@@ -552,6 +562,7 @@ C2F_API int c2f_create(c2f_ctx **out, int device) {
     int rc = ensure_device_constants(c);
     if (rc) return rc;
     CK(cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    CK(cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
   }
   *out = ctx.release();
   return C2F_OK;
