@@ -507,6 +507,46 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       __syncwarp();
     }
 
+    // drop Burned cells and cells with no open axis from the burning list
+    // (order kept); with a table pointer, prefetch the kept cells' rows
+    auto compact = [&](int32_t count, const int64_t *rows_tbl) -> int32_t {
+      int32_t out = 0;
+      for (int32_t b0 = 0; b0 < count; b0 += 32) {
+        const int32_t e = b0 + lane;
+        bool keep = false;
+        uint32_t rc = 0, m = 0, nx = kNone;
+        uint64_t c8 = 0;
+        int64_t P[8];
+        if (e < count) {
+          rc = erc[e];
+          m = emask[e];
+          const int32_t cr = (int32_t)(rc >> 16), cc = (int32_t)(rc & 0xFFFFu);
+          keep = m != 0 && !pl.burned(cr, cc);
+          if (keep) {
+            if (rows_tbl) prefetch_l2(rows_tbl + ((int64_t)cr * cols + cc) * 8);
+            nx = enext[e];
+            c8 = *reinterpret_cast<const uint64_t *>(ecofs + (size_t)e * 8);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) P[q] = eP[(size_t)e * 8 + q];
+          }
+        }
+        const uint32_t bal = __ballot_sync(FULL, keep);
+        const int32_t pos = out + __popc(bal & lt);
+        __syncwarp();
+        if (keep) {
+          erc[pos] = rc;
+          emask[pos] = (uint8_t)m;
+          enext[pos] = (uint8_t)nx;
+          *reinterpret_cast<uint64_t *>(ecofs + (size_t)pos * 8) = c8;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) eP[(size_t)pos * 8 + q] = P[q];
+        }
+        out += __popc(bal);
+        __syncwarp();
+      }
+      return out;
+    };
+
     for (int32_t h = 0; h < H && live > 0 && status == 0; ++h) {
       const int32_t s0 = h * sph + 1, L = s0 + sph - 1;
       const int64_t *baseh = J.base + (size_t)h * n * 8;
@@ -515,38 +555,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
 
       // ---- hour boundary (i): drop Burned cells and cells with no open axis;
       // prefetch the kept cells' table rows for (ii)
-      {
-        int32_t out = 0;
-        for (int32_t b0 = 0; b0 < cnt; b0 += 32) {
-          const int32_t e = b0 + lane;
-          bool keep = false;
-          uint32_t rc = 0, m = 0;
-          int64_t P[8];
-          if (e < cnt) {
-            rc = erc[e];
-            m = emask[e];
-            const int32_t cr = (int32_t)(rc >> 16), cc = (int32_t)(rc & 0xFFFFu);
-            keep = m != 0 && !pl.burned(cr, cc);
-            if (keep) {
-              prefetch_l2(baseh + ((int64_t)cr * cols + cc) * 8);
-#pragma unroll
-              for (int q = 0; q < 8; ++q) P[q] = eP[(size_t)e * 8 + q];
-            }
-          }
-          const uint32_t bal = __ballot_sync(FULL, keep);
-          const int32_t pos = out + __popc(bal & lt);
-          __syncwarp();
-          if (keep) {
-            erc[pos] = rc;
-            emask[pos] = (uint8_t)m;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) eP[(size_t)pos * 8 + q] = P[q];
-          }
-          out += __popc(bal);
-          __syncwarp();
-        }
-        cnt = out;
-      }
+      cnt = compact(cnt, baseh);
       // ---- hour boundary (ii): crossing periods of this hour, a group per cell,
       // four cells per group in flight
       for (int32_t b0 = 0; b0 < cnt; b0 += 16) {
@@ -614,6 +623,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       for (;;) {
         W += (long long)live * (long long)(s - s_done);
         s_done = s;
+        if (cnt > cap - cap / 4) cnt = compact(cnt, nullptr);   // keep room for new cells
         const uint32_t o = (uint32_t)(s - s0);
         uint32_t lmin = kNone;
         int32_t nnew = cnt;
