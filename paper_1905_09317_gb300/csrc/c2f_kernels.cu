@@ -556,13 +556,26 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       // ---- hour boundary (i): drop Burned cells and cells with no open axis;
       // prefetch the kept cells' table rows for (ii)
       cnt = compact(cnt, baseh);
-      // ---- hour boundary (ii): crossing periods of this hour, a group per cell,
+      // ---- hour boundary (ii): the perturbation of every listed cell for this
+      // hour, one lane per cell, parked as a 32.32 multiplier in the cell's
+      // crossing-offset slot (rewritten below)
+      for (int32_t b0 = 0; b0 < cnt; b0 += 32) {
+        const int32_t e = b0 + lane;
+        if (e < cnt) {
+          const uint32_t rc = erc[e];
+          const int64_t cell = (int64_t)(rc >> 16) * cols + (rc & 0xFFFFu);
+          const float f = noise_factor(seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, sigma);
+          *reinterpret_cast<uint64_t *>(ecofs + (size_t)e * 8) = noise_fixed(f);
+        }
+      }
+      __syncwarp();
+      // ---- hour boundary (iii): crossing periods of this hour, a group per cell,
       // four cells per group in flight
       for (int32_t b0 = 0; b0 < cnt; b0 += 16) {
         uint32_t rcu[4], mu[4], masku[4];
         int64_t Pu[4], bku[4];
+        uint64_t Fu[4];
         bool actu[4], openu[4];
-        float fu[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int32_t e = b0 + 4 * u + grp;
@@ -570,6 +583,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           rcu[u] = actu[u] ? erc[e] : 0u;
           mu[u] = actu[u] ? emask[e] : 0u;
           Pu[u] = actu[u] ? eP[(size_t)e * 8 + k] : 0;
+          Fu[u] = actu[u] ? *reinterpret_cast<const uint64_t *>(ecofs + (size_t)e * 8) : 0ull;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -581,12 +595,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) masku[u] = group_bits(openu[u]);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int64_t cell = (int64_t)(rcu[u] >> 16) * cols + (rcu[u] & 0xFFFFu);
-          fu[u] = (actu[u] && (masku[u] != 0 || delta > 0.0))
-                      ? noise_factor(seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, sigma) : 1.0f;
-        }
+        __syncwarp();   // every lane has read its cell's multiplier before the slot is rewritten
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int32_t e = b0 + 4 * u + grp;
@@ -595,14 +604,15 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           uint32_t cof = kNone;
           int64_t P = Pu[u];
           bool dying = false;
-          if (actu[u] && (masku[u] != 0 || delta > 0.0)) {
-            if (openu[u]) {
-              const int64_t inc = apply_noise(bku[u], noise_fixed(fu[u]), dk);
-              const int64_t rem = dk - P;
-              if (inc > 0 && inc * sph >= rem) cof = (uint32_t)(ceil_div_small(rem, inc) - 1);
-              else P += inc * sph;
-            }
-            if (delta > 0.0 && __dmul_rn(hrosh[cell], (double)fu[u]) < delta) {   // A5 (i)
+          if (openu[u]) {
+            const int64_t inc = apply_noise(bku[u], Fu[u], dk);
+            const int64_t rem = dk - P;
+            if (inc > 0 && inc * sph >= rem) cof = (uint32_t)(ceil_div_small(rem, inc) - 1);
+            else P += inc * sph;
+          }
+          if (actu[u] && delta > 0.0) {
+            const double f = (double)Fu[u] * 0x1p-32;   // exact: F = f 2^32 for a binary32 f
+            if (__dmul_rn(hrosh[cell], f) < delta) {    // A5 (i)
               if (k == 0) dying = pl.burn(cr, cc);
               if (cof != 0) cof = kNone;   // still sends in period s0, Burned after it
             }
