@@ -181,6 +181,15 @@ C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap);
  * tuning knobs. */
 C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem);
 
+/* Launch-shape autotuner for a batch: runs the same mix of simulations,
+ * scaled down to about `sample_replicas` replicas, under each candidate
+ * frontier launch shape (warps per CTA x shared-memory staging), keeps the
+ * fastest on the context and reports it.  Results of later runs are the same
+ * under any shape; only their speed changes.  Outputs may be NULL. */
+C2F_API int c2f_autotune(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
+                         const c2f_sim_params *params, int32_t sample_replicas, int32_t *best_threads,
+                         int32_t *best_smem, double *best_ms);
+
 /* Kernel timing: with profiling on, the context brackets each launch of its
  * kernel families with CUDA events on its stream.  c2f_kernel_times waits for
  * the stream, writes per family the summed milliseconds and the launch count

@@ -78,6 +78,8 @@ _SIGS = [
     ("c2f_get_counters", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("c2f_set_list_capacity", C.c_int, [C.c_void_p, C.c_int64]),
     ("c2f_set_frontier_config", C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
+    ("c2f_autotune", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                                _P(C.c_int32), _P(C.c_int32), _P(C.c_double)]),
     ("c2f_profile", C.c_int, [C.c_void_p, C.c_int]),
     ("c2f_kernel_times", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("c2f_release", C.c_int, [C.c_void_p, C.c_int32]),
@@ -229,6 +231,16 @@ class Context:
 
     def set_frontier_config(self, threads: int, smem_plane_bytes: int) -> None:
         self._check(self.lib.c2f_set_frontier_config(self.h, int(threads), int(smem_plane_bytes)))
+
+    def autotune(self, landscape_ids, params_list, sample_replicas=256):
+        """Pick the fastest frontier launch shape for this mix; returns (threads, smem, ms)."""
+        n = len(landscape_ids)
+        ids = (C.c_int32 * n)(*landscape_ids)
+        ps = (SimParams * n)(*params_list)
+        t, sm, ms = C.c_int32(), C.c_int32(), C.c_double()
+        self._check(self.lib.c2f_autotune(self.h, n, ids, ps, int(sample_replicas), C.byref(t),
+                                          C.byref(sm), C.byref(ms)))
+        return t.value, sm.value, ms.value
 
     def profile(self, enable: bool = True) -> None:
         self._check(self.lib.c2f_profile(self.h, int(bool(enable))))

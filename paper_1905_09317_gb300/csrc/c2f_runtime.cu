@@ -129,6 +129,7 @@ struct c2f_ctx {
   int64_t scratch_slots = 0, scratch_cap = 0, brn_words = 0, avail_words = 0;
   int smem_optin = 0, smem_per_sm = 0;
   int frontier_threads = 32;
+  int64_t graph_launches = 0;
   bool window_smem = true;                 // plane windows + lists in shared memory when they fit
   int64_t cap_override = 0;
   // kernel timing
@@ -264,18 +265,27 @@ TableKey key_of(const c2f_sim_params *p) {
   return k;
 }
 
-// K1 for hours [0, hours) into the landscape's table (a1: hour prep first)
-int build_table(c2f_ctx *ctx, Landscape &L, const c2f_sim_params *p) {
+// Table of a landscape for the options in *p, hours [0, p->hours):
+// allocation (prepare_table) and the kernels (launch_table: a1 hour prep,
+// then K1), split so that the kernels can be captured in a CUDA graph.
+int prepare_table(c2f_ctx *ctx, Landscape &L, const c2f_sim_params *p) {
   int rc;
   const int32_t H = p->hours;
   if ((rc = dalloc(ctx, L.hour_prep, sizeof(HourPrep) * (size_t)L.n_hours))) return rc;
   if ((rc = dalloc(ctx, L.base, sizeof(int64_t) * 8 * (size_t)L.n * H))) return rc;
   if ((rc = dalloc(ctx, L.hros, sizeof(double) * (size_t)L.n * H))) return rc;
+  if (!L.hros_pos.p && (rc = dalloc(ctx, L.hros_pos, 4))) return rc;
+  L.table_valid = false;
+  return C2F_OK;
+}
+
+int launch_table(c2f_ctx *ctx, Landscape &L, const c2f_sim_params *p) {
+  const int32_t H = p->hours;
   ProfScope prof(ctx, 0);
   k_hour_prep<<<grid1(L.n_hours, 64), 64, 0, ctx->stream>>>(
       L.weather_dev.as<double>(), L.n_hours, p->o1_curing_pct, L.hour_prep.as<HourPrep>());
   CKL("k_hour_prep");
-  L.table_valid = false;
+  CK(cudaMemsetAsync(L.hros_pos.p, 1, 4, ctx->stream));   // non-zero until a row says otherwise
   RosTableArgs a{};
   a.fuel = L.fuel.as<uint8_t>();
   a.slope = L.has_slope ? L.slope.as<float>() : nullptr;
@@ -291,11 +301,6 @@ int build_table(c2f_ctx *ctx, Landscape &L, const c2f_sim_params *p) {
   a.base = L.base.as<int64_t>();
   a.hros = L.hros.as<double>();
   a.ros8 = nullptr;
-  if (!L.hros_pos.p && (rc = dalloc(ctx, L.hros_pos, 4))) return rc;
-  {
-    const int32_t one = 1;
-    CK(cudaMemcpyAsync(L.hros_pos.p, &one, 4, cudaMemcpyHostToDevice, ctx->stream));
-  }
   a.hros_pos = L.hros_pos.as<int32_t>();
   a.order = L.order.as<int32_t>();
   dim3 grid(grid1(L.n, 128), (unsigned)H);
@@ -306,10 +311,16 @@ int build_table(c2f_ctx *ctx, Landscape &L, const c2f_sim_params *p) {
   return C2F_OK;
 }
 
-int ensure_table(c2f_ctx *ctx, Landscape &L, const c2f_sim_params *p, bool force) {
+bool table_ok(const Landscape &L, const c2f_sim_params *p) {
   const TableKey k = key_of(p);
-  if (!force && L.table_valid && L.key == k && L.key.hours >= k.hours) return C2F_OK;
-  return build_table(ctx, L, p);
+  return L.table_valid && L.key == k && L.key.hours >= k.hours;
+}
+
+int ensure_table(c2f_ctx *ctx, Landscape &L, const c2f_sim_params *p, bool force) {
+  if (!force && table_ok(L, p)) return C2F_OK;
+  int rc = prepare_table(ctx, L, p);
+  if (rc) return rc;
+  return launch_table(ctx, L, p);
 }
 
 Landscape *find_land(c2f_ctx *ctx, int32_t id) {
@@ -392,138 +403,192 @@ SimJob job_of(const Landscape &L, const Sim &s) {
   return j;
 }
 
-// one persistent frontier launch over the replicas of `jobs`; failed
-// (capacity) replicas are reset and re-run with a larger capacity
-int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim *> &sims) {
+// Frontier over the replicas of several simulations: one work list of
+// (simulation, replica) items, simulations ordered longest-expected-first so
+// that the long replicas start early.  FrontierPlan holds everything a launch
+// needs; plan_frontier allocates and uploads (not capturable), launch_frontier
+// issues K2 and the K3 launch (capturable in a CUDA graph), finish_frontier
+// reads the per-replica status and re-runs, with a larger burning list, any
+// replica whose list overflowed.
+struct FrontierPlan {
+  std::vector<Landscape *> lands;
+  std::vector<Sim *> sims;   // in work-list order
+  std::vector<int64_t> begin;
+  DevBuf djobs, dbegin;
+  int64_t cap = 0, max_n = 0, pw_max = 0, n_items = 0;
+  void (*kern)(FrontierArgs) = nullptr;
+  size_t dyn_smem = 0;
+  int threads = 32;
+  int64_t ctas = 0;
+  FrontierArgs A{};
+};
+
+int64_t replica_cost(const Landscape &L, const Sim &s) {
+  return (int64_t)s.p.hours * std::min<int64_t>(L.n_burnable, 50000);
+}
+
+// launch shape for `todo` items at burning-list capacity `cap_in`; attempt 0
+// sizes the shared-memory list so that the launch is resident at once (capped
+// at 8 warps per SM), later attempts give each replica more room
+int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, int64_t todo, int64_t cap_in, int attempt) {
+  int rc;
+  const int threads = ctx->frontier_threads;   // 32, 64 or 128: one replica per warp
+  const int wpc = threads / 32;
+  int64_t cap = (cap_in + 3) & ~int64_t(3);
+  int64_t win_cap = cap;
+  {
+    const int64_t want = std::max<int64_t>(1, (todo + ctx->sm_count - 1) / ctx->sm_count);
+    const int64_t warps_per_sm = attempt == 0 ? std::min<int64_t>(want, 8) : std::min<int64_t>(want, 2);
+    const int64_t per_warp = ((int64_t)ctx->smem_per_sm - 1024 * warps_per_sm / wpc) / warps_per_sm;
+    const int64_t room = (per_warp - 2 * (int64_t)kWinRows * kWinWords * 4 - 512) / 14;
+    win_cap = std::min<int64_t>(cap, std::max<int64_t>(256, room & ~int64_t(63)));
+    if (attempt > 0) win_cap = std::max<int64_t>(256, room & ~int64_t(63));
+  }
+  const int64_t budget = (int64_t)ctx->smem_optin - 2048;
+  const int64_t win_words = 2 * (int64_t)kWinRows * kWinWords + win_cap * 7 / 2;
+  const bool use_win = ctx->window_smem && win_words * 4 * wpc <= budget &&
+                       (attempt == 0 || win_cap >= cap);
+  if (use_win) cap = win_cap;
+  const int64_t warp_words = use_win ? win_words : 0;
+  F.kern = use_win ? (wpc == 1 ? k_frontier_w1 : wpc == 2 ? k_frontier_w2 : k_frontier_w4)
+                   : (wpc == 1 ? k_frontier_g1 : wpc == 2 ? k_frontier_g2 : k_frontier_g4);
+  F.dyn_smem = (size_t)warp_words * 4 * wpc;
+  F.threads = threads;
+  if (F.dyn_smem > 0)
+    CK(cudaFuncSetAttribute(F.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F.dyn_smem));
+  int bps = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, F.kern, threads, F.dyn_smem));
+  bps = std::max(bps, 1);
+  const int64_t max_ctas = (int64_t)ctx->sm_count * bps;
+  F.ctas = std::min<int64_t>((todo + wpc - 1) / wpc, max_ctas);
+  const int64_t slots = F.ctas * wpc;   // one warp per slot
+  if ((rc = ensure_scratch(ctx, slots, cap))) return rc;
+  if (slots * F.pw_max > ctx->brn_words) {
+    if ((rc = dalloc(ctx, ctx->brn_scratch, (size_t)slots * F.pw_max * 4))) return rc;
+    ctx->brn_words = slots * F.pw_max;
+  }
+  if (slots * F.pw_max > ctx->avail_words) {
+    if ((rc = dalloc(ctx, ctx->avail_scratch, (size_t)slots * F.pw_max * 4))) return rc;
+    ctx->avail_words = slots * F.pw_max;
+  }
+  FrontierArgs &A = F.A;
+  A = FrontierArgs{};
+  A.jobs = F.djobs.as<SimJob>();
+  A.n_jobs = (int32_t)F.sims.size();
+  A.item_begin = F.dbegin.as<int64_t>();
+  A.item_list = nullptr;
+  A.n_items = todo;
+  A.counter = ctx->counter.as<unsigned long long>();
+  A.cap = (int32_t)cap;
+  A.ent_cell = ctx->ent_cell.as<int32_t>();
+  A.ent_mask = ctx->ent_mask.as<uint8_t>();
+  A.ent_next = ctx->ent_next.as<uint8_t>();
+  A.ent_cofs = ctx->ent_cofs.as<uint8_t>();
+  A.ent_P = ctx->ent_P.as<int64_t>();
+  A.pw_max = F.pw_max;
+  A.brn_scratch = ctx->brn_scratch.as<uint32_t>();
+  A.avail_scratch = ctx->avail_scratch.as<uint32_t>();
+  A.smem_warp_words = warp_words;
+  F.cap = cap;
+  return C2F_OK;
+}
+
+int plan_frontier(c2f_ctx *ctx, std::vector<Landscape *> lands, std::vector<Sim *> sims,
+                  FrontierPlan &F) {
   int rc;
   const int32_t nj = (int32_t)sims.size();
+  std::vector<int32_t> order(nj);
+  for (int32_t i = 0; i < nj; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return replica_cost(*lands[a], *sims[a]) > replica_cost(*lands[b], *sims[b]);
+  });
+  F.lands.clear();
+  F.sims.clear();
+  for (int32_t i : order) { F.lands.push_back(lands[i]); F.sims.push_back(sims[i]); }
   std::vector<SimJob> jobs(nj);
-  std::vector<int64_t> begin(nj + 1, 0);
-  int64_t cap = 0;
-  int64_t max_n = 0;
+  F.begin.assign(nj + 1, 0);
+  F.cap = 0; F.max_n = 0; F.pw_max = 0;
   for (int32_t i = 0; i < nj; ++i) {
-    jobs[i] = job_of(*lands[i], *sims[i]);
-    begin[i + 1] = begin[i] + sims[i]->p.n_replicas;
-    cap = std::max(cap, default_cap(ctx, *lands[i]));
-    max_n = std::max(max_n, lands[i]->n);
+    jobs[i] = job_of(*F.lands[i], *F.sims[i]);
+    F.begin[i + 1] = F.begin[i] + F.sims[i]->p.n_replicas;
+    F.cap = std::max(F.cap, default_cap(ctx, *F.lands[i]));
+    F.max_n = std::max(F.max_n, F.lands[i]->n);
+    F.pw_max = std::max<int64_t>(F.pw_max, (int64_t)F.lands[i]->rows * F.lands[i]->wpr);
   }
-  const int64_t n_items = begin[nj];
-  DevBuf djobs, dbegin, dlist;
-  if ((rc = dalloc(ctx, djobs, sizeof(SimJob) * nj))) return rc;
-  if ((rc = dalloc(ctx, dbegin, sizeof(int64_t) * (nj + 1)))) return rc;
-  CK(cudaMemcpyAsync(djobs.p, jobs.data(), sizeof(SimJob) * nj, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(dbegin.p, begin.data(), sizeof(int64_t) * (nj + 1), cudaMemcpyHostToDevice,
+  F.n_items = F.begin[nj];
+  if ((rc = dalloc(ctx, F.djobs, sizeof(SimJob) * nj))) return rc;
+  if ((rc = dalloc(ctx, F.dbegin, sizeof(int64_t) * (nj + 1)))) return rc;
+  CK(cudaMemcpyAsync(F.djobs.p, jobs.data(), sizeof(SimJob) * nj, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(F.dbegin.p, F.begin.data(), sizeof(int64_t) * (nj + 1), cudaMemcpyHostToDevice,
                      ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));   // host arrays above are about to go out of scope
+  return shape_frontier(ctx, F, F.n_items, F.cap, 0);
+}
+
+int launch_frontier(c2f_ctx *ctx, FrontierPlan &F) {
   {
     ProfScope prof(ctx, 1);
-    for (int32_t i = 0; i < nj; ++i) {
-      k_ignite<<<grid1(sims[i]->p.n_replicas, 128), 128, 0, ctx->stream>>>(djobs.as<SimJob>(), i);
+    for (size_t i = 0; i < F.sims.size(); ++i) {
+      k_ignite<<<grid1(F.sims[i]->p.n_replicas, 128), 128, 0, ctx->stream>>>(F.djobs.as<SimJob>(), (int32_t)i);
       CKL("k_ignite");
     }
   }
-  int64_t pw_max = 0;
-  for (int32_t i = 0; i < nj; ++i) pw_max = std::max<int64_t>(pw_max, (int64_t)lands[i]->rows * lands[i]->wpr);
-  const int threads = ctx->frontier_threads;   // 32, 64 or 128: one replica per warp
-  const int wpc = threads / 32;
-  std::vector<int64_t> items;  // empty: all
-  for (int attempt = 0;; ++attempt) {
-    const int64_t todo = items.empty() ? n_items : (int64_t)items.size();
-    // launch shape: plane windows and list arrays in shared memory, with the
-    // list capacity sized so that every replica of the launch is resident at
-    // once (first attempt); a replica that outgrows it re-runs with a larger
-    // list in global memory
-    cap = (cap + 3) & ~int64_t(3);
-    int64_t win_cap = cap;
-    if (attempt == 0) {
-      const int64_t warps_per_sm = std::max<int64_t>(1, (todo + ctx->sm_count - 1) / ctx->sm_count);
-      const int64_t per_warp = ((int64_t)ctx->smem_per_sm - 1024 * warps_per_sm / wpc) / warps_per_sm;
-      const int64_t room = (per_warp - 2 * (int64_t)kWinRows * kWinWords * 4 - 512) / 14;
-      win_cap = std::min<int64_t>(cap, std::max<int64_t>(256, room & ~int64_t(63)));
-    }
-    const int64_t budget = (int64_t)ctx->smem_optin - 2048;
-    const int64_t win_words = 2 * (int64_t)kWinRows * kWinWords + win_cap * 7 / 2;
-    const bool use_win = ctx->window_smem && attempt == 0 && win_words * 4 * wpc <= budget;
-    if (use_win) cap = win_cap;
-    const int64_t warp_words = use_win ? win_words : 0;
-    void (*kern)(FrontierArgs) =
-        use_win ? (wpc == 1 ? k_frontier_w1 : wpc == 2 ? k_frontier_w2 : k_frontier_w4)
-                : (wpc == 1 ? k_frontier_g1 : wpc == 2 ? k_frontier_g2 : k_frontier_g4);
-    const size_t dyn_smem = (size_t)warp_words * 4 * wpc;
-    if (dyn_smem > 0)
-      CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem));
-    int bps = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, threads, dyn_smem));
-    bps = std::max(bps, 1);
-    const int64_t max_ctas = (int64_t)ctx->sm_count * bps;
-    int64_t ctas = std::min<int64_t>((todo + wpc - 1) / wpc, max_ctas);
-    if (attempt > 0) ctas = std::min<int64_t>(ctas, std::max<int64_t>(1, ctx->sm_count));
-    const int64_t slots = ctas * wpc;   // one warp per slot
-    if ((rc = ensure_scratch(ctx, slots, cap))) return rc;
-    if (slots * pw_max > ctx->brn_words) {
-      if ((rc = dalloc(ctx, ctx->brn_scratch, (size_t)slots * pw_max * 4))) return rc;
-      ctx->brn_words = slots * pw_max;
-    }
-    if (slots * pw_max > ctx->avail_words) {
-      if ((rc = dalloc(ctx, ctx->avail_scratch, (size_t)slots * pw_max * 4))) return rc;
-      ctx->avail_words = slots * pw_max;
-    }
-    FrontierArgs A{};
-    A.jobs = djobs.as<SimJob>();
-    A.n_jobs = nj;
-    A.item_begin = dbegin.as<int64_t>();
-    A.item_list = nullptr;
-    if (!items.empty()) {
-      if ((rc = dalloc(ctx, dlist, sizeof(int64_t) * items.size()))) return rc;
-      CK(cudaMemcpyAsync(dlist.p, items.data(), sizeof(int64_t) * items.size(),
-                         cudaMemcpyHostToDevice, ctx->stream));
-      A.item_list = dlist.as<int64_t>();
-    }
-    A.n_items = todo;
-    A.counter = ctx->counter.as<unsigned long long>();
-    A.cap = (int32_t)cap;
-    A.ent_cell = ctx->ent_cell.as<int32_t>();
-    A.ent_mask = ctx->ent_mask.as<uint8_t>();
-    A.ent_next = ctx->ent_next.as<uint8_t>();
-    A.ent_cofs = ctx->ent_cofs.as<uint8_t>();
-    A.ent_P = ctx->ent_P.as<int64_t>();
-    A.pw_max = pw_max;
-    A.brn_scratch = ctx->brn_scratch.as<uint32_t>();
-    A.avail_scratch = ctx->avail_scratch.as<uint32_t>();
-    A.smem_warp_words = warp_words;
-    CK(cudaMemsetAsync(ctx->counter.p, 0, 8, ctx->stream));
-    {
-      ProfScope prof(ctx, 2);
-      kern<<<(unsigned)ctas, threads, dyn_smem, ctx->stream>>>(A);
-      CKL("k_frontier");
-    }
-    // gather failed replicas
+  CK(cudaMemsetAsync(ctx->counter.p, 0, 8, ctx->stream));
+  ProfScope prof(ctx, 2);
+  F.kern<<<(unsigned)F.ctas, F.threads, F.dyn_smem, ctx->stream>>>(F.A);
+  CKL("k_frontier");
+  return C2F_OK;
+}
+
+int finish_frontier(c2f_ctx *ctx, FrontierPlan &F) {
+  int rc;
+  const int32_t nj = (int32_t)F.sims.size();
+  for (int attempt = 1;; ++attempt) {
     std::vector<int64_t> failed;
     for (int32_t i = 0; i < nj; ++i) {
-      const int32_t R = sims[i]->p.n_replicas;
+      const int32_t R = F.sims[i]->p.n_replicas;
       std::vector<int32_t> st(R);
-      CK(cudaMemcpyAsync(st.data(), sims[i]->status.p, 4 * (size_t)R, cudaMemcpyDeviceToHost,
+      CK(cudaMemcpyAsync(st.data(), F.sims[i]->status.p, 4 * (size_t)R, cudaMemcpyDeviceToHost,
                          ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));
       for (int32_t r = 0; r < R; ++r) {
         if (st[r] == 2) return fail(ctx, C2F_ECUDA, "internal frontier error (replica %d)", r);
-        if (st[r]) failed.push_back(begin[i] + r);
+        if (st[r]) failed.push_back(F.begin[i] + r);
       }
     }
     if (failed.empty()) return C2F_OK;
-    if (cap >= max_n) return fail(ctx, C2F_ECUDA, "frontier list overflow at full capacity");
-    cap = std::min<int64_t>(max_n, std::max<int64_t>(cap * 4, default_cap(ctx, *lands[0])));
-    // reset the failed replicas' state before the re-run
-    for (int64_t it : failed) {
-      int32_t i = (int32_t)(std::upper_bound(begin.begin(), begin.end(), it) - begin.begin() - 1);
-      const int64_t r = it - begin[i];
-      Sim &s = *sims[i];
-      const size_t pw = (size_t)s.rows * s.wpr;
+    if (F.cap >= F.max_n) return fail(ctx, C2F_ECUDA, "frontier list overflow at full capacity");
+    const int64_t cap = std::min<int64_t>(F.max_n, std::max<int64_t>(F.cap * 4, 1024));
+    for (int64_t it : failed) {   // those replicas start again from scratch
+      const int32_t i = (int32_t)(std::upper_bound(F.begin.begin(), F.begin.end(), it) - F.begin.begin() - 1);
+      const int64_t r = it - F.begin[i];
+      Sim &s = *F.sims[i];
       CK(cudaMemsetAsync(s.status.as<int32_t>() + r, 0, 4, ctx->stream));
       if (s.ign_step.p)
         CK(cudaMemsetAsync(s.ign_step.as<int32_t>() + r * s.n, 0xFF, (size_t)s.n * 4, ctx->stream));
     }
-    items = failed;
+    if ((rc = shape_frontier(ctx, F, (int64_t)failed.size(), cap, attempt))) return rc;
+    DevBuf dlist;
+    if ((rc = dalloc(ctx, dlist, sizeof(int64_t) * failed.size()))) return rc;
+    CK(cudaMemcpyAsync(dlist.p, failed.data(), sizeof(int64_t) * failed.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    F.A.item_list = dlist.as<int64_t>();
+    CK(cudaMemsetAsync(ctx->counter.p, 0, 8, ctx->stream));
+    {
+      ProfScope prof(ctx, 2);
+      F.kern<<<(unsigned)F.ctas, F.threads, F.dyn_smem, ctx->stream>>>(F.A);
+      CKL("k_frontier(retry)");
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
   }
+}
+
+int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim *> &sims) {
+  FrontierPlan F;
+  int rc = plan_frontier(ctx, lands, sims, F);
+  if (rc) return rc;
+  if ((rc = launch_frontier(ctx, F))) return rc;
+  return finish_frontier(ctx, F);
 }
 
 }  // namespace
@@ -785,17 +850,22 @@ static int simulate_many(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_
     if (rc) return rc;
   }
   int rc;
+  // tables: which landscapes need one (the longest run on a landscape sets its hours)
+  std::vector<std::pair<Landscape *, c2f_sim_params>> builds;
   for (int32_t i = 0; i < n; ++i) {
-    // jobs on one landscape must agree on the table options
     for (int32_t k = 0; k < i; ++k)
       if (ids[k] == ids[i] && !(key_of(&params[k]) == key_of(&params[i])))
         return fail(ctx, C2F_EINVAL, "batch entries %d and %d share a landscape with different ROS options", k, i);
-    TableKey want = key_of(&params[i]);
-    for (int32_t k = 0; k < n; ++k)
-      if (ids[k] == ids[i]) want.hours = std::max(want.hours, params[k].hours);
+    bool first = true;
+    for (int32_t k = 0; k < i; ++k) if (ids[k] == ids[i]) first = false;
+    if (!first) continue;
     c2f_sim_params q = params[i];
-    q.hours = want.hours;
-    if ((rc = ensure_table(ctx, *lands[i], &q, false))) return rc;
+    for (int32_t k = i + 1; k < n; ++k)
+      if (ids[k] == ids[i]) q.hours = std::max(q.hours, params[k].hours);
+    if (!table_ok(*lands[i], &q)) {
+      if ((rc = prepare_table(ctx, *lands[i], &q))) return rc;
+      builds.emplace_back(lands[i], q);
+    }
   }
   std::vector<std::unique_ptr<Sim>> owned(n);
   std::vector<Sim *> sims(n);
@@ -806,7 +876,33 @@ static int simulate_many(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_
     if ((rc = alloc_sim(ctx, *lands[i], *owned[i]))) return rc;
     sims[i] = owned[i].get();
   }
-  if ((rc = run_frontier(ctx, lands, sims))) return rc;
+  FrontierPlan F;
+  if ((rc = plan_frontier(ctx, lands, sims, F))) return rc;
+  // a batch's launches (table builds, ignitions, the frontier) go out as one
+  // CUDA graph; a single simulation is launched directly
+  const bool graph = n > 1 && !ctx->profiling;
+  if (graph) {
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    int lrc = C2F_OK;
+    for (auto &b : builds) if (!lrc) lrc = launch_table(ctx, *b.first, &b.second);
+    if (!lrc) lrc = launch_frontier(ctx, F);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+    if (lrc) { if (g) cudaGraphDestroy(g); return lrc; }
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+    const cudaError_t le = cudaGraphLaunch(ge, ctx->stream);
+    cudaGraphExecDestroy(ge);
+    if (le != cudaSuccess) return cuda_fail(ctx, le, "cudaGraphLaunch");
+    ++ctx->graph_launches;
+  } else {
+    for (auto &b : builds) if ((rc = launch_table(ctx, *b.first, &b.second))) return rc;
+    if ((rc = launch_frontier(ctx, F))) return rc;
+  }
+  if ((rc = finish_frontier(ctx, F))) return rc;
   for (int32_t i = 0; i < n; ++i) {
     const int32_t id = ctx->next_id++;
     ctx->sims[id] = std::move(owned[i]);
@@ -919,6 +1015,52 @@ C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem) {
   if (smem < 0) return fail(ctx, C2F_EINVAL, "smem must be >= 0");
   ctx->frontier_threads = threads;
   ctx->window_smem = smem != 0;
+  return C2F_OK;
+}
+
+C2F_API int c2f_autotune(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
+                         const c2f_sim_params *params, int32_t sample_replicas, int32_t *best_threads,
+                         int32_t *best_smem, double *best_ms) {
+  if (!ctx) return C2F_EINVAL;
+  if (n < 1 || !landscape_ids || !params || sample_replicas < 1)
+    return fail(ctx, C2F_EINVAL, "bad autotune arguments");
+  int64_t total = 0;
+  for (int32_t i = 0; i < n; ++i) total += std::max(params[i].n_replicas, 1);
+  std::vector<c2f_sim_params> q(params, params + n);
+  for (int32_t i = 0; i < n; ++i) {   // the same mix of simulations, scaled down
+    const int64_t r = (int64_t)params[i].n_replicas * sample_replicas / std::max<int64_t>(total, 1);
+    q[i].n_replicas = (int32_t)std::max<int64_t>(1, std::min<int64_t>(r, params[i].n_replicas));
+    q[i].outputs = C2F_OUT_SCARS | C2F_OUT_COUNTERS;
+  }
+  const int cand_threads[5] = {32, 64, 128, 32, 128};
+  const int cand_smem[5] = {1, 1, 1, 0, 0};
+  const int keep_threads = ctx->frontier_threads;
+  const bool keep_win = ctx->window_smem, keep_prof = ctx->profiling;
+  double best = 1e300;
+  int bi = 0;
+  std::vector<int32_t> sids(n);
+  for (int c = 0; c < 5; ++c) {
+    ctx->frontier_threads = cand_threads[c];
+    ctx->window_smem = cand_smem[c] != 0;
+    ctx->profiling = true;
+    double ms[C2F_KT_FAMILIES];
+    int64_t cnt[C2F_KT_FAMILIES];
+    int rc = c2f_kernel_times(ctx, ms, cnt);   // reset
+    if (!rc) rc = simulate_many(ctx, n, landscape_ids, q.data(), sids.data());
+    if (!rc) rc = c2f_kernel_times(ctx, ms, cnt);
+    if (rc) {
+      ctx->frontier_threads = keep_threads; ctx->window_smem = keep_win; ctx->profiling = keep_prof;
+      return rc;
+    }
+    for (int32_t i = 0; i < n; ++i) ctx->sims.erase(sids[i]);
+    if (ms[2] < best) { best = ms[2]; bi = c; }
+  }
+  ctx->frontier_threads = cand_threads[bi];
+  ctx->window_smem = cand_smem[bi] != 0;
+  ctx->profiling = keep_prof;
+  if (best_threads) *best_threads = cand_threads[bi];
+  if (best_smem) *best_smem = cand_smem[bi];
+  if (best_ms) *best_ms = best;
   return C2F_OK;
 }
 

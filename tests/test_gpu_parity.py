@@ -250,3 +250,18 @@ def test_errors(ctx):
     assert e.value.code == c2f.C2F_EINVAL
     ctx.release(l2)
     ctx.release(lid)
+
+
+def test_autotune_keeps_results(ctx):
+    ws = [S.config2(side=s, n_replicas=r, hours=3) for s, r in ((60, 30), (90, 12))]
+    lids = [load(ctx, w) for w in ws]
+    ps = [gpu_params(**w.params) for w in ws]
+    before = [ctx.get_scars(sid, p.n_replicas, w.landscape.fuel.size, ign_steps=True)[1]
+              for sid, p, w in zip(ctx.simulate_batch(lids, ps), ps, ws)]
+    threads, smem, ms = ctx.autotune(lids, ps, sample_replicas=16)
+    assert threads in (32, 64, 128) and smem in (0, 1) and ms > 0
+    after = [ctx.get_scars(sid, p.n_replicas, w.landscape.fuel.size, ign_steps=True)[1]
+             for sid, p, w in zip(ctx.simulate_batch(lids, ps), ps, ws)]
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    ctx.set_frontier_config(32, 1)
