@@ -11,6 +11,17 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referenc
 Under torchrun each rank runs its own 1000 replicas (replica ids offset by
 rank), so per-GPU work is fixed (weak scaling) and no collective touches the
 data path; the timing is max-over-ranks.
+
+Other workloads (one GPU; each prints its own JSON line):
+  --workload batch   64 landscapes of 64^2..2048^2 cells, 16..4096 replicas,
+                     48 h: one request per call ("plain") vs one batched call
+                     (tables and frontier in one CUDA graph) ("batched").
+  --workload serve   Poisson arrivals (50/s for 60 s) over a pool of 16
+                     landscapes of 128^2..2048^2 cells, 32..2048 replicas,
+                     12..72 h, served with submit/poll (continuous batching):
+                     throughput and p50/p99 latency from arrival to the burn
+                     counts on the host.
+  --workload large   4096^2 cells, 72 h with a 90-degree wind shift, 256 replicas.
 """
 from __future__ import annotations
 
@@ -85,15 +96,20 @@ class ClockSampler:
         self.dev = device_index
         self.proc = None
         self.lines = []
+        self.skip = 0
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)            # sampling is running before the timed region starts
+            self.skip = len(self.lines)
         except Exception:
             self.proc = None
         return self
@@ -113,7 +129,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.skip:] or self.lines[-1:]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -302,7 +318,7 @@ def roofline(dom, fam, w, work_per_step, peaks):
 
 # algorithmic figures (the design doc states how they are derived)
 FRONTIER_BYTES_PER_UPDATE = 194.0
-FP64_OPS_PER_CELL_HOUR = 700.0
+FP64_OPS_PER_CELL_HOUR = 795.0      # ncu: (2 x DFMA + DMUL + DADD) / (cells x hours)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x DFMA/clk x flop/DFMA x GHz
 
 
@@ -332,10 +348,212 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------------ other workloads
+def _params_of(c2f, w, **over):
+    keys = {f[0] for f in c2f.SimParams._fields_}
+    d = {k: v for k, v in w.params.items() if k in keys}
+    d.update(over)
+    return c2f.default_params(**d)
+
+
+def run_batch(args):
+    """64-landscape batch: plain (one simulate per landscape) vs batched (one call)."""
+    import torch
+    import paper_1905_09317_gb300 as c2f
+    c2f.build()
+    specs = S.config3_specs()
+    ws = [S.config3_workload(sp) for sp in specs]
+    ctx = c2f.Context(0)
+    lids = []
+    for w in ws:
+        L = w.landscape
+        lid = ctx.load_landscape(L.fuel, L.slope, L.aspect, cell_size=L.cell_size)
+        ctx.set_weather(lid, w.weather)
+        lids.append(lid)
+    ps = [_params_of(c2f, w) for w in ws]
+    ns = [w.landscape.fuel.size for w in ws]
+
+    def plain():
+        sids = []
+        for lid, p, w in zip(lids, ps, ws):
+            ctx.set_weather(lid, w.weather)          # the table is rebuilt inside the step
+            sids.append(ctx.simulate(lid, p))
+        return sids
+
+    def batched():
+        for lid, w in zip(lids, ws):
+            ctx.set_weather(lid, w.weather)
+        return ctx.simulate_batch(lids, ps)
+
+    out = {}
+    work = None
+    for name, fn in (("plain", plain), ("batched", batched)):
+        for _ in range(max(args.warmup, 1)):
+            for sid in fn():
+                ctx.release(sid)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sids = fn()
+            for sid, n in zip(sids, ns):
+                ctx.burn_prob(sid, n)
+            wk = sum(int(ctx.get_counters(sid, p.n_replicas)[0].sum()) for sid, p in zip(sids, ps))
+            for sid in sids:
+                ctx.release(sid)
+            assert work is None or wk == work, "work count differs between plain and batched"
+            work = wk
+        dt = (time.perf_counter() - t0) / args.steps
+        out[name] = dict(s_per_step=dt, cell_updates_per_s=work / dt,
+                         replicas_per_s=sum(p.n_replicas for p in ps) / dt)
+    ctx.close()
+    return {"metric": METRIC, "value": out["batched"]["cell_updates_per_s"], "unit": METRIC,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * out["batched"]["s_per_step"], "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batch of 64 landscapes, sides log-uniform 64..2048 cells, "
+                                   "replicas log-uniform 16..4096, 48 h weather, random ignitions, "
+                                   "lognormal(0,0.1) noise", "cells": int(sum(ns)),
+                       "replicas": int(sum(p.n_replicas for p in ps)),
+                       "cell_updates_per_step": work,
+                       "timing": "host wall clock per step incl. table builds, burn counts to host"},
+            "plain": out["plain"], "batched": out["batched"],
+            "batched_over_plain": out["plain"]["s_per_step"] / out["batched"]["s_per_step"]}
+
+
+def run_serve(args):
+    """Poisson request stream served with submit/poll; latency = arrival -> counts on host."""
+    import torch
+    import paper_1905_09317_gb300 as c2f
+    c2f.build()
+    sides, reqs = S.serving_requests(rate=args.rate, duration_s=args.duration)
+    lands = [S.heterogeneous_landscape(side, seed=500 + i) for i, side in enumerate(sides)]
+    weathers = [S.weather_stream(72, seed=600 + i) for i in range(len(sides))]
+    ctx = c2f.Context(0)
+    ctx.set_serving(max_inflight=args.max_inflight)
+    lids = [None] * len(sides)
+
+    def params(r):
+        return c2f.default_params(seed=r["seed"], n_replicas=r["n_replicas"], hours=r["hours"],
+                                  ignition_mode=1, ros_sigma=0.1)
+
+    def load(k):
+        L = lands[k]
+        lid = ctx.load_landscape(L.fuel, L.slope, L.aspect, cell_size=L.cell_size)
+        ctx.set_weather(lid, weathers[k])
+        return lid
+
+    def serve(mode):
+        for k in range(len(lids)):
+            if lids[k] is not None:
+                ctx.release(lids[k])
+                lids[k] = None
+        torch.cuda.synchronize()
+        lat, work, i = [], 0, 0
+        outstanding = {}
+        t0 = time.perf_counter()
+        while i < len(reqs) or outstanding:
+            now = time.perf_counter() - t0
+            busy = False
+            while i < len(reqs) and reqs[i]["arrival_s"] <= now:
+                r = reqs[i]
+                k = r["pool_index"]
+                if lids[k] is None:
+                    lids[k] = load(k)                 # a new load: inside the request's latency
+                n = lands[k].fuel.size
+                if mode == "served":
+                    outstanding[ctx.submit(lids[k], params(r))] = (i, n)
+                else:                                 # plain: one synchronous call per request
+                    sid = ctx.simulate(lids[k], params(r))
+                    ctx.burn_prob(sid, n)
+                    work += int(ctx.get_counters(sid, r["n_replicas"])[0].sum())
+                    lat.append(time.perf_counter() - t0 - r["arrival_s"])
+                    ctx.release(sid)
+                i += 1
+                busy = True
+            if mode == "served" and outstanding:
+                for sid in [s for s in outstanding if ctx.poll(s)]:
+                    j, n = outstanding.pop(sid)
+                    ctx.burn_prob(sid, n)
+                    work += int(ctx.get_counters(sid, reqs[j]["n_replicas"])[0].sum())
+                    lat.append(time.perf_counter() - t0 - reqs[j]["arrival_s"])
+                    ctx.release(sid)
+                    busy = True
+            if not busy:
+                nxt = reqs[i]["arrival_s"] - (time.perf_counter() - t0) if i < len(reqs) else 0.0
+                time.sleep(min(max(nxt, 0.0), 0.0005) if outstanding else max(min(nxt, 0.01), 0.0))
+        wall = time.perf_counter() - t0
+        lat = np.array(lat)
+        return dict(wall_s=wall, requests=len(lat), cell_updates_per_s=work / wall,
+                    replicas_per_s=sum(r["n_replicas"] for r in reqs) / wall,
+                    p50_latency_s=float(np.percentile(lat, 50)),
+                    p99_latency_s=float(np.percentile(lat, 99)),
+                    mean_latency_s=float(lat.mean()), cell_updates=work)
+
+    out = {"served": serve("served")}
+    if args.serve_plain:
+        out["plain"] = serve("plain")
+    ctx.close()
+    sv = out["served"]
+    return {"metric": METRIC, "value": sv["cell_updates_per_s"], "unit": METRIC, "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": 1e3 * sv["wall_s"], "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"Poisson arrivals {args.rate}/s for {args.duration} s, pool of "
+                                   f"{len(sides)} landscapes (sides {min(sides)}..{max(sides)}), "
+                                   "replicas 32..2048, 12..72 h", "requests": len(reqs),
+                       "max_inflight_epochs": args.max_inflight,
+                       "timing": "host wall clock from the first arrival to the last result; "
+                                 "latency from arrival to burn counts on the host"},
+            **out}
+
+
+def run_large(args):
+    """4096^2 cells, 72 h, 256 replicas: table build + frontier + burn counts."""
+    import torch
+    import paper_1905_09317_gb300 as c2f
+    c2f.build()
+    w = S.config4()
+    L = w.landscape
+    n = L.fuel.size
+    p = _params_of(c2f, w)
+    ctx = c2f.Context(0)
+    lid = ctx.load_landscape(L.fuel, L.slope, L.aspect, cell_size=L.cell_size)
+    ctx.set_weather(lid, w.weather)
+    counts = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx.set_stream(torch.cuda.current_stream().cuda_stream)
+
+    def step():
+        ctx.build_ros(lid, p, force=True)
+        sid = ctx.simulate(lid, p)
+        ctx.burn_prob_device(sid, counts.data_ptr())
+        return sid
+
+    sid = step()
+    work = int(ctx.get_counters(sid, p.n_replicas)[0].sum())
+    ctx.release(sid)
+    ctx.profile(True)
+    ctx.kernel_times()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.release(step())
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    kt = ctx.kernel_times()
+    ctx.close()
+    return {"metric": METRIC, "value": work / dt, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "ms_per_step": 1e3 * dt, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "4096x4096 heterogeneous landscape, 72 h weather with a +90 deg "
+                                   "wind shift at hour 36, 256 replicas", "cells": int(n),
+                       "cell_updates_per_step": work},
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+            "replicas_per_s": p.n_replicas / dt}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--replicas", type=int, default=1000,
@@ -347,7 +565,17 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1000)
     ap.add_argument("--ref-sample", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="landscape", choices=["landscape", "batch", "serve", "large"])
+    ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--max-inflight", type=int, default=3, help="serve: concurrent epochs")
+    ap.add_argument("--serve-plain", action="store_true",
+                    help="serve: also replay the stream with one synchronous call per request")
     args = ap.parse_args()
+    if args.workload != "landscape" and args.impl == "ours":
+        fn = {"batch": run_batch, "serve": run_serve, "large": run_large}[args.workload]
+        print(json.dumps(fn(args)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -150,6 +150,33 @@ C2F_API int c2f_simulate(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_param
 C2F_API int c2f_simulate_batch(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
                                const c2f_sim_params *params, int32_t *sim_ids);
 
+/* ---------------------------------------------------------------------------
+ * Serving: asynchronous simulations with continuous batching.  c2f_submit
+ * validates and queues a simulation (building its landscape's rate-of-spread
+ * table first if needed) and returns at once.  Queued simulations are
+ * launched together as one "epoch" of the frontier kernel when fewer than
+ * max_inflight epochs are running and free device memory covers the epoch
+ * plus a reserve; epochs run concurrently on their own streams, so requests
+ * that arrive while others are on the GPU join the next epoch and overlap on
+ * the device.  Results are the same as c2f_simulate's, alone or in any mix.
+ * Every serving call (and c2f_pump) finishes epochs that are done and
+ * launches queued work.  c2f_poll sets *done; c2f_wait blocks until the
+ * simulation is finished; c2f_cancel drops a queued simulation (a running
+ * one finishes, and its result is discarded: later reads give
+ * C2F_ECANCELED).  Reading a simulation that is not finished gives C2F_EBUSY.
+ * ------------------------------------------------------------------------- */
+C2F_API int c2f_submit(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p, int32_t *sim_id);
+C2F_API int c2f_pump(c2f_ctx *ctx);
+C2F_API int c2f_poll(c2f_ctx *ctx, int32_t sim_id, int32_t *done);
+C2F_API int c2f_wait(c2f_ctx *ctx, int32_t sim_id);
+C2F_API int c2f_cancel(c2f_ctx *ctx, int32_t sim_id);
+
+/* Serving limits: concurrent epochs (1..16, default 3), replicas per epoch
+ * (default 65536) and device bytes kept free when admitting an epoch
+ * (default 2 GiB; an epoch is still admitted when nothing else runs). */
+C2F_API int c2f_set_serving(c2f_ctx *ctx, int32_t max_inflight, int64_t max_epoch_replicas,
+                            int64_t hbm_reserve_bytes);
+
 /* Burn-probability counts (Sec. 3.6 (i), Sec. 3.1 outputs): counts[c] = number
  * of replicas in which cell c ignited, uint32, rows*cols entries, host memory. */
 C2F_API int c2f_burn_prob(c2f_ctx *ctx, int32_t sim_id, uint32_t *counts);

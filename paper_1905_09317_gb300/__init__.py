@@ -72,6 +72,12 @@ _SIGS = [
                               C.c_void_p, C.c_void_p]),
     ("c2f_simulate", C.c_int, [C.c_void_p, C.c_int32, _P(SimParams), _P(C.c_int32)]),
     ("c2f_simulate_batch", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("c2f_submit", C.c_int, [C.c_void_p, C.c_int32, _P(SimParams), _P(C.c_int32)]),
+    ("c2f_pump", C.c_int, [C.c_void_p]),
+    ("c2f_poll", C.c_int, [C.c_void_p, C.c_int32, _P(C.c_int32)]),
+    ("c2f_wait", C.c_int, [C.c_void_p, C.c_int32]),
+    ("c2f_cancel", C.c_int, [C.c_void_p, C.c_int32]),
+    ("c2f_set_serving", C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_int64]),
     ("c2f_burn_prob", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_burn_prob_device", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_get_scars", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
@@ -203,6 +209,30 @@ class Context:
         out = (C.c_int32 * n)()
         self._check(self.lib.c2f_simulate_batch(self.h, n, ids, ps, out))
         return list(out)
+
+    # ---- serving
+    def submit(self, landscape_id: int, params: SimParams) -> int:
+        sid = C.c_int32()
+        self._check(self.lib.c2f_submit(self.h, int(landscape_id), C.byref(params), C.byref(sid)))
+        return sid.value
+
+    def pump(self) -> None:
+        self._check(self.lib.c2f_pump(self.h))
+
+    def poll(self, sim_id: int) -> bool:
+        d = C.c_int32()
+        self._check(self.lib.c2f_poll(self.h, int(sim_id), C.byref(d)))
+        return bool(d.value)
+
+    def wait(self, sim_id: int) -> None:
+        self._check(self.lib.c2f_wait(self.h, int(sim_id)))
+
+    def cancel(self, sim_id: int) -> None:
+        self._check(self.lib.c2f_cancel(self.h, int(sim_id)))
+
+    def set_serving(self, max_inflight=3, max_epoch_replicas=1 << 16, hbm_reserve_bytes=2 << 30):
+        self._check(self.lib.c2f_set_serving(self.h, int(max_inflight), int(max_epoch_replicas),
+                                             int(hbm_reserve_bytes)))
 
     # ---- outputs
     def burn_prob(self, sim_id: int, n_cells: int) -> np.ndarray:

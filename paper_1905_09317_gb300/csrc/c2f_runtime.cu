@@ -1,14 +1,26 @@
 // c2f_runtime.cu -- host runtime behind the C ABI of include/c2f.h.
 //
-// A context owns one CUDA stream, the landscapes loaded on it (device copies
-// of the fuel, slope and aspect grids, the burnable bit plane and list, the
-// hoisted per-cell FBP terms, the weather stream and the cached rate-of-spread
-// tables) and the simulation results (per-replica scar planes, optional
-// ignition steps and counters).  Device memory comes from the stream-ordered
-// allocator (cudaMallocAsync) so that allocation never synchronises the
-// device.  The frontier kernel runs one CTA per replica over a work list; a
-// replica whose burning list outgrows the per-CTA capacity is re-run with a
-// larger capacity, so results never depend on that capacity.
+// Objects and ownership
+//   Landscape  device copies of the fuel / slope / aspect grids, the burnable
+//              bit plane and list, the cell order and hoisted per-cell FBP
+//              terms, the weather stream, and the current rate-of-spread
+//              Table (shared_ptr: a simulation keeps the table it ran on alive
+//              even if the landscape gets a new one meanwhile).
+//   Sim        one simulation: its parameters, its landscape and table, and the
+//              per-replica outputs (scar planes, optional ignition steps,
+//              counters, status); state PENDING -> RUNNING -> DONE (or
+//              CANCELED / FAILED).
+//   Epoch      one launch of the frontier kernel over the replicas of one or
+//              more simulations, with its own stream, scratch and completion
+//              event.  c2f_simulate / c2f_simulate_batch run one epoch to
+//              completion; c2f_submit queues simulations and c2f_pump forms
+//              epochs from whatever is queued (continuous batching: new
+//              requests join the next epoch while earlier epochs still run,
+//              and epochs overlap on the device), subject to a free-HBM check.
+// Device memory comes from the stream-ordered allocator (cudaMallocAsync) so
+// that allocation never synchronises the device.  A replica whose burning
+// list outgrows its capacity is re-run with a larger one, so results never
+// depend on launch shapes or capacities.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,6 +28,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <list>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -76,10 +89,20 @@ struct DevBuf {
 struct TableKey {
   int32_t hours = 0, dt = 0, ellipse = 0;
   double pc = 0, curing = 0, const_ros = 0;
-  bool operator==(const TableKey &o) const {
+  bool same_options(const TableKey &o) const {
     return dt == o.dt && ellipse == o.ellipse && pc == o.pc && curing == o.curing &&
            const_ros == o.const_ros;
   }
+};
+
+struct Table {
+  TableKey key;
+  DevBuf hour_prep, base, hros, hros_pos;
+  cudaEvent_t ready = nullptr;   // recorded after the build; epochs on other streams wait on it
+  Table() = default;
+  Table(const Table &) = delete;
+  Table &operator=(const Table &) = delete;
+  ~Table() { if (ready) cudaEventDestroy(ready); }
 };
 
 struct Landscape {
@@ -87,30 +110,66 @@ struct Landscape {
   int64_t n = 0;
   double cell_size = 0;
   int32_t n_burnable = 0;
-  std::vector<uint8_t> burnable_host;  // for validation of fixed ignitions
+  std::vector<uint8_t> burnable_host;   // validation of fixed ignition cells
   DevBuf fuel, slope, aspect, burnable, burnable_list, cell_prep, order;
   bool has_slope = false;
   int32_t n_hours = 0;
   std::vector<double> weather;          // n_hours x 4
-  DevBuf weather_dev, hour_prep;
-  bool table_valid = false;
-  TableKey key;
-  DevBuf base, hros, hros_pos;
+  std::shared_ptr<DevBuf> weather_dev;
+  std::shared_ptr<Table> table;
 };
 
+enum SimState { S_PENDING = 0, S_RUNNING, S_DONE, S_CANCELED, S_FAILED };
+
 struct Sim {
-  int32_t landscape = -1;
   c2f_sim_params p{};
+  std::shared_ptr<Landscape> land;
+  std::shared_ptr<Table> table;
   int32_t rows = 0, cols = 0, wpr = 0;
   int64_t n = 0;
   DevBuf ign_plane, ign_step, work, n_ignited, ign_cell, status;
+  int state = S_PENDING;
+  int rc = C2F_OK;
+  bool cancel_requested = false;
+};
+
+struct Scratch {
+  DevBuf ent_cell, ent_mask, ent_next, ent_cofs, ent_P, counter, brn, avail;
+  int64_t slots = 0, cap = 0, brn_words = 0, avail_words = 0;
+  void reset() {
+    ent_cell.reset(); ent_mask.reset(); ent_next.reset(); ent_cofs.reset(); ent_P.reset();
+    counter.reset(); brn.reset(); avail.reset();
+    slots = cap = brn_words = avail_words = 0;
+  }
+};
+
+struct FrontierPlan {
+  std::vector<Landscape *> lands;
+  std::vector<Sim *> sims;   // in work-list order
+  std::vector<int64_t> begin;
+  std::vector<SimJob> jobs;      // host copies stay alive while their uploads are in flight
+  std::vector<int64_t> retry;
+  DevBuf djobs, dbegin, dlist;
+  int64_t cap = 0, max_n = 0, pw_max = 0, n_items = 0;
+  void (*kern)(FrontierArgs) = nullptr;
+  size_t dyn_smem = 0;
+  int threads = 32;
+  int64_t ctas = 0;
+  FrontierArgs A{};
+};
+
+struct Epoch {
+  std::vector<std::shared_ptr<Sim>> sims;
+  FrontierPlan F;
+  Scratch scratch;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
 };
 
 struct DeviceInit {
   std::once_flag once;
   cudaError_t err = cudaSuccess;
 };
-
 DeviceInit g_devinit[64];
 
 }  // namespace
@@ -118,20 +177,29 @@ DeviceInit g_devinit[64];
 struct c2f_ctx {
   int device = 0;
   int sm_count = 0;
+  int smem_optin = 0, smem_per_sm = 0;
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
+  std::recursive_mutex mu;
   std::string last_error;
   int32_t next_id = 1;
-  std::unordered_map<int32_t, std::unique_ptr<Landscape>> lands;
-  std::unordered_map<int32_t, std::unique_ptr<Sim>> sims;
-  // frontier scratch
-  DevBuf ent_cell, ent_mask, ent_next, ent_cofs, ent_P, counter, brn_scratch, avail_scratch;
-  int64_t scratch_slots = 0, scratch_cap = 0, brn_words = 0, avail_words = 0;
-  int smem_optin = 0, smem_per_sm = 0;
+  std::unordered_map<int32_t, std::shared_ptr<Landscape>> lands;
+  std::unordered_map<int32_t, std::shared_ptr<Sim>> sims;
+  // synchronous runs
+  Scratch scratch;
+  // launch shape
   int frontier_threads = 32;
-  int64_t graph_launches = 0;
-  bool window_smem = true;                 // plane windows + lists in shared memory when they fit
+  bool window_smem = true;
   int64_t cap_override = 0;
+  int64_t graph_launches = 0;
+  // serving
+  std::vector<std::shared_ptr<Sim>> pending;
+  std::list<std::unique_ptr<Epoch>> inflight;
+  std::vector<cudaStream_t> stream_pool;
+  int max_inflight = 3;
+  int64_t max_epoch_replicas = 1 << 16;
+  int64_t hbm_reserve = int64_t(2) << 30;
+  cudaStream_t read_stream = nullptr;   // result reads: not queued behind table builds
   // kernel timing
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[C2F_KT_FAMILIES];
@@ -168,11 +236,11 @@ int cuda_fail(c2f_ctx *ctx, cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what);   \
   } while (0)
 
-int dalloc(c2f_ctx *ctx, DevBuf &b, size_t bytes) {
+int dalloc_on(c2f_ctx *ctx, DevBuf &b, size_t bytes, cudaStream_t st) {
   b.reset();
-  b.st = ctx->stream;
+  b.st = st;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMallocAsync(&b.p, bytes, ctx->stream);
+  cudaError_t e = cudaMallocAsync(&b.p, bytes, st);
   if (e != cudaSuccess) {
     b.p = nullptr;
     return cuda_fail(ctx, e, "cudaMallocAsync");
@@ -180,6 +248,8 @@ int dalloc(c2f_ctx *ctx, DevBuf &b, size_t bytes) {
   b.bytes = bytes;
   return C2F_OK;
 }
+
+int dalloc(c2f_ctx *ctx, DevBuf &b, size_t bytes) { return dalloc_on(ctx, b, bytes, ctx->stream); }
 
 int ensure_device_constants(c2f_ctx *ctx) {
   if (ctx->device < 0 || ctx->device >= 64) return fail(ctx, C2F_EINVAL, "device index out of range");
@@ -204,15 +274,16 @@ cudaEvent_t get_event(c2f_ctx *ctx) {
 struct ProfScope {
   c2f_ctx *ctx;
   int fam;
+  cudaStream_t st;
   cudaEvent_t a = nullptr;
-  ProfScope(c2f_ctx *c, int f) : ctx(c), fam(f) {
-    if (ctx->profiling && (a = get_event(ctx))) cudaEventRecord(a, ctx->stream);
+  ProfScope(c2f_ctx *c, int f, cudaStream_t s) : ctx(c), fam(f), st(s) {
+    if (ctx->profiling && (a = get_event(ctx))) cudaEventRecord(a, st);
   }
   ~ProfScope() {
     if (!a) return;
     cudaEvent_t b = get_event(ctx);
     if (!b) { ctx->event_pool.push_back(a); return; }
-    cudaEventRecord(b, ctx->stream);
+    cudaEventRecord(b, st);
     ctx->prof_events[fam].emplace_back(a, b);
   }
 };
@@ -228,8 +299,6 @@ int validate_params(c2f_ctx *ctx, const Landscape &L, const c2f_sim_params *p) {
   if (p->hours > L.n_hours)
     return fail(ctx, C2F_EINVAL, "hours (%d) exceeds the weather stream (%d hours)", p->hours,
                 L.n_hours);
-  if ((int64_t)p->hours * (60 / p->minutes_per_step) > 2000000000LL)
-    return fail(ctx, C2F_EINVAL, "too many fire periods");
   if (!(p->ros_sigma >= 0.0 && p->ros_sigma <= 1.0))
     return fail(ctx, C2F_EINVAL, "ros_sigma must lie in [0, 1]");
   if (!std::isfinite(p->ros_threshold) || !std::isfinite(p->burnout_delta) ||
@@ -265,72 +334,77 @@ TableKey key_of(const c2f_sim_params *p) {
   return k;
 }
 
-// Table of a landscape for the options in *p, hours [0, p->hours):
-// allocation (prepare_table) and the kernels (launch_table: a1 hour prep,
-// then K1), split so that the kernels can be captured in a CUDA graph.
-int prepare_table(c2f_ctx *ctx, Landscape &L, const c2f_sim_params *p) {
+bool table_ok(const Landscape &L, const TableKey &k) {
+  return L.table && L.table->key.same_options(k) && L.table->key.hours >= k.hours;
+}
+
+// A new table object for the options in k (allocation only); the previous one
+// stays alive while simulations that ran on it still hold it.
+int prepare_table(c2f_ctx *ctx, Landscape &L, const TableKey &k) {
   int rc;
-  const int32_t H = p->hours;
-  if ((rc = dalloc(ctx, L.hour_prep, sizeof(HourPrep) * (size_t)L.n_hours))) return rc;
-  if ((rc = dalloc(ctx, L.base, sizeof(int64_t) * 8 * (size_t)L.n * H))) return rc;
-  if ((rc = dalloc(ctx, L.hros, sizeof(double) * (size_t)L.n * H))) return rc;
-  if (!L.hros_pos.p && (rc = dalloc(ctx, L.hros_pos, 4))) return rc;
-  L.table_valid = false;
+  auto T = std::make_shared<Table>();
+  T->key = k;
+  CK(cudaEventCreateWithFlags(&T->ready, cudaEventDisableTiming));
+  if ((rc = dalloc(ctx, T->hour_prep, sizeof(HourPrep) * (size_t)L.n_hours))) return rc;
+  if ((rc = dalloc(ctx, T->base, sizeof(int64_t) * 8 * (size_t)L.n * k.hours))) return rc;
+  if ((rc = dalloc(ctx, T->hros, sizeof(double) * (size_t)L.n * k.hours))) return rc;
+  if ((rc = dalloc(ctx, T->hros_pos, 4))) return rc;
+  L.table = T;
   return C2F_OK;
 }
 
-int launch_table(c2f_ctx *ctx, Landscape &L, const c2f_sim_params *p) {
-  const int32_t H = p->hours;
-  ProfScope prof(ctx, 0);
-  k_hour_prep<<<grid1(L.n_hours, 64), 64, 0, ctx->stream>>>(
-      L.weather_dev.as<double>(), L.n_hours, p->o1_curing_pct, L.hour_prep.as<HourPrep>());
+// a1 (hour prep) and K1 for L.table, on stream st (capturable)
+int launch_table(c2f_ctx *ctx, Landscape &L, cudaStream_t st) {
+  Table &T = *L.table;
+  const TableKey &k = T.key;
+  ProfScope prof(ctx, 0, st);
+  k_hour_prep<<<grid1(L.n_hours, 64), 64, 0, st>>>(L.weather_dev->as<double>(), L.n_hours, k.curing,
+                                                    T.hour_prep.as<HourPrep>());
   CKL("k_hour_prep");
-  CK(cudaMemsetAsync(L.hros_pos.p, 1, 4, ctx->stream));   // non-zero until a row says otherwise
+  CK(cudaMemsetAsync(T.hros_pos.p, 1, 4, st));   // non-zero until a row says otherwise
   RosTableArgs a{};
   a.fuel = L.fuel.as<uint8_t>();
   a.slope = L.has_slope ? L.slope.as<float>() : nullptr;
   a.burnable = L.burnable.as<uint32_t>();
   a.rows = L.rows; a.cols = L.cols; a.wpr = L.wpr;
   a.cell = L.cell_prep.as<CellPrep>();
-  a.hour = L.hour_prep.as<HourPrep>();
+  a.hour = T.hour_prep.as<HourPrep>();
   a.hour0 = 0;
-  a.pcf = p->m1_pc / 100.0;
-  a.const_ros = p->const_ros;
-  a.dt2p32 = (double)p->minutes_per_step * 4294967296.0;
-  a.ellipse_mode = p->ellipse_mode;
-  a.base = L.base.as<int64_t>();
-  a.hros = L.hros.as<double>();
+  a.pcf = k.pc / 100.0;
+  a.const_ros = k.const_ros;
+  a.dt2p32 = (double)k.dt * 4294967296.0;
+  a.ellipse_mode = k.ellipse;
+  a.base = T.base.as<int64_t>();
+  a.hros = T.hros.as<double>();
   a.ros8 = nullptr;
-  a.hros_pos = L.hros_pos.as<int32_t>();
+  a.hros_pos = T.hros_pos.as<int32_t>();
   a.order = L.order.as<int32_t>();
-  dim3 grid(grid1(L.n, 128), (unsigned)H);
-  k_ros_table<<<grid, 128, 0, ctx->stream>>>(a);
+  dim3 grid(grid1(L.n, 128), (unsigned)k.hours);
+  k_ros_table<<<grid, 128, 0, st>>>(a);
   CKL("k_ros_table");
-  L.key = key_of(p);
-  L.table_valid = true;
+  // inside a graph capture the event is left unrecorded (reads as complete):
+  // the graph runs to completion before the capturing call returns
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cs));
+  if (cs == cudaStreamCaptureStatusNone) CK(cudaEventRecord(T.ready, st));
   return C2F_OK;
 }
 
-bool table_ok(const Landscape &L, const c2f_sim_params *p) {
-  const TableKey k = key_of(p);
-  return L.table_valid && L.key == k && L.key.hours >= k.hours;
-}
-
-int ensure_table(c2f_ctx *ctx, Landscape &L, const c2f_sim_params *p, bool force) {
-  if (!force && table_ok(L, p)) return C2F_OK;
-  int rc = prepare_table(ctx, L, p);
+int ensure_table(c2f_ctx *ctx, Landscape &L, const TableKey &k, bool force) {
+  if (!force && table_ok(L, k)) return C2F_OK;
+  int rc = prepare_table(ctx, L, k);
   if (rc) return rc;
-  return launch_table(ctx, L, p);
+  return launch_table(ctx, L, ctx->stream);
 }
 
-Landscape *find_land(c2f_ctx *ctx, int32_t id) {
+std::shared_ptr<Landscape> find_land(c2f_ctx *ctx, int32_t id) {
   auto it = ctx->lands.find(id);
-  return it == ctx->lands.end() ? nullptr : it->second.get();
+  return it == ctx->lands.end() ? nullptr : it->second;
 }
 
-Sim *find_sim(c2f_ctx *ctx, int32_t id) {
+std::shared_ptr<Sim> find_sim(c2f_ctx *ctx, int32_t id) {
   auto it = ctx->sims.find(id);
-  return it == ctx->sims.end() ? nullptr : it->second.get();
+  return it == ctx->sims.end() ? nullptr : it->second;
 }
 
 int64_t default_cap(const c2f_ctx *ctx, const Landscape &L) {
@@ -339,50 +413,62 @@ int64_t default_cap(const c2f_ctx *ctx, const Landscape &L) {
   return std::min<int64_t>(L.n, c);
 }
 
-int ensure_scratch(c2f_ctx *ctx, int64_t slots, int64_t cap) {
-  if (slots <= ctx->scratch_slots && cap <= ctx->scratch_cap && ctx->ent_cell.p) return C2F_OK;
-  slots = std::max(slots, ctx->scratch_slots);
-  cap = std::max(cap, ctx->scratch_cap);
+int ensure_scratch(c2f_ctx *ctx, Scratch &S, cudaStream_t st, int64_t slots, int64_t cap, int64_t pw) {
   int rc;
-  const size_t sc = (size_t)slots * cap;
-  if ((rc = dalloc(ctx, ctx->ent_cell, sc * 4))) return rc;
-  if ((rc = dalloc(ctx, ctx->ent_mask, sc))) return rc;
-  if ((rc = dalloc(ctx, ctx->ent_next, sc))) return rc;
-  if ((rc = dalloc(ctx, ctx->ent_cofs, sc * 8))) return rc;  // 8 offsets per entry
-  if ((rc = dalloc(ctx, ctx->ent_P, sc * 64))) return rc;
-  if (!ctx->counter.p && (rc = dalloc(ctx, ctx->counter, 64))) return rc;
-  ctx->scratch_slots = slots;
-  ctx->scratch_cap = cap;
+  if (!(slots <= S.slots && cap <= S.cap && S.ent_cell.p)) {
+    slots = std::max(slots, S.slots);
+    cap = std::max(cap, S.cap);
+    const size_t sc = (size_t)slots * cap;
+    if ((rc = dalloc_on(ctx, S.ent_cell, sc * 4, st))) return rc;
+    if ((rc = dalloc_on(ctx, S.ent_mask, sc, st))) return rc;
+    if ((rc = dalloc_on(ctx, S.ent_next, sc, st))) return rc;
+    if ((rc = dalloc_on(ctx, S.ent_cofs, sc * 8, st))) return rc;
+    if ((rc = dalloc_on(ctx, S.ent_P, sc * 64, st))) return rc;
+    S.slots = slots;
+    S.cap = cap;
+  }
+  if (!S.counter.p && (rc = dalloc_on(ctx, S.counter, 64, st))) return rc;
+  if (S.slots * pw > S.brn_words) {
+    if ((rc = dalloc_on(ctx, S.brn, (size_t)S.slots * pw * 4, st))) return rc;
+    S.brn_words = S.slots * pw;
+  }
+  if (S.slots * pw > S.avail_words) {
+    if ((rc = dalloc_on(ctx, S.avail, (size_t)S.slots * pw * 4, st))) return rc;
+    S.avail_words = S.slots * pw;
+  }
   return C2F_OK;
 }
 
-int alloc_sim(c2f_ctx *ctx, const Landscape &L, Sim &s) {
+// output buffers of a simulation, allocated and initialised on stream st
+int alloc_sim(c2f_ctx *ctx, Sim &s, cudaStream_t st) {
   int rc;
+  const Landscape &L = *s.land;
   const int64_t R = s.p.n_replicas;
   const size_t pw = (size_t)L.rows * L.wpr;
-  if ((rc = dalloc(ctx, s.ign_plane, pw * 4 * R))) return rc;
+  if ((rc = dalloc_on(ctx, s.ign_plane, pw * 4 * R, st))) return rc;
   if (s.p.outputs & C2F_OUT_IGN_STEPS) {
-    if ((rc = dalloc(ctx, s.ign_step, (size_t)L.n * 4 * R))) return rc;
-    CK(cudaMemsetAsync(s.ign_step.p, 0xFF, (size_t)L.n * 4 * R, ctx->stream));
+    if ((rc = dalloc_on(ctx, s.ign_step, (size_t)L.n * 4 * R, st))) return rc;
+    CK(cudaMemsetAsync(s.ign_step.p, 0xFF, (size_t)L.n * 4 * R, st));
   }
-  if ((rc = dalloc(ctx, s.work, 8 * R))) return rc;
-  if ((rc = dalloc(ctx, s.n_ignited, 4 * R))) return rc;
-  if ((rc = dalloc(ctx, s.ign_cell, 4 * R))) return rc;
-  if ((rc = dalloc(ctx, s.status, 4 * R))) return rc;
-  CK(cudaMemsetAsync(s.status.p, 0, 4 * R, ctx->stream));
-  s.rows = L.rows; s.cols = L.cols; s.wpr = L.wpr; s.n = L.n;
+  if ((rc = dalloc_on(ctx, s.work, 8 * R, st))) return rc;
+  if ((rc = dalloc_on(ctx, s.n_ignited, 4 * R, st))) return rc;
+  if ((rc = dalloc_on(ctx, s.ign_cell, 4 * R, st))) return rc;
+  if ((rc = dalloc_on(ctx, s.status, 4 * R, st))) return rc;
+  CK(cudaMemsetAsync(s.status.p, 0, 4 * R, st));
   return C2F_OK;
 }
 
-SimJob job_of(const Landscape &L, const Sim &s) {
+SimJob job_of(const Sim &s) {
+  const Landscape &L = *s.land;
+  const Table &T = *s.table;
   SimJob j{};
   j.rows = L.rows; j.cols = L.cols; j.wpr = L.wpr;
   j.n_burnable = L.n_burnable;
   j.burnable = L.burnable.as<uint32_t>();
   j.burnable_list = L.burnable_list.as<int32_t>();
-  j.base = L.base.as<int64_t>();
-  j.hros = L.hros.as<double>();
-  j.hros_pos = L.hros_pos.as<int32_t>();
+  j.base = T.base.as<int64_t>();
+  j.hros = T.hros.as<double>();
+  j.hros_pos = T.hros_pos.as<int32_t>();
   j.seed = s.p.seed;
   j.sigma = (float)s.p.ros_sigma;
   j.ignition_mode = s.p.ignition_mode;
@@ -403,26 +489,13 @@ SimJob job_of(const Landscape &L, const Sim &s) {
   return j;
 }
 
+// ------------------------------------------------------------------ frontier epochs
 // Frontier over the replicas of several simulations: one work list of
 // (simulation, replica) items, simulations ordered longest-expected-first so
-// that the long replicas start early.  FrontierPlan holds everything a launch
-// needs; plan_frontier allocates and uploads (not capturable), launch_frontier
-// issues K2 and the K3 launch (capturable in a CUDA graph), finish_frontier
-// reads the per-replica status and re-runs, with a larger burning list, any
-// replica whose list overflowed.
-struct FrontierPlan {
-  std::vector<Landscape *> lands;
-  std::vector<Sim *> sims;   // in work-list order
-  std::vector<int64_t> begin;
-  DevBuf djobs, dbegin;
-  int64_t cap = 0, max_n = 0, pw_max = 0, n_items = 0;
-  void (*kern)(FrontierArgs) = nullptr;
-  size_t dyn_smem = 0;
-  int threads = 32;
-  int64_t ctas = 0;
-  FrontierArgs A{};
-};
-
+// that the long replicas start early.  plan_frontier allocates and uploads
+// (not capturable), launch_frontier issues K2 and the K3 launch (capturable
+// in a CUDA graph), finish_frontier reads the per-replica status and re-runs,
+// with a larger burning list, any replica whose list overflowed.
 int64_t replica_cost(const Landscape &L, const Sim &s) {
   return (int64_t)s.p.hours * std::min<int64_t>(L.n_burnable, 50000);
 }
@@ -430,7 +503,8 @@ int64_t replica_cost(const Landscape &L, const Sim &s) {
 // launch shape for `todo` items at burning-list capacity `cap_in`; attempt 0
 // sizes the shared-memory list so that the launch is resident at once (capped
 // at 8 warps per SM), later attempts give each replica more room
-int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, int64_t todo, int64_t cap_in, int attempt) {
+int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, int64_t todo,
+                   int64_t cap_in, int attempt) {
   int rc;
   const int threads = ctx->frontier_threads;   // 32, 64 or 128: one replica per warp
   const int wpc = threads / 32;
@@ -462,15 +536,7 @@ int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, int64_t todo, int64_t cap_in, 
   const int64_t max_ctas = (int64_t)ctx->sm_count * bps;
   F.ctas = std::min<int64_t>((todo + wpc - 1) / wpc, max_ctas);
   const int64_t slots = F.ctas * wpc;   // one warp per slot
-  if ((rc = ensure_scratch(ctx, slots, cap))) return rc;
-  if (slots * F.pw_max > ctx->brn_words) {
-    if ((rc = dalloc(ctx, ctx->brn_scratch, (size_t)slots * F.pw_max * 4))) return rc;
-    ctx->brn_words = slots * F.pw_max;
-  }
-  if (slots * F.pw_max > ctx->avail_words) {
-    if ((rc = dalloc(ctx, ctx->avail_scratch, (size_t)slots * F.pw_max * 4))) return rc;
-    ctx->avail_words = slots * F.pw_max;
-  }
+  if ((rc = ensure_scratch(ctx, S, st, slots, cap, F.pw_max))) return rc;
   FrontierArgs &A = F.A;
   A = FrontierArgs{};
   A.jobs = F.djobs.as<SimJob>();
@@ -478,82 +544,80 @@ int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, int64_t todo, int64_t cap_in, 
   A.item_begin = F.dbegin.as<int64_t>();
   A.item_list = nullptr;
   A.n_items = todo;
-  A.counter = ctx->counter.as<unsigned long long>();
+  A.counter = S.counter.as<unsigned long long>();
   A.cap = (int32_t)cap;
-  A.ent_cell = ctx->ent_cell.as<int32_t>();
-  A.ent_mask = ctx->ent_mask.as<uint8_t>();
-  A.ent_next = ctx->ent_next.as<uint8_t>();
-  A.ent_cofs = ctx->ent_cofs.as<uint8_t>();
-  A.ent_P = ctx->ent_P.as<int64_t>();
+  A.ent_cell = S.ent_cell.as<int32_t>();
+  A.ent_mask = S.ent_mask.as<uint8_t>();
+  A.ent_next = S.ent_next.as<uint8_t>();
+  A.ent_cofs = S.ent_cofs.as<uint8_t>();
+  A.ent_P = S.ent_P.as<int64_t>();
   A.pw_max = F.pw_max;
-  A.brn_scratch = ctx->brn_scratch.as<uint32_t>();
-  A.avail_scratch = ctx->avail_scratch.as<uint32_t>();
+  A.brn_scratch = S.brn.as<uint32_t>();
+  A.avail_scratch = S.avail.as<uint32_t>();
   A.smem_warp_words = warp_words;
   F.cap = cap;
   return C2F_OK;
 }
 
-int plan_frontier(c2f_ctx *ctx, std::vector<Landscape *> lands, std::vector<Sim *> sims,
-                  FrontierPlan &F) {
-  int rc;
+int plan_frontier(c2f_ctx *ctx, const std::vector<Sim *> &sims, FrontierPlan &F, Scratch &S,
+                  cudaStream_t st) {
   const int32_t nj = (int32_t)sims.size();
   std::vector<int32_t> order(nj);
   for (int32_t i = 0; i < nj; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    return replica_cost(*lands[a], *sims[a]) > replica_cost(*lands[b], *sims[b]);
+    return replica_cost(*sims[a]->land, *sims[a]) > replica_cost(*sims[b]->land, *sims[b]);
   });
   F.lands.clear();
   F.sims.clear();
-  for (int32_t i : order) { F.lands.push_back(lands[i]); F.sims.push_back(sims[i]); }
-  std::vector<SimJob> jobs(nj);
+  for (int32_t i : order) { F.lands.push_back(sims[i]->land.get()); F.sims.push_back(sims[i]); }
+  std::vector<SimJob> &jobs = F.jobs;
+  jobs.assign(nj, SimJob{});
   F.begin.assign(nj + 1, 0);
   F.cap = 0; F.max_n = 0; F.pw_max = 0;
   for (int32_t i = 0; i < nj; ++i) {
-    jobs[i] = job_of(*F.lands[i], *F.sims[i]);
+    jobs[i] = job_of(*F.sims[i]);
     F.begin[i + 1] = F.begin[i] + F.sims[i]->p.n_replicas;
     F.cap = std::max(F.cap, default_cap(ctx, *F.lands[i]));
     F.max_n = std::max(F.max_n, F.lands[i]->n);
     F.pw_max = std::max<int64_t>(F.pw_max, (int64_t)F.lands[i]->rows * F.lands[i]->wpr);
   }
   F.n_items = F.begin[nj];
-  if ((rc = dalloc(ctx, F.djobs, sizeof(SimJob) * nj))) return rc;
-  if ((rc = dalloc(ctx, F.dbegin, sizeof(int64_t) * (nj + 1)))) return rc;
-  CK(cudaMemcpyAsync(F.djobs.p, jobs.data(), sizeof(SimJob) * nj, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(F.dbegin.p, F.begin.data(), sizeof(int64_t) * (nj + 1), cudaMemcpyHostToDevice,
-                     ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));   // host arrays above are about to go out of scope
-  return shape_frontier(ctx, F, F.n_items, F.cap, 0);
+  int rc;
+  if ((rc = dalloc_on(ctx, F.djobs, sizeof(SimJob) * nj, st))) return rc;
+  if ((rc = dalloc_on(ctx, F.dbegin, sizeof(int64_t) * (nj + 1), st))) return rc;
+  CK(cudaMemcpyAsync(F.djobs.p, jobs.data(), sizeof(SimJob) * nj, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(F.dbegin.p, F.begin.data(), sizeof(int64_t) * (nj + 1), cudaMemcpyHostToDevice, st));
+  return shape_frontier(ctx, F, S, st, F.n_items, F.cap, 0);
 }
 
-int launch_frontier(c2f_ctx *ctx, FrontierPlan &F) {
+int launch_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st) {
   {
-    ProfScope prof(ctx, 1);
+    ProfScope prof(ctx, 1, st);
     for (size_t i = 0; i < F.sims.size(); ++i) {
-      k_ignite<<<grid1(F.sims[i]->p.n_replicas, 128), 128, 0, ctx->stream>>>(F.djobs.as<SimJob>(), (int32_t)i);
+      k_ignite<<<grid1(F.sims[i]->p.n_replicas, 128), 128, 0, st>>>(F.djobs.as<SimJob>(), (int32_t)i);
       CKL("k_ignite");
     }
   }
-  CK(cudaMemsetAsync(ctx->counter.p, 0, 8, ctx->stream));
-  ProfScope prof(ctx, 2);
-  F.kern<<<(unsigned)F.ctas, F.threads, F.dyn_smem, ctx->stream>>>(F.A);
+  CK(cudaMemsetAsync(S.counter.p, 0, 8, st));
+  ProfScope prof(ctx, 2, st);
+  F.kern<<<(unsigned)F.ctas, F.threads, F.dyn_smem, st>>>(F.A);
   CKL("k_frontier");
   return C2F_OK;
 }
 
-int finish_frontier(c2f_ctx *ctx, FrontierPlan &F) {
+int finish_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st) {
   int rc;
   const int32_t nj = (int32_t)F.sims.size();
   for (int attempt = 1;; ++attempt) {
     std::vector<int64_t> failed;
     for (int32_t i = 0; i < nj; ++i) {
       const int32_t R = F.sims[i]->p.n_replicas;
-      std::vector<int32_t> st(R);
-      CK(cudaMemcpyAsync(st.data(), F.sims[i]->status.p, 4 * (size_t)R, cudaMemcpyDeviceToHost,
-                         ctx->stream));
-      CK(cudaStreamSynchronize(ctx->stream));
+      std::vector<int32_t> stv(R);
+      CK(cudaMemcpyAsync(stv.data(), F.sims[i]->status.p, 4 * (size_t)R, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
       for (int32_t r = 0; r < R; ++r) {
-        if (st[r] == 2) return fail(ctx, C2F_ECUDA, "internal frontier error (replica %d)", r);
-        if (st[r]) failed.push_back(F.begin[i] + r);
+        if (stv[r] == 2) return fail(ctx, C2F_ECUDA, "internal frontier error (replica %d)", r);
+        if (stv[r]) failed.push_back(F.begin[i] + r);
       }
     }
     if (failed.empty()) return C2F_OK;
@@ -563,33 +627,239 @@ int finish_frontier(c2f_ctx *ctx, FrontierPlan &F) {
       const int32_t i = (int32_t)(std::upper_bound(F.begin.begin(), F.begin.end(), it) - F.begin.begin() - 1);
       const int64_t r = it - F.begin[i];
       Sim &s = *F.sims[i];
-      CK(cudaMemsetAsync(s.status.as<int32_t>() + r, 0, 4, ctx->stream));
+      CK(cudaMemsetAsync(s.status.as<int32_t>() + r, 0, 4, st));
       if (s.ign_step.p)
-        CK(cudaMemsetAsync(s.ign_step.as<int32_t>() + r * s.n, 0xFF, (size_t)s.n * 4, ctx->stream));
+        CK(cudaMemsetAsync(s.ign_step.as<int32_t>() + r * s.n, 0xFF, (size_t)s.n * 4, st));
     }
-    if ((rc = shape_frontier(ctx, F, (int64_t)failed.size(), cap, attempt))) return rc;
-    DevBuf dlist;
-    if ((rc = dalloc(ctx, dlist, sizeof(int64_t) * failed.size()))) return rc;
-    CK(cudaMemcpyAsync(dlist.p, failed.data(), sizeof(int64_t) * failed.size(), cudaMemcpyHostToDevice,
-                       ctx->stream));
-    F.A.item_list = dlist.as<int64_t>();
-    CK(cudaMemsetAsync(ctx->counter.p, 0, 8, ctx->stream));
+    if ((rc = shape_frontier(ctx, F, S, st, (int64_t)failed.size(), cap, attempt))) return rc;
+    F.retry = failed;
+    if ((rc = dalloc_on(ctx, F.dlist, sizeof(int64_t) * F.retry.size(), st))) return rc;
+    CK(cudaMemcpyAsync(F.dlist.p, F.retry.data(), sizeof(int64_t) * F.retry.size(), cudaMemcpyHostToDevice, st));
+    F.A.item_list = F.dlist.as<int64_t>();
+    CK(cudaMemsetAsync(S.counter.p, 0, 8, st));
     {
-      ProfScope prof(ctx, 2);
-      F.kern<<<(unsigned)F.ctas, F.threads, F.dyn_smem, ctx->stream>>>(F.A);
+      ProfScope prof(ctx, 2, st);
+      F.kern<<<(unsigned)F.ctas, F.threads, F.dyn_smem, st>>>(F.A);
       CKL("k_frontier(retry)");
     }
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaStreamSynchronize(st));
   }
 }
 
-int run_frontier(c2f_ctx *ctx, std::vector<Landscape *> &lands, std::vector<Sim *> &sims) {
-  FrontierPlan F;
-  int rc = plan_frontier(ctx, lands, sims, F);
-  if (rc) return rc;
-  if ((rc = launch_frontier(ctx, F))) return rc;
-  return finish_frontier(ctx, F);
+// validate + create simulations; their tables are built on ctx->stream (or,
+// when `built` is given, allocated and listed for the caller to launch).
+// `serving`: tables cover the whole weather stream, so that later requests on
+// the landscape reuse them, and output buffers are left for the epoch to
+// allocate on its own stream when it is admitted.
+int make_sims(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_sim_params *params,
+              std::vector<std::shared_ptr<Sim>> &out, std::vector<Landscape *> *built,
+              bool serving = false) {
+  int rc;
+  std::vector<std::shared_ptr<Landscape>> lands(n);
+  for (int32_t i = 0; i < n; ++i) {
+    lands[i] = find_land(ctx, ids[i]);
+    if (!lands[i]) return fail(ctx, C2F_ENOTFOUND, "unknown landscape %d", ids[i]);
+    if (lands[i]->n_hours < 1) return fail(ctx, C2F_EINVAL, "landscape %d has no weather", ids[i]);
+    if ((rc = validate_params(ctx, *lands[i], &params[i]))) return rc;
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    for (int32_t k = 0; k < i; ++k)
+      if (ids[k] == ids[i] && !key_of(&params[k]).same_options(key_of(&params[i])))
+        return fail(ctx, C2F_EINVAL, "batch entries %d and %d share a landscape with different ROS options", k, i);
+    bool first = true;
+    for (int32_t k = 0; k < i; ++k) if (ids[k] == ids[i]) first = false;
+    if (!first) continue;
+    TableKey want = key_of(&params[i]);
+    for (int32_t k = i + 1; k < n; ++k)
+      if (ids[k] == ids[i]) want.hours = std::max(want.hours, params[k].hours);
+    if (serving && !table_ok(*lands[i], want)) want.hours = std::max(want.hours, lands[i]->n_hours);
+    if (!table_ok(*lands[i], want)) {
+      if ((rc = prepare_table(ctx, *lands[i], want))) return rc;
+      if (built) built->push_back(lands[i].get());
+      else if ((rc = launch_table(ctx, *lands[i], ctx->stream))) return rc;
+    }
+  }
+  out.resize(n);
+  for (int32_t i = 0; i < n; ++i) {
+    auto s = std::make_shared<Sim>();
+    s->p = params[i];
+    s->land = lands[i];
+    s->table = lands[i]->table;
+    s->rows = lands[i]->rows; s->cols = lands[i]->cols; s->wpr = lands[i]->wpr; s->n = lands[i]->n;
+    out[i] = s;
+  }
+  return C2F_OK;
 }
+
+void register_sims(c2f_ctx *ctx, std::vector<std::shared_ptr<Sim>> &sims, int32_t *ids) {
+  for (size_t i = 0; i < sims.size(); ++i) {
+    const int32_t id = ctx->next_id++;
+    ctx->sims[id] = sims[i];
+    ids[i] = id;
+  }
+}
+
+// synchronous: one epoch on ctx->stream, run to completion
+int simulate_many(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_sim_params *params,
+                  int32_t *sim_ids) {
+  if (n < 1 || !ids || !params || !sim_ids) return fail(ctx, C2F_EINVAL, "bad batch arguments");
+  CK(cudaSetDevice(ctx->device));
+  int rc;
+  const bool graph = n > 1 && !ctx->profiling;
+  std::vector<Landscape *> builds;
+  std::vector<std::shared_ptr<Sim>> sims;
+  if ((rc = make_sims(ctx, n, ids, params, sims, graph ? &builds : nullptr))) return rc;
+  std::vector<Sim *> raw;
+  for (auto &s : sims) raw.push_back(s.get());
+  for (auto &s : sims)   // tables built earlier, possibly on another stream
+    if (std::find(builds.begin(), builds.end(), s->land.get()) == builds.end())
+      CK(cudaStreamWaitEvent(ctx->stream, s->table->ready, 0));
+  for (auto &s : sims)
+    if ((rc = alloc_sim(ctx, *s, ctx->stream))) return rc;
+  FrontierPlan F;
+  if ((rc = plan_frontier(ctx, raw, F, ctx->scratch, ctx->stream))) return rc;
+  // a batch's launches (table builds, ignitions, the frontier) go out as one
+  // CUDA graph; a single simulation is launched directly
+  if (graph) {
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    int lrc = C2F_OK;
+    for (Landscape *L : builds) if (!lrc) lrc = launch_table(ctx, *L, ctx->stream);
+    if (!lrc) lrc = launch_frontier(ctx, F, ctx->scratch, ctx->stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+    if (lrc) { if (g) cudaGraphDestroy(g); return lrc; }
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+    const cudaError_t le = cudaGraphLaunch(ge, ctx->stream);
+    cudaGraphExecDestroy(ge);
+    if (le != cudaSuccess) return cuda_fail(ctx, le, "cudaGraphLaunch");
+    ++ctx->graph_launches;
+  } else {
+    if ((rc = launch_frontier(ctx, F, ctx->scratch, ctx->stream))) return rc;
+  }
+  if ((rc = finish_frontier(ctx, F, ctx->scratch, ctx->stream))) return rc;
+  for (auto &s : sims) s->state = S_DONE;
+  register_sims(ctx, sims, sim_ids);
+  return C2F_OK;
+}
+
+// ------------------------------------------------------------------ serving
+cudaStream_t take_stream(c2f_ctx *ctx) {
+  if (!ctx->stream_pool.empty()) {
+    cudaStream_t s = ctx->stream_pool.back();
+    ctx->stream_pool.pop_back();
+    return s;
+  }
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return s;
+}
+
+// device bytes an epoch needs beyond what its simulations already hold
+int64_t epoch_bytes(c2f_ctx *ctx, const std::vector<std::shared_ptr<Sim>> &sims) {
+  int64_t R = 0, pw = 0, cap = 0, outputs = 0;
+  for (auto &s : sims) {
+    const int64_t r = s->p.n_replicas, spw = (int64_t)s->rows * s->wpr;
+    R += r;
+    pw = std::max<int64_t>(pw, spw);
+    cap = std::max(cap, default_cap(ctx, *s->land));
+    outputs += r * (spw * 4 + 24);
+    if (s->p.outputs & C2F_OUT_IGN_STEPS) outputs += r * s->n * 4;
+  }
+  const int64_t slots = std::min<int64_t>(R, (int64_t)ctx->sm_count * 8);
+  return outputs + slots * (cap * 78 + pw * 8) + 4096;
+}
+
+// finish the epochs whose work is done (all of them, when `block`)
+int reap(c2f_ctx *ctx, bool block) {
+  int first_rc = C2F_OK;
+  for (auto it = ctx->inflight.begin(); it != ctx->inflight.end();) {
+    Epoch &E = **it;
+    if (!block) {
+      const cudaError_t q = cudaEventQuery(E.done);
+      if (q == cudaErrorNotReady) { ++it; continue; }
+      if (q != cudaSuccess) return cuda_fail(ctx, q, "cudaEventQuery");
+    }
+    const int rc = finish_frontier(ctx, E.F, E.scratch, E.stream);
+    for (auto &s : E.sims) {
+      if (rc) { s->state = S_FAILED; s->rc = rc; }
+      else s->state = s->cancel_requested ? S_CANCELED : S_DONE;
+    }
+    if (rc && !first_rc) first_rc = rc;
+    cudaStreamSynchronize(E.stream);
+    cudaEventDestroy(E.done);
+    E.F.djobs.reset(); E.F.dbegin.reset(); E.F.dlist.reset();
+    E.scratch.reset();
+    cudaStreamSynchronize(E.stream);   // the scratch frees above are ordered on it
+    ctx->stream_pool.push_back(E.stream);
+    it = ctx->inflight.erase(it);
+  }
+  return first_rc;
+}
+
+// launch the queued simulations as one epoch when a slot and memory allow
+int launch_pending(c2f_ctx *ctx) {
+  if (ctx->pending.empty() || (int)ctx->inflight.size() >= ctx->max_inflight) return C2F_OK;
+  std::vector<std::shared_ptr<Sim>> batch;
+  int64_t R = 0;
+  while (!ctx->pending.empty() &&
+         (batch.empty() || R + ctx->pending.front()->p.n_replicas <= ctx->max_epoch_replicas)) {
+    R += ctx->pending.front()->p.n_replicas;
+    batch.push_back(ctx->pending.front());
+    ctx->pending.erase(ctx->pending.begin());
+  }
+  size_t freeb = 0, totalb = 0;
+  CK(cudaMemGetInfo(&freeb, &totalb));
+  if ((int64_t)freeb < epoch_bytes(ctx, batch) + ctx->hbm_reserve && !ctx->inflight.empty()) {
+    ctx->pending.insert(ctx->pending.begin(), batch.begin(), batch.end());   // admission: wait for memory
+    return C2F_OK;
+  }
+  std::unique_ptr<Epoch> E(new Epoch());
+  E->sims = batch;
+  E->stream = take_stream(ctx);
+  if (!E->stream) return fail(ctx, C2F_ECUDA, "cannot create a stream");
+  CK(cudaEventCreateWithFlags(&E->done, cudaEventDisableTiming));
+  // the epoch waits for its own tables only, not for other builds queued behind them
+  std::vector<Sim *> raw;
+  int rc = C2F_OK;
+  for (auto &s : batch) {
+    raw.push_back(s.get());
+    s->state = S_RUNNING;
+    if (!rc && cudaStreamWaitEvent(E->stream, s->table->ready, 0) != cudaSuccess)
+      rc = cuda_fail(ctx, cudaGetLastError(), "cudaStreamWaitEvent");
+    if (!rc) rc = alloc_sim(ctx, *s, E->stream);
+  }
+  if (!rc) rc = plan_frontier(ctx, raw, E->F, E->scratch, E->stream);
+  if (!rc) rc = launch_frontier(ctx, E->F, E->scratch, E->stream);
+  if (rc) {
+    for (auto &s : batch) { s->state = S_FAILED; s->rc = rc; }
+    cudaStreamSynchronize(E->stream);
+    cudaEventDestroy(E->done);
+    ctx->stream_pool.push_back(E->stream);
+    return rc;
+  }
+  CK(cudaEventRecord(E->done, E->stream));
+  ctx->inflight.push_back(std::move(E));
+  return C2F_OK;
+}
+
+int pump(c2f_ctx *ctx) {
+  int rc = reap(ctx, false);
+  if (rc) return rc;
+  return launch_pending(ctx);
+}
+
+int sim_ready(c2f_ctx *ctx, const Sim &s) {
+  if (s.state == S_DONE) return C2F_OK;
+  if (s.state == S_CANCELED) return fail(ctx, C2F_ECANCELED, "simulation was cancelled");
+  if (s.state == S_FAILED) return s.rc ? s.rc : C2F_ECUDA;
+  return fail(ctx, C2F_EBUSY, "simulation has not finished");
+}
+
+#define LOCK std::lock_guard<std::recursive_mutex> lock_(ctx->mu)
 
 }  // namespace
 
@@ -615,44 +885,48 @@ C2F_API int c2f_create(c2f_ctx **out, int device) {
     cudaGetLastError();
     return C2F_EINVAL;
   }
-  std::unique_ptr<c2f_ctx> ctx(new c2f_ctx());
+  std::unique_ptr<c2f_ctx> holder(new c2f_ctx());
+  c2f_ctx *ctx = holder.get();
   ctx->device = device;
-  c2f_ctx *c = ctx.get();
-  {
-    c2f_ctx *ctx = c;  // for CK
-    CK(cudaSetDevice(device));
-    CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
-    CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
-    c->stream = c->own_stream;
-    int rc = ensure_device_constants(c);
-    if (rc) return rc;
-    CK(cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
-    CK(cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
-  }
-  *out = ctx.release();
+  CK(cudaSetDevice(device));
+  CK(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
+  CK(cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  CK(cudaDeviceGetAttribute(&ctx->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
+  CK(cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking));
+  ctx->stream = ctx->own_stream;
+  CK(cudaStreamCreateWithFlags(&ctx->read_stream, cudaStreamNonBlocking));
+  int rc = ensure_device_constants(ctx);
+  if (rc) return rc;
+  *out = holder.release();
   return C2F_OK;
 }
 
 C2F_API int c2f_set_stream(c2f_ctx *ctx, void *stream) {
   if (!ctx) return C2F_EINVAL;
+  LOCK;
   ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
   return C2F_OK;
 }
 
 C2F_API void c2f_destroy(c2f_ctx *ctx) {
   if (!ctx) return;
-  cudaSetDevice(ctx->device);
-  cudaStreamSynchronize(ctx->stream);
-  ctx->sims.clear();
-  ctx->lands.clear();
-  ctx->ent_cell.reset(); ctx->ent_mask.reset(); ctx->ent_next.reset();
-  ctx->ent_cofs.reset(); ctx->ent_P.reset(); ctx->counter.reset(); ctx->brn_scratch.reset();
-  ctx->avail_scratch.reset();
-  cudaStreamSynchronize(ctx->stream);
-  for (int f = 0; f < C2F_KT_FAMILIES; ++f)
-    for (auto &pr : ctx->prof_events[f]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
-  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
-  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  {
+    LOCK;
+    cudaSetDevice(ctx->device);
+    reap(ctx, true);
+    cudaStreamSynchronize(ctx->stream);
+    ctx->pending.clear();
+    ctx->sims.clear();
+    ctx->lands.clear();
+    ctx->scratch.reset();
+    cudaStreamSynchronize(ctx->stream);
+    for (int f = 0; f < C2F_KT_FAMILIES; ++f)
+      for (auto &pr : ctx->prof_events[f]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    for (cudaStream_t s : ctx->stream_pool) cudaStreamDestroy(s);
+    if (ctx->read_stream) cudaStreamDestroy(ctx->read_stream);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  }
   delete ctx;
 }
 
@@ -665,6 +939,7 @@ C2F_API int c2f_load_landscape(c2f_ctx *ctx, int32_t rows, int32_t cols, double 
                                const float *aspect_deg, const uint8_t *unburnable,
                                int32_t *landscape_id) {
   if (!ctx) return C2F_EINVAL;
+  LOCK;
   if (!fuel || !landscape_id) return fail(ctx, C2F_EINVAL, "fuel and landscape_id are required");
   if (rows < 1 || cols < 1 || rows > 65535 || cols > 65535 || (int64_t)rows * cols >= (1LL << 31))
     return fail(ctx, C2F_EINVAL, "rows and cols must lie in [1, 65535] and rows*cols < 2^31");
@@ -682,7 +957,7 @@ C2F_API int c2f_load_landscape(c2f_ctx *ctx, int32_t rows, int32_t cols, double 
       if (!std::isfinite(aspect_deg[i]) || std::fabs(aspect_deg[i]) > 1e6f)
         return fail(ctx, C2F_EINVAL, "aspect at cell %lld is not finite", (long long)i);
   CK(cudaSetDevice(ctx->device));
-  std::unique_ptr<Landscape> L(new Landscape());
+  auto L = std::make_shared<Landscape>();
   L->rows = rows; L->cols = cols; L->n = n; L->cell_size = cell_size_m;
   L->wpr = (cols + 31) / 32;
   L->burnable_host.resize(n);
@@ -747,7 +1022,7 @@ C2F_API int c2f_load_landscape(c2f_ctx *ctx, int32_t rows, int32_t cols, double 
   CKL("k_cell_prep");
   CK(cudaStreamSynchronize(ctx->stream));
   const int32_t id = ctx->next_id++;
-  ctx->lands[id] = std::move(L);
+  ctx->lands[id] = L;
   *landscape_id = id;
   return C2F_OK;
 }
@@ -755,7 +1030,8 @@ C2F_API int c2f_load_landscape(c2f_ctx *ctx, int32_t rows, int32_t cols, double 
 C2F_API int c2f_set_weather(c2f_ctx *ctx, int32_t landscape_id, int32_t n_hours,
                             const c2f_weather_hour *w) {
   if (!ctx) return C2F_EINVAL;
-  Landscape *L = find_land(ctx, landscape_id);
+  LOCK;
+  auto L = find_land(ctx, landscape_id);
   if (!L) return fail(ctx, C2F_ENOTFOUND, "unknown landscape %d", landscape_id);
   if (n_hours < 1 || n_hours > 65535 || !w) return fail(ctx, C2F_EINVAL, "n_hours must lie in [1, 65535]");
   for (int32_t h = 0; h < n_hours; ++h) {
@@ -767,49 +1043,56 @@ C2F_API int c2f_set_weather(c2f_ctx *ctx, int32_t landscape_id, int32_t n_hours,
   }
   CK(cudaSetDevice(ctx->device));
   L->n_hours = n_hours;
-  L->weather.assign(n_hours * 4, 0.0);
+  L->weather.assign((size_t)n_hours * 4, 0.0);
   for (int32_t h = 0; h < n_hours; ++h) {
     L->weather[h * 4 + 0] = w[h].ws_kmh;
     L->weather[h * 4 + 1] = w[h].wd_from_deg;
     L->weather[h * 4 + 2] = w[h].ffmc;
     L->weather[h * 4 + 3] = w[h].bui;
   }
+  // a fresh device copy: tables still being built from the old one keep it
+  auto wd = std::make_shared<DevBuf>();
   int rc;
-  if ((rc = dalloc(ctx, L->weather_dev, sizeof(double) * 4 * n_hours))) return rc;
-  CK(cudaMemcpyAsync(L->weather_dev.p, L->weather.data(), sizeof(double) * 4 * n_hours,
-                     cudaMemcpyHostToDevice, ctx->stream));
-  L->table_valid = false;
+  if ((rc = dalloc(ctx, *wd, sizeof(double) * 4 * n_hours))) return rc;
+  CK(cudaMemcpyAsync(wd->p, L->weather.data(), sizeof(double) * 4 * n_hours, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  L->weather_dev = wd;
+  L->table.reset();   // running simulations keep the table they started with
   return C2F_OK;
 }
 
 C2F_API int c2f_build_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p, int force) {
   if (!ctx) return C2F_EINVAL;
-  Landscape *L = find_land(ctx, landscape_id);
+  LOCK;
+  auto L = find_land(ctx, landscape_id);
   if (!L) return fail(ctx, C2F_ENOTFOUND, "unknown landscape %d", landscape_id);
   if (L->n_hours < 1) return fail(ctx, C2F_EINVAL, "landscape has no weather");
   int rc = validate_params(ctx, *L, p);
   if (rc) return rc;
   CK(cudaSetDevice(ctx->device));
-  return ensure_table(ctx, *L, p, force != 0);
+  return ensure_table(ctx, *L, key_of(p), force != 0);
 }
 
 C2F_API int c2f_get_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p, int32_t hour,
                         double *ros8, double *hros, int64_t *base) {
   if (!ctx) return C2F_EINVAL;
-  Landscape *L = find_land(ctx, landscape_id);
+  LOCK;
+  auto L = find_land(ctx, landscape_id);
   if (!L) return fail(ctx, C2F_ENOTFOUND, "unknown landscape %d", landscape_id);
   if (L->n_hours < 1) return fail(ctx, C2F_EINVAL, "landscape has no weather");
   int rc = validate_params(ctx, *L, p);
   if (rc) return rc;
   if (hour < 0 || hour >= p->hours) return fail(ctx, C2F_EINVAL, "hour out of range");
   CK(cudaSetDevice(ctx->device));
-  if ((rc = ensure_table(ctx, *L, p, false))) return rc;
+  if ((rc = ensure_table(ctx, *L, key_of(p), false))) return rc;
+  const Table &T = *L->table;
+  CK(cudaStreamWaitEvent(ctx->stream, T.ready, 0));
   const size_t n = (size_t)L->n;
   if (base)
-    CK(cudaMemcpyAsync(base, L->base.as<int64_t>() + (size_t)hour * n * 8, n * 64,
+    CK(cudaMemcpyAsync(base, T.base.as<int64_t>() + (size_t)hour * n * 8, n * 64,
                        cudaMemcpyDeviceToHost, ctx->stream));
   if (hros)
-    CK(cudaMemcpyAsync(hros, L->hros.as<double>() + (size_t)hour * n, n * 8, cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(hros, T.hros.as<double>() + (size_t)hour * n, n * 8, cudaMemcpyDeviceToHost,
                        ctx->stream));
   if (ros8) {
     DevBuf tmp;
@@ -820,7 +1103,7 @@ C2F_API int c2f_get_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params
     a.burnable = L->burnable.as<uint32_t>();
     a.rows = L->rows; a.cols = L->cols; a.wpr = L->wpr;
     a.cell = L->cell_prep.as<CellPrep>();
-    a.hour = L->hour_prep.as<HourPrep>();
+    a.hour = T.hour_prep.as<HourPrep>();
     a.hour0 = hour;
     a.pcf = p->m1_pc / 100.0;
     a.const_ros = p->const_ros;
@@ -836,102 +1119,96 @@ C2F_API int c2f_get_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params
   return C2F_OK;
 }
 
-static int simulate_many(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_sim_params *params,
-                         int32_t *sim_ids) {
-  if (!ctx) return C2F_EINVAL;
-  if (n < 1 || !ids || !params || !sim_ids) return fail(ctx, C2F_EINVAL, "bad batch arguments");
-  CK(cudaSetDevice(ctx->device));
-  std::vector<Landscape *> lands(n);
-  for (int32_t i = 0; i < n; ++i) {
-    lands[i] = find_land(ctx, ids[i]);
-    if (!lands[i]) return fail(ctx, C2F_ENOTFOUND, "unknown landscape %d", ids[i]);
-    if (lands[i]->n_hours < 1) return fail(ctx, C2F_EINVAL, "landscape %d has no weather", ids[i]);
-    int rc = validate_params(ctx, *lands[i], &params[i]);
-    if (rc) return rc;
-  }
-  int rc;
-  // tables: which landscapes need one (the longest run on a landscape sets its hours)
-  std::vector<std::pair<Landscape *, c2f_sim_params>> builds;
-  for (int32_t i = 0; i < n; ++i) {
-    for (int32_t k = 0; k < i; ++k)
-      if (ids[k] == ids[i] && !(key_of(&params[k]) == key_of(&params[i])))
-        return fail(ctx, C2F_EINVAL, "batch entries %d and %d share a landscape with different ROS options", k, i);
-    bool first = true;
-    for (int32_t k = 0; k < i; ++k) if (ids[k] == ids[i]) first = false;
-    if (!first) continue;
-    c2f_sim_params q = params[i];
-    for (int32_t k = i + 1; k < n; ++k)
-      if (ids[k] == ids[i]) q.hours = std::max(q.hours, params[k].hours);
-    if (!table_ok(*lands[i], &q)) {
-      if ((rc = prepare_table(ctx, *lands[i], &q))) return rc;
-      builds.emplace_back(lands[i], q);
-    }
-  }
-  std::vector<std::unique_ptr<Sim>> owned(n);
-  std::vector<Sim *> sims(n);
-  for (int32_t i = 0; i < n; ++i) {
-    owned[i].reset(new Sim());
-    owned[i]->landscape = ids[i];
-    owned[i]->p = params[i];
-    if ((rc = alloc_sim(ctx, *lands[i], *owned[i]))) return rc;
-    sims[i] = owned[i].get();
-  }
-  FrontierPlan F;
-  if ((rc = plan_frontier(ctx, lands, sims, F))) return rc;
-  // a batch's launches (table builds, ignitions, the frontier) go out as one
-  // CUDA graph; a single simulation is launched directly
-  const bool graph = n > 1 && !ctx->profiling;
-  if (graph) {
-    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    int lrc = C2F_OK;
-    for (auto &b : builds) if (!lrc) lrc = launch_table(ctx, *b.first, &b.second);
-    if (!lrc) lrc = launch_frontier(ctx, F);
-    cudaGraph_t g = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
-    if (lrc) { if (g) cudaGraphDestroy(g); return lrc; }
-    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
-    cudaGraphExec_t ge = nullptr;
-    cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
-    cudaGraphDestroy(g);
-    if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
-    const cudaError_t le = cudaGraphLaunch(ge, ctx->stream);
-    cudaGraphExecDestroy(ge);
-    if (le != cudaSuccess) return cuda_fail(ctx, le, "cudaGraphLaunch");
-    ++ctx->graph_launches;
-  } else {
-    for (auto &b : builds) if ((rc = launch_table(ctx, *b.first, &b.second))) return rc;
-    if ((rc = launch_frontier(ctx, F))) return rc;
-  }
-  if ((rc = finish_frontier(ctx, F))) return rc;
-  for (int32_t i = 0; i < n; ++i) {
-    const int32_t id = ctx->next_id++;
-    ctx->sims[id] = std::move(owned[i]);
-    sim_ids[i] = id;
-  }
-  return C2F_OK;
-}
-
 C2F_API int c2f_simulate(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p,
                          int32_t *sim_id) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
   return simulate_many(ctx, 1, &landscape_id, p, sim_id);
 }
 
 C2F_API int c2f_simulate_batch(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
                                const c2f_sim_params *params, int32_t *sim_ids) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
   return simulate_many(ctx, n, landscape_ids, params, sim_ids);
 }
 
-static int burn_prob_into(c2f_ctx *ctx, Sim &s, uint32_t *dst) {
+C2F_API int c2f_submit(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p, int32_t *sim_id) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  if (!sim_id) return fail(ctx, C2F_EINVAL, "sim_id is NULL");
+  CK(cudaSetDevice(ctx->device));
+  std::vector<std::shared_ptr<Sim>> sims;
+  int rc = make_sims(ctx, 1, &landscape_id, p, sims, nullptr, true);
+  if (rc) return rc;
+  ctx->pending.push_back(sims[0]);
+  register_sims(ctx, sims, sim_id);
+  return pump(ctx);
+}
+
+C2F_API int c2f_pump(c2f_ctx *ctx) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  CK(cudaSetDevice(ctx->device));
+  return pump(ctx);
+}
+
+C2F_API int c2f_poll(c2f_ctx *ctx, int32_t sim_id, int32_t *done) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  auto s = find_sim(ctx, sim_id);
+  if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  CK(cudaSetDevice(ctx->device));
+  int rc = pump(ctx);
+  if (done) *done = (s->state == S_DONE || s->state == S_CANCELED || s->state == S_FAILED) ? 1 : 0;
+  if (s->state == S_FAILED) return s->rc;
+  return rc;
+}
+
+C2F_API int c2f_wait(c2f_ctx *ctx, int32_t sim_id) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  auto s = find_sim(ctx, sim_id);
+  if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  CK(cudaSetDevice(ctx->device));
+  while (s->state == S_PENDING || s->state == S_RUNNING) {
+    int rc = pump(ctx);
+    if (rc && s->state != S_FAILED) return rc;
+    if (s->state == S_PENDING && ctx->inflight.empty()) return fail(ctx, C2F_ECUDA, "scheduler stalled");
+    if ((s->state == S_PENDING || s->state == S_RUNNING) && !ctx->inflight.empty())
+      CK(cudaEventSynchronize(ctx->inflight.front()->done));   // the oldest epoch frees a slot
+  }
+  if (s->state == S_CANCELED) return fail(ctx, C2F_ECANCELED, "simulation was cancelled");
+  if (s->state == S_FAILED) return s->rc;
+  return C2F_OK;
+}
+
+C2F_API int c2f_cancel(c2f_ctx *ctx, int32_t sim_id) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  auto s = find_sim(ctx, sim_id);
+  if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  if (s->state == S_PENDING) {
+    auto it = std::find(ctx->pending.begin(), ctx->pending.end(), s);
+    if (it != ctx->pending.end()) ctx->pending.erase(it);
+    s->state = S_CANCELED;
+  } else if (s->state == S_RUNNING) {
+    s->cancel_requested = true;   // its epoch runs to the end; the result is discarded
+  }
+  return C2F_OK;
+}
+
+static int burn_prob_into(c2f_ctx *ctx, Sim &s, uint32_t *dst, cudaStream_t st) {
   const int32_t R = s.p.n_replicas;
   const int64_t words = (int64_t)s.rows * s.wpr;
   const int64_t target = (int64_t)ctx->sm_count * 4 * 256;
   int32_t chunks = (int32_t)std::min<int64_t>(R, std::max<int64_t>(1, target / std::max<int64_t>(words, 1)));
   int32_t per = (R + chunks - 1) / chunks;
-  if (per > 65535) { per = 65535; chunks = (R + per - 1) / per; }
+  if (per > 65535) per = 65535;
   chunks = (R + per - 1) / per;
-  ProfScope prof(ctx, 3);
-  if (chunks > 1) CK(cudaMemsetAsync(dst, 0, (size_t)s.n * 4, ctx->stream));
-  k_burn_prob<<<dim3(grid1(words, 256), (unsigned)chunks), 256, 0, ctx->stream>>>(
+  ProfScope prof(ctx, 3, st);
+  if (chunks > 1) CK(cudaMemsetAsync(dst, 0, (size_t)s.n * 4, st));
+  k_burn_prob<<<dim3(grid1(words, 256), (unsigned)chunks), 256, 0, st>>>(
       s.ign_plane.as<uint32_t>(), R, s.rows, s.cols, s.wpr, per, dst, chunks > 1 ? 1 : 0);
   CKL("k_burn_prob");
   return C2F_OK;
@@ -939,70 +1216,82 @@ static int burn_prob_into(c2f_ctx *ctx, Sim &s, uint32_t *dst) {
 
 C2F_API int c2f_burn_prob(c2f_ctx *ctx, int32_t sim_id, uint32_t *counts) {
   if (!ctx) return C2F_EINVAL;
-  Sim *s = find_sim(ctx, sim_id);
+  LOCK;
+  auto s = find_sim(ctx, sim_id);
   if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
   if (!counts) return fail(ctx, C2F_EINVAL, "counts is NULL");
+  int rc = sim_ready(ctx, *s);
+  if (rc) return rc;
   CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->read_stream;
   DevBuf tmp;
-  int rc;
-  if ((rc = dalloc(ctx, tmp, (size_t)s->n * 4))) return rc;
-  if ((rc = burn_prob_into(ctx, *s, tmp.as<uint32_t>()))) return rc;
-  CK(cudaMemcpyAsync(counts, tmp.p, (size_t)s->n * 4, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
+  if ((rc = dalloc_on(ctx, tmp, (size_t)s->n * 4, st))) return rc;
+  if ((rc = burn_prob_into(ctx, *s, tmp.as<uint32_t>(), st))) return rc;
+  CK(cudaMemcpyAsync(counts, tmp.p, (size_t)s->n * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   return C2F_OK;
 }
 
 C2F_API int c2f_burn_prob_device(c2f_ctx *ctx, int32_t sim_id, uint32_t *counts_dev) {
   if (!ctx) return C2F_EINVAL;
-  Sim *s = find_sim(ctx, sim_id);
+  LOCK;
+  auto s = find_sim(ctx, sim_id);
   if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
   if (!counts_dev) return fail(ctx, C2F_EINVAL, "counts_dev is NULL");
+  int rc = sim_ready(ctx, *s);
+  if (rc) return rc;
   CK(cudaSetDevice(ctx->device));
-  return burn_prob_into(ctx, *s, counts_dev);
+  return burn_prob_into(ctx, *s, counts_dev, ctx->stream);
 }
 
 C2F_API int c2f_get_scars(c2f_ctx *ctx, int32_t sim_id, uint8_t *scars, int32_t *ign_step) {
   if (!ctx) return C2F_EINVAL;
-  Sim *s = find_sim(ctx, sim_id);
+  LOCK;
+  auto s = find_sim(ctx, sim_id);
   if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  int rc = sim_ready(ctx, *s);
+  if (rc) return rc;
   if (ign_step && !s->ign_step.p)
     return fail(ctx, C2F_EINVAL, "simulation did not keep ignition steps (C2F_OUT_IGN_STEPS)");
   CK(cudaSetDevice(ctx->device));
   const int32_t R = s->p.n_replicas;
   const size_t total = (size_t)s->n * R;
+  cudaStream_t st = ctx->read_stream;
   if (scars) {
     DevBuf tmp;
-    int rc;
-    if ((rc = dalloc(ctx, tmp, total))) return rc;
-    k_scar_bytes<<<grid1((int64_t)total, 256), 256, 0, ctx->stream>>>(
+    if ((rc = dalloc_on(ctx, tmp, total, st))) return rc;
+    k_scar_bytes<<<grid1((int64_t)total, 256), 256, 0, st>>>(
         s->ign_plane.as<uint32_t>(), R, s->rows, s->cols, s->wpr, tmp.as<uint8_t>());
     CKL("k_scar_bytes");
-    CK(cudaMemcpyAsync(scars, tmp.p, total, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(scars, tmp.p, total, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
   }
-  if (ign_step) {
-    CK(cudaMemcpyAsync(ign_step, s->ign_step.p, total * 4, cudaMemcpyDeviceToHost, ctx->stream));
-  }
-  CK(cudaStreamSynchronize(ctx->stream));
+  if (ign_step) CK(cudaMemcpyAsync(ign_step, s->ign_step.p, total * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   return C2F_OK;
 }
 
 C2F_API int c2f_get_counters(c2f_ctx *ctx, int32_t sim_id, int64_t *work, int32_t *ignited,
                              int32_t *ign_cell) {
   if (!ctx) return C2F_EINVAL;
-  Sim *s = find_sim(ctx, sim_id);
+  LOCK;
+  auto s = find_sim(ctx, sim_id);
   if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  int rc = sim_ready(ctx, *s);
+  if (rc) return rc;
   CK(cudaSetDevice(ctx->device));
   const size_t R = (size_t)s->p.n_replicas;
-  if (work) CK(cudaMemcpyAsync(work, s->work.p, R * 8, cudaMemcpyDeviceToHost, ctx->stream));
-  if (ignited) CK(cudaMemcpyAsync(ignited, s->n_ignited.p, R * 4, cudaMemcpyDeviceToHost, ctx->stream));
-  if (ign_cell) CK(cudaMemcpyAsync(ign_cell, s->ign_cell.p, R * 4, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
+  cudaStream_t st = ctx->read_stream;
+  if (work) CK(cudaMemcpyAsync(work, s->work.p, R * 8, cudaMemcpyDeviceToHost, st));
+  if (ignited) CK(cudaMemcpyAsync(ignited, s->n_ignited.p, R * 4, cudaMemcpyDeviceToHost, st));
+  if (ign_cell) CK(cudaMemcpyAsync(ign_cell, s->ign_cell.p, R * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   return C2F_OK;
 }
 
 C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap) {
   if (!ctx) return C2F_EINVAL;
+  LOCK;
   if (cap < 0 || cap > (1LL << 31)) return fail(ctx, C2F_EINVAL, "capacity out of range");
   ctx->cap_override = cap;
   return C2F_OK;
@@ -1010,6 +1299,7 @@ C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap) {
 
 C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem) {
   if (!ctx) return C2F_EINVAL;
+  LOCK;
   if (threads != 32 && threads != 64 && threads != 128)
     return fail(ctx, C2F_EINVAL, "threads must be 32, 64 or 128 (one replica per warp)");
   if (smem < 0) return fail(ctx, C2F_EINVAL, "smem must be >= 0");
@@ -1018,10 +1308,25 @@ C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem) {
   return C2F_OK;
 }
 
+C2F_API int c2f_set_serving(c2f_ctx *ctx, int32_t max_inflight, int64_t max_epoch_replicas,
+                            int64_t hbm_reserve_bytes) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  if (max_inflight < 1 || max_inflight > 16 || max_epoch_replicas < 1 || hbm_reserve_bytes < 0)
+    return fail(ctx, C2F_EINVAL, "bad serving limits");
+  ctx->max_inflight = max_inflight;
+  ctx->max_epoch_replicas = max_epoch_replicas;
+  ctx->hbm_reserve = hbm_reserve_bytes;
+  return C2F_OK;
+}
+
+C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches);
+
 C2F_API int c2f_autotune(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
                          const c2f_sim_params *params, int32_t sample_replicas, int32_t *best_threads,
                          int32_t *best_smem, double *best_ms) {
   if (!ctx) return C2F_EINVAL;
+  LOCK;
   if (n < 1 || !landscape_ids || !params || sample_replicas < 1)
     return fail(ctx, C2F_EINVAL, "bad autotune arguments");
   int64_t total = 0;
@@ -1066,14 +1371,17 @@ C2F_API int c2f_autotune(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
 
 C2F_API int c2f_profile(c2f_ctx *ctx, int enable) {
   if (!ctx) return C2F_EINVAL;
+  LOCK;
   ctx->profiling = enable != 0;
   return C2F_OK;
 }
 
 C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches) {
   if (!ctx) return C2F_EINVAL;
+  LOCK;
   CK(cudaSetDevice(ctx->device));
   CK(cudaStreamSynchronize(ctx->stream));
+  for (auto &E : ctx->inflight) CK(cudaStreamSynchronize(E->stream));
   for (int f = 0; f < C2F_KT_FAMILIES; ++f) {
     double tot = 0.0;
     for (auto &pr : ctx->prof_events[f]) {
@@ -1092,9 +1400,21 @@ C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches) {
 
 C2F_API int c2f_release(c2f_ctx *ctx, int32_t id) {
   if (!ctx) return C2F_EINVAL;
+  LOCK;
   CK(cudaSetDevice(ctx->device));
-  if (ctx->sims.erase(id)) return C2F_OK;
-  if (ctx->lands.erase(id)) return C2F_OK;
+  auto s = find_sim(ctx, id);
+  if (s) {
+    if (s->state == S_PENDING) {
+      auto it = std::find(ctx->pending.begin(), ctx->pending.end(), s);
+      if (it != ctx->pending.end()) ctx->pending.erase(it);
+      s->state = S_CANCELED;
+    } else if (s->state == S_RUNNING) {
+      s->cancel_requested = true;   // the epoch still holds it until it finishes
+    }
+    ctx->sims.erase(id);
+    return C2F_OK;
+  }
+  if (ctx->lands.erase(id)) return C2F_OK;   // simulations holding it keep it alive
   return fail(ctx, C2F_ENOTFOUND, "unknown id %d", id);
 }
 
