@@ -306,8 +306,11 @@ def roofline(dom, fam, w, work_per_step, peaks):
     if dom == "frontier":
         by = FRONTIER_BYTES_PER_UPDATE * work_per_step
         ach = by / per_launch_s / 1e9
+        traffic = FRONTIER_DRAM_BYTES_PER_REPLICA * w.params["n_replicas"]
         return {"kernel": "k_frontier", "bound": "hbm", "achieved": ach, "peak": hbm,
-                "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read+write of a 200-replica launch, "
+                                  "scaled by replicas",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     by = w.params["n_replicas"] * ((w.landscape.fuel.shape[1] + 31) // 32) * 4 * \
         w.landscape.fuel.shape[0] + 4 * n
@@ -318,6 +321,7 @@ def roofline(dom, fam, w, work_per_step, peaks):
 
 # algorithmic figures (the design doc states how they are derived)
 FRONTIER_BYTES_PER_UPDATE = 194.0
+FRONTIER_DRAM_BYTES_PER_REPLICA = 94.31e6 / 200   # ncu, 512^2 x 24 h, 200 replicas
 FP64_OPS_PER_CELL_HOUR = 795.0      # ncu: (2 x DFMA + DMUL + DADD) / (cells x hours)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x DFMA/clk x flop/DFMA x GHz
 
