@@ -180,15 +180,39 @@ def run_ours(args, rank, world, local_rank):
     ctx.set_weather(lid, w.weather)
     counts_dev = torch.empty(n, dtype=torch.int32, device=dev)
 
+    table_mode = 2 if args.lazy_tables else 1
+    ctx.set_table_mode(not args.lazy_tables)
+
     def step():
-        ctx.build_ros(lid, params, force=True)                  # a1 + a2 (K1)
+        ctx.build_ros(lid, params, force=table_mode)            # a1 + a2 (K1; on demand when lazy)
         sid = ctx.simulate(lid, params)                         # a3..a8 (K2, K3)
         ctx.burn_prob_device(sid, counts_dev.data_ptr())        # a9 (K4)
         return sid
 
+    # Pipelined steps: each step's table is built (K1, context stream) while the
+    # previous step's frontier runs (its own stream, submitted asynchronously);
+    # the work of a step is the same as in the serial form.
+    ctx.set_serving(max_inflight=2, max_epoch_replicas=R, hbm_reserve_bytes=0)
+
+    def run_steps(k):
+        if args.serial:
+            return [step() for _ in range(k)]
+        done, prev = [], None
+        for _ in range(k):
+            ctx.build_ros(lid, params, force=table_mode)        # a1 + a2 (K1)
+            sid = ctx.submit(lid, params)                       # a3..a8 (K2, K3), asynchronous
+            if prev is not None:
+                ctx.wait(prev)
+                ctx.burn_prob_device(prev, counts_dev.data_ptr())   # a9 (K4)
+                done.append(prev)
+            prev = sid
+        ctx.wait(prev)
+        ctx.burn_prob_device(prev, counts_dev.data_ptr())
+        done.append(prev)
+        return done
+
     # warm-up (also fixes the deterministic work count of the step)
-    for _ in range(max(args.warmup, 0)):
-        sid = step()
+    for sid in run_steps(max(args.warmup, 1)):
         work, _, _ = ctx.get_counters(sid, R)
         ctx.release(sid)
     work_per_step = int(work.sum())
@@ -206,9 +230,7 @@ def run_ours(args, rank, world, local_rank):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        sids = []
-        for _ in range(args.steps):
-            sids.append(step())
+        sids = run_steps(args.steps)
         ev1.record(stream)
         barrier()
     ms = ev0.elapsed_time(ev1)
@@ -272,7 +294,10 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD, "replicas_per_gpu": R, "hours": 24,
                        "cells": int(n), "cell_updates_per_step_per_gpu": work_per_step,
                        "l2": "inputs larger than L2 (ROS table 453 MB rebuilt every step)",
-                       "parallelism": f"replica-sharded x{world}"},
+                       "parallelism": f"replica-sharded x{world}",
+                       "schedule": "serial" if args.serial else
+                       "pipelined: step i+1's table (K1) overlaps step i's frontier (K3)",
+                       "tables": "on demand in K3" if args.lazy_tables else "K1, every row"},
             "replicas_per_s": R * world * args.steps / (ms_max / 1e3),
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in fam.items()},
             "roofline": roof,
@@ -368,6 +393,7 @@ def run_batch(args):
     specs = S.config3_specs()
     ws = [S.config3_workload(sp) for sp in specs]
     ctx = c2f.Context(0)
+    ctx.set_table_mode(not args.lazy_tables)
     lids = []
     for w in ws:
         L = w.landscape
@@ -433,6 +459,7 @@ def run_serve(args):
     lands = [S.heterogeneous_landscape(side, seed=500 + i) for i, side in enumerate(sides)]
     weathers = [S.weather_stream(72, seed=600 + i) for i in range(len(sides))]
     ctx = c2f.Context(0)
+    ctx.set_table_mode(not args.lazy_tables)
     ctx.set_serving(max_inflight=args.max_inflight)
     lids = [None] * len(sides)
 
@@ -525,8 +552,10 @@ def run_large(args):
     counts = torch.empty(n, dtype=torch.int32, device="cuda")
     ctx.set_stream(torch.cuda.current_stream().cuda_stream)
 
+    ctx.set_table_mode(not args.lazy_tables)
+
     def step():
-        ctx.build_ros(lid, p, force=True)
+        ctx.build_ros(lid, p, force=2 if args.lazy_tables else 1)
         sid = ctx.simulate(lid, p)
         ctx.burn_prob_device(sid, counts.data_ptr())
         return sid
@@ -569,6 +598,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1000)
     ap.add_argument("--ref-sample", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lazy-tables", action="store_true",
+                    help="ROS-table rows computed on demand inside the frontier instead of by K1")
+    ap.add_argument("--serial", action="store_true",
+                    help="one synchronous step at a time (no overlap of K1 with the previous frontier)")
     ap.add_argument("--workload", default="landscape", choices=["landscape", "batch", "serve", "large"])
     ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")

@@ -123,13 +123,27 @@ C2F_API int c2f_load_landscape(c2f_ctx *ctx, int32_t rows, int32_t cols, double 
 C2F_API int c2f_set_weather(c2f_ctx *ctx, int32_t landscape_id, int32_t n_hours,
                             const c2f_weather_hour *w);
 
-/* Builds (or rebuilds, when `force` != 0) the rate-of-spread table of a
- * landscape for the FBP/ellipse options in *p (Sec. 3.7, Eqs. 1-4): per
- * (hour, cell) the 8 directional ROS in 2^32 fixed point per fire period,
- * and HROS.  c2f_simulate builds it on demand; this call lets a caller pay
- * for it up front or time it.  Asynchronous on the context stream. */
+/* The rate-of-spread table of a landscape for the FBP/ellipse options in *p
+ * (Sec. 3.7, Eqs. 1-4): per (hour, cell) the 8 directional ROS in 2^32 fixed
+ * point per fire period, and HROS.  A table is either eager (every row
+ * written up front by the table kernel) or lazy (rows written by the
+ * simulations that read them, 32 cells at a time, the first time a burning
+ * cell needs them); both hold the same bits wherever a simulation reads.
+ *   force 0: make sure an eager table exists (a lazy one is completed);
+ *   force 1: discard the table and build a new eager one;
+ *   force 2: discard the table; the next simulation fills a new lazy one.
+ * c2f_simulate creates a table when none fits (eager by default, see
+ * c2f_set_table_mode).  Asynchronous on the context stream; force outside
+ * [0, 2] gives C2F_EINVAL. */
 C2F_API int c2f_build_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p,
                           int force);
+
+/* Whether tables that simulations create are eager (nonzero, the default)
+ * or lazy (0).  Results are identical either way.  Lazy tables pay for the
+ * rows inside the frontier kernel, at a lower FP64 rate than the table
+ * kernel; they win only when the replicas touch a small part of the
+ * landscape-hours (few replicas on a large landscape). */
+C2F_API int c2f_set_table_mode(c2f_ctx *ctx, int eager);
 
 /* Exports one hour of the rate-of-spread table for checking: ros8
  * (rows*cols*8 doubles, m/min, axis k = 45k degrees counter-clockwise from

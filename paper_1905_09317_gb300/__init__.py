@@ -78,6 +78,7 @@ _SIGS = [
     ("c2f_wait", C.c_int, [C.c_void_p, C.c_int32]),
     ("c2f_cancel", C.c_int, [C.c_void_p, C.c_int32]),
     ("c2f_set_serving", C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_int64]),
+    ("c2f_set_table_mode", C.c_int, [C.c_void_p, C.c_int]),
     ("c2f_burn_prob", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_burn_prob_device", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_get_scars", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
@@ -229,6 +230,10 @@ class Context:
 
     def cancel(self, sim_id: int) -> None:
         self._check(self.lib.c2f_cancel(self.h, int(sim_id)))
+
+    def set_table_mode(self, eager: bool) -> None:
+        """Tables created by simulations: eager (K1 up front) or lazy (filled on demand)."""
+        self._check(self.lib.c2f_set_table_mode(self.h, 1 if eager else 0))
 
     def set_serving(self, max_inflight=3, max_epoch_replicas=1 << 16, hbm_reserve_bytes=2 << 30):
         self._check(self.lib.c2f_set_serving(self.h, int(max_inflight), int(max_epoch_replicas),

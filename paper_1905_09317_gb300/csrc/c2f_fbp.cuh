@@ -137,6 +137,19 @@ __device__ inline void hour_prep(double ws, double wd_from, double ffmc, double 
     }
     hp->rszf[f] = rz;
   }
+  // A lower bound on every fuel's HROS this hour: the RSI curve grows with the
+  // ISI and the ISI with the wind (wind_fn >= 1 for w >= 0), so RSI >= RSI at
+  // zero wind (rszf); a C2/D1 mixture is at least 0.2 x its smaller part.
+  int32_t pos = 1;
+  for (int f = 1; f < F_NCODES; ++f) {
+    double lo = hp->rszf[f];
+    if (f == F_M1 || f == F_M2) {
+      const double c2 = hp->rszf[F_C2], d1 = hp->rszf[F_D1];
+      lo = __dmul_rn(0.2, c2 < d1 ? c2 : d1);
+    }
+    if (!(__dmul_rn(lo, hp->be[f]) > 1e-150)) pos = 0;
+  }
+  hp->pos = pos;
 }
 
 // per cell: slope factor and the upslope direction (aspect is the downslope azimuth)

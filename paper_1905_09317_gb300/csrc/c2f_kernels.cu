@@ -179,6 +179,34 @@ __global__ void k_order_scatter(const uint8_t *fuel, const float *slope, const u
   if (b >= 0) order[base[b] + local] = (int32_t)cell;
 }
 
+// the 8 axis rates and HROS of one burnable cell at one hour
+__device__ __forceinline__ double row_rates(int fuel, const float *slope, int64_t cell,
+                                            const CellPrep &cp, const HourPrep &hp, double pcf,
+                                            double const_ros, int ellipse_mode, double ros[8]) {
+  if (const_ros > 0.0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ros[k] = const_ros;
+    return const_ros;
+  }
+  const double gs = slope ? (double)slope[cell] : 0.0;
+  FbpOut o;
+  fbp_row(fuel, gs, cp, hp, pcf, ellipse_mode, &o);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) ros[k] = o.ros[k];
+  return o.hros;
+}
+
+// a table row: the 8 per-period increments B_k = fixed(ros_k * dt * 2^32) in one
+// 64-byte line (four 16-byte stores), HROS beside it in its own array
+__device__ __forceinline__ void row_store(int64_t *row, double *hros_at, const double ros[8],
+                                          double hr, double dt2p32) {
+  longlong2 *dst = reinterpret_cast<longlong2 *>(row);
+#pragma unroll
+  for (int k = 0; k < 8; k += 2)
+    dst[k / 2] = make_longlong2(fixed_of(__dmul_rn(ros[k], dt2p32)), fixed_of(__dmul_rn(ros[k + 1], dt2p32)));
+  *hros_at = hr;
+}
+
 __global__ void __launch_bounds__(128) k_ros_table(RosTableArgs a) {
   const int64_t n = (int64_t)a.rows * a.cols;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -192,29 +220,17 @@ __global__ void __launch_bounds__(128) k_ros_table(RosTableArgs a) {
   if (!burn) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) ros[k] = 0.0;
-  } else if (a.const_ros > 0.0) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) ros[k] = a.const_ros;
-    hr = a.const_ros;
   } else {
-    const int fuel = a.fuel[cell];
-    const double gs = a.slope ? (double)a.slope[cell] : 0.0;
-    FbpOut o;
-    fbp_row(fuel, gs, a.cell[cell], a.hour[h], a.pcf, a.ellipse_mode, &o);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) ros[k] = o.ros[k];
-    hr = o.hros;
+    hr = row_rates(a.fuel[cell], a.slope, cell, a.cell[cell], a.hour[h], a.pcf, a.const_ros,
+                   a.ellipse_mode, ros);
   }
   const size_t idx = (size_t)h * n + cell;
   if (a.base) {
-    longlong2 *dst = reinterpret_cast<longlong2 *>(a.base + idx * 8);
-#pragma unroll
-    for (int k = 0; k < 8; k += 2)
-      dst[k / 2] = make_longlong2(fixed_of(__dmul_rn(ros[k], a.dt2p32)),
-                                  fixed_of(__dmul_rn(ros[k + 1], a.dt2p32)));
+    double scratch;
+    row_store(a.base + idx * 8, a.hros ? a.hros + idx : &scratch, ros, hr, a.dt2p32);
+  } else if (a.hros) {
+    a.hros[idx] = hr;
   }
-  if (a.hros) a.hros[idx] = hr;
-  if (a.hros_pos && burn && !(hr > 1e-200)) atomicAnd(a.hros_pos, 0);
   if (a.ros8) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) a.ros8[(size_t)cell * 8 + k] = ros[k];
@@ -265,7 +281,7 @@ __device__ __forceinline__ int32_t ceil_div_small(int64_t rem, int64_t inc) {
 // receive test of a messaged Available cell (Sec. 3.1): HROS * f > threshold
 __device__ inline bool receive_ok(const SimJob &J, int32_t r, int64_t j, int32_t h, int64_t n) {
   if (J.thr < 0.0) return true;
-  const double hr = J.hros[(size_t)h * n + j];
+  const double hr = __ldcg(J.hros + (size_t)h * n + j);
   if (J.thr == 0.0) {
     if (hr > 1e-200) return true;   // f >= exp(-5.9) for sigma <= 1, so HROS * f > 0
     if (!(hr > 0.0)) return false;
@@ -320,6 +336,38 @@ __device__ __forceinline__ uint32_t rc_pack(int32_t r, int32_t c) {
 // the scar plane (burnable and no longer Available) is written at the end.
 __device__ __forceinline__ void prefetch_l2(const void *p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// waits for a table chunk that another warp is computing give up after this
+// many polls (about a second); the replica then reports an internal error
+constexpr uint32_t kChunkSpinLimit = 1u << 23;
+
+// On-demand table rows: the rows at hour h of the 32 cells of bit-plane word w
+// (one lane per cell, all 32 lanes of the warp), then the chunk's state goes
+// to done once every lane's stores are visible device-wide.
+__device__ __forceinline__ void table_chunk(const SimJob &J, int32_t h, int32_t w) {
+  const int lane = threadIdx.x & 31;
+  const int32_t row = w / J.wpr, cw = w - row * J.wpr;
+  const int32_t col = cw * 32 + lane;
+  if (col < J.cols && ((__ldg(&J.burnable[w]) >> lane) & 1u)) {
+    const int64_t n = (int64_t)J.rows * J.cols;
+    const int64_t cell = (int64_t)row * J.cols + col;
+    double ros[8];
+    const double hr = row_rates(__ldg(&J.fuel[cell]), J.slope, cell, J.cell[cell], J.hour[h], J.pcf,
+                                J.const_ros, J.ellipse_mode, ros);
+    const size_t idx = (size_t)h * n + cell;
+    row_store(J.base + idx * 8, J.hros + idx, ros, hr, J.dt2p32);
+  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) atomicExch(J.chunk_state + (size_t)h * J.rows * J.wpr + w, 2u);
+  __syncwarp();
 }
 
 // The replica's Available and Burned bit planes.  With WIN, a window of
@@ -396,7 +444,7 @@ struct Planes {
 // single winner) and a Burned plane; with WIN their window around the
 // ignition cell and the burning-list arrays sit in shared memory.  The scar
 // plane (burnable and no longer Available) is written at the end.
-template <int WPC, bool WIN>
+template <int WPC, bool WIN, bool LAZY>
 __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
   extern __shared__ __align__(16) uint32_t s_dyn[];
   __shared__ SimJob s_job[WPC];
@@ -429,7 +477,11 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
   }
   int64_t *eP = A.ent_P + slot * (size_t)cap * 8;
   __shared__ int32_t s_hits[WPC][64];
+  __shared__ uint32_t s_dbits[WPC][LAZY ? kWinRows * kWinWords / 32 : 1];   // chunks known done this hour
+  __shared__ int32_t s_claim[WPC][LAZY ? 32 : 1];
   int32_t *hitbuf = s_hits[wib];
+  uint32_t *dbits = s_dbits[wib];
+  int32_t *claim = s_claim[wib];
   SimJob &J = s_job[wib];
 
   for (;;) {
@@ -452,7 +504,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
     const int64_t n = (int64_t)rows * cols;
     const int32_t pw = rows * wpr;
     const int32_t sph = J.sph, H = J.hours;
-    const bool gate_free = (J.thr < 0.0) || (J.thr == 0.0 && J.hros_pos && *J.hros_pos);
+    const bool lazy = LAZY && J.chunk_state != nullptr;
     const double delta = J.delta;
     const uint64_t seed = J.seed;
     const float sigma = J.sigma;
@@ -461,6 +513,9 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
     const int64_t dk = (k & 1) ? J.d_diag : J.d_orth;   // this lane's axis length
     const int32_t ic = J.ign_cell[r];
     const int32_t ir = ic / cols, icc = ic - ir * cols;
+    // window of the done-chunk bitmap, centred on the ignition cell like the planes'
+    const int32_t dr0 = min(max(ir - kWinRows / 2, 0), max(rows - kWinRows, 0));
+    const int32_t dw0 = min(max((icc >> 5) - kWinWords / 2, 0), max(wpr - kWinWords, 0));
     pl.wpr = wpr;
     bool need_global = true;
     if constexpr (WIN) {   // window centred on the ignition cell, clamped to the grid
@@ -507,6 +562,58 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       __syncwarp();
     }
 
+    // On-demand table rows (lazy tables): before a row of hour h is read, the
+    // chunk holding it must be done.  `slots` bit 0 asks for the cell's own
+    // chunk, bit 1 + k for the chunk of its neighbour on axis k.  A chunk is
+    // looked up in the bitmap of chunks known done this hour, else in
+    // chunk_state: claimed when empty (the warp computes its claims at once,
+    // all lanes on one chunk), waited for when another warp is computing it --
+    // that warp is running and never waits while it holds a claim.
+    auto ensure = [&](int32_t h, bool valid, int32_t cr, int32_t cc, uint32_t slots) {
+      if (!valid) slots = 0;
+      uint32_t todo = __reduce_or_sync(FULL, slots);
+      uint32_t *sth = J.chunk_state + (size_t)h * pw;
+      while (todo) {
+        const int q = __ffs(todo) - 1;
+        todo &= todo - 1;
+        int32_t wr = -1, wc = 0;
+        if ((slots >> q) & 1u) {
+          int32_t nr = cr, nc = cc;
+          if (q > 0) { nr += kDR[q - 1]; nc += kDC[q - 1]; }
+          if (nr >= 0 && nr < rows && nc >= 0 && nc < cols) { wr = nr; wc = nc >> 5; }
+        }
+        const int32_t w = wr * wpr + wc;
+        const bool inwin = wr >= dr0 && wr < dr0 + kWinRows && wc >= dw0 && wc < dw0 + kWinWords;
+        const int32_t bi = inwin ? (wr - dr0) * kWinWords + (wc - dw0) : 0;
+        bool need = false, mine = false;
+        if (wr >= 0 && !(inwin && ((dbits[bi >> 5] >> (bi & 31)) & 1u))) {
+          uint32_t st = ld_acquire(sth + w);
+          if (st == 0u) {
+            st = atomicCAS(sth + w, 0u, 1u);
+            mine = st == 0u;
+          }
+          need = !mine && st < 2u;
+          if (st >= 2u && inwin) atomicOr(&dbits[bi >> 5], 1u << (bi & 31));
+        }
+        const uint32_t mb = __ballot_sync(FULL, mine);
+        if (mine) claim[__popc(mb & lt)] = w;
+        __syncwarp();
+        const int nm = __popc(mb);
+        for (int i = 0; i < nm; ++i) table_chunk(J, h, claim[i]);
+        if (mine && inwin) atomicOr(&dbits[bi >> 5], 1u << (bi & 31));
+        if (need) {
+          uint32_t polls = 0;
+          while (ld_acquire(sth + w) < 2u) {
+            if (++polls > kChunkSpinLimit) { status = 2; break; }
+            __nanosleep(128);
+          }
+          if (polls <= kChunkSpinLimit && inwin) atomicOr(&dbits[bi >> 5], 1u << (bi & 31));
+        }
+        __syncwarp();
+      }
+      if (__any_sync(FULL, status == 2)) status = 2;
+    };
+
     // drop Burned cells and cells with no open axis from the burning list
     // (order kept); with a table pointer, prefetch the kept cells' rows
     auto compact = [&](int32_t count, const int64_t *rows_tbl) -> int32_t {
@@ -551,7 +658,15 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       const int32_t s0 = h * sph + 1, L = s0 + sph - 1;
       const int64_t *baseh = J.base + (size_t)h * n * 8;
       const double *hrosh = J.hros + (size_t)h * n;
+      // receive tests can be skipped when the threshold is 0 and every HROS of
+      // the hour is positive (then HROS * f > 0), or when the threshold is < 0
+      const bool gate_free = (J.thr < 0.0) ||
+                             (J.thr == 0.0 && (J.const_ros > 0.0 || (J.hour && J.hour[h].pos)));
       int32_t burned = 0;   // cells Burned at the end of the period being visited
+      if (lazy) {
+        for (int32_t i = lane; i < kWinRows * kWinWords / 32; i += 32) dbits[i] = 0u;
+        __syncwarp();
+      }
 
       // ---- hour boundary (i): drop Burned cells and cells with no open axis;
       // prefetch the kept cells' table rows for (ii)
@@ -561,6 +676,10 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       // crossing-offset slot (rewritten below)
       for (int32_t b0 = 0; b0 < cnt; b0 += 32) {
         const int32_t e = b0 + lane;
+        if (lazy) {   // this hour's rows of the listed cells
+          const uint32_t rc = e < cnt ? erc[e] : 0u;
+          ensure(h, e < cnt, (int32_t)(rc >> 16), (int32_t)(rc & 0xFFFFu), 1u);
+        }
         if (e < cnt) {
           const uint32_t rc = erc[e];
           const int64_t cell = (int64_t)(rc >> 16) * cols + (rc & 0xFFFFu);
@@ -569,6 +688,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         }
       }
       __syncwarp();
+      if (status) break;
       // ---- hour boundary (iii): crossing periods of this hour, a group per cell,
       // four cells per group in flight
       for (int32_t b0 = 0; b0 < cnt; b0 += 16) {
@@ -591,7 +711,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           bool open = actu[u] && ((mu[u] >> k) & 1u);
           if (open) open = pl.avail(cr + kDR[k], cc + kDC[k]);
           openu[u] = open;
-          bku[u] = open ? baseh[((int64_t)cr * cols + cc) * 8 + k] : 0;
+          bku[u] = open ? __ldcg(baseh + ((int64_t)cr * cols + cc) * 8 + k) : 0;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) masku[u] = group_bits(openu[u]);
@@ -612,7 +732,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           }
           if (actu[u] && delta > 0.0) {
             const double f = (double)Fu[u] * 0x1p-32;   // exact: F = f 2^32 for a binary32 f
-            if (__dmul_rn(hrosh[cell], f) < delta) {    // A5 (i)
+            if (__dmul_rn(__ldcg(hrosh + cell), f) < delta) {    // A5 (i)
               if (k == 0) dying = pl.burn(cr, cc);
               if (cof != 0) cof = kNone;   // still sends in period s0, Burned after it
             }
@@ -668,6 +788,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
 #pragma unroll
           for (int q = 0; q < 8; ++q) cm |= (((cof8 >> (8 * q)) & 0xFFull) == o ? 1u : 0u) << q;
           const int32_t cr = (int32_t)(rc >> 16), cc = (int32_t)(rc & 0xFFFFu);
+          if (lazy && !gate_free) ensure(h, ent >= 0, cr, cc, cm << 1);   // receivers' HROS
           uint32_t todo = cm;
           const int rounds = (int)__reduce_max_sync(FULL, (uint32_t)__popc(cm));
           for (int it2 = 0; it2 < rounds; ++it2) {
@@ -717,6 +838,14 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         if (__any_sync(FULL, ovf)) { status = 1; break; }
         __syncwarp();
         // (C) cells ignited in period s: open axes, first crossings, burn-out tests
+        if (lazy) {   // this hour's rows of the new cells
+          for (int32_t b0 = cnt; b0 < nnew; b0 += 32) {
+            const int32_t e = b0 + lane;
+            const uint32_t rc = e < nnew ? erc[e] : 0u;
+            ensure(h, e < nnew, (int32_t)(rc >> 16), (int32_t)(rc & 0xFFFFu), 1u);
+          }
+          if (status) break;
+        }
         for (int32_t b0 = cnt; b0 < nnew; b0 += 4) {
           const int32_t e = b0 + grp;
           const bool act = e < nnew;
@@ -725,7 +854,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           const int64_t cell = (int64_t)cr * cols + cc;
           const int32_t nr = cr + kDR[k], nc = cc + kDC[k];
           const bool ingrid = act && nr >= 0 && nr < rows && nc >= 0 && nc < cols;
-          const int64_t bk = act ? baseh[cell * 8 + k] : 0;   // issue the table load early
+          const int64_t bk = act ? __ldcg(baseh + cell * 8 + k) : 0;   // issue the table load early
           const bool open = ingrid && pl.avail(nr, nc);
           const bool ignq = ingrid && !open;   // ignited, or never burnable (pre-marked Burned)
           const uint32_t omask = group_bits(open);
@@ -735,7 +864,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           if (act && delta > 0.0) {
             f = noise_factor(seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, sigma);
             have_f = true;
-            if (__dmul_rn(hrosh[cell], (double)f) < delta) { dies = true; mask = 0; }   // A5 (i)
+            if (__dmul_rn(__ldcg(hrosh + cell), (double)f) < delta) { dies = true; mask = 0; }   // A5 (i)
           }
           uint32_t cof = kNone;
           int64_t P = 0;
@@ -800,13 +929,17 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
 }
 
 // Variants: warps per CTA (1, 2, 4); planes windowed and lists in shared
-// memory (w), or everything in global memory (g).
-__global__ void __launch_bounds__(32) k_frontier_g1(FrontierArgs A) { frontier_warp<1, false>(A); }
-__global__ void __launch_bounds__(64) k_frontier_g2(FrontierArgs A) { frontier_warp<2, false>(A); }
-__global__ void __launch_bounds__(128) k_frontier_g4(FrontierArgs A) { frontier_warp<4, false>(A); }
-__global__ void __launch_bounds__(32) k_frontier_w1(FrontierArgs A) { frontier_warp<1, true>(A); }
-__global__ void __launch_bounds__(64) k_frontier_w2(FrontierArgs A) { frontier_warp<2, true>(A); }
-__global__ void __launch_bounds__(128) k_frontier_w4(FrontierArgs A) { frontier_warp<4, true>(A); }
+// memory (w), or everything in global memory (g); l: tables filled on demand.
+__global__ void __launch_bounds__(32) k_frontier_g1(FrontierArgs A) { frontier_warp<1, false, false>(A); }
+__global__ void __launch_bounds__(64) k_frontier_g2(FrontierArgs A) { frontier_warp<2, false, false>(A); }
+__global__ void __launch_bounds__(128) k_frontier_g4(FrontierArgs A) { frontier_warp<4, false, false>(A); }
+__global__ void __launch_bounds__(32) k_frontier_w1(FrontierArgs A) { frontier_warp<1, true, false>(A); }
+__global__ void __launch_bounds__(64) k_frontier_w2(FrontierArgs A) { frontier_warp<2, true, false>(A); }
+__global__ void __launch_bounds__(128) k_frontier_w4(FrontierArgs A) { frontier_warp<4, true, false>(A); }
+// on-demand table rows: one warp per CTA; the FBP code inlined into the
+// frontier needs the whole register budget of a one-warp CTA
+__global__ void __launch_bounds__(32, 1) k_frontier_lg1(FrontierArgs A) { frontier_warp<1, false, true>(A); }
+__global__ void __launch_bounds__(32, 1) k_frontier_lw1(FrontierArgs A) { frontier_warp<1, true, true>(A); }
 
 // ------------------------------------------------------------------ K4
 // counts[c] = sum over replicas of the scar bit of c.  Each thread owns one

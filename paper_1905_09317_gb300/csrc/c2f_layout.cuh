@@ -29,6 +29,7 @@ struct HourPrep {
   double cf;              // O1 curing factor
   double be[F_NCODES];    // build-up effect per fuel code
   double rszf[F_NCODES];  // RSI at zero wind and slope per code (O1 includes curing)
+  int32_t pos;            // 1: every fuel's HROS this hour is > 1e-200 (a lower bound says so)
 };
 
 struct CellPrep { double sf, sin_s, cos_s; };
@@ -41,9 +42,18 @@ struct SimJob {
   const uint32_t *burnable;       // rows*wpr words, bit = burnable and not harvested
   const int32_t *burnable_list;   // burnable cell ids in row-major order
   // rate-of-spread table of this run
-  const int64_t *base;            // [hours][N][8] fixed-point per-period increments
-  const double *hros;             // [hours][N]
-  const int32_t *hros_pos;        // 1 if HROS > 1e-200 on every burnable cell and hour
+  int64_t *base;                  // [hours][N][8] fixed-point per-period increments
+  double *hros;                   // [hours][N]
+  // Rows of the table are filled on demand, 32 cells (one bit-plane word) at a
+  // time, when chunk_state is set: [hours][rows*wpr], 0 empty, 1 being
+  // computed, >= 2 done.  nullptr: every row is present.
+  uint32_t *chunk_state;
+  const HourPrep *hour;           // [hours], or nullptr (no positivity shortcut)
+  const uint8_t *fuel;            // FBP inputs of the on-demand rows
+  const float *slope;             // nullable
+  const CellPrep *cell;
+  double pcf, const_ros, dt2p32;
+  int32_t ellipse_mode;
   // run parameters
   uint64_t seed;
   float sigma;
@@ -94,7 +104,6 @@ struct RosTableArgs {
   int64_t *base;           // [hour][N][8] (absolute hour), or nullptr
   double *hros;            // [hour][N], or nullptr
   double *ros8;            // export: [N][8] of hour0 only, or nullptr
-  int32_t *hros_pos;       // cleared if some burnable cell has HROS <= 1e-200
   const int32_t *order;    // cells grouped by (fuel code, sloped); nullptr = identity
 };
 

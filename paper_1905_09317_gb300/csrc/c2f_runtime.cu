@@ -59,6 +59,8 @@ __global__ void k_frontier_g4(FrontierArgs);
 __global__ void k_frontier_w1(FrontierArgs);
 __global__ void k_frontier_w2(FrontierArgs);
 __global__ void k_frontier_w4(FrontierArgs);
+__global__ void k_frontier_lg1(FrontierArgs);
+__global__ void k_frontier_lw1(FrontierArgs);
 __global__ void k_burn_prob(const uint32_t *, int32_t, int32_t, int32_t, int32_t, int32_t,
                             uint32_t *, int32_t);
 __global__ void k_scar_bytes(const uint32_t *, int32_t, int32_t, int32_t, int32_t, uint8_t *);
@@ -95,9 +97,13 @@ struct TableKey {
   }
 };
 
+// The rate-of-spread table of a landscape under one set of options.  Eager:
+// every row written by K1.  Lazy: rows written on demand by the frontier, 32
+// cells at a time, tracked by chunk_state ([hours][rows*wpr], 0 = empty).
 struct Table {
   TableKey key;
-  DevBuf hour_prep, base, hros, hros_pos;
+  DevBuf hour_prep, base, hros, chunk_state;
+  bool eager = false;
   cudaEvent_t ready = nullptr;   // recorded after the build; epochs on other streams wait on it
   Table() = default;
   Table(const Table &) = delete;
@@ -151,6 +157,7 @@ struct FrontierPlan {
   std::vector<int64_t> retry;
   DevBuf djobs, dbegin, dlist;
   int64_t cap = 0, max_n = 0, pw_max = 0, n_items = 0;
+  bool lazy = false;   // some simulation's table is filled on demand
   void (*kern)(FrontierArgs) = nullptr;
   size_t dyn_smem = 0;
   int threads = 32;
@@ -190,6 +197,7 @@ struct c2f_ctx {
   // launch shape
   int frontier_threads = 32;
   bool window_smem = true;
+  bool eager_tables = true;   // simulations build their tables with K1 up front
   int64_t cap_override = 0;
   int64_t graph_launches = 0;
   // serving
@@ -348,20 +356,16 @@ int prepare_table(c2f_ctx *ctx, Landscape &L, const TableKey &k) {
   if ((rc = dalloc(ctx, T->hour_prep, sizeof(HourPrep) * (size_t)L.n_hours))) return rc;
   if ((rc = dalloc(ctx, T->base, sizeof(int64_t) * 8 * (size_t)L.n * k.hours))) return rc;
   if ((rc = dalloc(ctx, T->hros, sizeof(double) * (size_t)L.n * k.hours))) return rc;
-  if ((rc = dalloc(ctx, T->hros_pos, 4))) return rc;
+  if ((rc = dalloc(ctx, T->chunk_state, sizeof(uint32_t) * (size_t)L.rows * L.wpr * k.hours))) return rc;
   L.table = T;
   return C2F_OK;
 }
 
-// a1 (hour prep) and K1 for L.table, on stream st (capturable)
-int launch_table(c2f_ctx *ctx, Landscape &L, cudaStream_t st) {
+// K1 over every row of L.table, then every chunk marked done (capturable)
+int fill_table(c2f_ctx *ctx, Landscape &L, cudaStream_t st) {
   Table &T = *L.table;
   const TableKey &k = T.key;
   ProfScope prof(ctx, 0, st);
-  k_hour_prep<<<grid1(L.n_hours, 64), 64, 0, st>>>(L.weather_dev->as<double>(), L.n_hours, k.curing,
-                                                    T.hour_prep.as<HourPrep>());
-  CKL("k_hour_prep");
-  CK(cudaMemsetAsync(T.hros_pos.p, 1, 4, st));   // non-zero until a row says otherwise
   RosTableArgs a{};
   a.fuel = L.fuel.as<uint8_t>();
   a.slope = L.has_slope ? L.slope.as<float>() : nullptr;
@@ -377,11 +381,32 @@ int launch_table(c2f_ctx *ctx, Landscape &L, cudaStream_t st) {
   a.base = T.base.as<int64_t>();
   a.hros = T.hros.as<double>();
   a.ros8 = nullptr;
-  a.hros_pos = T.hros_pos.as<int32_t>();
   a.order = L.order.as<int32_t>();
   dim3 grid(grid1(L.n, 128), (unsigned)k.hours);
   k_ros_table<<<grid, 128, 0, st>>>(a);
   CKL("k_ros_table");
+  CK(cudaMemsetAsync(T.chunk_state.p, 0x02, T.chunk_state.bytes, st));   // >= 2: done
+  T.eager = true;
+  return C2F_OK;
+}
+
+// a1 (hour prep) for L.table and either K1 (eager) or empty chunk states
+// (lazy), on stream st (capturable)
+int launch_table(c2f_ctx *ctx, Landscape &L, cudaStream_t st, bool eager) {
+  Table &T = *L.table;
+  const TableKey &k = T.key;
+  {
+    ProfScope prof(ctx, 0, st);
+    k_hour_prep<<<grid1(L.n_hours, 64), 64, 0, st>>>(L.weather_dev->as<double>(), L.n_hours, k.curing,
+                                                      T.hour_prep.as<HourPrep>());
+    CKL("k_hour_prep");
+  }
+  if (eager) {
+    int rc = fill_table(ctx, L, st);
+    if (rc) return rc;
+  } else {
+    CK(cudaMemsetAsync(T.chunk_state.p, 0, T.chunk_state.bytes, st));
+  }
   // inside a graph capture the event is left unrecorded (reads as complete):
   // the graph runs to completion before the capturing call returns
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -390,11 +415,19 @@ int launch_table(c2f_ctx *ctx, Landscape &L, cudaStream_t st) {
   return C2F_OK;
 }
 
-int ensure_table(c2f_ctx *ctx, Landscape &L, const TableKey &k, bool force) {
-  if (!force && table_ok(L, k)) return C2F_OK;
+// mode 0: an eager table (a lazy one is completed in place); 1: a new eager
+// table; 2: a new lazy table
+int ensure_table(c2f_ctx *ctx, Landscape &L, const TableKey &k, int mode) {
+  if (mode == 0 && table_ok(L, k)) {
+    if (L.table->eager) return C2F_OK;
+    int rc = fill_table(ctx, L, ctx->stream);
+    if (rc) return rc;
+    CK(cudaEventRecord(L.table->ready, ctx->stream));
+    return C2F_OK;
+  }
   int rc = prepare_table(ctx, L, k);
   if (rc) return rc;
-  return launch_table(ctx, L, ctx->stream);
+  return launch_table(ctx, L, ctx->stream, mode != 2);
 }
 
 std::shared_ptr<Landscape> find_land(c2f_ctx *ctx, int32_t id) {
@@ -468,7 +501,15 @@ SimJob job_of(const Sim &s) {
   j.burnable_list = L.burnable_list.as<int32_t>();
   j.base = T.base.as<int64_t>();
   j.hros = T.hros.as<double>();
-  j.hros_pos = T.hros_pos.as<int32_t>();
+  j.chunk_state = T.eager ? nullptr : T.chunk_state.as<uint32_t>();
+  j.hour = T.hour_prep.as<HourPrep>();
+  j.fuel = L.fuel.as<uint8_t>();
+  j.slope = L.has_slope ? L.slope.as<float>() : nullptr;
+  j.cell = L.cell_prep.as<CellPrep>();
+  j.pcf = T.key.pc / 100.0;
+  j.const_ros = T.key.const_ros;
+  j.dt2p32 = (double)T.key.dt * 4294967296.0;
+  j.ellipse_mode = T.key.ellipse;
   j.seed = s.p.seed;
   j.sigma = (float)s.p.ros_sigma;
   j.ignition_mode = s.p.ignition_mode;
@@ -506,14 +547,16 @@ int64_t replica_cost(const Landscape &L, const Sim &s) {
 int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, int64_t todo,
                    int64_t cap_in, int attempt) {
   int rc;
-  const int threads = ctx->frontier_threads;   // 32, 64 or 128: one replica per warp
+  const int threads = F.lazy ? 32 : ctx->frontier_threads;   // 32, 64 or 128: one replica per warp
   const int wpc = threads / 32;
   int64_t cap = (cap_in + 3) & ~int64_t(3);
   int64_t win_cap = cap;
   {
     const int64_t want = std::max<int64_t>(1, (todo + ctx->sm_count - 1) / ctx->sm_count);
     const int64_t warps_per_sm = attempt == 0 ? std::min<int64_t>(want, 8) : std::min<int64_t>(want, 2);
-    const int64_t per_warp = ((int64_t)ctx->smem_per_sm - 1024 * warps_per_sm / wpc) / warps_per_sm;
+    // per CTA: 1 KB reserved by the system and about 1 KB of static shared memory per warp
+    const int64_t per_warp = ((int64_t)ctx->smem_per_sm - (1024 * warps_per_sm) / wpc - 1024 * warps_per_sm) /
+                             warps_per_sm;
     const int64_t room = (per_warp - 2 * (int64_t)kWinRows * kWinWords * 4 - 512) / 14;
     win_cap = std::min<int64_t>(cap, std::max<int64_t>(256, room & ~int64_t(63)));
     if (attempt > 0) win_cap = std::max<int64_t>(256, room & ~int64_t(63));
@@ -526,6 +569,7 @@ int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, i
   const int64_t warp_words = use_win ? win_words : 0;
   F.kern = use_win ? (wpc == 1 ? k_frontier_w1 : wpc == 2 ? k_frontier_w2 : k_frontier_w4)
                    : (wpc == 1 ? k_frontier_g1 : wpc == 2 ? k_frontier_g2 : k_frontier_g4);
+  if (F.lazy) F.kern = use_win ? k_frontier_lw1 : k_frontier_lg1;
   F.dyn_smem = (size_t)warp_words * 4 * wpc;
   F.threads = threads;
   if (F.dyn_smem > 0)
@@ -574,8 +618,10 @@ int plan_frontier(c2f_ctx *ctx, const std::vector<Sim *> &sims, FrontierPlan &F,
   jobs.assign(nj, SimJob{});
   F.begin.assign(nj + 1, 0);
   F.cap = 0; F.max_n = 0; F.pw_max = 0;
+  F.lazy = false;
   for (int32_t i = 0; i < nj; ++i) {
     jobs[i] = job_of(*F.sims[i]);
+    if (jobs[i].chunk_state) F.lazy = true;
     F.begin[i + 1] = F.begin[i] + F.sims[i]->p.n_replicas;
     F.cap = std::max(F.cap, default_cap(ctx, *F.lands[i]));
     F.max_n = std::max(F.max_n, F.lands[i]->n);
@@ -676,7 +722,7 @@ int make_sims(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_sim_params 
     if (!table_ok(*lands[i], want)) {
       if ((rc = prepare_table(ctx, *lands[i], want))) return rc;
       if (built) built->push_back(lands[i].get());
-      else if ((rc = launch_table(ctx, *lands[i], ctx->stream))) return rc;
+      else if ((rc = launch_table(ctx, *lands[i], ctx->stream, ctx->eager_tables))) return rc;
     }
   }
   out.resize(n);
@@ -723,7 +769,7 @@ int simulate_many(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_sim_par
   if (graph) {
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     int lrc = C2F_OK;
-    for (Landscape *L : builds) if (!lrc) lrc = launch_table(ctx, *L, ctx->stream);
+    for (Landscape *L : builds) if (!lrc) lrc = launch_table(ctx, *L, ctx->stream, ctx->eager_tables);
     if (!lrc) lrc = launch_frontier(ctx, F, ctx->scratch, ctx->stream);
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
@@ -753,8 +799,15 @@ cudaStream_t take_stream(c2f_ctx *ctx) {
     ctx->stream_pool.pop_back();
     return s;
   }
+  // epochs run at the highest stream priority: their frontier CTAs are placed
+  // before table builds queued at the same time on the context stream
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) { cudaGetLastError(); greatest = 0; }
   cudaStream_t s = nullptr;
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
   return s;
 }
 
@@ -1064,13 +1117,14 @@ C2F_API int c2f_set_weather(c2f_ctx *ctx, int32_t landscape_id, int32_t n_hours,
 C2F_API int c2f_build_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p, int force) {
   if (!ctx) return C2F_EINVAL;
   LOCK;
+  if (force < 0 || force > 2) return fail(ctx, C2F_EINVAL, "force must be 0, 1 or 2");
   auto L = find_land(ctx, landscape_id);
   if (!L) return fail(ctx, C2F_ENOTFOUND, "unknown landscape %d", landscape_id);
   if (L->n_hours < 1) return fail(ctx, C2F_EINVAL, "landscape has no weather");
   int rc = validate_params(ctx, *L, p);
   if (rc) return rc;
   CK(cudaSetDevice(ctx->device));
-  return ensure_table(ctx, *L, key_of(p), force != 0);
+  return ensure_table(ctx, *L, key_of(p), force);
 }
 
 C2F_API int c2f_get_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p, int32_t hour,
@@ -1084,7 +1138,7 @@ C2F_API int c2f_get_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params
   if (rc) return rc;
   if (hour < 0 || hour >= p->hours) return fail(ctx, C2F_EINVAL, "hour out of range");
   CK(cudaSetDevice(ctx->device));
-  if ((rc = ensure_table(ctx, *L, key_of(p), false))) return rc;
+  if ((rc = ensure_table(ctx, *L, key_of(p), 0))) return rc;
   const Table &T = *L->table;
   CK(cudaStreamWaitEvent(ctx->stream, T.ready, 0));
   const size_t n = (size_t)L->n;
@@ -1305,6 +1359,13 @@ C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem) {
   if (smem < 0) return fail(ctx, C2F_EINVAL, "smem must be >= 0");
   ctx->frontier_threads = threads;
   ctx->window_smem = smem != 0;
+  return C2F_OK;
+}
+
+C2F_API int c2f_set_table_mode(c2f_ctx *ctx, int eager) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  ctx->eager_tables = eager != 0;
   return C2F_OK;
 }
 

@@ -120,9 +120,10 @@ extern "C" C2F_API int c2f_frontier_static(const c2f_frontier_io *io, const c2f_
   SimJob job{};
   job.rows = io->rows; job.cols = io->cols; job.wpr = wpr;
   job.burnable = io->burnable;
-  job.base = io->base;
-  job.hros = io->hros;
-  job.hros_pos = nullptr;   // receive tests read HROS when the threshold is 0
+  job.base = const_cast<int64_t *>(io->base);
+  job.hros = const_cast<double *>(io->hros);
+  job.chunk_state = nullptr;   // the caller's table is complete
+  job.hour = nullptr;          // receive tests read HROS when the threshold is 0
   job.seed = p->seed;
   job.sigma = (float)p->ros_sigma;
   job.ignition_mode = 0;
