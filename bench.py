@@ -147,6 +147,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ multi-rank pieces
+def rank_seed(seed: int, rank: int) -> int:
+    """Each rank runs its own replicas: the run seed is offset per rank (the
+    replica index keys the counter, the seed keys Philox), so no replica of one
+    rank repeats another rank's."""
+    return int(seed) + 7919 * int(rank)
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's time (all_reduce MAX; identity for one rank)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: int, world: int, steps: int, seconds: float) -> float:
+    """Units all ranks processed over the slowest rank's time (weak scaling)."""
+    return units_per_rank_step * world * steps / seconds
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -169,7 +191,7 @@ def run_ours(args, rank, world, local_rank):
     R = w.params["n_replicas"]
     keys = {f[0] for f in c2f.SimParams._fields_}
     params = c2f.default_params(**{k: v for k, v in w.params.items() if k in keys})
-    params.seed = params.seed + 7919 * rank          # each rank: its own replicas
+    params.seed = rank_seed(params.seed, rank)       # each rank: its own replicas
 
     ctx = c2f.Context(local_rank)
     if args.frontier_threads:
@@ -241,10 +263,7 @@ def run_ours(args, rank, world, local_rank):
     for s in sids:
         ctx.release(s)
 
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
 
     # e2e: host buffers through the C ABI, copies inside the timed region
     e2e = None
@@ -263,17 +282,14 @@ def run_ours(args, rank, world, local_rank):
             ctx.release(l2)
         torch.cuda.synchronize(dev)
         e2e_s = time.perf_counter() - t0
-        te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-        e2e = dict(value=work_per_step * world * e2e_steps / float(te.item()), unit=METRIC,
+        e2e_max = max_over_ranks(e2e_s, world, dev)
+        e2e = dict(value=whole_job_rate(work_per_step, world, e2e_steps, e2e_max), unit=METRIC,
                    h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(host_counts.nbytes),
                    steps=e2e_steps)
 
     out = None
     if rank == 0:
-        total_work = work_per_step * world * args.steps
-        value = total_work / (ms_max / 1e3)
+        value = whole_job_rate(work_per_step, world, args.steps, ms_max / 1e3)
         peaks = measured_peaks()
         fam = {k: v for k, v in kt.items()}
         dom = max(fam, key=lambda k: fam[k][0])

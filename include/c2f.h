@@ -29,6 +29,7 @@
 #ifndef C2F_H
 #define C2F_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -96,6 +97,25 @@ C2F_API void c2f_default_params(c2f_sim_params *p);
  * Errors: C2F_EINVAL (no such device), C2F_ECUDA. */
 C2F_API int c2f_create(c2f_ctx **out, int device);
 
+/* Device-memory hooks.  With hooks, every device buffer of the context comes
+ * from alloc(bytes, stream, user) and goes back through free(ptr, bytes,
+ * stream, user) instead of cudaMallocAsync / cudaFreeAsync, with the same
+ * stream-ordered meaning: the block is used by work on `stream` (and by other
+ * streams only between host synchronisations), and a block freed on a stream
+ * may be handed out again for work queued later on that stream.  alloc
+ * returns NULL when it cannot allocate (the call then fails with
+ * C2F_ENOMEM).  A host framework's caching allocator (e.g. PyTorch's) can
+ * own the library's memory this way.  The hooks must stay valid until
+ * c2f_destroy returns. */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *stream, void *user);
+  void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+  void *user;
+} c2f_alloc_hooks;
+
+/* c2f_create with allocation hooks (NULL hooks = cudaMallocAsync). */
+C2F_API int c2f_create_with_hooks(c2f_ctx **out, int device, const c2f_alloc_hooks *hooks);
+
 /* Makes the context issue its work on `stream` (a cudaStream_t of the same
  * device, e.g. a PyTorch stream); NULL restores the context's own stream. */
 C2F_API int c2f_set_stream(c2f_ctx *ctx, void *stream);
@@ -103,7 +123,8 @@ C2F_API int c2f_set_stream(c2f_ctx *ctx, void *stream);
 /* Frees everything the context owns.  NULL is accepted. */
 C2F_API void c2f_destroy(c2f_ctx *ctx);
 
-/* Text of the last error raised on ctx (empty string if none). */
+/* Text of the last error the calling thread got from the library (empty
+ * string if none); valid until that thread's next library call. */
 C2F_API const char *c2f_last_error(const c2f_ctx *ctx);
 
 /* Loads a landscape (Sec. 3.3 cell fields; Sec. 3.5 (i)): `fuel` codes
@@ -203,6 +224,19 @@ C2F_API int c2f_burn_prob_device(c2f_ctx *ctx, int32_t sim_id, uint32_t *counts_
  * in replica r (n_replicas*N bytes), and, if the simulation kept them,
  * ignition steps ign_step[r*N + c] (-1 = never).  Either pointer may be NULL. */
 C2F_API int c2f_get_scars(c2f_ctx *ctx, int32_t sim_id, uint8_t *scars, int32_t *ign_step);
+
+/* The same burn grids bit-packed, as kept on the device: for replica r, row y
+ * and word x (x < wpr = ceil(cols/32)), words[(r*rows + y)*wpr + x] holds
+ * cells (y, 32x .. 32x+31), bit b = column 32x+b; padding bits are 0
+ * (n_replicas*rows*wpr uint32 words, host memory). */
+C2F_API int c2f_get_scar_bits(c2f_ctx *ctx, int32_t sim_id, uint32_t *words);
+
+/* Fire-scar evolution (Sec. 3.6 (ii)): scars[r*N + c] = 1 if cell c ignited in
+ * replica r by the end of weather hour `hour` (0-based; fire periods up to
+ * (hour+1)*60/minutes_per_step).  Needs the ignition steps
+ * (C2F_OUT_IGN_STEPS), else C2F_EINVAL; hour outside [0, hours) is
+ * C2F_EINVAL. */
+C2F_API int c2f_get_scars_at_hour(c2f_ctx *ctx, int32_t sim_id, int32_t hour, uint8_t *scars);
 
 /* Per-replica counters: work[r] = sum over fire periods of the number of
  * burning cells (cell-updates), ignited[r] = cells ever ignited, ign_cell[r]

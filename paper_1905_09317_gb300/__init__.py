@@ -56,11 +56,37 @@ class FrontierIO(C.Structure):
 _lib = None
 _lock = threading.Lock()
 
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class AllocHooks(C.Structure):
+    """c2f_alloc_hooks: device allocations routed through the host framework."""
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", C.c_void_p)]
+
+
+def torch_alloc_hooks(device: int) -> AllocHooks:
+    """Hooks that take the library's device memory from PyTorch's caching
+    allocator (stream-ordered on the stream the library names)."""
+    import torch
+
+    def alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+        except Exception:
+            return None
+
+    def free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return AllocHooks(_ALLOC_FN(alloc), _FREE_FN(free), None)
+
 # (name, restype, argtypes)
 _P = C.POINTER
 _SIGS = [
     ("c2f_default_params", None, [_P(SimParams)]),
     ("c2f_create", C.c_int, [_P(C.c_void_p), C.c_int]),
+    ("c2f_create_with_hooks", C.c_int, [_P(C.c_void_p), C.c_int, _P(AllocHooks)]),
     ("c2f_set_stream", C.c_int, [C.c_void_p, C.c_void_p]),
     ("c2f_destroy", None, [C.c_void_p]),
     ("c2f_last_error", C.c_char_p, [C.c_void_p]),
@@ -82,6 +108,8 @@ _SIGS = [
     ("c2f_burn_prob", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_burn_prob_device", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_get_scars", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    ("c2f_get_scar_bits", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    ("c2f_get_scars_at_hour", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     ("c2f_get_counters", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("c2f_set_list_capacity", C.c_int, [C.c_void_p, C.c_int64]),
     ("c2f_set_frontier_config", C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
@@ -137,10 +165,19 @@ def _ptr(a):
 class Context:
     """One c2f context on a CUDA device (owns a stream and all device memory)."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, allocator: str | None = None):
+        """allocator: None (the library's stream-ordered cudaMallocAsync) or
+        "torch" (device memory from PyTorch's caching allocator)."""
         self.lib = load_library()
         h = C.c_void_p()
-        rc = self.lib.c2f_create(C.byref(h), int(device))
+        self._hooks = None
+        if allocator == "torch":
+            self._hooks = torch_alloc_hooks(int(device))
+            rc = self.lib.c2f_create_with_hooks(C.byref(h), int(device), C.byref(self._hooks))
+        elif allocator is None:
+            rc = self.lib.c2f_create(C.byref(h), int(device))
+        else:
+            raise ValueError(f"unknown allocator {allocator!r}")
         if rc != C2F_OK:
             raise C2FError(rc, f"c2f_create(device={device}) failed (no usable CUDA device?)")
         self.h = h
@@ -253,6 +290,17 @@ class Context:
         ign = np.empty((n_replicas, n_cells), dtype=np.int32) if ign_steps else None
         self._check(self.lib.c2f_get_scars(self.h, int(sim_id), _ptr(scars), _ptr(ign)))
         return scars, ign
+
+    def get_scar_bits(self, sim_id: int, n_replicas: int, rows: int, cols: int) -> np.ndarray:
+        """(n_replicas, rows, ceil(cols/32)) uint32 words; bit b of word x = column 32x+b."""
+        words = np.empty((n_replicas, rows, (cols + 31) // 32), dtype=np.uint32)
+        self._check(self.lib.c2f_get_scar_bits(self.h, int(sim_id), _ptr(words)))
+        return words
+
+    def get_scars_at_hour(self, sim_id: int, hour: int, n_replicas: int, n_cells: int) -> np.ndarray:
+        scars = np.empty((n_replicas, n_cells), dtype=np.uint8)
+        self._check(self.lib.c2f_get_scars_at_hour(self.h, int(sim_id), int(hour), _ptr(scars)))
+        return scars
 
     def get_counters(self, sim_id: int, n_replicas: int):
         work = np.empty(n_replicas, dtype=np.int64)

@@ -978,6 +978,15 @@ __global__ void k_burn_prob(const uint32_t *__restrict__ planes, int32_t R, int3
   }
 }
 
+// ignition steps -> one byte per (replica, cell): ignited by period smax
+__global__ void k_scar_at_step(const int32_t *__restrict__ ign_step, int64_t total, int32_t smax,
+                               uint8_t *out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int32_t s = ign_step[i];
+  out[i] = (s >= 0 && s <= smax) ? 1 : 0;
+}
+
 // scar bits -> one byte per (replica, cell)
 __global__ void k_scar_bytes(const uint32_t *__restrict__ planes, int32_t R, int32_t rows,
                              int32_t cols, int32_t wpr, uint8_t *out) {

@@ -64,6 +64,7 @@ __global__ void k_frontier_lw1(FrontierArgs);
 __global__ void k_burn_prob(const uint32_t *, int32_t, int32_t, int32_t, int32_t, int32_t,
                             uint32_t *, int32_t);
 __global__ void k_scar_bytes(const uint32_t *, int32_t, int32_t, int32_t, int32_t, uint8_t *);
+__global__ void k_scar_at_step(const int32_t *, int64_t, int32_t, uint8_t *);
 cudaError_t upload_constants();
 }  // namespace c2f
 
@@ -72,16 +73,22 @@ using namespace c2f;
 namespace {
 
 // ------------------------------------------------------------------ device buffers
+// A device buffer, stream-ordered: freed on the stream it was allocated on,
+// through the context's allocation hooks when it has them.
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
   cudaStream_t st = nullptr;
+  const c2f_alloc_hooks *hooks = nullptr;
   DevBuf() = default;
   DevBuf(const DevBuf &) = delete;
   DevBuf &operator=(const DevBuf &) = delete;
   ~DevBuf() { reset(); }
   void reset() {
-    if (p) cudaFreeAsync(p, st);
+    if (p) {
+      if (hooks) hooks->free(p, bytes, st, hooks->user);
+      else cudaFreeAsync(p, st);
+    }
     p = nullptr;
     bytes = 0;
   }
@@ -183,6 +190,8 @@ DeviceInit g_devinit[64];
 
 struct c2f_ctx {
   int device = 0;
+  bool has_hooks = false;
+  c2f_alloc_hooks hooks{};
   int sm_count = 0;
   int smem_optin = 0, smem_per_sm = 0;
   cudaStream_t own_stream = nullptr;
@@ -216,6 +225,8 @@ struct c2f_ctx {
 
 namespace {
 
+thread_local std::string tl_last_error;   // what c2f_last_error reports to this thread
+
 int fail(c2f_ctx *ctx, int code, const char *fmt, ...) {
   char buf[512];
   va_list ap;
@@ -223,6 +234,7 @@ int fail(c2f_ctx *ctx, int code, const char *fmt, ...) {
   vsnprintf(buf, sizeof buf, fmt, ap);
   va_end(ap);
   if (ctx) ctx->last_error = buf;
+  tl_last_error = buf;
   return code;
 }
 
@@ -247,11 +259,17 @@ int cuda_fail(c2f_ctx *ctx, cudaError_t e, const char *what) {
 int dalloc_on(c2f_ctx *ctx, DevBuf &b, size_t bytes, cudaStream_t st) {
   b.reset();
   b.st = st;
+  b.hooks = ctx->has_hooks ? &ctx->hooks : nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMallocAsync(&b.p, bytes, st);
-  if (e != cudaSuccess) {
-    b.p = nullptr;
-    return cuda_fail(ctx, e, "cudaMallocAsync");
+  if (b.hooks) {
+    b.p = b.hooks->alloc(bytes, st, b.hooks->user);
+    if (!b.p) return fail(ctx, C2F_ENOMEM, "allocation hook returned no memory for %zu bytes", bytes);
+  } else {
+    cudaError_t e = cudaMallocAsync(&b.p, bytes, st);
+    if (e != cudaSuccess) {
+      b.p = nullptr;
+      return cuda_fail(ctx, e, "cudaMallocAsync");
+    }
   }
   b.bytes = bytes;
   return C2F_OK;
@@ -930,9 +948,12 @@ C2F_API void c2f_default_params(c2f_sim_params *p) {
   p->outputs = C2F_OUT_SCARS | C2F_OUT_COUNTERS;
 }
 
-C2F_API int c2f_create(c2f_ctx **out, int device) {
+C2F_API int c2f_create(c2f_ctx **out, int device) { return c2f_create_with_hooks(out, device, nullptr); }
+
+C2F_API int c2f_create_with_hooks(c2f_ctx **out, int device, const c2f_alloc_hooks *hooks) {
   if (!out) return C2F_EINVAL;
   *out = nullptr;
+  if (hooks && (!hooks->alloc || !hooks->free)) return C2F_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();
@@ -941,6 +962,7 @@ C2F_API int c2f_create(c2f_ctx **out, int device) {
   std::unique_ptr<c2f_ctx> holder(new c2f_ctx());
   c2f_ctx *ctx = holder.get();
   ctx->device = device;
+  if (hooks) { ctx->hooks = *hooks; ctx->has_hooks = true; }
   CK(cudaSetDevice(device));
   CK(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
   CK(cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
@@ -984,7 +1006,8 @@ C2F_API void c2f_destroy(c2f_ctx *ctx) {
 }
 
 C2F_API const char *c2f_last_error(const c2f_ctx *ctx) {
-  return ctx ? ctx->last_error.c_str() : "";
+  (void)ctx;
+  return tl_last_error.c_str();
 }
 
 C2F_API int c2f_load_landscape(c2f_ctx *ctx, int32_t rows, int32_t cols, double cell_size_m,
@@ -1321,6 +1344,45 @@ C2F_API int c2f_get_scars(c2f_ctx *ctx, int32_t sim_id, uint8_t *scars, int32_t 
     CK(cudaStreamSynchronize(st));
   }
   if (ign_step) CK(cudaMemcpyAsync(ign_step, s->ign_step.p, total * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return C2F_OK;
+}
+
+C2F_API int c2f_get_scar_bits(c2f_ctx *ctx, int32_t sim_id, uint32_t *words) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  auto s = find_sim(ctx, sim_id);
+  if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  if (!words) return fail(ctx, C2F_EINVAL, "words is NULL");
+  int rc = sim_ready(ctx, *s);
+  if (rc) return rc;
+  CK(cudaSetDevice(ctx->device));
+  const size_t bytes = (size_t)s->p.n_replicas * s->rows * s->wpr * 4;
+  CK(cudaMemcpyAsync(words, s->ign_plane.p, bytes, cudaMemcpyDeviceToHost, ctx->read_stream));
+  CK(cudaStreamSynchronize(ctx->read_stream));
+  return C2F_OK;
+}
+
+C2F_API int c2f_get_scars_at_hour(c2f_ctx *ctx, int32_t sim_id, int32_t hour, uint8_t *scars) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  auto s = find_sim(ctx, sim_id);
+  if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  if (!scars) return fail(ctx, C2F_EINVAL, "scars is NULL");
+  int rc = sim_ready(ctx, *s);
+  if (rc) return rc;
+  if (!s->ign_step.p)
+    return fail(ctx, C2F_EINVAL, "simulation did not keep ignition steps (C2F_OUT_IGN_STEPS)");
+  if (hour < 0 || hour >= s->p.hours) return fail(ctx, C2F_EINVAL, "hour out of range");
+  CK(cudaSetDevice(ctx->device));
+  const int64_t total = (int64_t)s->n * s->p.n_replicas;
+  const int32_t smax = (hour + 1) * (60 / s->p.minutes_per_step);
+  cudaStream_t st = ctx->read_stream;
+  DevBuf tmp;
+  if ((rc = dalloc_on(ctx, tmp, (size_t)total, st))) return rc;
+  k_scar_at_step<<<grid1(total, 256), 256, 0, st>>>(s->ign_step.as<int32_t>(), total, smax, tmp.as<uint8_t>());
+  CKL("k_scar_at_step");
+  CK(cudaMemcpyAsync(scars, tmp.p, (size_t)total, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return C2F_OK;
 }

@@ -141,8 +141,8 @@ def test_random_small_cases(ctx, seed):
     w = S.random_small_case(seed)
     if not (w.landscape.fuel != 0).any():
         pytest.skip("no fuel")
-    burnable = (w.landscape.fuel != 0) & ~(w.landscape.unburnable.astype(bool)
-                                          if w.landscape.unburnable is not None else False)
+    unb = w.landscape.unburnable
+    burnable = (w.landscape.fuel != 0) & (unb == 0 if unb is not None else True)
     if not burnable.any():
         pytest.skip("no burnable cell")
     R = 37

@@ -59,3 +59,12 @@ def test_defaults_and_no_device_path(lib):
     # NULL context arguments are rejected without touching a device
     assert lib.c2f_simulate(None, 1, None, None) == c2f.C2F_EINVAL
     assert lib.c2f_release(None, 1) == c2f.C2F_EINVAL
+
+
+def test_hooks_are_checked_before_any_device_call(lib):
+    h = ctypes.c_void_p()
+    bad = c2f.AllocHooks()            # NULL alloc / free
+    assert lib.c2f_create_with_hooks(ctypes.byref(h), 0, ctypes.byref(bad)) == c2f.C2F_EINVAL
+    assert lib.c2f_create_with_hooks(None, 0, None) == c2f.C2F_EINVAL
+    assert lib.c2f_get_scar_bits(None, 1, None) == c2f.C2F_EINVAL
+    assert lib.c2f_get_scars_at_hour(None, 1, 0, None) == c2f.C2F_EINVAL
