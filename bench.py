@@ -410,6 +410,8 @@ def run_batch(args):
     ws = [S.config3_workload(sp) for sp in specs]
     ctx = c2f.Context(0)
     ctx.set_table_mode(not args.lazy_tables)
+    if args.frontier_threads:
+        ctx.set_frontier_config(args.frontier_threads, args.smem_plane_bytes)
     lids = []
     for w in ws:
         L = w.landscape
@@ -418,6 +420,9 @@ def run_batch(args):
         lids.append(lid)
     ps = [_params_of(c2f, w) for w in ws]
     ns = [w.landscape.fuel.size for w in ws]
+    tuned = None
+    if not args.frontier_threads:   # launch shape chosen by the autotuner on a scaled-down copy
+        tuned = ctx.autotune(lids, ps, sample_replicas=args.tune_sample)
 
     def plain():
         sids = []
@@ -449,8 +454,17 @@ def run_batch(args):
             assert work is None or wk == work, "work count differs between plain and batched"
             work = wk
         dt = (time.perf_counter() - t0) / args.steps
+        # one more pass, outside the timing, with per-kernel device times
+        ctx.profile(True)
+        ctx.kernel_times()
+        for sid in fn():
+            ctx.release(sid)
+        kt = ctx.kernel_times()
+        ctx.profile(False)
         out[name] = dict(s_per_step=dt, cell_updates_per_s=work / dt,
-                         replicas_per_s=sum(p.n_replicas for p in ps) / dt)
+                         replicas_per_s=sum(p.n_replicas for p in ps) / dt,
+                         kernel_ms={k: v[0] for k, v in kt.items()},
+                         kernel_launches={k: v[1] for k, v in kt.items()})
     ctx.close()
     return {"metric": METRIC, "value": out["batched"]["cell_updates_per_s"], "unit": METRIC,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -462,6 +476,9 @@ def run_batch(args):
                        "replicas": int(sum(p.n_replicas for p in ps)),
                        "cell_updates_per_step": work,
                        "timing": "host wall clock per step incl. table builds, burn counts to host"},
+            "autotuned": None if tuned is None else
+            {"threads": tuned[0], "smem_lists": tuned[1], "sample_frontier_ms": tuned[2],
+             "sample_replicas": args.tune_sample},
             "plain": out["plain"], "batched": out["batched"],
             "batched_over_plain": out["plain"]["s_per_step"] / out["batched"]["s_per_step"]}
 
@@ -619,6 +636,7 @@ def main():
     ap.add_argument("--serial", action="store_true",
                     help="one synchronous step at a time (no overlap of K1 with the previous frontier)")
     ap.add_argument("--workload", default="landscape", choices=["landscape", "batch", "serve", "large"])
+    ap.add_argument("--tune-sample", type=int, default=4096, help="batch: autotuner replica sample")
     ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--max-inflight", type=int, default=3, help="serve: concurrent epochs")

@@ -45,13 +45,24 @@
 
 /* ======================================================================
  * 1. binary64 elementary functions (own implementation)
+ *    Series forms (exp_series, log_series), used to fill the tables below:
  *    exp: Cody-Waite reduction x = k ln2 + r, |r| <= ln2/2, Taylor series
  *         of degree 13 by Horner with fused multiply-add, then scale by 2^k.
  *    log: x = 2^e m, m in [sqrt(1/2), sqrt(2)], log m = 2 atanh(s),
  *         s = (m-1)/(m+1), odd series to s^21.
+ *    Table forms, the ones the method uses (Tang's table-driven method):
+ *    exp: x = (64 k + j) ln2/64 + r, |r| <= ln2/128:
+ *         exp x = 2^k T_j (1 + p(r)), T_j = 2^(j/64) (exp_series), p the
+ *         Taylor polynomial of exp(r) - 1 to r^5.
+ *    log: x = 2^e m, m in [1, 2), j = first 7 fraction bits of m,
+ *         V_j = RN(1 / (1 + j/128)), r = m V_j - 1 (one fused rounding):
+ *         log x = e ln2 - log V_j + log(1 + r), log V_j by log_series,
+ *         log(1 + r) by its Taylor polynomial to r^8 (|r| < 1/128).
  *    sincos in degrees: quadrant reduction by exact subtraction of a
  *         multiple of 90, Taylor series of sin (to t^17) and cos (to t^18).
- *    pow(x,y) = exp(y log x) for x > 0.
+ *    pow(x,y), x > 0: for y a positive multiple of 1/2 up to 8,
+ *         x^n (n = floor y, n-1 products from the left) times sqrt(x) when
+ *         2y is odd; otherwise exp(y log x).
  * The constants are ln 2 split into a 29-bit head and a tail, 1/ln 2 and
  * pi/180, each the double nearest to the real number; Taylor coefficients
  * are 1/k! computed as a correctly rounded division.
@@ -66,11 +77,17 @@ static double g_inv_fact[24];  /* 1/k!            */
 static double g_log_c[12];     /* 1/(2n+1)        */
 static double g_sin_c[10];     /* (-1)^n/(2n+1)!  */
 static double g_cos_c[10];     /* (-1)^n/(2n)!    */
+static double g_exp_tab[64];   /* 2^(j/64)               */
+static double g_log_inv[128];  /* RN(1 / (1 + j/128))    */
+static double g_log_tab[128];  /* -log(g_log_inv[j])     */
+static double g_log_c3, g_log_c4, g_log_c5, g_log_c6, g_log_c7, g_log_c8;   /* 1/n */
 static float g_inv_fact_f[12];
 static float g_log_cf[8];
 static float g_sin_cf[8];
 static float g_cos_cf[8];
 static int g_init = 0;
+
+static void fill_fn_tables(void);
 
 static void or_init_tables(void) {
   if (g_init) return;
@@ -94,7 +111,10 @@ static void or_init_tables(void) {
     g_sin_cf[n] = (float)g_sin_c[n];
     g_cos_cf[n] = (float)g_cos_c[n];
   }
+  g_log_c3 = 1.0 / 3.0; g_log_c4 = 1.0 / 4.0; g_log_c5 = 1.0 / 5.0;
+  g_log_c6 = 1.0 / 6.0; g_log_c7 = 1.0 / 7.0; g_log_c8 = 1.0 / 8.0;
   g_init = 1;
+  fill_fn_tables();
 }
 
 static double pow2i(int k) { /* exact 2^k, -1022 <= k <= 1023 */
@@ -110,8 +130,7 @@ static double scale2(double p, int k) {
   return p * pow2i(k);
 }
 
-OR_API double or_exp(double x) {
-  or_init_tables();
+static double exp_series(double x) {
   if (x != x) return x;
   if (x > 709.78) return INFINITY;
   if (x < -745.2) return 0.0;
@@ -122,8 +141,7 @@ OR_API double or_exp(double x) {
   return scale2(p, (int)kd);
 }
 
-OR_API double or_log(double x) {
-  or_init_tables();
+static double log_series(double x) {
   if (x != x) return x;
   if (x < 0.0) return NAN;
   if (x == 0.0) return -INFINITY;
@@ -148,8 +166,75 @@ OR_API double or_log(double x) {
   return ed * LN2_HI + fma(ed, LN2_LO, lm);
 }
 
+static void fill_fn_tables(void) {
+  for (int j = 0; j < 64; ++j) g_exp_tab[j] = exp_series((double)j * (LN2_HI / 64.0) + (double)j * (LN2_LO / 64.0));
+  for (int j = 0; j < 128; ++j) {
+    g_log_inv[j] = 1.0 / (1.0 + (double)j / 128.0);
+    g_log_tab[j] = -log_series(g_log_inv[j]);
+  }
+}
+
+OR_API double or_exp(double x) {
+  or_init_tables();
+  if (x != x) return x;
+  if (x > 709.78) return INFINITY;
+  if (x < -745.2) return 0.0;
+  double kd = nearbyint(x * (INV_LN2 * 64.0));
+  double r = (x - kd * (LN2_HI / 64.0)) - kd * (LN2_LO / 64.0);
+  double q = fma(fma(g_inv_fact[5], r, g_inv_fact[4]), r, g_inv_fact[3]);
+  q = fma(q, r, g_inv_fact[2]);
+  double p = fma(q, r * r, r);          /* exp(r) - 1 to r^5 */
+  long long k = (long long)kd;
+  double t = g_exp_tab[k & 63];
+  return scale2(fma(t, p, t), (int)(k >> 6));
+}
+
+OR_API double or_log(double x) {
+  or_init_tables();
+  if (x != x) return x;
+  if (x < 0.0) return NAN;
+  if (x == 0.0) return -INFINITY;
+  if (isinf(x)) return x;
+  int e = 0;
+  if (x < 0x1p-1022) { x = x * 0x1p54; e = -54; }
+  uint64_t b;
+  memcpy(&b, &x, 8);
+  e += (int)((b >> 52) & 0x7ff) - 1023;
+  int j = (int)((b >> 45) & 127);
+  b = (b & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL;
+  double m;
+  memcpy(&m, &b, 8);
+  double r = fma(m, g_log_inv[j], -1.0);
+  /* log(1 + r) = r - r^2/2 + r^3/3 - ... - r^8/8 */
+  double q = -g_log_c8;
+  q = fma(q, r, g_log_c7);
+  q = fma(q, r, -g_log_c6);
+  q = fma(q, r, g_log_c5);
+  q = fma(q, r, -g_log_c4);
+  q = fma(q, r, g_log_c3);
+  q = fma(q, r, -0.5);
+  double lp = fma(q, r * r, r);
+  double ed = (double)e;
+  double hi = ed * LN2_HI + g_log_tab[j];
+  double lo = fma(ed, LN2_LO, lp);
+  return hi + lo;
+}
+
 OR_API double or_pow(double x, double y) {
-  if (x > 0.0) return or_exp(y * or_log(x));
+  if (x > 0.0) {
+    double y2 = y + y;
+    if (y > 0.0 && y2 <= 16.0 && nearbyint(y2) == y2) {   /* y = n or n + 1/2, n <= 8 */
+      int n = (int)y;
+      double r = 1.0;
+      if (n > 0) {
+        r = x;
+        for (int i = 1; i < n; ++i) r = r * x;
+      }
+      if (((int)y2) & 1) r = (n > 0) ? r * sqrt(x) : sqrt(x);
+      return r;
+    }
+    return or_exp(y * or_log(x));
+  }
   if (x == 0.0) return (y > 0.0) ? 0.0 : ((y == 0.0) ? 1.0 : INFINITY);
   return NAN;
 }

@@ -48,7 +48,10 @@ inline void make_fuel_table(FuelCoef t[F_NCODES]) {
       {40.0, 0.0438, 1.7, 0.75, 63.0},    // S2 white spruce / balsam slash
       {55.0, 0.0829, 3.2, 0.75, 31.0},    // S3 coastal cedar / hemlock slash
   };
-  for (int i = 0; i < F_NCODES; ++i) t[i] = v[i];
+  for (int i = 0; i < F_NCODES; ++i) {
+    t[i] = v[i];
+    t[i].inv_c = v[i].c != 0.0 ? 1.0 / v[i].c : 0.0;   // the quotient isf_curve divides out
+  }
 }
 
 __device__ __forceinline__ bool is_o1(int f) { return f == F_O1A || f == F_O1B; }
@@ -82,7 +85,7 @@ __device__ inline double rsi_of(int fuel, double isi, double pcf, double cf) {
 // held at >= 0.01
 __device__ inline double isf_curve(const FuelCoef &k, double mult, double rsf) {
   if (!(rsf > 0.0)) return 0.0;
-  double x = __dsub_rn(1.0, dpow(__ddiv_rn(rsf, __dmul_rn(k.a, mult)), __ddiv_rn(1.0, k.c)));
+  double x = __dsub_rn(1.0, dpow(__ddiv_rn(rsf, __dmul_rn(k.a, mult)), k.inv_c));
   if (x < 0.01) x = 0.01;
   return __ddiv_rn(dlog(x), -k.b);
 }

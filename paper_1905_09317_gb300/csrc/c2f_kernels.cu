@@ -28,6 +28,7 @@
 // happens.  All progress arithmetic is int64, so the crossing periods are the
 // ones the period-by-period loop produces.
 #include <cstdint>
+#include <mutex>
 
 #include "c2f_fbp.cuh"
 
@@ -41,7 +42,21 @@ cudaError_t upload_constants() {
   make_fuel_table(ft);
   cudaError_t e = cudaMemcpyToSymbol(g_mc, &mc, sizeof mc);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_fuel, ft, sizeof ft);
+  if (e == cudaSuccess) {
+    k_math_tables<<<1, 128>>>();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   return e;
+}
+
+// once per device and process, for every entry point that launches kernels
+cudaError_t init_device_constants(int device) {
+  static std::once_flag once[64];
+  static cudaError_t err[64];
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+  std::call_once(once[device], [device] { err[device] = upload_constants(); });
+  return err[device];
 }
 
 __device__ __constant__ int kDR[8] = {0, -1, -1, -1, 0, 1, 1, 1};
@@ -338,9 +353,14 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+// chunk state, read at device scope from L2.  A relaxed load suffices: a warp
+// reads a chunk's rows (with L2 loads, __ldcg) only after a branch on the
+// state it loaded has resolved, and the computing warp made its rows visible
+// device-wide (__threadfence) before it set the state.  An acquire load would
+// also invalidate the SM's L1 on every check.
+__device__ __forceinline__ uint32_t ld_state(const uint32_t *p) {
   uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -587,7 +607,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         const int32_t bi = inwin ? (wr - dr0) * kWinWords + (wc - dw0) : 0;
         bool need = false, mine = false;
         if (wr >= 0 && !(inwin && ((dbits[bi >> 5] >> (bi & 31)) & 1u))) {
-          uint32_t st = ld_acquire(sth + w);
+          uint32_t st = ld_state(sth + w);
           if (st == 0u) {
             st = atomicCAS(sth + w, 0u, 1u);
             mine = st == 0u;
@@ -603,7 +623,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         if (mine && inwin) atomicOr(&dbits[bi >> 5], 1u << (bi & 31));
         if (need) {
           uint32_t polls = 0;
-          while (ld_acquire(sth + w) < 2u) {
+          while (ld_state(sth + w) < 2u) {
             if (++polls > kChunkSpinLimit) { status = 2; break; }
             __nanosleep(128);
           }

@@ -22,7 +22,7 @@ enum FuelCode : int {
   F_O1A, F_O1B, F_S1, F_S2, F_S3, F_NCODES
 };
 
-struct FuelCoef { double a, b, c, q, bui0; };
+struct FuelCoef { double a, b, c, q, bui0, inv_c; };   // inv_c = RN(1/c), 0 when c = 0
 
 struct HourPrep {
   double ws, ff, isz, sin_w, cos_w;

@@ -6,10 +6,18 @@
 // with no compiler contraction: the library is built with --fmad=false and
 // the fused steps are explicit __fma_rn calls), so that a CPU build of the
 // same construction reproduces every bit.  Constructions:
-//   exp   x = k ln2 + r (Cody-Waite, 29-bit head of ln2), Taylor to r^13, 2^k
-//   log   x = 2^e m, m in [sqrt(1/2), sqrt(2)], 2 atanh((m-1)/(m+1)) to s^21
+//   series forms (dexp_series, dlog_series), which fill the tables below:
+//     exp   x = k ln2 + r (Cody-Waite, 29-bit head of ln2), Taylor to r^13, 2^k
+//     log   x = 2^e m, m in [sqrt(1/2), sqrt(2)], 2 atanh((m-1)/(m+1)) to s^21
+//   table forms (Tang's method), used everywhere else:
+//     exp   x = (64k + j) ln2/64 + r: 2^k T_j (1 + p(r)), T_j = 2^(j/64),
+//           p = Taylor of exp(r) - 1 to r^5
+//     log   x = 2^e m, m in [1, 2), j = top 7 fraction bits, V_j = 1/(1 + j/128)
+//           rounded, r = m V_j - 1 (one fused rounding):
+//           e ln2 - log V_j + (Taylor of log(1 + r) to r^8)
 //   sin/cos of degrees: exact reduction by multiples of 90, Taylor to t^17/t^18
-//   pow(x, y) = exp(y log x)
+//   pow(x, y) = x^n sqrt(x)^(2y odd) for y a positive multiple of 1/2 up to
+//               8 (n = floor y, products from the left), else exp(y log x)
 // and the same in binary32 (exp to r^7, log to s^11, cos of a fraction of a
 // turn) for the perturbation draw.  Taylor coefficients are 1/k! as correctly
 // rounded binary64 quotients; they live in __constant__ memory, filled once per
@@ -23,6 +31,11 @@ namespace c2f {
 
 // coefficient tables, filled once per device by upload_constants()
 __constant__ MathConstants g_mc;
+// exp / log tables (lanes index them independently, so global memory through
+// the read-only cache rather than __constant__), filled by k_math_tables
+__device__ double g_exp_tab[64];    // 2^(j/64)
+__device__ double g_log_inv[128];   // RN(1 / (1 + j/128))
+__device__ double g_log_tab[128];   // -log(g_log_inv[j])
 
 // host: compute the coefficient tables (plain IEEE binary64 arithmetic)
 inline void make_math_constants(MathConstants *m) {
@@ -66,7 +79,7 @@ __device__ __forceinline__ double scale2(double p, int k) {
   return __dmul_rn(p, pow2i(k));
 }
 
-__device__ inline double dexp(double x) {
+__device__ inline double dexp_series(double x) {
   // |x| < 704 (integer test of the high word) skips the range checks below
   if ((__double2hiint(x) & 0x7fffffff) >= 0x40860000) {
     if (x != x) return x;
@@ -81,7 +94,7 @@ __device__ inline double dexp(double x) {
   return scale2(p, (int)kd);
 }
 
-__device__ inline double dlog(double x) {
+__device__ inline double dlog_series(double x) {
   int e = 0;
   const int hx = __double2hiint(x);
   if (hx < 0x00100000 || hx >= 0x7ff00000) {   // not a positive normal finite number
@@ -108,12 +121,82 @@ __device__ inline double dlog(double x) {
   return __dadd_rn(__dmul_rn(ed, kLn2Hi), __fma_rn(ed, kLn2Lo, lm));
 }
 
+__device__ inline double dexp(double x) {
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x40860000) {   // |x| >= 704
+    if (x != x) return x;
+    if (x > 709.78) return __longlong_as_double(0x7ff0000000000000LL);
+    if (x < -745.2) return 0.0;
+  }
+  const double kd = rint(__dmul_rn(x, kInvLn2 * 64.0));
+  const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(kd, kLn2Hi / 64.0)), __dmul_rn(kd, kLn2Lo / 64.0));
+  double q = __fma_rn(__fma_rn(g_mc.inv_fact[5], r, g_mc.inv_fact[4]), r, g_mc.inv_fact[3]);
+  q = __fma_rn(q, r, g_mc.inv_fact[2]);
+  const double p = __fma_rn(q, __dmul_rn(r, r), r);   // exp(r) - 1 to r^5
+  const long long k = (long long)kd;
+  const double t = __ldg(&g_exp_tab[k & 63]);
+  return scale2(__fma_rn(t, p, t), (int)(k >> 6));
+}
+
+__device__ inline double dlog(double x) {
+  int e = 0;
+  const int hx = __double2hiint(x);
+  if (hx < 0x00100000 || hx >= 0x7ff00000) {   // not a positive normal finite number
+    if (x != x) return x;
+    if (x < 0.0) return __longlong_as_double(0x7ff8000000000000LL);
+    if (x == 0.0) return __longlong_as_double((long long)0xfff0000000000000ULL);
+    if (__double_as_longlong(x) == 0x7ff0000000000000LL) return x;
+    if (x < 0x1p-1022) { x = __dmul_rn(x, 0x1p54); e = -54; }
+  }
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  e += (int)((b >> 52) & 0x7ff) - 1023;
+  const int j = (int)((b >> 45) & 127);
+  b = (b & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL;
+  const double m = __longlong_as_double((long long)b);
+  const double r = __fma_rn(m, __ldg(&g_log_inv[j]), -1.0);
+  // log(1 + r) = r - r^2/2 + r^3/3 - ... - r^8/8
+  double q = -0.125;
+  q = __fma_rn(q, r, g_mc.log_c[3]);        // 1/7
+  q = __fma_rn(q, r, -g_mc.inv_fact[3]);    // -1/6
+  q = __fma_rn(q, r, g_mc.log_c[2]);        // 1/5
+  q = __fma_rn(q, r, -0.25);
+  q = __fma_rn(q, r, g_mc.log_c[1]);        // 1/3
+  q = __fma_rn(q, r, -0.5);
+  const double lp = __fma_rn(q, __dmul_rn(r, r), r);
+  const double ed = (double)e;
+  const double hi = __dadd_rn(__dmul_rn(ed, kLn2Hi), __ldg(&g_log_tab[j]));
+  const double lo = __fma_rn(ed, kLn2Lo, lp);
+  return __dadd_rn(hi, lo);
+}
+
 __device__ inline double dpow(double x, double y) {
-  const long long bx = __double_as_longlong(x);
-  if (bx > 0 && bx < 0x7ff0000000000000LL) return dexp(__dmul_rn(y, dlog(x)));   // 0 < x < inf
-  if (x > 0.0) return dexp(__dmul_rn(y, dlog(x)));
+  if (x > 0.0) {
+    const double y2 = __dadd_rn(y, y);
+    if (y > 0.0 && y2 <= 16.0 && rint(y2) == y2) {   // y = n or n + 1/2, n <= 8
+      const int n = (int)y;
+      double r = 1.0;
+      if (n > 0) {
+        r = x;
+        for (int i = 1; i < n; ++i) r = __dmul_rn(r, x);
+      }
+      if (((int)y2) & 1) r = (n > 0) ? __dmul_rn(r, __dsqrt_rn(x)) : __dsqrt_rn(x);
+      return r;
+    }
+    return dexp(__dmul_rn(y, dlog(x)));
+  }
   if (x == 0.0) return (y > 0.0) ? 0.0 : ((y == 0.0) ? 1.0 : __longlong_as_double(0x7ff0000000000000LL));
   return __longlong_as_double(0x7ff8000000000000LL);
+}
+
+// fills g_exp_tab / g_log_inv / g_log_tab with the series forms (one block of 128)
+__global__ void k_math_tables() {
+  const int j = threadIdx.x;
+  if (j < 64)
+    g_exp_tab[j] = dexp_series(__dadd_rn(__dmul_rn((double)j, kLn2Hi / 64.0), __dmul_rn((double)j, kLn2Lo / 64.0)));
+  if (j < 128) {
+    const double v = __ddiv_rn(1.0, __dadd_rn(1.0, __ddiv_rn((double)j, 128.0)));
+    g_log_inv[j] = v;
+    g_log_tab[j] = -dlog_series(v);
+  }
 }
 
 __device__ inline void dsincos_deg(double x, double *s_out, double *c_out) {

@@ -65,7 +65,7 @@ __global__ void k_burn_prob(const uint32_t *, int32_t, int32_t, int32_t, int32_t
                             uint32_t *, int32_t);
 __global__ void k_scar_bytes(const uint32_t *, int32_t, int32_t, int32_t, int32_t, uint8_t *);
 __global__ void k_scar_at_step(const int32_t *, int64_t, int32_t, uint8_t *);
-cudaError_t upload_constants();
+cudaError_t init_device_constants(int device);
 }  // namespace c2f
 
 using namespace c2f;
@@ -180,11 +180,6 @@ struct Epoch {
   cudaEvent_t done = nullptr;
 };
 
-struct DeviceInit {
-  std::once_flag once;
-  cudaError_t err = cudaSuccess;
-};
-DeviceInit g_devinit[64];
 
 }  // namespace
 
@@ -279,9 +274,8 @@ int dalloc(c2f_ctx *ctx, DevBuf &b, size_t bytes) { return dalloc_on(ctx, b, byt
 
 int ensure_device_constants(c2f_ctx *ctx) {
   if (ctx->device < 0 || ctx->device >= 64) return fail(ctx, C2F_EINVAL, "device index out of range");
-  DeviceInit &d = g_devinit[ctx->device];
-  std::call_once(d.once, [&] { d.err = upload_constants(); });
-  if (d.err != cudaSuccess) return cuda_fail(ctx, d.err, "uploading constant tables");
+  const cudaError_t e = init_device_constants(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "uploading constant tables");
   return C2F_OK;
 }
 
@@ -555,6 +549,8 @@ SimJob job_of(const Sim &s) {
 // (not capturable), launch_frontier issues K2 and the K3 launch (capturable
 // in a CUDA graph), finish_frontier reads the per-replica status and re-runs,
 // with a larger burning list, any replica whose list overflowed.
+cudaStream_t take_stream(c2f_ctx *ctx);
+
 int64_t replica_cost(const Landscape &L, const Sim &s) {
   return (int64_t)s.p.hours * std::min<int64_t>(L.n_burnable, 50000);
 }
@@ -581,8 +577,10 @@ int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, i
   }
   const int64_t budget = (int64_t)ctx->smem_optin - 2048;
   const int64_t win_words = 2 * (int64_t)kWinRows * kWinWords + win_cap * 7 / 2;
+  // shared-memory lists only when they hold at least half the default capacity:
+  // smaller ones overflow on large fires and those replicas run twice
   const bool use_win = ctx->window_smem && win_words * 4 * wpc <= budget &&
-                       (attempt == 0 || win_cap >= cap);
+                       (attempt == 0 ? 2 * win_cap >= cap : win_cap >= cap);
   if (use_win) cap = win_cap;
   const int64_t warp_words = use_win ? win_words : 0;
   F.kern = use_win ? (wpc == 1 ? k_frontier_w1 : wpc == 2 ? k_frontier_w2 : k_frontier_w4)
@@ -590,8 +588,12 @@ int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, i
   if (F.lazy) F.kern = use_win ? k_frontier_lw1 : k_frontier_lg1;
   F.dyn_smem = (size_t)warp_words * 4 * wpc;
   F.threads = threads;
-  if (F.dyn_smem > 0)
-    CK(cudaFuncSetAttribute(F.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F.dyn_smem));
+  if (F.dyn_smem > 0) {   // only ever raised: plans made earlier may still be launched
+    cudaFuncAttributes fa{};
+    CK(cudaFuncGetAttributes(&fa, F.kern));
+    if ((int)F.dyn_smem > fa.maxDynamicSharedSizeBytes)
+      CK(cudaFuncSetAttribute(F.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F.dyn_smem));
+  }
   int bps = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, F.kern, threads, F.dyn_smem));
   bps = std::max(bps, 1);
@@ -763,7 +765,15 @@ void register_sims(c2f_ctx *ctx, std::vector<std::shared_ptr<Sim>> &sims, int32_
   }
 }
 
-// synchronous: one epoch on ctx->stream, run to completion
+// synchronous: the simulations of one call, run to completion.
+//
+// When the call builds tables for several landscapes, the landscapes are cut
+// into up to four groups by table cost (largest first, about equal build
+// time per group) and each group's frontier is launched on its own stream as
+// soon as the group's tables are built, so table builds (FP64-bound) overlap
+// the frontiers (latency-bound) of earlier groups.  A batch's launches go out
+// as one CUDA graph (fork/join over the group streams); a single simulation
+// is launched directly.
 int simulate_many(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_sim_params *params,
                   int32_t *sim_ids) {
   if (n < 1 || !ids || !params || !sim_ids) return fail(ctx, C2F_EINVAL, "bad batch arguments");
@@ -772,39 +782,110 @@ int simulate_many(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_sim_par
   const bool graph = n > 1 && !ctx->profiling;
   std::vector<Landscape *> builds;
   std::vector<std::shared_ptr<Sim>> sims;
-  if ((rc = make_sims(ctx, n, ids, params, sims, graph ? &builds : nullptr))) return rc;
-  std::vector<Sim *> raw;
-  for (auto &s : sims) raw.push_back(s.get());
+  if ((rc = make_sims(ctx, n, ids, params, sims, &builds))) return rc;
   for (auto &s : sims)   // tables built earlier, possibly on another stream
     if (std::find(builds.begin(), builds.end(), s->land.get()) == builds.end())
       CK(cudaStreamWaitEvent(ctx->stream, s->table->ready, 0));
   for (auto &s : sims)
     if ((rc = alloc_sim(ctx, *s, ctx->stream))) return rc;
-  FrontierPlan F;
-  if ((rc = plan_frontier(ctx, raw, F, ctx->scratch, ctx->stream))) return rc;
-  // a batch's launches (table builds, ignitions, the frontier) go out as one
-  // CUDA graph; a single simulation is launched directly
+
+  // groups of landscapes to build, largest table first
+  auto cost = [](const Landscape *L) { return (double)L->n * (double)L->table->key.hours; };
+  std::stable_sort(builds.begin(), builds.end(),
+                   [&](const Landscape *a, const Landscape *b) { return cost(a) > cost(b); });
+  const int G = (int)std::min<size_t>(4, std::max<size_t>(1, builds.size()));
+  std::vector<int> group_of_build(builds.size(), 0);
+  {
+    double total = 0.0, acc = 0.0;
+    for (Landscape *L : builds) total += cost(L);
+    for (size_t i = 0; i < builds.size(); ++i) {
+      group_of_build[i] = std::min(G - 1, (int)(acc * G / std::max(total, 1.0)));
+      acc += cost(builds[i]);
+    }
+  }
+  std::vector<std::vector<Sim *>> gsims(G);
+  for (auto &s : sims) {
+    int g = 0;   // simulations on landscapes with a table already run in the first group
+    for (size_t i = 0; i < builds.size(); ++i)
+      if (builds[i] == s->land.get()) g = group_of_build[i];
+    gsims[g].push_back(s.get());
+  }
+  std::vector<FrontierPlan> F(G);
+  std::vector<Scratch> extra(G > 1 ? G : 0);
+  auto scratch_of = [&](int g) -> Scratch & { return G > 1 ? extra[g] : ctx->scratch; };
+  for (int g = 0; g < G; ++g)
+    if (!gsims[g].empty() && (rc = plan_frontier(ctx, gsims[g], F[g], scratch_of(g), ctx->stream))) return rc;
+
+  std::vector<cudaStream_t> gst(G, ctx->stream);
+  std::vector<cudaEvent_t> ev;   // fork and join events
+  auto cleanup = [&]() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (int g = 1; g < G; ++g)
+      if (gst[g] != ctx->stream) ctx->stream_pool.push_back(gst[g]);
+  };
+  for (int g = 1; g < G; ++g) {
+    gst[g] = take_stream(ctx);
+    if (!gst[g]) { gst[g] = ctx->stream; cleanup(); return fail(ctx, C2F_ECUDA, "cannot create a stream"); }
+  }
+  auto new_event = [&](cudaEvent_t *e) {
+    const cudaError_t r = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+    if (r == cudaSuccess) ev.push_back(*e);
+    return r;
+  };
+  // issue: builds of group g, then (fork) group g's frontier on its stream; join at the end
+  auto issue = [&]() -> int {
+    int lrc = C2F_OK;
+    size_t b = 0;
+    std::vector<cudaEvent_t> done;
+    for (int g = 0; g < G && !lrc; ++g) {
+      for (; b < builds.size() && group_of_build[b] == g && !lrc; ++b)
+        lrc = launch_table(ctx, *builds[b], ctx->stream, ctx->eager_tables);
+      if (lrc || gsims[g].empty()) continue;
+      if (gst[g] != ctx->stream) {
+        cudaEvent_t fork;
+        cudaError_t e = new_event(&fork);
+        if (e == cudaSuccess) e = cudaEventRecord(fork, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(gst[g], fork, 0);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "fork");
+      }
+      lrc = launch_frontier(ctx, F[g], scratch_of(g), gst[g]);
+      if (!lrc && gst[g] != ctx->stream) {
+        cudaEvent_t join;
+        cudaError_t e = new_event(&join);
+        if (e == cudaSuccess) e = cudaEventRecord(join, gst[g]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "join");
+        done.push_back(join);
+      }
+    }
+    for (cudaEvent_t j : done) {
+      const cudaError_t e = cudaStreamWaitEvent(ctx->stream, j, 0);
+      if (e != cudaSuccess && !lrc) lrc = cuda_fail(ctx, e, "join");
+    }
+    return lrc;
+  };
   if (graph) {
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    int lrc = C2F_OK;
-    for (Landscape *L : builds) if (!lrc) lrc = launch_table(ctx, *L, ctx->stream, ctx->eager_tables);
-    if (!lrc) lrc = launch_frontier(ctx, F, ctx->scratch, ctx->stream);
-    cudaGraph_t g = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
-    if (lrc) { if (g) cudaGraphDestroy(g); return lrc; }
-    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+    const int lrc = issue();
+    cudaGraph_t gr = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &gr);
+    if (lrc) { if (gr) cudaGraphDestroy(gr); cleanup(); return lrc; }
+    if (ce != cudaSuccess) { cleanup(); return cuda_fail(ctx, ce, "cudaStreamEndCapture"); }
     cudaGraphExec_t ge = nullptr;
-    const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
-    cudaGraphDestroy(g);
-    if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+    const cudaError_t ie = cudaGraphInstantiate(&ge, gr, 0);
+    cudaGraphDestroy(gr);
+    if (ie != cudaSuccess) { cleanup(); return cuda_fail(ctx, ie, "cudaGraphInstantiate"); }
     const cudaError_t le = cudaGraphLaunch(ge, ctx->stream);
     cudaGraphExecDestroy(ge);
-    if (le != cudaSuccess) return cuda_fail(ctx, le, "cudaGraphLaunch");
+    if (le != cudaSuccess) { cleanup(); return cuda_fail(ctx, le, "cudaGraphLaunch"); }
     ++ctx->graph_launches;
   } else {
-    if ((rc = launch_frontier(ctx, F, ctx->scratch, ctx->stream))) return rc;
+    if ((rc = issue())) { cudaStreamSynchronize(ctx->stream); cleanup(); return rc; }
   }
-  if ((rc = finish_frontier(ctx, F, ctx->scratch, ctx->stream))) return rc;
+  for (int g = 0; g < G && !rc; ++g)
+    if (!gsims[g].empty()) rc = finish_frontier(ctx, F[g], scratch_of(g), ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  cleanup();
+  if (rc) return rc;
   for (auto &s : sims) s->state = S_DONE;
   register_sims(ctx, sims, sim_ids);
   return C2F_OK;

@@ -28,6 +28,7 @@
 
 namespace c2f {
 __global__ void k_frontier_g1(FrontierArgs);
+cudaError_t init_device_constants(int device);
 }
 using namespace c2f;
 
@@ -108,6 +109,7 @@ extern "C" C2F_API int c2f_frontier_static(const c2f_frontier_io *io, const c2f_
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return C2F_ECUDA; }
+  if (init_device_constants(dev) != cudaSuccess) { cudaGetLastError(); return C2F_ECUDA; }   // noise tables
   DeviceScratch &ds = g_scratch_of_device[dev];
   std::call_once(ds.once, [&] {
     void *ptr = nullptr;
