@@ -225,6 +225,12 @@ C2F_API int c2f_burn_prob_device(c2f_ctx *ctx, int32_t sim_id, uint32_t *counts_
  * ignition steps ign_step[r*N + c] (-1 = never).  Either pointer may be NULL. */
 C2F_API int c2f_get_scars(c2f_ctx *ctx, int32_t sim_id, uint8_t *scars, int32_t *ign_step);
 
+/* One replica's burn grid (N bytes, 1 = ignited) and, if kept, its ignition
+ * steps (N int32, -1 = never; NULL to skip).  replica outside [0, n_replicas)
+ * is C2F_EINVAL. */
+C2F_API int c2f_get_replica_scar(c2f_ctx *ctx, int32_t sim_id, int32_t replica, uint8_t *scar,
+                                 int32_t *ign_step);
+
 /* The same burn grids bit-packed, as kept on the device: for replica r, row y
  * and word x (x < wpr = ceil(cols/32)), words[(r*rows + y)*wpr + x] holds
  * cells (y, 32x .. 32x+31), bit b = column 32x+b; padding bits are 0

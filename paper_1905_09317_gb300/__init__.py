@@ -108,6 +108,7 @@ _SIGS = [
     ("c2f_burn_prob", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_burn_prob_device", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_get_scars", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    ("c2f_get_replica_scar", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     ("c2f_get_scar_bits", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_get_scars_at_hour", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     ("c2f_get_counters", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -290,6 +291,12 @@ class Context:
         ign = np.empty((n_replicas, n_cells), dtype=np.int32) if ign_steps else None
         self._check(self.lib.c2f_get_scars(self.h, int(sim_id), _ptr(scars), _ptr(ign)))
         return scars, ign
+
+    def get_replica_scar(self, sim_id: int, replica: int, n_cells: int, ign_steps=False):
+        scar = np.empty(n_cells, dtype=np.uint8)
+        ign = np.empty(n_cells, dtype=np.int32) if ign_steps else None
+        self._check(self.lib.c2f_get_replica_scar(self.h, int(sim_id), int(replica), _ptr(scar), _ptr(ign)))
+        return scar, ign
 
     def get_scar_bits(self, sim_id: int, n_replicas: int, rows: int, cols: int) -> np.ndarray:
         """(n_replicas, rows, ceil(cols/32)) uint32 words; bit b of word x = column 32x+b."""

@@ -1429,6 +1429,34 @@ C2F_API int c2f_get_scars(c2f_ctx *ctx, int32_t sim_id, uint8_t *scars, int32_t 
   return C2F_OK;
 }
 
+C2F_API int c2f_get_replica_scar(c2f_ctx *ctx, int32_t sim_id, int32_t replica, uint8_t *scar,
+                                 int32_t *ign_step) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  auto s = find_sim(ctx, sim_id);
+  if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  if (!scar) return fail(ctx, C2F_EINVAL, "scar is NULL");
+  int rc = sim_ready(ctx, *s);
+  if (rc) return rc;
+  if (replica < 0 || replica >= s->p.n_replicas) return fail(ctx, C2F_EINVAL, "replica out of range");
+  if (ign_step && !s->ign_step.p)
+    return fail(ctx, C2F_EINVAL, "simulation did not keep ignition steps (C2F_OUT_IGN_STEPS)");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->read_stream;
+  const size_t pw = (size_t)s->rows * s->wpr;
+  DevBuf tmp;
+  if ((rc = dalloc_on(ctx, tmp, (size_t)s->n, st))) return rc;
+  k_scar_bytes<<<grid1(s->n, 256), 256, 0, st>>>(s->ign_plane.as<uint32_t>() + (size_t)replica * pw, 1,
+                                                 s->rows, s->cols, s->wpr, tmp.as<uint8_t>());
+  CKL("k_scar_bytes");
+  CK(cudaMemcpyAsync(scar, tmp.p, (size_t)s->n, cudaMemcpyDeviceToHost, st));
+  if (ign_step)
+    CK(cudaMemcpyAsync(ign_step, s->ign_step.as<int32_t>() + (size_t)replica * s->n, (size_t)s->n * 4,
+                       cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return C2F_OK;
+}
+
 C2F_API int c2f_get_scar_bits(c2f_ctx *ctx, int32_t sim_id, uint32_t *words) {
   if (!ctx) return C2F_EINVAL;
   LOCK;
