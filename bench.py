@@ -214,23 +214,27 @@ def run_ours(args, rank, world, local_rank):
     # Pipelined steps: each step's table is built (K1, context stream) while the
     # previous step's frontier runs (its own stream, submitted asynchronously);
     # the work of a step is the same as in the serial form.
-    ctx.set_serving(max_inflight=2, max_epoch_replicas=R, hbm_reserve_bytes=0)
+    depth = max(2, args.depth)                  # steps in flight
+    ctx.set_serving(max_inflight=depth, max_epoch_replicas=R, hbm_reserve_bytes=0)
 
     def run_steps(k):
         if args.serial:
             return [step() for _ in range(k)]
-        done, prev = [], None
+        done, inflight = [], []
+
+        def retire():
+            sid = inflight.pop(0)
+            ctx.wait(sid)
+            ctx.burn_prob_device(sid, counts_dev.data_ptr())    # a9 (K4)
+            done.append(sid)
+
         for _ in range(k):
             ctx.build_ros(lid, params, force=table_mode)        # a1 + a2 (K1)
-            sid = ctx.submit(lid, params)                       # a3..a8 (K2, K3), asynchronous
-            if prev is not None:
-                ctx.wait(prev)
-                ctx.burn_prob_device(prev, counts_dev.data_ptr())   # a9 (K4)
-                done.append(prev)
-            prev = sid
-        ctx.wait(prev)
-        ctx.burn_prob_device(prev, counts_dev.data_ptr())
-        done.append(prev)
+            inflight.append(ctx.submit(lid, params))            # a3..a8 (K2, K3), asynchronous
+            if len(inflight) >= depth:
+                retire()
+        while inflight:
+            retire()
         return done
 
     # warm-up (also fixes the deterministic work count of the step)
@@ -312,7 +316,8 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs larger than L2 (ROS table 453 MB rebuilt every step)",
                        "parallelism": f"replica-sharded x{world}",
                        "schedule": "serial" if args.serial else
-                       "pipelined: step i+1's table (K1) overlaps step i's frontier (K3)",
+                       f"pipelined, {max(2, args.depth)} steps in flight: the next steps' tables (K1) "
+                       "overlap the current frontier (K3)",
                        "tables": "on demand in K3" if args.lazy_tables else "K1, every row"},
             "replicas_per_s": R * world * args.steps / (ms_max / 1e3),
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in fam.items()},
@@ -633,6 +638,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lazy-tables", action="store_true",
                     help="ROS-table rows computed on demand inside the frontier instead of by K1")
+    ap.add_argument("--depth", type=int, default=3, help="pipelined steps in flight (>= 2)")
     ap.add_argument("--serial", action="store_true",
                     help="one synchronous step at a time (no overlap of K1 with the previous frontier)")
     ap.add_argument("--workload", default="landscape", choices=["landscape", "batch", "serve", "large"])

@@ -819,12 +819,12 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
               const int q = __ffs(todo) - 1;
               todo &= todo - 1;
               const int32_t nr = cr + kDR[q], nc = cc + kDC[q];
-              if (pl.avail(nr, nc)) {                                      // Available
-                jc = (int64_t)nr * cols + nc;
-                if (gate_free || receive_ok(J, r, jc, h, n)) {             // else consumed
-                  won = pl.take(nr, nc);
-                  wrc = rc_pack(nr, nc);
-                }
+              jc = (int64_t)nr * cols + nc;
+              wrc = rc_pack(nr, nc);
+              if (gate_free) {
+                won = pl.take(nr, nc);   // taken iff it was Available; one atomic decides
+              } else if (pl.avail(nr, nc) && receive_ok(J, r, jc, h, n)) {   // else consumed
+                won = pl.take(nr, nc);
               }
             }
             const uint32_t wins = __ballot_sync(FULL, won);
@@ -876,20 +876,18 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           const bool ingrid = act && nr >= 0 && nr < rows && nc >= 0 && nc < cols;
           const int64_t bk = act ? __ldcg(baseh + cell * 8 + k) : 0;   // issue the table load early
           const bool open = ingrid && pl.avail(nr, nc);
+          // the perturbation does not depend on the loads above: computed while they are in flight
+          const float f = act ? noise_factor(seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, sigma) : 1.0f;
           const bool ignq = ingrid && !open;   // ignited, or never burnable (pre-marked Burned)
           const uint32_t omask = group_bits(open);
           uint32_t mask = omask;
-          float f = 1.0f;
-          bool have_f = false, dies = false;
+          bool dies = false;
           if (act && delta > 0.0) {
-            f = noise_factor(seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, sigma);
-            have_f = true;
             if (__dmul_rn(__ldcg(hrosh + cell), (double)f) < delta) { dies = true; mask = 0; }   // A5 (i)
           }
           uint32_t cof = kNone;
           int64_t P = 0;
           if (act && mask != 0 && s < L) {
-            if (!have_f) f = noise_factor(seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, sigma);
             if ((mask >> k) & 1u) {
               const int32_t nmax = L - s;
               const int64_t inc = apply_noise(bk, noise_fixed(f), dk);
