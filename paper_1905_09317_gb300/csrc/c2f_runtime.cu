@@ -187,6 +187,7 @@ struct c2f_ctx {
   int device = 0;
   bool has_hooks = false;
   c2f_alloc_hooks hooks{};
+  cudaMemPool_t pool = nullptr;   // the context's stream-ordered pool; keeps freed memory
   int sm_count = 0;
   int smem_optin = 0, smem_per_sm = 0;
   cudaStream_t own_stream = nullptr;
@@ -260,10 +261,10 @@ int dalloc_on(c2f_ctx *ctx, DevBuf &b, size_t bytes, cudaStream_t st) {
     b.p = b.hooks->alloc(bytes, st, b.hooks->user);
     if (!b.p) return fail(ctx, C2F_ENOMEM, "allocation hook returned no memory for %zu bytes", bytes);
   } else {
-    cudaError_t e = cudaMallocAsync(&b.p, bytes, st);
+    cudaError_t e = cudaMallocFromPoolAsync(&b.p, bytes, ctx->pool, st);
     if (e != cudaSuccess) {
       b.p = nullptr;
-      return cuda_fail(ctx, e, "cudaMallocAsync");
+      return cuda_fail(ctx, e, "cudaMallocFromPoolAsync");
     }
   }
   b.bytes = bytes;
@@ -1050,6 +1051,17 @@ C2F_API int c2f_create_with_hooks(c2f_ctx **out, int device, const c2f_alloc_hoo
   CK(cudaDeviceGetAttribute(&ctx->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
   CK(cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking));
   ctx->stream = ctx->own_stream;
+  if (!ctx->has_hooks) {
+    // a pool of the context's own that keeps what it frees (tables of tens of
+    // GB are freed and allocated again step after step); returned at c2f_destroy
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    CK(cudaMemPoolCreate(&ctx->pool, &props));
+    uint64_t keep = UINT64_MAX;
+    CK(cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  }
   CK(cudaStreamCreateWithFlags(&ctx->read_stream, cudaStreamNonBlocking));
   int rc = ensure_device_constants(ctx);
   if (rc) return rc;
@@ -1081,6 +1093,8 @@ C2F_API void c2f_destroy(c2f_ctx *ctx) {
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     for (cudaStream_t s : ctx->stream_pool) cudaStreamDestroy(s);
     if (ctx->read_stream) cudaStreamDestroy(ctx->read_stream);
+    cudaDeviceSynchronize();
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   }
   delete ctx;
