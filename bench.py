@@ -261,11 +261,17 @@ def run_ours(args, rank, world, local_rank):
         barrier()
     ms = ev0.elapsed_time(ev1)
     kt = ctx.kernel_times()
-    ctx.profile(False)
     last_work, _, _ = ctx.get_counters(sids[-1], R)
     assert int(last_work.sum()) == work_per_step, "work count changed between steps"
     for s in sids:
         ctx.release(s)
+    kt_alone = None
+    if not args.serial:   # a few steps one at a time (outside the timing): each kernel alone
+        ctx.kernel_times()
+        for _ in range(3):
+            ctx.release(step())
+        kt_alone = ctx.kernel_times()
+    ctx.profile(False)
 
     ms_max = max_over_ranks(ms, world, dev)
 
@@ -317,7 +323,13 @@ def run_ours(args, rank, world, local_rank):
         fam = {k: v for k, v in kt.items()}
         dom = max(fam, key=lambda k: fam[k][0])
         roof = roofline(dom, fam, w, work_per_step, peaks)
-        launches = int(sum(v[1] for v in fam.values())) + 1 * args.steps   # + hour prep per K1
+        if roof is not None and kt_alone is not None and dom in kt_alone:
+            alone = roofline(dom, kt_alone, w, work_per_step, peaks)
+            if alone is not None:   # the same kernel when a step runs by itself
+                roof["alone"] = {"achieved": alone["achieved"], "frac": alone["frac"],
+                                 "ms_per_launch": kt_alone[dom][0] / max(kt_alone[dom][1], 1)}
+            roof["ms_per_launch"] = fam[dom][0] / max(fam[dom][1], 1)
+        launches = int(sum(v[1] for v in fam.values()))   # every kernel of the timed steps
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             procs = os.cpu_count() or 1
@@ -361,7 +373,7 @@ def roofline(dom, fam, w, work_per_step, peaks):
     hbm = peaks.get("hbm_gbs", 6800.0)
     per_launch_s = ms / launches / 1e3
     if dom == "ros_table":
-        # FP64-ALU bound: binary64 operations per cell-hour
+        # FP64-ALU bound: binary64 flops per cell-hour, counted by ncu on this kernel
         flops = FP64_OPS_PER_CELL_HOUR * n * H
         peak = FP64_PEAK_GFLOPS
         ach = flops / per_launch_s / 1e9
@@ -384,7 +396,11 @@ def roofline(dom, fam, w, work_per_step, peaks):
             "frac": ach / hbm, "traffic": None}
 
 
-# algorithmic figures (the design doc states how they are derived)
+# Algorithmic figures.  Frontier: bytes per cell-update of the period-by-period
+# method (8 x 8 B progress read and written, 8 x 8 B rates read, ~2 B of
+# neighbour state).  ROS table: binary64 flops per cell-hour (2 x DFMA + DMUL +
+# DADD from ncu's instruction counts over cells x hours).  FP64 peak: 152 SMs x 2
+# DFMA per clock x 2 flop x 2.07 GHz.
 FRONTIER_BYTES_PER_UPDATE = 194.0
 FRONTIER_DRAM_BYTES_PER_REPLICA = 93.85e6 / 200   # ncu, 512^2 x 24 h, 200 replicas
 FP64_OPS_PER_CELL_HOUR = 488.0      # ncu: (2 x DFMA + DMUL + DADD) / (cells x hours)

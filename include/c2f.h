@@ -258,8 +258,12 @@ C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap);
 /* Frontier-kernel launch shape: CTA size `threads` (32, 64 or 128; each warp
  * simulates one replica) and whether a window of each replica's bit planes
  * and its burning list are staged in shared memory (`smem` != 0, the default)
- * or kept in global memory (0).  Results do not depend on either; they are
- * tuning knobs. */
+ * or kept in global memory (0).  With shared memory, smem = 1 sizes each
+ * warp's share so that the launch's own replicas are resident at once (up to
+ * 8 warps per SM); smem = N in [2, 16] sizes it for N warps per SM, leaving
+ * room for frontier launches that run at the same time (serving epochs,
+ * pipelined steps).  Results do not depend on any of this; they are tuning
+ * knobs.  smem outside [0, 16] is C2F_EINVAL. */
 C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem);
 
 /* Launch-shape autotuner for a batch: runs the same mix of simulations,

@@ -59,8 +59,14 @@ cudaError_t init_device_constants(int device) {
   return err[device];
 }
 
-__device__ __constant__ int kDR[8] = {0, -1, -1, -1, 0, 1, 1, 1};
-__device__ __constant__ int kDC[8] = {1, 1, 0, -1, -1, -1, 0, 1};
+// axis k = 0..7 at 45 k degrees counter-clockwise from east: (row, col) offsets
+// E (0,+1), NE (-1,+1), N (-1,0), NW (-1,-1), W (0,-1), SW (+1,-1), S (+1,0),
+// SE (+1,+1), packed two bits per axis (offset + 1) so that lanes with
+// different axes read them from a register, not from divergent memory
+constexpr uint32_t kDRPack = 0xa901u;   // 1,0,0,0,1,2,2,2
+constexpr uint32_t kDCPack = 0x901au;   // 2,2,1,0,0,0,1,2
+__device__ __forceinline__ int axis_dr(int k) { return (int)((kDRPack >> (2 * k)) & 3u) - 1; }
+__device__ __forceinline__ int axis_dc(int k) { return (int)((kDCPack >> (2 * k)) & 3u) - 1; }
 
 // ------------------------------------------------------------------ set-up
 // burnable plane (bit per cell, rows padded to 32-bit words) and per-word counts
@@ -285,7 +291,7 @@ __device__ __forceinline__ int64_t axis_len(const SimJob &J, int k) {
 
 // smallest n >= 1 with n * inc >= rem, given that it is at most a few dozen
 __device__ __forceinline__ int32_t ceil_div_small(int64_t rem, int64_t inc) {
-  const float q = __fdiv_rn((float)rem, (float)inc);
+  const float q = __fdividef((float)rem, (float)inc);   // a first guess; the loops make n exact
   int32_t n = (q < 4096.0f) ? (int32_t)ceilf(q) : 4096;
   if (n < 1) n = 1;
   while ((int64_t)n * inc < rem) ++n;
@@ -568,7 +574,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       __syncwarp();
       bool open = false;
       if (lane < 8) {
-        const int32_t nr = ir + kDR[k], nc = icc + kDC[k];
+        const int32_t nr = ir + axis_dr(k), nc = icc + axis_dc(k);
         open = nr >= 0 && nr < rows && nc >= 0 && nc < cols && pl.avail(nr, nc);
       }
       const uint32_t mask0 = __ballot_sync(FULL, open) & 0xFFu;
@@ -599,7 +605,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         int32_t wr = -1, wc = 0;
         if ((slots >> q) & 1u) {
           int32_t nr = cr, nc = cc;
-          if (q > 0) { nr += kDR[q - 1]; nc += kDC[q - 1]; }
+          if (q > 0) { nr += axis_dr(q - 1); nc += axis_dc(q - 1); }
           if (nr >= 0 && nr < rows && nc >= 0 && nc < cols) { wr = nr; wc = nc >> 5; }
         }
         const int32_t w = wr * wpr + wc;
@@ -729,7 +735,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         for (int u = 0; u < 4; ++u) {
           const int32_t cr = (int32_t)(rcu[u] >> 16), cc = (int32_t)(rcu[u] & 0xFFFFu);
           bool open = actu[u] && ((mu[u] >> k) & 1u);
-          if (open) open = pl.avail(cr + kDR[k], cc + kDC[k]);
+          if (open) open = pl.avail(cr + axis_dr(k), cc + axis_dc(k));
           openu[u] = open;
           bku[u] = open ? __ldcg(baseh + ((int64_t)cr * cols + cc) * 8 + k) : 0;
         }
@@ -818,7 +824,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
             if (todo) {
               const int q = __ffs(todo) - 1;
               todo &= todo - 1;
-              const int32_t nr = cr + kDR[q], nc = cc + kDC[q];
+              const int32_t nr = cr + axis_dr(q), nc = cc + axis_dc(q);
               jc = (int64_t)nr * cols + nc;
               wrc = rc_pack(nr, nc);
               if (gate_free) {
@@ -872,7 +878,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           const uint32_t rc = act ? erc[e] : 0u;
           const int32_t cr = (int32_t)(rc >> 16), cc = (int32_t)(rc & 0xFFFFu);
           const int64_t cell = (int64_t)cr * cols + cc;
-          const int32_t nr = cr + kDR[k], nc = cc + kDC[k];
+          const int32_t nr = cr + axis_dr(k), nc = cc + axis_dc(k);
           const bool ingrid = act && nr >= 0 && nr < rows && nc >= 0 && nc < cols;
           const int64_t bk = act ? __ldcg(baseh + cell * 8 + k) : 0;   // issue the table load early
           const bool open = ingrid && pl.avail(nr, nc);

@@ -202,6 +202,7 @@ struct c2f_ctx {
   // launch shape
   int frontier_threads = 32;
   bool window_smem = true;
+  int warps_per_sm = 0;        // shared-memory sizing target; 0: this launch's own replicas
   bool eager_tables = true;   // simulations build their tables with K1 up front
   int64_t cap_override = 0;
   int64_t graph_launches = 0;
@@ -568,7 +569,9 @@ int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, i
   int64_t win_cap = cap;
   {
     const int64_t want = std::max<int64_t>(1, (todo + ctx->sm_count - 1) / ctx->sm_count);
-    const int64_t warps_per_sm = attempt == 0 ? std::min<int64_t>(want, 8) : std::min<int64_t>(want, 2);
+    const int64_t warps_per_sm =
+        attempt == 0 ? (ctx->warps_per_sm > 0 ? (int64_t)ctx->warps_per_sm : std::min<int64_t>(want, 8))
+                     : std::min<int64_t>(want, 2);
     // per CTA: 1 KB reserved by the system and about 1 KB of static shared memory per warp
     const int64_t per_warp = ((int64_t)ctx->smem_per_sm - (1024 * warps_per_sm) / wpc - 1024 * warps_per_sm) /
                              warps_per_sm;
@@ -581,7 +584,7 @@ int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, i
   // shared-memory lists only when they hold at least half the default capacity:
   // smaller ones overflow on large fires and those replicas run twice
   const bool use_win = ctx->window_smem && win_words * 4 * wpc <= budget &&
-                       (attempt == 0 ? 2 * win_cap >= cap : win_cap >= cap);
+                       (attempt == 0 ? (ctx->warps_per_sm > 0 || 2 * win_cap >= cap) : win_cap >= cap);
   if (use_win) cap = win_cap;
   const int64_t warp_words = use_win ? win_words : 0;
   F.kern = use_win ? (wpc == 1 ? k_frontier_w1 : wpc == 2 ? k_frontier_w2 : k_frontier_w4)
@@ -1541,9 +1544,10 @@ C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem) {
   LOCK;
   if (threads != 32 && threads != 64 && threads != 128)
     return fail(ctx, C2F_EINVAL, "threads must be 32, 64 or 128 (one replica per warp)");
-  if (smem < 0) return fail(ctx, C2F_EINVAL, "smem must be >= 0");
+  if (smem < 0 || smem > 16) return fail(ctx, C2F_EINVAL, "smem must lie in [0, 16]");
   ctx->frontier_threads = threads;
   ctx->window_smem = smem != 0;
+  ctx->warps_per_sm = smem >= 2 ? (int)smem : 0;
   return C2F_OK;
 }
 
