@@ -60,13 +60,11 @@ cudaError_t init_device_constants(int device) {
 }
 
 // axis k = 0..7 at 45 k degrees counter-clockwise from east: (row, col) offsets
-// E (0,+1), NE (-1,+1), N (-1,0), NW (-1,-1), W (0,-1), SW (+1,-1), S (+1,0),
-// SE (+1,+1), packed two bits per axis (offset + 1) so that lanes with
-// different axes read them from a register, not from divergent memory
-constexpr uint32_t kDRPack = 0xa901u;   // 1,0,0,0,1,2,2,2
-constexpr uint32_t kDCPack = 0x901au;   // 2,2,1,0,0,0,1,2
-__device__ __forceinline__ int axis_dr(int k) { return (int)((kDRPack >> (2 * k)) & 3u) - 1; }
-__device__ __forceinline__ int axis_dc(int k) { return (int)((kDCPack >> (2 * k)) & 3u) - 1; }
+// E (0,+1), NE (-1,+1), N (-1,0), NW (-1,-1), W (0,-1), SW (+1,-1), S (+1,0), SE (+1,+1)
+__device__ __constant__ int kDR[8] = {0, -1, -1, -1, 0, 1, 1, 1};
+__device__ __constant__ int kDC[8] = {1, 1, 0, -1, -1, -1, 0, 1};
+__device__ __forceinline__ int axis_dr(int k) { return kDR[k]; }
+__device__ __forceinline__ int axis_dc(int k) { return kDC[k]; }
 
 // ------------------------------------------------------------------ set-up
 // burnable plane (bit per cell, rows padded to 32-bit words) and per-word counts
