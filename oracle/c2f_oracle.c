@@ -54,10 +54,10 @@
  *    exp: x = (64 k + j) ln2/64 + r, |r| <= ln2/128:
  *         exp x = 2^k T_j (1 + p(r)), T_j = 2^(j/64) (exp_series), p the
  *         Taylor polynomial of exp(r) - 1 to r^5.
- *    log: x = 2^e m, m in [1, 2), j = first 7 fraction bits of m,
- *         V_j = RN(1 / (1 + j/128)), r = m V_j - 1 (one fused rounding):
+ *    log: x = 2^e m, m in [1, 2), j = first 8 fraction bits of m,
+ *         V_j = RN(1 / (1 + j/256)), r = m V_j - 1 (one fused rounding):
  *         log x = e ln2 - log V_j + log(1 + r), log V_j by log_series,
- *         log(1 + r) by its Taylor polynomial to r^8 (|r| < 1/128).
+ *         log(1 + r) by its Taylor polynomial to r^6 (|r| < 1/256).
  *    sincos in degrees: quadrant reduction by exact subtraction of a
  *         multiple of 90, Taylor series of sin (to t^17) and cos (to t^18).
  *    pow(x,y), x > 0: for y a positive multiple of 1/2 up to 8,
@@ -78,9 +78,9 @@ static double g_log_c[12];     /* 1/(2n+1)        */
 static double g_sin_c[10];     /* (-1)^n/(2n+1)!  */
 static double g_cos_c[10];     /* (-1)^n/(2n)!    */
 static double g_exp_tab[64];   /* 2^(j/64)               */
-static double g_log_inv[128];  /* RN(1 / (1 + j/128))    */
-static double g_log_tab[128];  /* -log(g_log_inv[j])     */
-static double g_log_c3, g_log_c4, g_log_c5, g_log_c6, g_log_c7, g_log_c8;   /* 1/n */
+static double g_log_inv[256];  /* RN(1 / (1 + j/256))    */
+static double g_log_tab[256];  /* -log(g_log_inv[j])     */
+static double g_log_c3, g_log_c4, g_log_c5, g_log_c6;   /* 1/n */
 static float g_inv_fact_f[12];
 static float g_log_cf[8];
 static float g_sin_cf[8];
@@ -112,7 +112,7 @@ static void or_init_tables(void) {
     g_cos_cf[n] = (float)g_cos_c[n];
   }
   g_log_c3 = 1.0 / 3.0; g_log_c4 = 1.0 / 4.0; g_log_c5 = 1.0 / 5.0;
-  g_log_c6 = 1.0 / 6.0; g_log_c7 = 1.0 / 7.0; g_log_c8 = 1.0 / 8.0;
+  g_log_c6 = 1.0 / 6.0;
   g_init = 1;
   fill_fn_tables();
 }
@@ -168,8 +168,8 @@ static double log_series(double x) {
 
 static void fill_fn_tables(void) {
   for (int j = 0; j < 64; ++j) g_exp_tab[j] = exp_series((double)j * (LN2_HI / 64.0) + (double)j * (LN2_LO / 64.0));
-  for (int j = 0; j < 128; ++j) {
-    g_log_inv[j] = 1.0 / (1.0 + (double)j / 128.0);
+  for (int j = 0; j < 256; ++j) {
+    g_log_inv[j] = 1.0 / (1.0 + (double)j / 256.0);
     g_log_tab[j] = -log_series(g_log_inv[j]);
   }
 }
@@ -200,15 +200,13 @@ OR_API double or_log(double x) {
   uint64_t b;
   memcpy(&b, &x, 8);
   e += (int)((b >> 52) & 0x7ff) - 1023;
-  int j = (int)((b >> 45) & 127);
+  int j = (int)((b >> 44) & 255);
   b = (b & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL;
   double m;
   memcpy(&m, &b, 8);
   double r = fma(m, g_log_inv[j], -1.0);
-  /* log(1 + r) = r - r^2/2 + r^3/3 - ... - r^8/8 */
-  double q = -g_log_c8;
-  q = fma(q, r, g_log_c7);
-  q = fma(q, r, -g_log_c6);
+  /* log(1 + r) = r - r^2/2 + r^3/3 - ... - r^6/6 */
+  double q = -g_log_c6;
   q = fma(q, r, g_log_c5);
   q = fma(q, r, -g_log_c4);
   q = fma(q, r, g_log_c3);
@@ -446,12 +444,14 @@ static double rsi_fuel(int fuel, double isi, double pcf, double cf) {
   }
 }
 
-/* inverse of RSI for one (a,b,c) curve scaled by mult: the ISI that gives rsf */
+/* inverse of RSI for one (a,b,c) curve scaled by mult: the ISI that gives rsf.
+ * The divisions by a*mult and by -b are multiplications by the rounded
+ * reciprocals (divisors fixed per fuel and hour). */
 static double isf_abc(const fbp_coef *k, double mult, double rsf) {
   if (!(rsf > 0.0)) return 0.0;
-  double x = 1.0 - or_pow(rsf / (k->a * mult), 1.0 / k->c);
+  double x = 1.0 - or_pow(rsf * (1.0 / (k->a * mult)), 1.0 / k->c);
   if (x < 0.01) x = 0.01;
-  return or_log(x) / (-k->b);
+  return or_log(x) * (-1.0 / k->b);
 }
 
 /* slope-equivalent ISI (ISF) at slope factor sf */
@@ -536,7 +536,7 @@ OR_API void or_fbp_cell(int fuel, double gs, double aspect_deg, double ws, doubl
     double sf = or_exp(3.533 * or_pow(g, 1.2));
     double isf = isf_fuel(fuel, isz, sf, pcf, cf);
     if (isf > 0.0) {
-      wse = or_log(isf / isz) / 0.05039;
+      wse = or_log(isf * (1.0 / isz)) * (1.0 / 0.05039);
       if (wse > 40.0) {
         if (isf < 0.999 * 2.496 * ff)
           wse = 28.0 - or_log(1.0 - isf / (2.496 * ff)) / 0.0818;
@@ -550,7 +550,11 @@ OR_API void or_fbp_cell(int fuel, double gs, double aspect_deg, double ws, doubl
   double wsy = ws * cos_w + wse * cos_s;
   double wsv = sqrt(wsx * wsx + wsy * wsy);
   double ux = 1.0, uy = 0.0;
-  if (wsv > 0.0) { ux = wsx / wsv; uy = wsy / wsv; }
+  if (wsv > 0.0) {
+    double iw = 1.0 / wsv;
+    ux = wsx * iw;
+    uy = wsy * iw;
+  }
   double isi = isz * wind_fn(wsv);
   double hros = rsi_fuel(fuel, isi, pcf, cf) * be;
   double bisi = isz * or_exp(-0.05039 * wsv);

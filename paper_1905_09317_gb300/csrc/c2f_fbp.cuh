@@ -50,7 +50,8 @@ inline void make_fuel_table(FuelCoef t[F_NCODES]) {
   };
   for (int i = 0; i < F_NCODES; ++i) {
     t[i] = v[i];
-    t[i].inv_c = v[i].c != 0.0 ? 1.0 / v[i].c : 0.0;   // the quotient isf_curve divides out
+    t[i].inv_c = v[i].c != 0.0 ? 1.0 / v[i].c : 0.0;          // divisors of isf_curve,
+    t[i].neg_inv_b = v[i].b != 0.0 ? -1.0 / v[i].b : 0.0;     // fixed per fuel
   }
 }
 
@@ -82,12 +83,13 @@ __device__ inline double rsi_of(int fuel, double isi, double pcf, double cf) {
 }
 
 // ISI at which the (a*mult, b, c) curve gives rsf; the 1 - (rsf/a)^(1/c) term is
-// held at >= 0.01
-__device__ inline double isf_curve(const FuelCoef &k, double mult, double rsf) {
+// held at >= 0.01.  inv_am = RN(1 / (a mult)); the divisions by a mult and by
+// -b are multiplications by rounded reciprocals.
+__device__ inline double isf_curve(const FuelCoef &k, double inv_am, double rsf) {
   if (!(rsf > 0.0)) return 0.0;
-  double x = __dsub_rn(1.0, dpow(__ddiv_rn(rsf, __dmul_rn(k.a, mult)), k.inv_c));
+  double x = __dsub_rn(1.0, dpow(__dmul_rn(rsf, inv_am), k.inv_c));
   if (x < 0.01) x = 0.01;
-  return __ddiv_rn(dlog(x), -k.b);
+  return __dmul_rn(dlog(x), k.neg_inv_b);
 }
 
 __device__ inline double isf_of(int fuel, const HourPrep &hp, double sf, double pcf) {
@@ -95,17 +97,17 @@ __device__ inline double isf_of(int fuel, const HourPrep &hp, double sf, double 
   if (fuel == F_M1) {
     const double rsf_c2 = __dmul_rn(hp.rszf[F_C2], sf);
     const double rsf_d1 = __dmul_rn(hp.rszf[F_D1], sf);
-    return __dadd_rn(__dmul_rn(pcf, isf_curve(g_fuel[F_C2], 1.0, rsf_c2)),
-                     __dmul_rn(__dsub_rn(1.0, pcf), isf_curve(g_fuel[F_D1], 1.0, rsf_d1)));
+    return __dadd_rn(__dmul_rn(pcf, isf_curve(g_fuel[F_C2], hp.inv_a[F_C2], rsf_c2)),
+                     __dmul_rn(__dsub_rn(1.0, pcf), isf_curve(g_fuel[F_D1], hp.inv_a[F_D1], rsf_d1)));
   }
   if (fuel == F_M2) {
     const double rsf_c2 = __dmul_rn(hp.rszf[F_C2], sf);
     const double rsf_d1 = __dmul_rn(__dmul_rn(0.2, hp.rszf[F_D1]), sf);
-    return __dadd_rn(__dmul_rn(pcf, isf_curve(g_fuel[F_C2], 1.0, rsf_c2)),
-                     __dmul_rn(__dsub_rn(1.0, pcf), isf_curve(g_fuel[F_D1], 0.2, rsf_d1)));
+    return __dadd_rn(__dmul_rn(pcf, isf_curve(g_fuel[F_C2], hp.inv_a[F_C2], rsf_c2)),
+                     __dmul_rn(__dsub_rn(1.0, pcf), isf_curve(g_fuel[F_D1], hp.inv_a_d1m2, rsf_d1)));
   }
   const double rsf = __dmul_rn(hp.rszf[fuel], sf);
-  return isf_curve(g_fuel[fuel], is_o1(fuel) ? cf : 1.0, rsf);
+  return isf_curve(g_fuel[fuel], hp.inv_a[fuel], rsf);
 }
 
 // wind function of the ISI; above 40 km/h the saturating branch of the 2009 update
@@ -139,7 +141,11 @@ __device__ inline void hour_prep(double ws, double wd_from, double ffmc, double 
       if (is_o1(f)) rz = __dmul_rn(rz, cf);
     }
     hp->rszf[f] = rz;
+    const double mult = is_o1(f) ? cf : 1.0;
+    hp->inv_a[f] = g_fuel[f].a != 0.0 ? __ddiv_rn(1.0, __dmul_rn(g_fuel[f].a, mult)) : 0.0;
   }
+  hp->inv_a_d1m2 = __ddiv_rn(1.0, __dmul_rn(g_fuel[F_D1].a, 0.2));
+  hp->inv_isz = __ddiv_rn(1.0, hp->isz);
   // A lower bound on every fuel's HROS this hour: the RSI curve grows with the
   // ISI and the ISI with the wind (wind_fn >= 1 for w >= 0), so RSI >= RSI at
   // zero wind (rszf); a C2/D1 mixture is at least 0.2 x its smaller part.
@@ -177,7 +183,7 @@ __device__ inline void fbp_row(int fuel, double gs, const CellPrep &cp, const Ho
   if (gs > 0.0) {
     const double isf = isf_of(fuel, hp, cp.sf, pcf);
     if (isf > 0.0) {
-      wse = __ddiv_rn(dlog(__ddiv_rn(isf, hp.isz)), 0.05039);
+      wse = __dmul_rn(dlog(__dmul_rn(isf, hp.inv_isz)), 1.0 / 0.05039);
       if (wse > 40.0) {
         if (isf < __dmul_rn(__dmul_rn(0.999, 2.496), hp.ff))
           wse = __dsub_rn(28.0, __ddiv_rn(dlog(__dsub_rn(1.0, __ddiv_rn(isf, __dmul_rn(2.496, hp.ff)))),
@@ -191,7 +197,11 @@ __device__ inline void fbp_row(int fuel, double gs, const CellPrep &cp, const Ho
   const double wsy = __dadd_rn(__dmul_rn(hp.ws, hp.cos_w), __dmul_rn(wse, cp.cos_s));
   const double wsv = __dsqrt_rn(__dadd_rn(__dmul_rn(wsx, wsx), __dmul_rn(wsy, wsy)));
   double ux = 1.0, uy = 0.0;
-  if (wsv > 0.0) { ux = __ddiv_rn(wsx, wsv); uy = __ddiv_rn(wsy, wsv); }
+  if (wsv > 0.0) {
+    const double iw = __ddiv_rn(1.0, wsv);
+    ux = __dmul_rn(wsx, iw);
+    uy = __dmul_rn(wsy, iw);
+  }
   const double isi = __dmul_rn(hp.isz, wind_fn(wsv));
   const double be = hp.be[fuel];
   const double hros = __dmul_rn(rsi_of(fuel, isi, pcf, cf), be);

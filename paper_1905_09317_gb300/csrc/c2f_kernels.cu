@@ -43,7 +43,7 @@ cudaError_t upload_constants() {
   cudaError_t e = cudaMemcpyToSymbol(g_mc, &mc, sizeof mc);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_fuel, ft, sizeof ft);
   if (e == cudaSuccess) {
-    k_math_tables<<<1, 128>>>();
+    k_math_tables<<<1, 256>>>();
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -22,13 +22,16 @@ enum FuelCode : int {
   F_O1A, F_O1B, F_S1, F_S2, F_S3, F_NCODES
 };
 
-struct FuelCoef { double a, b, c, q, bui0, inv_c; };   // inv_c = RN(1/c), 0 when c = 0
+struct FuelCoef { double a, b, c, q, bui0, inv_c, neg_inv_b; };   // RN(1/c), RN(-1/b); 0 when c / b = 0
 
 struct HourPrep {
   double ws, ff, isz, sin_w, cos_w;
   double cf;              // O1 curing factor
   double be[F_NCODES];    // build-up effect per fuel code
   double rszf[F_NCODES];  // RSI at zero wind and slope per code (O1 includes curing)
+  double inv_a[F_NCODES]; // RN(1 / (a mult)) of each code's own curve (mult = curing for O1, else 1)
+  double inv_a_d1m2;      // RN(1 / (a_D1 0.2)), the D1 part of M2
+  double inv_isz;         // RN(1 / ISZ)
   int32_t pos;            // 1: every fuel's HROS this hour is > 1e-200 (a lower bound says so)
 };
 

@@ -12,9 +12,9 @@
 //   table forms (Tang's method), used everywhere else:
 //     exp   x = (64k + j) ln2/64 + r: 2^k T_j (1 + p(r)), T_j = 2^(j/64),
 //           p = Taylor of exp(r) - 1 to r^5
-//     log   x = 2^e m, m in [1, 2), j = top 7 fraction bits, V_j = 1/(1 + j/128)
+//     log   x = 2^e m, m in [1, 2), j = top 8 fraction bits, V_j = 1/(1 + j/256)
 //           rounded, r = m V_j - 1 (one fused rounding):
-//           e ln2 - log V_j + (Taylor of log(1 + r) to r^8)
+//           e ln2 - log V_j + (Taylor of log(1 + r) to r^6)
 //   sin/cos of degrees: exact reduction by multiples of 90, Taylor to t^17/t^18
 //   pow(x, y) = x^n sqrt(x)^(2y odd) for y a positive multiple of 1/2 up to
 //               8 (n = floor y, products from the left), else exp(y log x)
@@ -34,8 +34,8 @@ __constant__ MathConstants g_mc;
 // exp / log tables (lanes index them independently, so global memory through
 // the read-only cache rather than __constant__), filled by k_math_tables
 __device__ double g_exp_tab[64];    // 2^(j/64)
-__device__ double g_log_inv[128];   // RN(1 / (1 + j/128))
-__device__ double g_log_tab[128];   // -log(g_log_inv[j])
+__device__ double g_log_inv[256];   // RN(1 / (1 + j/256))
+__device__ double g_log_tab[256];   // -log(g_log_inv[j])
 
 // host: compute the coefficient tables (plain IEEE binary64 arithmetic)
 inline void make_math_constants(MathConstants *m) {
@@ -149,14 +149,12 @@ __device__ inline double dlog(double x) {
   }
   unsigned long long b = (unsigned long long)__double_as_longlong(x);
   e += (int)((b >> 52) & 0x7ff) - 1023;
-  const int j = (int)((b >> 45) & 127);
+  const int j = (int)((b >> 44) & 255);
   b = (b & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL;
   const double m = __longlong_as_double((long long)b);
   const double r = __fma_rn(m, __ldg(&g_log_inv[j]), -1.0);
-  // log(1 + r) = r - r^2/2 + r^3/3 - ... - r^8/8
-  double q = -0.125;
-  q = __fma_rn(q, r, g_mc.log_c[3]);        // 1/7
-  q = __fma_rn(q, r, -g_mc.inv_fact[3]);    // -1/6
+  // log(1 + r) = r - r^2/2 + r^3/3 - ... - r^6/6
+  double q = -g_mc.inv_fact[3];             // -1/6
   q = __fma_rn(q, r, g_mc.log_c[2]);        // 1/5
   q = __fma_rn(q, r, -0.25);
   q = __fma_rn(q, r, g_mc.log_c[1]);        // 1/3
@@ -187,13 +185,13 @@ __device__ inline double dpow(double x, double y) {
   return __longlong_as_double(0x7ff8000000000000LL);
 }
 
-// fills g_exp_tab / g_log_inv / g_log_tab with the series forms (one block of 128)
+// fills g_exp_tab / g_log_inv / g_log_tab with the series forms (one block of 256)
 __global__ void k_math_tables() {
   const int j = threadIdx.x;
   if (j < 64)
     g_exp_tab[j] = dexp_series(__dadd_rn(__dmul_rn((double)j, kLn2Hi / 64.0), __dmul_rn((double)j, kLn2Lo / 64.0)));
-  if (j < 128) {
-    const double v = __ddiv_rn(1.0, __dadd_rn(1.0, __ddiv_rn((double)j, 128.0)));
+  if (j < 256) {
+    const double v = __ddiv_rn(1.0, __dadd_rn(1.0, __ddiv_rn((double)j, 256.0)));
     g_log_inv[j] = v;
     g_log_tab[j] = -dlog_series(v);
   }
