@@ -312,9 +312,9 @@ C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches);
  * the whole array gives C2F_ENOMEM.  Each call clears what must start at
  * zero; all calls share the array and it keeps the last call's contents, so
  * calls that overlap on the GPU (other streams, other host threads) race.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Synchronous: returns after the work on `stream` has finished.
+ * The first call on a device looks up the array's device address and loads
+ * the library's constant tables (once per device, with that device current);
+ * make that first call before any stream capture.  Synchronous: returns after the work on `stream` has finished.
  * ------------------------------------------------------------------------- */
 typedef struct {
   int32_t rows, cols;

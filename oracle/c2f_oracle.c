@@ -51,7 +51,7 @@
  *    log: x = 2^e m, m in [sqrt(1/2), sqrt(2)], log m = 2 atanh(s),
  *         s = (m-1)/(m+1), odd series to s^21.
  *    Table forms, the ones the method uses (Tang's table-driven method):
- *    exp: x = (64 k + j) ln2/64 + r, |r| <= ln2/128:
+ *    exp: x = (64 k + j) ln2/64 + r, |r| <= ln2/128 (r by two fused steps):
  *         exp x = 2^k T_j (1 + p(r)), T_j = 2^(j/64) (exp_series), p the
  *         Taylor polynomial of exp(r) - 1 to r^5.
  *    log: x = 2^e m, m in [1, 2), j = first 8 fraction bits of m,
@@ -180,7 +180,7 @@ OR_API double or_exp(double x) {
   if (x > 709.78) return INFINITY;
   if (x < -745.2) return 0.0;
   double kd = nearbyint(x * (INV_LN2 * 64.0));
-  double r = (x - kd * (LN2_HI / 64.0)) - kd * (LN2_LO / 64.0);
+  double r = fma(-kd, LN2_LO / 64.0, fma(-kd, LN2_HI / 64.0, x));
   double q = fma(fma(g_inv_fact[5], r, g_inv_fact[4]), r, g_inv_fact[3]);
   q = fma(q, r, g_inv_fact[2]);
   double p = fma(q, r * r, r);          /* exp(r) - 1 to r^5 */

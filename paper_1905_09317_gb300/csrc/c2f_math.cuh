@@ -128,13 +128,17 @@ __device__ inline double dexp(double x) {
     if (x < -745.2) return 0.0;
   }
   const double kd = rint(__dmul_rn(x, kInvLn2 * 64.0));
-  const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(kd, kLn2Hi / 64.0)), __dmul_rn(kd, kLn2Lo / 64.0));
+  const double r = __fma_rn(-kd, kLn2Lo / 64.0, __fma_rn(-kd, kLn2Hi / 64.0, x));
   double q = __fma_rn(__fma_rn(g_mc.inv_fact[5], r, g_mc.inv_fact[4]), r, g_mc.inv_fact[3]);
   q = __fma_rn(q, r, g_mc.inv_fact[2]);
   const double p = __fma_rn(q, __dmul_rn(r, r), r);   // exp(r) - 1 to r^5
   const long long k = (long long)kd;
   const double t = __ldg(&g_exp_tab[k & 63]);
-  return scale2(__fma_rn(t, p, t), (int)(k >> 6));
+  const double y = __fma_rn(t, p, t);                  // in [2^(-1/128), 2)
+  const int m = (int)(k >> 6);
+  // y 2^m is exact while it stays normal: add m to the exponent field
+  if (m >= -1020 && m <= 1022) return __longlong_as_double(__double_as_longlong(y) + ((long long)m << 52));
+  return scale2(y, m);
 }
 
 __device__ inline double dlog(double x) {
