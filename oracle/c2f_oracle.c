@@ -565,9 +565,10 @@ OR_API void or_fbp_cell(int fuel, double gs, double aspect_deg, double ws, doubl
   else
     lb = 1.0 + 8.729 * or_pow(1.0 - or_exp(-0.030 * wsv), 2.155);
   /* Eqs. (2)-(4) */
-  double fros = (hros + bros) / (2.0 * lb);
+  double ilb = 1.0 / lb;   /* one reciprocal for FROS and e */
+  double fros = ((hros + bros) * ilb) * 0.5;
   double a = (hros + bros) * 0.5;
-  double e = sqrt(1.0 - 1.0 / (lb * lb));
+  double e = sqrt(1.0 - ilb * ilb);
   out[0] = hros; out[1] = bros; out[2] = lb; out[3] = fros;
   out[4] = a; out[5] = e; out[6] = ux; out[7] = uy; out[8] = wsv; out[9] = wse;
   double ct[8], st[8];

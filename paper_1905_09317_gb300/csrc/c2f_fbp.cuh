@@ -213,9 +213,10 @@ __device__ inline void fbp_row(int fuel, double gs, const CellPrep &cp, const Ho
   else
     lb = __dadd_rn(1.0, __dmul_rn(8.729, dpow(__dsub_rn(1.0, dexp(__dmul_rn(-0.030, wsv))), 2.155)));
   const double hb = __dadd_rn(hros, bros);
-  const double fros = __ddiv_rn(hb, __dmul_rn(2.0, lb));
+  const double ilb = __ddiv_rn(1.0, lb);   // one reciprocal for FROS and e
+  const double fros = __dmul_rn(__dmul_rn(hb, ilb), 0.5);
   const double a = __dmul_rn(hb, 0.5);
-  const double e = __dsqrt_rn(__dsub_rn(1.0, __ddiv_rn(1.0, __dmul_rn(lb, lb))));
+  const double e = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(ilb, ilb)));
   o->hros = hros; o->bros = bros; o->lb = lb; o->fros = fros; o->a = a; o->e = e;
   o->ux = ux; o->uy = uy; o->wsv = wsv; o->wse = wse;
   const double h = __dsqrt_rn(0.5);
