@@ -195,8 +195,10 @@ C2F_API int c2f_simulate_batch(c2f_ctx *ctx, int32_t n, const int32_t *landscape
  * that arrive while others are on the GPU join the next epoch and overlap on
  * the device.  Results are the same as c2f_simulate's, alone or in any mix.
  * Every serving call (and c2f_pump) finishes epochs that are done and
- * launches queued work.  c2f_poll sets *done; c2f_wait blocks until the
- * simulation is finished; c2f_cancel drops a queued simulation (a running
+ * launches queued work.  Free memory for admission is the device's free
+ * memory plus what the context's pool keeps unused.  c2f_poll sets *done;
+ * c2f_wait blocks until the simulation is finished, holding the context (other
+ * threads' calls on it wait too); c2f_cancel drops a queued simulation (a running
  * one finishes, and its result is discarded: later reads give
  * C2F_ECANCELED).  Reading a simulation that is not finished gives C2F_EBUSY.
  * ------------------------------------------------------------------------- */

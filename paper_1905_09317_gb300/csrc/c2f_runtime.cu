@@ -969,7 +969,14 @@ int launch_pending(c2f_ctx *ctx) {
   }
   size_t freeb = 0, totalb = 0;
   CK(cudaMemGetInfo(&freeb, &totalb));
-  if ((int64_t)freeb < epoch_bytes(ctx, batch) + ctx->hbm_reserve && !ctx->inflight.empty()) {
+  int64_t avail = (int64_t)freeb;
+  if (ctx->pool) {   // blocks the context's pool keeps but does not use count as free
+    uint64_t reserved = 0, used = 0;
+    CK(cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+    CK(cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    if (reserved > used) avail += (int64_t)(reserved - used);
+  }
+  if (avail < epoch_bytes(ctx, batch) + ctx->hbm_reserve && !ctx->inflight.empty()) {
     ctx->pending.insert(ctx->pending.begin(), batch.begin(), batch.end());   // admission: wait for memory
     return C2F_OK;
   }
