@@ -219,14 +219,19 @@ __device__ inline void fbp_row(int fuel, double gs, const CellPrep &cp, const Ho
   const double e = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(ilb, ilb)));
   o->hros = hros; o->bros = bros; o->lb = lb; o->fros = fros; o->a = a; o->e = e;
   o->ux = ux; o->uy = uy; o->wsv = wsv; o->wse = wse;
-  const double h = __dsqrt_rn(0.5);
-  const double ct[8] = {1.0, h, 0.0, -h, -1.0, -h, 0.0, h};
-  const double st[8] = {0.0, h, 1.0, h, 0.0, -h, -1.0, -h};
+  // cos(phi_k) = (cos theta_k) ux + (sin theta_k) uy for the 8 axes, whose
+  // cosines and sines are 0, +-1 and +-h (h = RN(sqrt(1/2))): products by 0 and
+  // +-1 are exact, so the sums are ux, uy, their negatives and +-(h ux) +- (h uy)
+  // -- the same values (up to the sign of a zero, which no test below sees)
+  const double h = 0x1.6a09e667f3bcdp-1;
+  const double hx = __dmul_rn(h, ux), hy = __dmul_rn(h, uy);
+  const double dpp = __dadd_rn(hx, hy), dmp = __dsub_rn(hy, hx);
+  const double cphk[8] = {ux, dpp, uy, dmp, -ux, -dpp, -uy, -dmp};
   if (ellipse_mode == 0) {
     const double A = __dmul_rn(a, __dsub_rn(1.0, __dmul_rn(e, e)));
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const double cphi = __dadd_rn(__dmul_rn(ct[k], ux), __dmul_rn(st[k], uy));
+      const double cphi = cphk[k];
       o->ros[k] = (cphi > 0.0) ? __ddiv_rn(A, __dsub_rn(1.0, __dmul_rn(e, cphi))) : A;
     }
   } else {
@@ -234,7 +239,7 @@ __device__ inline void fbp_row(int fuel, double gs, const CellPrep &cp, const Ho
     const double c = __dmul_rn(__dsub_rn(hros, bros), 0.5);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const double cphi = __dadd_rn(__dmul_rn(ct[k], ux), __dmul_rn(st[k], uy));
+      const double cphi = cphk[k];
       double sphi2 = __dsub_rn(1.0, __dmul_rn(cphi, cphi));
       if (sphi2 < 0.0) sphi2 = 0.0;
       const double bc = __dmul_rn(__dmul_rn(__dmul_rn(b, b), cphi), cphi);
