@@ -253,11 +253,12 @@ __device__ inline void fbp_row(int fuel, double gs, const CellPrep &cp, const Ho
   }
 }
 
-// 2^32 fixed point of a non-negative real: 0 for non-positive / NaN, capped at 2^62
+// 2^32 fixed point of a non-negative real: 0 for non-positive / NaN, capped at
+// 2^62.  The conversion saturates (and gives INT64_MIN for NaN), so clamping
+// the integer gives the same result as testing x first, without FP64 compares.
 __device__ __forceinline__ int64_t fixed_of(double x) {
-  if (!(x > 0.0)) return 0;
-  if (x >= 4611686018427387904.0) return 4611686018427387904LL;
-  return (int64_t)__double2ll_rn(x);
+  const long long v = __double2ll_rn(x);
+  return v <= 0 ? 0 : (v >= 4611686018427387904LL ? 4611686018427387904LL : (int64_t)v);
 }
 
 }  // namespace c2f
