@@ -52,6 +52,8 @@ inline void make_fuel_table(FuelCoef t[F_NCODES]) {
     t[i] = v[i];
     t[i].inv_c = v[i].c != 0.0 ? 1.0 / v[i].c : 0.0;          // divisors of isf_curve,
     t[i].neg_inv_b = v[i].b != 0.0 ? -1.0 / v[i].b : 0.0;     // fixed per fuel
+    t[i].c2 = pow_half_steps(v[i].c);
+    t[i].inv_c2 = pow_half_steps(t[i].inv_c);
   }
 }
 
@@ -63,7 +65,7 @@ __device__ __forceinline__ bool is_o1(int f) { return f == F_O1A || f == F_O1B; 
 
 __device__ __forceinline__ double rsi_curve(const FuelCoef &k, double isi) {
   const double x = __dsub_rn(1.0, dexp(__dmul_rn(-k.b, isi)));
-  return __dmul_rn(k.a, dpow(x, k.c));
+  return __dmul_rn(k.a, dpow_n2(x, k.c, k.c2));
 }
 
 __device__ inline double curing_factor(double c) {
@@ -87,7 +89,7 @@ __device__ inline double rsi_of(int fuel, double isi, double pcf, double cf) {
 // -b are multiplications by rounded reciprocals.
 __device__ inline double isf_curve(const FuelCoef &k, double inv_am, double rsf) {
   if (!(rsf > 0.0)) return 0.0;
-  double x = __dsub_rn(1.0, dpow(__dmul_rn(rsf, inv_am), k.inv_c));
+  double x = __dsub_rn(1.0, dpow_n2(__dmul_rn(rsf, inv_am), k.inv_c, k.inv_c2));
   if (x < 0.01) x = 0.01;
   return __dmul_rn(dlog(x), k.neg_inv_b);
 }
@@ -209,9 +211,9 @@ __device__ inline void fbp_row(int fuel, double gs, const CellPrep &cp, const Ho
   const double bros = __dmul_rn(rsi_of(fuel, bisi, pcf, cf), be);
   double lb;
   if (is_o1(fuel))
-    lb = (wsv >= 1.0) ? __dmul_rn(1.1, dpow(wsv, 0.464)) : 1.0;
+    lb = (wsv >= 1.0) ? __dmul_rn(1.1, dpow_n2(wsv, 0.464, 0)) : 1.0;
   else
-    lb = __dadd_rn(1.0, __dmul_rn(8.729, dpow(__dsub_rn(1.0, dexp(__dmul_rn(-0.030, wsv))), 2.155)));
+    lb = __dadd_rn(1.0, __dmul_rn(8.729, dpow_n2(__dsub_rn(1.0, dexp(__dmul_rn(-0.030, wsv))), 2.155, 0)));
   const double hb = __dadd_rn(hros, bros);
   const double ilb = __ddiv_rn(1.0, lb);   // one reciprocal for FROS and e
   const double fros = __dmul_rn(__dmul_rn(hb, ilb), 0.5);
@@ -232,7 +234,8 @@ __device__ inline void fbp_row(int fuel, double gs, const CellPrep &cp, const Ho
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const double cphi = cphk[k];
-      o->ros[k] = (cphi > 0.0) ? __ddiv_rn(A, __dsub_rn(1.0, __dmul_rn(e, cphi))) : A;
+      // cphi > 0 as a sign test on the bits (cphi is never NaN)
+      o->ros[k] = (__double_as_longlong(cphi) > 0) ? __ddiv_rn(A, __dsub_rn(1.0, __dmul_rn(e, cphi))) : A;
     }
   } else {
     const double b = fros;

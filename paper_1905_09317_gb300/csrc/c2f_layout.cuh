@@ -22,7 +22,11 @@ enum FuelCode : int {
   F_O1A, F_O1B, F_S1, F_S2, F_S3, F_NCODES
 };
 
-struct FuelCoef { double a, b, c, q, bui0, inv_c, neg_inv_b; };   // RN(1/c), RN(-1/b); 0 when c / b = 0
+struct FuelCoef {
+  double a, b, c, q, bui0;
+  double inv_c, neg_inv_b;   // RN(1/c), RN(-1/b); 0 when c / b = 0
+  int32_t c2, inv_c2;        // 2c and 2/c when they are small integers (half-integer powers), else 0
+};
 
 struct HourPrep {
   double ws, ff, isz, sin_w, cos_w;

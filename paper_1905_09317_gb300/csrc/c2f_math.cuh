@@ -23,6 +23,7 @@
 // rounded binary64 quotients; they live in __constant__ memory, filled once per
 // device by upload_constants().
 #pragma once
+#include <cmath>
 #include <cstdint>
 
 #include "c2f_layout.cuh"
@@ -187,6 +188,33 @@ __device__ inline double dpow(double x, double y) {
   }
   if (x == 0.0) return (y > 0.0) ? 0.0 : ((y == 0.0) ? 1.0 : __longlong_as_double(0x7ff0000000000000LL));
   return __longlong_as_double(0x7ff8000000000000LL);
+}
+
+// dpow with the exponent's kind decided ahead: n2 = 2y when y is a positive
+// multiple of 1/2 up to 8 (the case dpow treats with products and a square
+// root), else 0 -- the same results as dpow(x, y) without testing y
+__device__ inline double dpow_n2(double x, double y, int n2) {
+  if (x > 0.0) {
+    if (n2 > 0) {
+      const int n = n2 >> 1;
+      double r = 1.0;
+      if (n > 0) {
+        r = x;
+        for (int i = 1; i < n; ++i) r = __dmul_rn(r, x);
+      }
+      if (n2 & 1) r = (n > 0) ? __dmul_rn(r, __dsqrt_rn(x)) : __dsqrt_rn(x);
+      return r;
+    }
+    return dexp(__dmul_rn(y, dlog(x)));
+  }
+  if (x == 0.0) return (y > 0.0) ? 0.0 : ((y == 0.0) ? 1.0 : __longlong_as_double(0x7ff0000000000000LL));
+  return __longlong_as_double(0x7ff8000000000000LL);
+}
+
+// host: n2 of dpow_n2 for a constant exponent
+inline int pow_half_steps(double y) {
+  const double y2 = y + y;
+  return (y > 0.0 && y2 <= 16.0 && std::nearbyint(y2) == y2) ? (int)y2 : 0;
 }
 
 // fills g_exp_tab / g_log_inv / g_log_tab with the series forms (one block of 256)
