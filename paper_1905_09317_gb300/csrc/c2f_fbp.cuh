@@ -88,9 +88,9 @@ __device__ inline double rsi_of(int fuel, double isi, double pcf, double cf) {
 // held at >= 0.01.  inv_am = RN(1 / (a mult)); the divisions by a mult and by
 // -b are multiplications by rounded reciprocals.
 __device__ inline double isf_curve(const FuelCoef &k, double inv_am, double rsf) {
-  if (!(rsf > 0.0)) return 0.0;
+  if (!pos(rsf)) return 0.0;
   double x = __dsub_rn(1.0, dpow_n2(__dmul_rn(rsf, inv_am), k.inv_c, k.inv_c2));
-  if (x < 0.01) x = 0.01;
+  if (lt_c(x, 0.01)) x = 0.01;
   return __dmul_rn(dlog(x), k.neg_inv_b);
 }
 
@@ -114,7 +114,7 @@ __device__ inline double isf_of(int fuel, const HourPrep &hp, double sf, double 
 
 // wind function of the ISI; above 40 km/h the saturating branch of the 2009 update
 __device__ __forceinline__ double wind_fn(double w) {
-  if (w <= 40.0) return dexp(__dmul_rn(0.05039, w));
+  if (le_c(w, 40.0)) return dexp(__dmul_rn(0.05039, w));
   return __dmul_rn(12.0, __dsub_rn(1.0, dexp(__dmul_rn(-0.0818, __dsub_rn(w, 28.0)))));
 }
 
@@ -148,6 +148,8 @@ __device__ inline void hour_prep(double ws, double wd_from, double ffmc, double 
   }
   hp->inv_a_d1m2 = __ddiv_rn(1.0, __dmul_rn(g_fuel[F_D1].a, 0.2));
   hp->inv_isz = __ddiv_rn(1.0, hp->isz);
+  hp->wsx_w = __dmul_rn(hp->ws, hp->sin_w);
+  hp->wsy_w = __dmul_rn(hp->ws, hp->cos_w);
   // A lower bound on every fuel's HROS this hour: the RSI curve grows with the
   // ISI and the ISI with the wind (wind_fn >= 1 for w >= 0), so RSI >= RSI at
   // zero wind (rszf); a C2/D1 mixture is at least 0.2 x its smaller part.
@@ -182,11 +184,11 @@ __device__ inline void fbp_row(int fuel, double gs, const CellPrep &cp, const Ho
                                double pcf, int ellipse_mode, FbpOut *o) {
   const double cf = hp.cf;
   double wse = 0.0;
-  if (gs > 0.0) {
+  if (pos(gs)) {
     const double isf = isf_of(fuel, hp, cp.sf, pcf);
-    if (isf > 0.0) {
+    if (pos(isf)) {
       wse = __dmul_rn(dlog(__dmul_rn(isf, hp.inv_isz)), 1.0 / 0.05039);
-      if (wse > 40.0) {
+      if (gt_c(wse, 40.0)) {
         if (isf < __dmul_rn(__dmul_rn(0.999, 2.496), hp.ff))
           wse = __dsub_rn(28.0, __ddiv_rn(dlog(__dsub_rn(1.0, __ddiv_rn(isf, __dmul_rn(2.496, hp.ff)))),
                                           0.0818));
@@ -195,11 +197,11 @@ __device__ inline void fbp_row(int fuel, double gs, const CellPrep &cp, const Ho
       }
     }
   }
-  const double wsx = __dadd_rn(__dmul_rn(hp.ws, hp.sin_w), __dmul_rn(wse, cp.sin_s));
-  const double wsy = __dadd_rn(__dmul_rn(hp.ws, hp.cos_w), __dmul_rn(wse, cp.cos_s));
+  const double wsx = __dadd_rn(hp.wsx_w, __dmul_rn(wse, cp.sin_s));
+  const double wsy = __dadd_rn(hp.wsy_w, __dmul_rn(wse, cp.cos_s));
   const double wsv = __dsqrt_rn(__dadd_rn(__dmul_rn(wsx, wsx), __dmul_rn(wsy, wsy)));
   double ux = 1.0, uy = 0.0;
-  if (wsv > 0.0) {
+  if (pos(wsv)) {
     const double iw = __ddiv_rn(1.0, wsv);
     ux = __dmul_rn(wsx, iw);
     uy = __dmul_rn(wsy, iw);
@@ -211,7 +213,7 @@ __device__ inline void fbp_row(int fuel, double gs, const CellPrep &cp, const Ho
   const double bros = __dmul_rn(rsi_of(fuel, bisi, pcf, cf), be);
   double lb;
   if (is_o1(fuel))
-    lb = (wsv >= 1.0) ? __dmul_rn(1.1, dpow_n2(wsv, 0.464, 0)) : 1.0;
+    lb = !lt_c(wsv, 1.0) ? __dmul_rn(1.1, dpow_n2(wsv, 0.464, 0)) : 1.0;
   else
     lb = __dadd_rn(1.0, __dmul_rn(8.729, dpow_n2(__dsub_rn(1.0, dexp(__dmul_rn(-0.030, wsv))), 2.155, 0)));
   const double hb = __dadd_rn(hros, bros);

@@ -202,7 +202,7 @@ __global__ void k_order_scatter(const uint8_t *fuel, const float *slope, const u
 __device__ __forceinline__ double row_rates(int fuel, const float *slope, int64_t cell,
                                             const CellPrep &cp, const HourPrep &hp, double pcf,
                                             double const_ros, int ellipse_mode, double ros[8]) {
-  if (const_ros > 0.0) {
+  if (pos(const_ros)) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) ros[k] = const_ros;
     return const_ros;

@@ -36,6 +36,7 @@ struct HourPrep {
   double inv_a[F_NCODES]; // RN(1 / (a mult)) of each code's own curve (mult = curing for O1, else 1)
   double inv_a_d1m2;      // RN(1 / (a_D1 0.2)), the D1 part of M2
   double inv_isz;         // RN(1 / ISZ)
+  double wsx_w, wsy_w;    // RN(WS sin WAZ), RN(WS cos WAZ): the wind's part of the net vector
   int32_t pos;            // 1: every fuel's HROS this hour is > 1e-200 (a lower bound says so)
 };
 

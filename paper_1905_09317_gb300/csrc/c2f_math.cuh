@@ -70,6 +70,17 @@ constexpr float kInvLn2F = 0x1.715476p+0f;
 constexpr float kTwoPiF = 0x1.921fb6p+2f;
 constexpr float kSqrt2F = 0x1.6a09e6p+0f;
 
+// Comparisons of a double with 0 or a positive constant as integer compares of
+// the bit patterns (the order of non-NaN doubles against a positive constant is
+// the order of their bits read as signed 64-bit integers).  The values tested
+// on the rate-of-spread path are never NaN; these keep the compares off the
+// FP64 unit, which the table kernel saturates.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool pos(double x) { return dbits(x) > 0; }   // x > 0
+__device__ __forceinline__ bool gt_c(double x, double c) { return dbits(x) > dbits(c); }   // x > c > 0
+__device__ __forceinline__ bool lt_c(double x, double c) { return dbits(x) < dbits(c); }   // x < c, c > 0
+__device__ __forceinline__ bool le_c(double x, double c) { return dbits(x) <= dbits(c); }  // x <= c, c > 0
+
 __device__ __forceinline__ double pow2i(int k) {  // exact 2^k for -1022 <= k <= 1023
   return __longlong_as_double((long long)(k + 1023) << 52);
 }
@@ -194,7 +205,7 @@ __device__ inline double dpow(double x, double y) {
 // multiple of 1/2 up to 8 (the case dpow treats with products and a square
 // root), else 0 -- the same results as dpow(x, y) without testing y
 __device__ inline double dpow_n2(double x, double y, int n2) {
-  if (x > 0.0) {
+  if (pos(x)) {
     if (n2 > 0) {
       const int n = n2 >> 1;
       double r = 1.0;
