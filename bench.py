@@ -402,8 +402,8 @@ def roofline(dom, fam, w, work_per_step, peaks):
 # DADD from ncu's instruction counts over cells x hours).  FP64 peak: 152 SMs x 2
 # DFMA per clock x 2 flop x 2.07 GHz.
 FRONTIER_BYTES_PER_UPDATE = 194.0
-FRONTIER_DRAM_BYTES_PER_REPLICA = 93.98e6 / 200   # ncu, 512^2 x 24 h, 200 replicas
-FP64_OPS_PER_CELL_HOUR = 379.0      # ncu: (2 x DFMA + DMUL + DADD) / (cells x hours)
+FRONTIER_DRAM_BYTES_PER_REPLICA = 94.59e6 / 200   # ncu, 512^2 x 24 h, 200 replicas
+FP64_OPS_PER_CELL_HOUR = 364.0      # ncu: (2 x DFMA + DMUL + DADD) / (cells x hours)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x DFMA/clk x flop/DFMA x GHz
 
 
