@@ -94,6 +94,10 @@ def _load():
         lib.or_base_inc.restype = None
         lib.or_base_inc.argtypes = [C.c_void_p, i32, i32, P(i64), P(d)]
         lib.or_ignition_cell.restype = i32; lib.or_ignition_cell.argtypes = [C.c_void_p, i32]
+        lib.or_scenario_thresholds.restype = C.c_int
+        lib.or_scenario_thresholds.argtypes = [i32, P(d), P(u64)]
+        lib.or_scenario.restype = i32
+        lib.or_scenario.argtypes = [u64, i32, i32, P(u64)]
         for name in ("or_run_replica", "or_run_replica_event"):
             fn = getattr(lib, name)
             fn.restype = C.c_int
@@ -230,6 +234,60 @@ class Oracle:
     def run_replica_event(self, replica: int) -> dict:
         """Label-setting search over ignition steps (O2); equals O1."""
         return self._run(self.lib.or_run_replica_event, replica)
+
+
+# ---------------------------------------------------------------- weather scenarios
+def scenario_thresholds(probs) -> np.ndarray:
+    """T_s = floor(2^32 cum_s / total), T_{S-1} = 2^32 (Sec. 3.1, uncertainty (3))."""
+    p = np.ascontiguousarray(probs, dtype=np.float64).ravel()
+    out = np.zeros(max(p.size, 1), dtype=np.uint64)
+    rc = _load().or_scenario_thresholds(int(p.size), p.ctypes.data_as(C.POINTER(C.c_double)),
+                                        out.ctypes.data_as(C.POINTER(C.c_uint64)))
+    if rc:
+        raise ValueError("scenario probabilities must be finite, >= 0 and not all 0")
+    return out
+
+
+def scenario_of(seed: int, replica: int, thresholds) -> int:
+    """The scenario replica `replica` runs under: the first s with x0 < T_s."""
+    t = np.ascontiguousarray(thresholds, dtype=np.uint64)
+    return int(_load().or_scenario(int(seed), int(replica), int(t.size),
+                                   t.ctypes.data_as(C.POINTER(C.c_uint64))))
+
+
+class ScenarioOracle:
+    """A request over several weather scenarios (Sec. 3.1, uncertainty (3)):
+    replica r runs Algorithm 1 under the weather stream of its drawn scenario
+    s(r), with everything else (ignition draw, perturbations, keyed by r)
+    as in a single-scenario run."""
+
+    def __init__(self, fuel, slope=None, aspect=None, unburnable=None, cell_size=100.0,
+                 weathers=(), probs=(), **params):
+        self.thresholds = scenario_thresholds(probs)
+        if len(weathers) != self.thresholds.size:
+            raise ValueError("one probability per weather scenario")
+        self.seed = int(params.get("seed", 0))
+        self.oracles = [Oracle(fuel, slope, aspect, unburnable, cell_size=cell_size, weather=w,
+                               **params) for w in weathers]
+
+    def scenario(self, replica: int) -> int:
+        return scenario_of(self.seed, replica, self.thresholds)
+
+    def ignition_cell(self, replica: int) -> int:
+        return self.oracles[0].ignition_cell(replica)
+
+    def base_inc(self, scenario: int, cell: int, hour: int):
+        return self.oracles[scenario].base_inc(cell, hour)
+
+    def run_replica(self, replica: int) -> dict:
+        s = self.scenario(replica)
+        out = self.oracles[s].run_replica(replica)
+        out["scenario"] = s
+        return out
+
+    def close(self):
+        for o in self.oracles:
+            o.close()
 
 
 def burn_prob(scars) -> np.ndarray:

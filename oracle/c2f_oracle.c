@@ -27,6 +27,8 @@
  *   Sec. 3.8 / App. A  send before receive within a step.
  *   Sec. 3.1 (uncertainty (1),(2))  random ignition cell, multiplicative
  *                   ROS perturbation.
+ *   Sec. 3.1 (uncertainty (3))  several weather scenarios with given
+ *                   probabilities; each replica runs under one of them.
  *
  * FBP rate-of-spread equations are not printed in the paper (it defers to
  * the Canadian FBP System, Forestry Canada 1992, and the 2009 update); the
@@ -1031,4 +1033,43 @@ OR_API int or_run_replica_event(or_ctx *c, int32_t replica, uint8_t *scar, int32
   if (ic_out) *ic_out = ic;
   free(t); free(done); free(death); free(heap);
   return 0;
+}
+
+/* ======================================================================
+ * 6. Weather scenarios (Sec. 3.1, uncertainty source (3)): a request may
+ *    carry several weather streams, scenario s occurring with probability
+ *    p_s.  Every replica runs under one scenario, drawn with those
+ *    probabilities from its own Philox block at counter (replica, 0, 0, 2):
+ *    with x0 the block's first word, the replica takes the first s with
+ *    x0 < T_s, where T_s = floor(2^32 (p_0 + ... + p_s) / (p_0 + ... +
+ *    p_{S-1})) (sums left to right in binary64) and T_{S-1} = 2^32.  So
+ *    P(s) = (T_s - T_{s-1}) / 2^32, within 2^-32 of p_s / sum p, and a
+ *    scenario with p_s = 0 is never taken.
+ * ====================================================================== */
+OR_API int or_scenario_thresholds(int32_t n, const double *prob, uint64_t *thr) {
+  if (n < 1) return -1;
+  double total = 0.0;
+  for (int32_t s = 0; s < n; ++s) {
+    if (!(prob[s] >= 0.0) || !isfinite(prob[s])) return -1;
+    total += prob[s];
+  }
+  if (!(total > 0.0) || !isfinite(total)) return -1;
+  double cum = 0.0;
+  for (int32_t s = 0; s < n; ++s) {
+    cum += prob[s];
+    if (s == n - 1) thr[s] = (uint64_t)1 << 32;
+    else thr[s] = (uint64_t)((cum / total) * FP_ONE);   /* cum <= total: at most 2^32 */
+  }
+  return 0;
+}
+
+OR_API int32_t or_scenario(uint64_t seed, int32_t replica, int32_t n, const uint64_t *thr) {
+  if (n <= 1) return 0;
+  uint32_t ctr[4] = {(uint32_t)replica, 0u, 0u, 2u};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t x[4];
+  or_philox4x32_10(ctr, key, x);
+  for (int32_t s = 0; s < n - 1; ++s)
+    if ((uint64_t)x[0] < thr[s]) return s;
+  return n - 1;
 }
