@@ -180,6 +180,18 @@ def config4(side=4096, n_replicas=256, hours=72) -> Workload:
     return Workload(land, weather_stream(hours, seed=104, shift_at=36), params)
 
 
+def scenario_set(n_scen=8, hours=24, seed=102):
+    """Weather scenarios of one request (Sec. 3.1, uncertainty (3)): n_scen
+    hourly streams, calm to strong wind (mean 8 + 4 s km/h) from directions
+    20 s degrees apart, with unnormalised weights rising then falling
+    (1, 2, ..., 2, 1).  Returns (weathers (n_scen, hours, 4), weights)."""
+    weathers = np.stack([weather_stream(hours, seed=seed + 31 * s, ws_mean=8.0 + 4.0 * s,
+                                        wd0=(270.0 + 20.0 * s) % 360.0) for s in range(n_scen)])
+    half = (n_scen + 1) // 2
+    w = np.concatenate([np.arange(1, half + 1), np.arange(n_scen - half, 0, -1)]).astype(np.float64)
+    return weathers, w
+
+
 def serving_requests(rate=50.0, duration_s=60.0, seed=5, pool=16):
     """Poisson arrivals of (arrival_s, pool index, replicas, hours) for the serving
     workload; landscape sides log-uniform in [128, 2048] over a pool of `pool`."""

@@ -144,6 +144,25 @@ C2F_API int c2f_load_landscape(c2f_ctx *ctx, int32_t rows, int32_t cols, double 
 C2F_API int c2f_set_weather(c2f_ctx *ctx, int32_t landscape_id, int32_t n_hours,
                             const c2f_weather_hour *w);
 
+/* Weather scenarios (Sec. 3.1, uncertainty source (3)): n_scenarios hourly
+ * streams of n_hours rows each, w[s*n_hours + h] (row-major, copied), scenario
+ * s occurring with probability prob[s] / (prob[0] + ... + prob[S-1]).  Every
+ * replica of a later simulation on the landscape runs under one scenario,
+ * drawn from its own Philox4x32-10 block at counter (replica, 0, 0, 2): with
+ * x0 the block's first word it takes the first s with x0 < T_s, where
+ * T_s = floor(2^32 (prob[0] + ... + prob[s]) / total) (binary64 sums from the
+ * left) and T_{S-1} = 2^32; a scenario of probability 0 is never drawn.  The
+ * ignition draw and the perturbations stay keyed by the replica alone, so a
+ * replica's fire under scenario s is the one a single-stream run with that
+ * stream gives.  The table holds one stacked table per scenario (device
+ * memory x n_scenarios).  1 <= n_scenarios <= 4096, n_scenarios * n_hours
+ * <= 65535; prob: finite, >= 0, not all 0 (NULL allowed when n_scenarios is
+ * 1); weather rows as c2f_set_weather.  c2f_set_weather is the same call
+ * with one scenario.  Invalidates the cached tables of the landscape. */
+C2F_API int c2f_set_weather_scenarios(c2f_ctx *ctx, int32_t landscape_id, int32_t n_scenarios,
+                                      int32_t n_hours, const c2f_weather_hour *w,
+                                      const double *prob);
+
 /* The rate-of-spread table of a landscape for the FBP/ellipse options in *p
  * (Sec. 3.7, Eqs. 1-4): per (hour, cell) the 8 directional ROS in 2^32 fixed
  * point per fire period, and HROS.  A table is either eager (every row
@@ -172,6 +191,13 @@ C2F_API int c2f_set_table_mode(c2f_ctx *ctx, int eager);
  * increment before the perturbation).  Any output may be NULL. Synchronous. */
 C2F_API int c2f_get_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p,
                         int32_t hour, double *ros8, double *hros, int64_t *base);
+
+/* c2f_get_ros for weather scenario `scenario` of c2f_set_weather_scenarios
+ * (c2f_get_ros is scenario 0); scenario outside [0, n_scenarios) is
+ * C2F_EINVAL. */
+C2F_API int c2f_get_ros_scenario(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p,
+                                 int32_t scenario, int32_t hour, double *ros8, double *hros,
+                                 int64_t *base);
 
 /* Runs all replicas of one simulation (Alg. 1 Steps 0-2 per replica) and
  * returns when they are finished.  The result stays on the device under
@@ -251,6 +277,10 @@ C2F_API int c2f_get_scars_at_hour(c2f_ctx *ctx, int32_t sim_id, int32_t hour, ui
  * = ignition cell.  Any pointer may be NULL. */
 C2F_API int c2f_get_counters(c2f_ctx *ctx, int32_t sim_id, int64_t *work, int32_t *ignited,
                              int32_t *ign_cell);
+
+/* The weather scenario each replica ran under (n_replicas int32, host
+ * memory; all 0 when the landscape had one weather stream). */
+C2F_API int c2f_get_scenarios(c2f_ctx *ctx, int32_t sim_id, int32_t *scenario);
 
 /* Initial burning-list capacity (entries per CTA) of the frontier kernel;
  * 0 = automatic.  A replica that outgrows it is re-run with a larger one, so

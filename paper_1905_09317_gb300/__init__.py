@@ -93,9 +93,13 @@ _SIGS = [
     ("c2f_load_landscape", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, _P(C.c_int32)]),
     ("c2f_set_weather", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
+    ("c2f_set_weather_scenarios", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                            C.c_void_p]),
     ("c2f_build_ros", C.c_int, [C.c_void_p, C.c_int32, _P(SimParams), C.c_int]),
     ("c2f_get_ros", C.c_int, [C.c_void_p, C.c_int32, _P(SimParams), C.c_int32, C.c_void_p,
                               C.c_void_p, C.c_void_p]),
+    ("c2f_get_ros_scenario", C.c_int, [C.c_void_p, C.c_int32, _P(SimParams), C.c_int32, C.c_int32,
+                                       C.c_void_p, C.c_void_p, C.c_void_p]),
     ("c2f_simulate", C.c_int, [C.c_void_p, C.c_int32, _P(SimParams), _P(C.c_int32)]),
     ("c2f_simulate_batch", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("c2f_submit", C.c_int, [C.c_void_p, C.c_int32, _P(SimParams), _P(C.c_int32)]),
@@ -112,6 +116,7 @@ _SIGS = [
     ("c2f_get_scar_bits", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_get_scars_at_hour", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     ("c2f_get_counters", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("c2f_get_scenarios", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_set_list_capacity", C.c_int, [C.c_void_p, C.c_int64]),
     ("c2f_set_frontier_config", C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
     ("c2f_autotune", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
@@ -224,15 +229,27 @@ class Context:
         w = np.ascontiguousarray(weather, dtype=np.float64).reshape(-1, 4)
         self._check(self.lib.c2f_set_weather(self.h, int(landscape_id), w.shape[0], _ptr(w)))
 
+    def set_weather_scenarios(self, landscape_id: int, weathers, probs) -> None:
+        """weathers: (n_scenarios, n_hours, 4); probs: n_scenarios weights."""
+        w = np.ascontiguousarray(weathers, dtype=np.float64)
+        if w.ndim != 3 or w.shape[2] != 4:
+            raise ValueError("weathers must have shape (n_scenarios, n_hours, 4)")
+        p = np.ascontiguousarray(probs, dtype=np.float64).ravel()
+        if p.size != w.shape[0]:
+            raise ValueError("one probability per scenario")
+        self._check(self.lib.c2f_set_weather_scenarios(self.h, int(landscape_id), w.shape[0],
+                                                       w.shape[1], _ptr(w), _ptr(p)))
+
     def build_ros(self, landscape_id: int, params: SimParams, force=False) -> None:
         self._check(self.lib.c2f_build_ros(self.h, int(landscape_id), C.byref(params), int(force)))
 
-    def get_ros(self, landscape_id: int, params: SimParams, hour: int, n_cells: int):
+    def get_ros(self, landscape_id: int, params: SimParams, hour: int, n_cells: int, scenario=0):
         ros8 = np.empty((n_cells, 8), dtype=np.float64)
         hros = np.empty(n_cells, dtype=np.float64)
         base = np.empty((n_cells, 8), dtype=np.int64)
-        self._check(self.lib.c2f_get_ros(self.h, int(landscape_id), C.byref(params), int(hour),
-                                         _ptr(ros8), _ptr(hros), _ptr(base)))
+        self._check(self.lib.c2f_get_ros_scenario(self.h, int(landscape_id), C.byref(params),
+                                                  int(scenario), int(hour), _ptr(ros8), _ptr(hros),
+                                                  _ptr(base)))
         return ros8, hros, base
 
     # ---- runs
@@ -315,6 +332,11 @@ class Context:
         cell = np.empty(n_replicas, dtype=np.int32)
         self._check(self.lib.c2f_get_counters(self.h, int(sim_id), _ptr(work), _ptr(ign), _ptr(cell)))
         return work, ign, cell
+
+    def get_scenarios(self, sim_id: int, n_replicas: int) -> np.ndarray:
+        out = np.empty(n_replicas, dtype=np.int32)
+        self._check(self.lib.c2f_get_scenarios(self.h, int(sim_id), _ptr(out)))
+        return out
 
     def set_list_capacity(self, cap: int) -> None:
         self._check(self.lib.c2f_set_list_capacity(self.h, int(cap)))

@@ -269,6 +269,13 @@ __global__ void k_ignite(const SimJob *jobs, int32_t job) {
     ic = J.burnable_list[idx];
   }
   J.ign_cell[r] = ic;
+  if (J.n_scen > 1) {   // Sec. 3.1 (3): the first s with x0 < T_s, x0 from counter (r, 0, 0, 2)
+    const U4 x = philox4x32_10(U4{(uint32_t)r, 0u, 0u, 2u}, (uint32_t)J.seed,
+                               (uint32_t)(J.seed >> 32));
+    int32_t s = 0;
+    while (s < J.n_scen - 1 && (uint64_t)x.x >= J.scen_thr[s]) ++s;
+    J.scen[r] = s;
+  }
 }
 
 // ------------------------------------------------------------------ K3
@@ -517,6 +524,14 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         item = A.item_list ? A.item_list[i] : (long long)i;
         jidx = (int32_t)find_job(A.item_begin, A.n_jobs, item);
         J = A.jobs[jidx];
+        if (J.n_scen > 1) {   // this replica's scenario: its stacked table
+          const int64_t s = J.scen[item - A.item_begin[jidx]];
+          const int64_t n = (int64_t)J.rows * J.cols;
+          J.base += s * J.scen_hours * n * 8;
+          J.hros += s * J.scen_hours * n;
+          J.hour += s * J.prep_hours;
+          if (J.chunk_state) J.chunk_state += s * J.scen_hours * J.rows * J.wpr;
+        }
       }
     }
     item = __shfl_sync(FULL, item, 0);

@@ -62,6 +62,13 @@ struct SimJob {
   const CellPrep *cell;
   double pcf, const_ros, dt2p32;
   int32_t ellipse_mode;
+  // weather scenarios (Sec. 3.1, uncertainty (3)): with n_scen > 1 the table
+  // holds n_scen stacked tables ([n_scen][scen_hours] rows of base / hros /
+  // chunk_state, [n_scen][prep_hours] hour preps); replica r draws scen[r]
+  // (K2) and the frontier reads that scenario's rows
+  int32_t n_scen, scen_hours, prep_hours;
+  const uint64_t *scen_thr;       // [n_scen] thresholds T_s (T_{S-1} = 2^32)
+  int32_t *scen;                  // [R] drawn scenario per replica
   // run parameters
   uint64_t seed;
   float sigma;

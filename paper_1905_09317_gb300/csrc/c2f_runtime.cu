@@ -109,6 +109,11 @@ struct TableKey {
 // cells at a time, tracked by chunk_state ([hours][rows*wpr], 0 = empty).
 struct Table {
   TableKey key;
+  // n_scen weather scenarios: n_scen stacked tables of key.hours hours each,
+  // hour preps [n_scen][prep_hours]; `weather` holds the scenarios' streams
+  // ([n_scen][prep_hours][4] doubles) and then their thresholds (n_scen uint64)
+  int32_t n_scen = 1, prep_hours = 0;
+  std::shared_ptr<DevBuf> weather;
   DevBuf hour_prep, base, hros, chunk_state;
   bool eager = false;
   cudaEvent_t ready = nullptr;   // recorded after the build; epochs on other streams wait on it
@@ -127,8 +132,9 @@ struct Landscape {
   DevBuf fuel, slope, aspect, burnable, burnable_list, cell_prep, order;
   bool has_slope = false;
   int32_t n_hours = 0;
-  std::vector<double> weather;          // n_hours x 4
-  std::shared_ptr<DevBuf> weather_dev;
+  int32_t n_scen = 1;                   // weather scenarios (Sec. 3.1, uncertainty (3))
+  std::vector<double> weather;          // n_scen x n_hours x 4
+  std::shared_ptr<DevBuf> weather_dev;  // the same, then n_scen uint64 thresholds
   std::shared_ptr<Table> table;
 };
 
@@ -140,7 +146,7 @@ struct Sim {
   std::shared_ptr<Table> table;
   int32_t rows = 0, cols = 0, wpr = 0;
   int64_t n = 0;
-  DevBuf ign_plane, ign_step, work, n_ignited, ign_cell, status;
+  DevBuf ign_plane, ign_step, work, n_ignited, ign_cell, status, scen;
   int state = S_PENDING;
   int rc = C2F_OK;
   bool cancel_requested = false;
@@ -366,16 +372,22 @@ int prepare_table(c2f_ctx *ctx, Landscape &L, const TableKey &k) {
   int rc;
   auto T = std::make_shared<Table>();
   T->key = k;
+  T->n_scen = L.n_scen;
+  T->prep_hours = L.n_hours;
+  T->weather = L.weather_dev;
+  const size_t S = (size_t)L.n_scen;
   CK(cudaEventCreateWithFlags(&T->ready, cudaEventDisableTiming));
-  if ((rc = dalloc(ctx, T->hour_prep, sizeof(HourPrep) * (size_t)L.n_hours))) return rc;
-  if ((rc = dalloc(ctx, T->base, sizeof(int64_t) * 8 * (size_t)L.n * k.hours))) return rc;
-  if ((rc = dalloc(ctx, T->hros, sizeof(double) * (size_t)L.n * k.hours))) return rc;
-  if ((rc = dalloc(ctx, T->chunk_state, sizeof(uint32_t) * (size_t)L.rows * L.wpr * k.hours))) return rc;
+  if ((rc = dalloc(ctx, T->hour_prep, sizeof(HourPrep) * S * (size_t)L.n_hours))) return rc;
+  if ((rc = dalloc(ctx, T->base, sizeof(int64_t) * 8 * S * (size_t)L.n * k.hours))) return rc;
+  if ((rc = dalloc(ctx, T->hros, sizeof(double) * S * (size_t)L.n * k.hours))) return rc;
+  if ((rc = dalloc(ctx, T->chunk_state, sizeof(uint32_t) * S * (size_t)L.rows * L.wpr * k.hours)))
+    return rc;
   L.table = T;
   return C2F_OK;
 }
 
-// K1 over every row of L.table, then every chunk marked done (capturable)
+// K1 over every row of L.table (one launch per weather scenario), then every
+// chunk marked done (capturable)
 int fill_table(c2f_ctx *ctx, Landscape &L, cudaStream_t st) {
   Table &T = *L.table;
   const TableKey &k = T.key;
@@ -397,8 +409,14 @@ int fill_table(c2f_ctx *ctx, Landscape &L, cudaStream_t st) {
   a.ros8 = nullptr;
   a.order = L.order.as<int32_t>();
   dim3 grid(grid1(L.n, 128), (unsigned)k.hours);
-  k_ros_table<<<grid, 128, 0, st>>>(a);
-  CKL("k_ros_table");
+  for (int32_t sc = 0; sc < T.n_scen; ++sc) {
+    const size_t rows_off = (size_t)sc * k.hours * (size_t)L.n;
+    a.hour = T.hour_prep.as<HourPrep>() + (size_t)sc * T.prep_hours;
+    a.base = T.base.as<int64_t>() + rows_off * 8;
+    a.hros = T.hros.as<double>() + rows_off;
+    k_ros_table<<<grid, 128, 0, st>>>(a);
+    CKL("k_ros_table");
+  }
   CK(cudaMemsetAsync(T.chunk_state.p, 0x02, T.chunk_state.bytes, st));   // >= 2: done
   T.eager = true;
   return C2F_OK;
@@ -411,8 +429,9 @@ int launch_table(c2f_ctx *ctx, Landscape &L, cudaStream_t st, bool eager) {
   const TableKey &k = T.key;
   {
     ProfScope prof(ctx, 0, st);
-    k_hour_prep<<<grid1(L.n_hours, 64), 64, 0, st>>>(L.weather_dev->as<double>(), L.n_hours, k.curing,
-                                                      T.hour_prep.as<HourPrep>());
+    const int32_t nh = T.n_scen * T.prep_hours;   // every scenario's hours, stacked
+    k_hour_prep<<<grid1(nh, 64), 64, 0, st>>>(T.weather->as<double>(), nh, k.curing,
+                                              T.hour_prep.as<HourPrep>());
     CKL("k_hour_prep");
   }
   if (eager) {
@@ -502,6 +521,9 @@ int alloc_sim(c2f_ctx *ctx, Sim &s, cudaStream_t st) {
   if ((rc = dalloc_on(ctx, s.ign_cell, 4 * R, st))) return rc;
   if ((rc = dalloc_on(ctx, s.status, 4 * R, st))) return rc;
   CK(cudaMemsetAsync(s.status.p, 0, 4 * R, st));
+  if (s.table->n_scen > 1) {
+    if ((rc = dalloc_on(ctx, s.scen, 4 * R, st))) return rc;
+  }
   return C2F_OK;
 }
 
@@ -524,6 +546,13 @@ SimJob job_of(const Sim &s) {
   j.const_ros = T.key.const_ros;
   j.dt2p32 = (double)T.key.dt * 4294967296.0;
   j.ellipse_mode = T.key.ellipse;
+  j.n_scen = T.n_scen;
+  j.scen_hours = T.key.hours;
+  j.prep_hours = T.prep_hours;
+  j.scen_thr = T.n_scen > 1
+      ? reinterpret_cast<const uint64_t *>(T.weather->as<double>() + (size_t)T.n_scen * T.prep_hours * 4)
+      : nullptr;
+  j.scen = s.scen.as<int32_t>();
   j.seed = s.p.seed;
   j.sigma = (float)s.p.ros_sigma;
   j.ignition_mode = s.p.ignition_mode;
@@ -794,7 +823,9 @@ int simulate_many(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_sim_par
     if ((rc = alloc_sim(ctx, *s, ctx->stream))) return rc;
 
   // groups of landscapes to build, largest table first
-  auto cost = [](const Landscape *L) { return (double)L->n * (double)L->table->key.hours; };
+  auto cost = [](const Landscape *L) {
+    return (double)L->n * (double)L->table->key.hours * (double)L->table->n_scen;
+  };
   std::stable_sort(builds.begin(), builds.end(),
                    [&](const Landscape *a, const Landscape *b) { return cost(a) > cost(b); });
   const int G = (int)std::min<size_t>(4, std::max<size_t>(1, builds.size()));
@@ -922,7 +953,7 @@ int64_t epoch_bytes(c2f_ctx *ctx, const std::vector<std::shared_ptr<Sim>> &sims)
     R += r;
     pw = std::max<int64_t>(pw, spw);
     cap = std::max(cap, default_cap(ctx, *s->land));
-    outputs += r * (spw * 4 + 24);
+    outputs += r * (spw * 4 + 28);   // scar plane, counters, status, scenario
     if (s->p.outputs & C2F_OUT_IGN_STEPS) outputs += r * s->n * 4;
   }
   const int64_t slots = std::min<int64_t>(R, (int64_t)ctx->sm_count * 8);
@@ -1208,38 +1239,86 @@ C2F_API int c2f_load_landscape(c2f_ctx *ctx, int32_t rows, int32_t cols, double 
   return C2F_OK;
 }
 
-C2F_API int c2f_set_weather(c2f_ctx *ctx, int32_t landscape_id, int32_t n_hours,
-                            const c2f_weather_hour *w) {
-  if (!ctx) return C2F_EINVAL;
-  LOCK;
+namespace {
+
+// Scenario thresholds (Sec. 3.1, uncertainty (3)): T_s = floor(2^32 cum_s /
+// total) with left-to-right binary64 sums, T_{S-1} = 2^32; a replica whose
+// Philox word x0 is below T_s and not below T_{s-1} runs scenario s.
+bool scenario_thresholds(int32_t n, const double *prob, std::vector<uint64_t> &thr) {
+  double total = 0.0;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!(prob[i] >= 0.0) || !std::isfinite(prob[i])) return false;
+    total += prob[i];
+  }
+  if (!(total > 0.0) || !std::isfinite(total)) return false;
+  thr.assign(n, 0);
+  double cum = 0.0;
+  for (int32_t i = 0; i < n; ++i) {
+    cum += prob[i];
+    const double q = cum / total;   // <= 1: the partial sums never pass the total
+    thr[i] = (i == n - 1) ? (uint64_t(1) << 32) : (uint64_t)(q * 4294967296.0);
+  }
+  return true;
+}
+
+int set_weather_impl(c2f_ctx *ctx, int32_t landscape_id, int32_t n_scen, int32_t n_hours,
+                     const c2f_weather_hour *w, const double *prob) {
   auto L = find_land(ctx, landscape_id);
   if (!L) return fail(ctx, C2F_ENOTFOUND, "unknown landscape %d", landscape_id);
+  if (n_scen < 1 || n_scen > 4096) return fail(ctx, C2F_EINVAL, "n_scenarios must lie in [1, 4096]");
   if (n_hours < 1 || n_hours > 65535 || !w) return fail(ctx, C2F_EINVAL, "n_hours must lie in [1, 65535]");
-  for (int32_t h = 0; h < n_hours; ++h) {
+  if ((int64_t)n_scen * n_hours > 65535)
+    return fail(ctx, C2F_EINVAL, "n_scenarios * n_hours must not exceed 65535");
+  std::vector<uint64_t> thr(1, uint64_t(1) << 32);
+  if (n_scen > 1 && (!prob || !scenario_thresholds(n_scen, prob, thr)))
+    return fail(ctx, C2F_EINVAL, "scenario probabilities must be finite, >= 0 and not all 0");
+  const int64_t nh = (int64_t)n_scen * n_hours;
+  for (int64_t h = 0; h < nh; ++h) {
     const c2f_weather_hour &x = w[h];
     if (!std::isfinite(x.ws_kmh) || x.ws_kmh < 0 || x.ws_kmh > 1000 || !std::isfinite(x.wd_from_deg) ||
         std::fabs(x.wd_from_deg) > 1e6 || !(x.ffmc >= 0.0 && x.ffmc < 101.0) ||
         !(x.bui > 0.0 && x.bui < 1e6))
-      return fail(ctx, C2F_EINVAL, "weather hour %d out of range", h);
+      return fail(ctx, C2F_EINVAL, "weather hour %lld out of range", (long long)h);
   }
   CK(cudaSetDevice(ctx->device));
-  L->n_hours = n_hours;
-  L->weather.assign((size_t)n_hours * 4, 0.0);
-  for (int32_t h = 0; h < n_hours; ++h) {
-    L->weather[h * 4 + 0] = w[h].ws_kmh;
-    L->weather[h * 4 + 1] = w[h].wd_from_deg;
-    L->weather[h * 4 + 2] = w[h].ffmc;
-    L->weather[h * 4 + 3] = w[h].bui;
+  std::vector<double> host((size_t)nh * 4 + (size_t)n_scen);
+  for (int64_t h = 0; h < nh; ++h) {
+    host[h * 4 + 0] = w[h].ws_kmh;
+    host[h * 4 + 1] = w[h].wd_from_deg;
+    host[h * 4 + 2] = w[h].ffmc;
+    host[h * 4 + 3] = w[h].bui;
   }
+  std::memcpy(host.data() + nh * 4, thr.data(), sizeof(uint64_t) * n_scen);
   // a fresh device copy: tables still being built from the old one keep it
   auto wd = std::make_shared<DevBuf>();
   int rc;
-  if ((rc = dalloc(ctx, *wd, sizeof(double) * 4 * n_hours))) return rc;
-  CK(cudaMemcpyAsync(wd->p, L->weather.data(), sizeof(double) * 4 * n_hours, cudaMemcpyHostToDevice,
+  if ((rc = dalloc(ctx, *wd, sizeof(double) * host.size()))) return rc;
+  CK(cudaMemcpyAsync(wd->p, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice,
                      ctx->stream));
+  L->n_hours = n_hours;
+  L->n_scen = n_scen;
+  L->weather = std::move(host);   // the same buffer: the copy's source stays alive
+  L->weather.resize((size_t)nh * 4);
   L->weather_dev = wd;
   L->table.reset();   // running simulations keep the table they started with
   return C2F_OK;
+}
+
+}  // namespace
+
+C2F_API int c2f_set_weather(c2f_ctx *ctx, int32_t landscape_id, int32_t n_hours,
+                            const c2f_weather_hour *w) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  return set_weather_impl(ctx, landscape_id, 1, n_hours, w, nullptr);
+}
+
+C2F_API int c2f_set_weather_scenarios(c2f_ctx *ctx, int32_t landscape_id, int32_t n_scenarios,
+                                      int32_t n_hours, const c2f_weather_hour *w,
+                                      const double *prob) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  return set_weather_impl(ctx, landscape_id, n_scenarios, n_hours, w, prob);
 }
 
 C2F_API int c2f_build_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p, int force) {
@@ -1255,8 +1334,9 @@ C2F_API int c2f_build_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_para
   return ensure_table(ctx, *L, key_of(p), force);
 }
 
-C2F_API int c2f_get_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p, int32_t hour,
-                        double *ros8, double *hros, int64_t *base) {
+C2F_API int c2f_get_ros_scenario(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p,
+                                 int32_t scenario, int32_t hour, double *ros8, double *hros,
+                                 int64_t *base) {
   if (!ctx) return C2F_EINVAL;
   LOCK;
   auto L = find_land(ctx, landscape_id);
@@ -1265,17 +1345,18 @@ C2F_API int c2f_get_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params
   int rc = validate_params(ctx, *L, p);
   if (rc) return rc;
   if (hour < 0 || hour >= p->hours) return fail(ctx, C2F_EINVAL, "hour out of range");
+  if (scenario < 0 || scenario >= L->n_scen) return fail(ctx, C2F_EINVAL, "scenario out of range");
   CK(cudaSetDevice(ctx->device));
   if ((rc = ensure_table(ctx, *L, key_of(p), 0))) return rc;
   const Table &T = *L->table;
   CK(cudaStreamWaitEvent(ctx->stream, T.ready, 0));
   const size_t n = (size_t)L->n;
+  const size_t row0 = ((size_t)scenario * T.key.hours + hour) * n;   // first row of (scenario, hour)
   if (base)
-    CK(cudaMemcpyAsync(base, T.base.as<int64_t>() + (size_t)hour * n * 8, n * 64,
-                       cudaMemcpyDeviceToHost, ctx->stream));
-  if (hros)
-    CK(cudaMemcpyAsync(hros, T.hros.as<double>() + (size_t)hour * n, n * 8, cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(base, T.base.as<int64_t>() + row0 * 8, n * 64, cudaMemcpyDeviceToHost,
                        ctx->stream));
+  if (hros)
+    CK(cudaMemcpyAsync(hros, T.hros.as<double>() + row0, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
   if (ros8) {
     DevBuf tmp;
     if ((rc = dalloc(ctx, tmp, n * 64))) return rc;
@@ -1285,7 +1366,7 @@ C2F_API int c2f_get_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params
     a.burnable = L->burnable.as<uint32_t>();
     a.rows = L->rows; a.cols = L->cols; a.wpr = L->wpr;
     a.cell = L->cell_prep.as<CellPrep>();
-    a.hour = T.hour_prep.as<HourPrep>();
+    a.hour = T.hour_prep.as<HourPrep>() + (size_t)scenario * T.prep_hours;
     a.hour0 = hour;
     a.pcf = p->m1_pc / 100.0;
     a.const_ros = p->const_ros;
@@ -1299,6 +1380,11 @@ C2F_API int c2f_get_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return C2F_OK;
+}
+
+C2F_API int c2f_get_ros(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p, int32_t hour,
+                        double *ros8, double *hros, int64_t *base) {
+  return c2f_get_ros_scenario(ctx, landscape_id, p, 0, hour, ros8, hros, base);
 }
 
 C2F_API int c2f_simulate(c2f_ctx *ctx, int32_t landscape_id, const c2f_sim_params *p,
@@ -1534,6 +1620,26 @@ C2F_API int c2f_get_counters(c2f_ctx *ctx, int32_t sim_id, int64_t *work, int32_
   if (work) CK(cudaMemcpyAsync(work, s->work.p, R * 8, cudaMemcpyDeviceToHost, st));
   if (ignited) CK(cudaMemcpyAsync(ignited, s->n_ignited.p, R * 4, cudaMemcpyDeviceToHost, st));
   if (ign_cell) CK(cudaMemcpyAsync(ign_cell, s->ign_cell.p, R * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return C2F_OK;
+}
+
+C2F_API int c2f_get_scenarios(c2f_ctx *ctx, int32_t sim_id, int32_t *scenario) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  auto s = find_sim(ctx, sim_id);
+  if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  if (!scenario) return fail(ctx, C2F_EINVAL, "scenario is NULL");
+  int rc = sim_ready(ctx, *s);
+  if (rc) return rc;
+  const size_t R = (size_t)s->p.n_replicas;
+  if (!s->scen.p) {   // one weather stream: every replica ran scenario 0
+    std::memset(scenario, 0, R * 4);
+    return C2F_OK;
+  }
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->read_stream;
+  CK(cudaMemcpyAsync(scenario, s->scen.p, R * 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return C2F_OK;
 }
