@@ -507,7 +507,10 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
     ecofs = A.ent_cofs + slot * (size_t)cap * 8;
   }
   int64_t *eP = A.ent_P + slot * (size_t)cap * 8;
-  __shared__ int32_t s_hits[WPC][64];
+  // next-event bytes are scanned four at a time when the list is word-aligned
+  // and its capacity a multiple of 4 (the runtime's lists are)
+  const bool words4 = (cap & 3) == 0 && (reinterpret_cast<uintptr_t>(enext) & 3u) == 0;
+  __shared__ int32_t s_hits[WPC][160];   // < 32 carried over + 128 gathered
   __shared__ uint32_t s_dbits[WPC][LAZY ? kWinRows * kWinWords / 32 : 1];   // chunks known done this hour
   __shared__ int32_t s_claim[WPC][LAZY ? 32 : 1];
   int32_t *hitbuf = s_hits[wib];
@@ -798,21 +801,43 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         int32_t nnew = cnt;
         bool ovf = false;
         // (A) send and receive: cells with a crossing at offset o.  Hits are
-        // gathered across the whole list, then each lane takes one hit cell:
+        // gathered across the whole list, four next-event bytes per lane (one
+        // 32-bit load, bytewise compares), then each lane takes one hit cell:
         // its 8 crossing offsets in one load, every axis crossing at o handled
         // in turn (targets tested, ignited, appended by ballot + popc).
-        int32_t hbase = 0;   // hits gathered so far in the buffer
-        for (int32_t b0 = 0; b0 < cnt || hbase > 0; b0 += 32) {
-          if (b0 < cnt) {
-            const int32_t e = b0 + lane;
-            const uint32_t nxe = (e < cnt) ? (uint32_t)enext[e] : kNone;
-            const bool hit = nxe == o;
-            if (!hit) lmin = min(lmin, nxe);
-            const uint32_t hits = __ballot_sync(FULL, hit);
-            if (hit) hitbuf[hbase + __popc(hits & lt)] = e;
-            hbase += __popc(hits);
+        int32_t hbase = 0;      // hits gathered so far in the buffer
+        uint32_t lmin4 = ~0u;   // bytewise minimum of the next offsets that are not hits
+        int32_t b0 = 0;
+        while (b0 < cnt || hbase > 0) {
+          if (b0 < cnt && hbase < 32) {
+            const int32_t e0 = b0 + 4 * lane;
+            uint32_t nx4 = ~0u;
+            if (e0 < cnt) {
+              if (words4) {   // the word lies inside the list
+                nx4 = *reinterpret_cast<const uint32_t *>(enext + e0);
+              } else {
+                nx4 = 0u;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) nx4 |= (e0 + q < cnt ? (uint32_t)enext[e0 + q] : 0xFFu) << (8 * q);
+              }
+              if (cnt - e0 < 4) nx4 |= ~0u << (8 * (cnt - e0));   // entries past the end: none
+            }
+            const uint32_t eq = __vcmpeq4(nx4, o * 0x01010101u);   // 0xFF where the offset is o
+            lmin4 = __vminu4(lmin4, nx4 | eq);
+            const uint32_t hb = eq & 0x01010101u;
+            const uint32_t h4 = (hb | (hb >> 7) | (hb >> 14) | (hb >> 21)) & 0xFu;
+            if (__any_sync(FULL, h4 != 0u)) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const bool hit = (h4 >> q) & 1u;
+                const uint32_t hits = __ballot_sync(FULL, hit);
+                if (hit) hitbuf[hbase + __popc(hits & lt)] = e0 + q;
+                hbase += __popc(hits);
+              }
+            }
             __syncwarp();
-            if (hbase < 32 && b0 + 32 < cnt) continue;   // gather a full round first
+            b0 += 128;
+            if (hbase < 32 && b0 < cnt) continue;   // gather a full round first
           }
           const int32_t take_n = min(hbase, 32);
           const int32_t ent = lane < take_n ? hitbuf[lane] : -1;
@@ -869,10 +894,18 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           // drop the processed round from the buffer
           __syncwarp();
           const int32_t rest = hbase - take_n;
-          if (lane < rest) hitbuf[lane] = hitbuf[take_n + lane];
-          __syncwarp();
+          for (int32_t i0 = 0; i0 < rest; i0 += 32) {
+            const int32_t v = (i0 + lane < rest) ? hitbuf[take_n + i0 + lane] : 0;
+            __syncwarp();
+            if (i0 + lane < rest) hitbuf[i0 + lane] = v;
+            __syncwarp();
+          }
           hbase = rest;
-          if (b0 >= cnt && hbase == 0) break;
+        }
+        {
+          uint32_t m = __vminu4(lmin4, lmin4 >> 16);
+          m = __vminu4(m, m >> 8);
+          lmin = min(lmin, m & 0xFFu);
         }
         if (__any_sync(FULL, ovf)) { status = 1; break; }
         __syncwarp();
