@@ -294,14 +294,18 @@ __device__ __forceinline__ int64_t axis_len(const SimJob &J, int k) {
   return (k & 1) ? J.d_diag : J.d_orth;
 }
 
-// smallest n >= 1 with n * inc >= rem, given that it is at most a few dozen
+// smallest n >= 1 with n * inc >= rem, for callers that know 64 * inc >= rem
+// (a crossing within the hour: at most 60 periods).  Six halving steps of
+// exact int64 products; a conversion of int64 operands to floating point costs
+// several times more on this GPU.
 __device__ __forceinline__ int32_t ceil_div_small(int64_t rem, int64_t inc) {
-  const float q = __fdividef((float)rem, (float)inc);   // a first guess; the loops make n exact
-  int32_t n = (q < 4096.0f) ? (int32_t)ceilf(q) : 4096;
-  if (n < 1) n = 1;
-  while ((int64_t)n * inc < rem) ++n;
-  while (n > 1 && (int64_t)(n - 1) * inc >= rem) --n;
-  return n;
+  int32_t n = 0;   // n * inc < rem, or n = 0
+#pragma unroll
+  for (int b = 5; b >= 0; --b) {
+    const int32_t t = n + (1 << b);
+    if ((int64_t)t * inc < rem) n = t;
+  }
+  return n + 1;
 }
 
 // receive test of a messaged Available cell (Sec. 3.1): HROS * f > threshold

@@ -361,10 +361,14 @@ __device__ inline float noise_factor(uint64_t seed, uint32_t replica, uint32_t c
   return fexp(__fmul_rn(sigma, z));
 }
 
-// the perturbation as a 32.32 fixed-point multiplier: exact, since f >= 2^-9
-// has a binary32 significand whose scaled value is an integer
+// the perturbation as a 32.32 fixed-point multiplier f 2^32: exact, since
+// f >= 2^-9 has a binary32 significand whose scaled value is an integer.  Built
+// from the bits (significand shifted by the exponent) rather than by a
+// float-to-int64 conversion, which is slow on this GPU.
 __device__ __forceinline__ uint64_t noise_fixed(float f) {
-  return (uint64_t)__float2ull_rn(__fmul_rn(f, 4294967296.0f));
+  const uint32_t b = __float_as_uint(f);
+  const uint64_t m = (uint64_t)((b & 0x7FFFFFu) | 0x800000u);
+  return m << ((int)(b >> 23) - 118);   // 2^(e - 127 - 23 + 32), e >= 118 for f >= 2^-9
 }
 
 // per-period increment (base * F + 2^31) >> 32, capped at the axis length
