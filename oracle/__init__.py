@@ -290,6 +290,52 @@ class ScenarioOracle:
             o.close()
 
 
+# ---------------------------------------------------------------- scar comparison
+# Sec. 4.1: two simulators' fire scars X^t, Y^t (0-1 matrices, 1 = burned by
+# the end of period t) are compared by the mean squared error, the structural
+# similarity SSIM of Wang et al. (2004), and, for the final scars, the norm of
+# X - Y.  The paper prints SSIM's second denominator factor as
+# mu_X^2 + mu_Y^2 + C_2; it is read here as Wang et al.'s sigma_X^2 + sigma_Y^2
+# + C_2 (with the printed form SSIM(X, X) would not be 1).  The statistics are
+# Wang et al.'s single-window ones over the whole matrix: means, standard
+# deviations and covariance with the 1/(N - 1) normalisation, C_1 = (K_1 L)^2,
+# C_2 = (K_2 L)^2 with K_1 = 0.01, K_2 = 0.03 and dynamic range L = 1; the norm
+# is the Frobenius norm.
+SSIM_C1 = (0.01 * 1.0) ** 2
+SSIM_C2 = (0.03 * 1.0) ** 2
+
+
+def scar_at_hour(ign_steps, hour: int, periods_per_hour: int) -> np.ndarray:
+    """X^t for t = end of weather hour `hour`: cells ignited at a step <= (hour+1) sph."""
+    s = np.asarray(ign_steps)
+    return ((s >= 0) & (s <= (hour + 1) * periods_per_hour)).astype(np.float64)
+
+
+def scar_mse(x, y) -> float:
+    """MSE(X, Y) = (1 / nm) sum_ij |X_ij - Y_ij|^2 (Sec. 4.1)."""
+    d = np.asarray(x, dtype=np.float64) - np.asarray(y, dtype=np.float64)
+    return float(np.mean(np.abs(d) ** 2))
+
+
+def scar_ssim(x, y) -> float:
+    """SSIM(X, Y) = (2 mu_x mu_y + C1)(2 sigma_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(sigma_x^2 + sigma_y^2 + C2))."""
+    x = np.asarray(x, dtype=np.float64).ravel()
+    y = np.asarray(y, dtype=np.float64).ravel()
+    n = x.size
+    mx, my = x.mean(), y.mean()
+    vx = np.sum((x - mx) ** 2) / (n - 1)
+    vy = np.sum((y - my) ** 2) / (n - 1)
+    cxy = np.sum((x - mx) * (y - my)) / (n - 1)
+    return float(((2 * mx * my + SSIM_C1) * (2 * cxy + SSIM_C2)) /
+                 ((mx * mx + my * my + SSIM_C1) * (vx + vy + SSIM_C2)))
+
+
+def scar_dnorm(x, y) -> float:
+    """delta_norm = ||X - Y|| (Frobenius), for the final scars (Sec. 4.1)."""
+    d = np.asarray(x, dtype=np.float64) - np.asarray(y, dtype=np.float64)
+    return float(np.linalg.norm(d.ravel()))
+
+
 def burn_prob(scars) -> np.ndarray:
     """count[c] = number of replicas whose scar contains c (uint32)."""
     s = np.asarray(scars)
