@@ -24,6 +24,8 @@ Other workloads (one GPU; each prints its own JSON line):
   --workload large   4096^2 cells, 72 h with a 90-degree wind shift, 256 replicas.
   --workload scenarios  the 512^2 landscape under 8 weather scenarios x 24 h with
                      probabilities; each of 1000 replicas draws its scenario.
+  --workload compare the Sec. 4.1 scar comparison (hourly MSE / SSIM, final
+                     norm) of two 1000-replica runs of the 512^2 workload.
 """
 from __future__ import annotations
 
@@ -198,7 +200,10 @@ def run_ours(args, rank, world, local_rank):
     ctx = c2f.Context(local_rank)
     if args.frontier_threads:
         ctx.set_frontier_config(args.frontier_threads, args.smem_plane_bytes)
-    stream = torch.cuda.current_stream(dev)
+    # the context issues its work (K1, K4, uploads) on this stream and the
+    # timing events are recorded on it; frontier epochs run on the context's own
+    # epoch streams and are waited for on the host before a step's K4
+    stream = torch.cuda.Stream(dev)
     ctx.set_stream(stream.cuda_stream)
     lid = ctx.load_landscape(L.fuel, L.slope, L.aspect, cell_size=L.cell_size)
     ctx.set_weather(lid, w.weather)
@@ -721,6 +726,67 @@ def run_scenarios(args):
                               "note": "the 8 stacked tables built once; each step K2 + K3 + K4"}}
 
 
+def run_compare(args):
+    """Sec. 4.1 scar comparison: the 512^2 workload run with Eq. (1) and with the
+    centre-offset ellipse ray (1000 replicas each, ignition steps kept), then
+    hourly MSE / SSIM and the final scars' norm for every replica pair."""
+    import torch
+    import paper_1905_09317_gb300 as c2f
+    c2f.build()
+    w = S.config2()
+    L = w.landscape
+    rows, cols = L.fuel.shape
+    n = L.fuel.size
+    R, H = w.params["n_replicas"], w.params["hours"]
+    ctx = c2f.Context(0)
+    lid = ctx.load_landscape(L.fuel, L.slope, L.aspect, cell_size=L.cell_size)
+    ctx.set_weather(lid, w.weather)
+    out = c2f.OUT_SCARS | c2f.OUT_COUNTERS | c2f.OUT_IGN_STEPS
+    sx = ctx.simulate(lid, _params_of(c2f, w, ellipse_mode=0, outputs=out))
+    sy = ctx.simulate(lid, _params_of(c2f, w, ellipse_mode=1, outputs=out))
+    stream = torch.cuda.Stream()   # a real stream (the default one would read as NULL)
+    ctx.set_stream(stream.cuda_stream)
+    mse = torch.empty(R * H, dtype=torch.float64, device="cuda")
+    ssim = torch.empty(R * H, dtype=torch.float64, device="cuda")
+    dn = torch.empty(R, dtype=torch.float64, device="cuda")
+
+    def step():
+        ctx.compare_scars_device(sx, sy, mse.data_ptr(), ssim.data_ptr(), dn.data_ptr())
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    m = mse.view(R, H).cpu().numpy()
+    q = ssim.view(R, H).cpu().numpy()
+    ctx.close()
+    wpr = (cols + 31) // 32
+    # algorithmic bytes of one launch pair: both runs' ignition steps and bit
+    # planes read once, the metrics written once
+    by = 2 * R * n * 4 + 2 * R * rows * wpr * 4 + R * H * 16 + R * 8
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ach = by / (ms / 1e3) / 1e9
+    return {"metric": "replica-pairs/s", "value": R / (ms / 1e3), "unit": "replica-pairs/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "512x512 heterogeneous landscape, 24 h, 1000 replicas run with Eq. (1) "
+                                   "and with the centre-offset ellipse ray; hourly MSE and SSIM and the "
+                                   "final scars' norm per replica pair (Sec. 4.1)",
+                       "inputs": "2.1 GB of ignition steps and scar planes, larger than L2"},
+            "roofline": {"kernel": "k_compare_hours + k_compare_final", "bound": "hbm", "achieved": ach,
+                         "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "result": {"mse_final_mean": float(m[:, -1].mean()), "ssim_final_mean": float(q[:, -1].mean()),
+                       "mse_hour1_mean": float(m[:, 0].mean()), "ssim_hour1_mean": float(q[:, 0].mean())}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -742,7 +808,7 @@ def main():
     ap.add_argument("--serial", action="store_true",
                     help="one synchronous step at a time (no overlap of K1 with the previous frontier)")
     ap.add_argument("--workload", default="landscape",
-                    choices=["landscape", "batch", "serve", "large", "scenarios"])
+                    choices=["landscape", "batch", "serve", "large", "scenarios", "compare"])
     ap.add_argument("--tune-sample", type=int, default=4096, help="batch: autotuner replica sample")
     ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
@@ -752,7 +818,7 @@ def main():
     args = ap.parse_args()
     if args.workload != "landscape" and args.impl == "ours":
         fn = {"batch": run_batch, "serve": run_serve, "large": run_large,
-              "scenarios": run_scenarios}[args.workload]
+              "scenarios": run_scenarios, "compare": run_compare}[args.workload]
         print(json.dumps(fn(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -282,6 +282,32 @@ C2F_API int c2f_get_counters(c2f_ctx *ctx, int32_t sim_id, int64_t *work, int32_
  * memory; all 0 when the landscape had one weather stream). */
 C2F_API int c2f_get_scenarios(c2f_ctx *ctx, int32_t sim_id, int32_t *scenario);
 
+/* Fire-scar comparison of Sec. 4.1 between two finished simulations X and Y
+ * of the same grid shape and replica count, replica r of X against replica r
+ * of Y.  With X^t, Y^t the 0-1 scars at the end of weather hour t (cells
+ * ignited at a step <= (t+1)*60/minutes_per_step) and N = rows*cols:
+ *   mse[r*H + t]  = (1/N) sum |X^t - Y^t|^2;
+ *   ssim[r*H + t] = (2 mu_X mu_Y + C1)(2 sigma_XY + C2) /
+ *                   ((mu_X^2 + mu_Y^2 + C1)(sigma_X^2 + sigma_Y^2 + C2)),
+ *                   Wang et al.'s structural similarity over the whole grid:
+ *                   means, 1/(N-1) variances and covariance, C1 = 0.01^2,
+ *                   C2 = 0.03^2 (the paper prints the second denominator
+ *                   factor as mu_X^2 + mu_Y^2 + C2; read as Wang et al.'s);
+ *   dnorm[r]      = ||X - Y|| (Frobenius) of the final scars.
+ * H = hours of the simulations.  mse / ssim (n_replicas*H doubles) need both
+ * simulations to have kept ignition steps (C2F_OUT_IGN_STEPS) with equal
+ * hours (<= 8192) and minutes_per_step, and N >= 2; dnorm (n_replicas
+ * doubles) works from the scars alone.  Any output may be NULL.  Host memory,
+ * synchronous.  Errors: C2F_ENOTFOUND, C2F_EBUSY, C2F_EINVAL (shapes or
+ * counts differ, steps missing). */
+C2F_API int c2f_compare_scars(c2f_ctx *ctx, int32_t sim_x, int32_t sim_y, double *mse, double *ssim,
+                              double *dnorm);
+
+/* The same into device memory of the context's device; asynchronous on the
+ * context stream. */
+C2F_API int c2f_compare_scars_device(c2f_ctx *ctx, int32_t sim_x, int32_t sim_y, double *mse_dev,
+                                     double *ssim_dev, double *dnorm_dev);
+
 /* Initial burning-list capacity (entries per CTA) of the frontier kernel;
  * 0 = automatic.  A replica that outgrows it is re-run with a larger one, so
  * results never depend on this value (a tuning and test knob). */

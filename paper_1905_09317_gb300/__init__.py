@@ -117,6 +117,9 @@ _SIGS = [
     ("c2f_get_scars_at_hour", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     ("c2f_get_counters", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("c2f_get_scenarios", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    ("c2f_compare_scars", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("c2f_compare_scars_device", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                           C.c_void_p]),
     ("c2f_set_list_capacity", C.c_int, [C.c_void_p, C.c_int64]),
     ("c2f_set_frontier_config", C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
     ("c2f_autotune", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
@@ -337,6 +340,22 @@ class Context:
         out = np.empty(n_replicas, dtype=np.int32)
         self._check(self.lib.c2f_get_scenarios(self.h, int(sim_id), _ptr(out)))
         return out
+
+    def compare_scars(self, sim_x: int, sim_y: int, n_replicas: int, hours: int, hourly=True):
+        """Sec. 4.1 metrics: (mse (R, H), ssim (R, H), dnorm (R,)); hourly=False: dnorm only."""
+        mse = np.empty((n_replicas, hours), dtype=np.float64) if hourly else None
+        ssim = np.empty((n_replicas, hours), dtype=np.float64) if hourly else None
+        dn = np.empty(n_replicas, dtype=np.float64)
+        self._check(self.lib.c2f_compare_scars(self.h, int(sim_x), int(sim_y), _ptr(mse), _ptr(ssim),
+                                               _ptr(dn)))
+        return mse, ssim, dn
+
+    def compare_scars_device(self, sim_x: int, sim_y: int, mse_ptr: int, ssim_ptr: int,
+                             dnorm_ptr: int) -> None:
+        self._check(self.lib.c2f_compare_scars_device(self.h, int(sim_x), int(sim_y),
+                                                      C.c_void_p(mse_ptr or None),
+                                                      C.c_void_p(ssim_ptr or None),
+                                                      C.c_void_p(dnorm_ptr or None)))
 
     def set_list_capacity(self, cap: int) -> None:
         self._check(self.lib.c2f_set_list_capacity(self.h, int(cap)))

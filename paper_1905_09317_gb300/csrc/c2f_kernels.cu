@@ -7,6 +7,7 @@
 //   k_frontier    (K3)  Step 2 of Alg. 1 for whole replicas: send / receive /
 //                       burn-out per fire period, one CTA per replica
 //   k_burn_prob   (K4)  burn-probability counts over replicas
+//   k_compare_hours / k_compare_final   scar comparison metrics of Sec. 4.1
 // plus landscape set-up (burnable bit plane and list) and result export.
 //
 // Frontier semantics (Sec. 3.1, 3.4, A5; Alg. 1):
@@ -1070,6 +1071,106 @@ __global__ void k_scar_bytes(const uint32_t *__restrict__ planes, int32_t R, int
   const int64_t r = i / n, cell = i % n;
   const int32_t row = (int32_t)(cell / cols), col = (int32_t)(cell % cols);
   out[i] = (planes[(size_t)r * rows * wpr + (size_t)row * wpr + (col >> 5)] >> (col & 31)) & 1u;
+}
+
+// ------------------------------------------------------------------ scar comparison
+// Sec. 4.1 compares two runs' scars X^t, Y^t (0-1 grids, 1 = ignited by the
+// end of weather hour t) by MSE, SSIM and, for the final scars, ||X - Y||.
+// For 0-1 grids all three are functions of a = |X|, b = |Y|, c = |X and Y|
+// and N: sum |X - Y|^2 = a + b - 2c; the means are a/N, b/N; the 1/(N-1)
+// variances a(N-a)/(N(N-1)), b(N-b)/(N(N-1)); the covariance
+// (cN - ab)/(N(N-1)).  SSIM takes Wang et al.'s C1 = 0.01^2, C2 = 0.03^2
+// (dynamic range 1) and sigma_X^2 + sigma_Y^2 + C2 in its denominator.
+constexpr double kSsimC1 = 0.0001;   // (0.01 * 1)^2
+constexpr double kSsimC2 = 0.0009;   // (0.03 * 1)^2
+
+__device__ inline void scar_metrics(double a, double b, double c, double n, double *mse,
+                                    double *ssim) {
+  *mse = (a + b - 2.0 * c) / n;
+  const double mx = a / n, my = b / n;
+  const double nn1 = n * (n - 1.0);
+  const double vx = a * (n - a) / nn1, vy = b * (n - b) / nn1;
+  const double cxy = (c * n - a * b) / nn1;
+  *ssim = ((2.0 * mx * my + kSsimC1) * (2.0 * cxy + kSsimC2)) /
+          ((mx * mx + my * my + kSsimC1) * (vx + vy + kSsimC2));
+}
+
+// weather hour in which ignition step s falls (step 0 = the ignition, hour 0);
+// -1 for a cell that never ignites
+__device__ __forceinline__ int32_t ign_hour(int32_t s, int32_t sph) {
+  return s < 0 ? -1 : (s == 0 ? 0 : (s - 1) / sph);
+}
+
+__device__ __forceinline__ void count_cell(int32_t sx, int32_t sy, int32_t sph, int32_t H,
+                                           uint32_t *hist) {
+  const int32_t hx = ign_hour(sx, sph), hy = ign_hour(sy, sph);
+  if (hx >= 0 && hx < H) atomicAdd(&hist[hx], 1u);
+  if (hy >= 0 && hy < H) atomicAdd(&hist[H + hy], 1u);
+  if (hx >= 0 && hy >= 0 && max(hx, hy) < H) atomicAdd(&hist[2 * H + max(hx, hy)], 1u);
+}
+
+// One CTA per replica: histograms of the ignition hours of X, of Y and of the
+// later of the two (cells both runs ignite), then prefix sums over hours give
+// a, b, c of every hour's scars; one pass over the two ignition-step arrays
+// (streamed, 16-byte loads when the rows are aligned).  Dynamic shared
+// memory: 3 H counters.
+__global__ void k_compare_hours(const int32_t *__restrict__ step_x, const int32_t *__restrict__ step_y,
+                                int64_t n, int32_t sph, int32_t H, double *mse, double *ssim) {
+  extern __shared__ uint32_t hist[];
+  const int32_t r = blockIdx.x;
+  for (int32_t i = threadIdx.x; i < 3 * H; i += blockDim.x) hist[i] = 0u;
+  __syncthreads();
+  const int32_t *x = step_x + (size_t)r * n;
+  const int32_t *y = step_y + (size_t)r * n;
+  if ((n & 3) == 0 && ((reinterpret_cast<uintptr_t>(step_x) | reinterpret_cast<uintptr_t>(step_y)) & 15u) == 0) {
+    const int4 *x4 = reinterpret_cast<const int4 *>(x);
+    const int4 *y4 = reinterpret_cast<const int4 *>(y);
+    for (int64_t i = threadIdx.x; i < n / 4; i += blockDim.x) {
+      const int4 a = __ldcs(x4 + i), b = __ldcs(y4 + i);
+      // a cell that neither run ignites (the common case) costs two compares
+      if ((a.x & a.y & a.z & a.w & b.x & b.y & b.z & b.w) < 0) continue;
+      count_cell(a.x, b.x, sph, H, hist);
+      count_cell(a.y, b.y, sph, H, hist);
+      count_cell(a.z, b.z, sph, H, hist);
+      count_cell(a.w, b.w, sph, H, hist);
+    }
+  } else {
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) count_cell(__ldcs(x + i), __ldcs(y + i), sph, H, hist);
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {   // counts of scars at hour t: inclusive prefix sums
+    uint32_t *h = hist + threadIdx.x * H;
+    uint32_t acc = 0u;
+    for (int32_t t = 0; t < H; ++t) { acc += h[t]; h[t] = acc; }
+  }
+  __syncthreads();
+  for (int32_t t = threadIdx.x; t < H; t += blockDim.x) {
+    double m, q;
+    scar_metrics((double)hist[t], (double)hist[H + t], (double)hist[2 * H + t], (double)n, &m, &q);
+    if (mse) mse[(size_t)r * H + t] = m;
+    if (ssim) ssim[(size_t)r * H + t] = q;
+  }
+}
+
+// ||X - Y|| of the final scars from the bit planes: one CTA per replica
+// (256 threads), popcounts of X, Y and X and Y over the replica's words.
+__global__ void k_compare_final(const uint32_t *__restrict__ px, const uint32_t *__restrict__ py,
+                                int64_t pw, double *dnorm) {
+  __shared__ unsigned long long part[8];
+  const int32_t r = blockIdx.x;
+  const uint32_t *x = px + (size_t)r * pw;
+  const uint32_t *y = py + (size_t)r * pw;
+  unsigned long long d = 0;   // sum |X - Y|^2 = |X xor Y|
+  for (int64_t i = threadIdx.x; i < pw; i += blockDim.x) d += (unsigned)__popc(__ldcs(x + i) ^ __ldcs(y + i));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    dnorm[r] = sqrt((double)t);
+  }
 }
 
 }  // namespace c2f

@@ -65,6 +65,8 @@ __global__ void k_burn_prob(const uint32_t *, int32_t, int32_t, int32_t, int32_t
                             uint32_t *, int32_t);
 __global__ void k_scar_bytes(const uint32_t *, int32_t, int32_t, int32_t, int32_t, uint8_t *);
 __global__ void k_scar_at_step(const int32_t *, int64_t, int32_t, uint8_t *);
+__global__ void k_compare_hours(const int32_t *, const int32_t *, int64_t, int32_t, int32_t, double *, double *);
+__global__ void k_compare_final(const uint32_t *, const uint32_t *, int64_t, double *);
 cudaError_t init_device_constants(int device);
 }  // namespace c2f
 
@@ -1604,6 +1606,83 @@ C2F_API int c2f_get_scars_at_hour(c2f_ctx *ctx, int32_t sim_id, int32_t hour, ui
   CK(cudaMemcpyAsync(scars, tmp.p, (size_t)total, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return C2F_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+constexpr int32_t kCompareMaxHours = 8192;   // 3 H counters in shared memory
+
+// Sec. 4.1 metrics of two finished simulations on st: hourly MSE / SSIM
+// ([R][H], from the ignition steps) and the final scars' norm ([R], from the
+// bit planes) into device memory.
+int compare_launch(c2f_ctx *ctx, int32_t sim_x, int32_t sim_y, double *mse, double *ssim,
+                   double *dnorm, cudaStream_t st) {
+  auto X = find_sim(ctx, sim_x), Y = find_sim(ctx, sim_y);
+  if (!X || !Y) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", !X ? sim_x : sim_y);
+  int rc;
+  if ((rc = sim_ready(ctx, *X)) || (rc = sim_ready(ctx, *Y))) return rc;
+  if (X->rows != Y->rows || X->cols != Y->cols || X->p.n_replicas != Y->p.n_replicas)
+    return fail(ctx, C2F_EINVAL, "simulations differ in grid shape or replica count");
+  const int32_t R = X->p.n_replicas;
+  if (mse || ssim) {
+    if (!X->ign_step.p || !Y->ign_step.p)
+      return fail(ctx, C2F_EINVAL, "hourly metrics need ignition steps (C2F_OUT_IGN_STEPS) in both");
+    if (X->p.hours != Y->p.hours || X->p.minutes_per_step != Y->p.minutes_per_step)
+      return fail(ctx, C2F_EINVAL, "simulations differ in hours or minutes_per_step");
+    if (X->p.hours > kCompareMaxHours) return fail(ctx, C2F_EINVAL, "at most %d hours", kCompareMaxHours);
+    if (X->n < 2) return fail(ctx, C2F_EINVAL, "SSIM needs at least 2 cells");
+  }
+  CK(cudaSetDevice(ctx->device));
+  if (mse || ssim) {
+    const int32_t H = X->p.hours;
+    const size_t smem = sizeof(uint32_t) * 3 * (size_t)H;
+    if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_compare_hours, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)smem));
+    k_compare_hours<<<R, 256, smem, st>>>(X->ign_step.as<int32_t>(), Y->ign_step.as<int32_t>(), X->n,
+                                          60 / X->p.minutes_per_step, H, mse, ssim);
+    CKL("k_compare_hours");
+  }
+  if (dnorm) {
+    k_compare_final<<<R, 256, 0, st>>>(X->ign_plane.as<uint32_t>(), Y->ign_plane.as<uint32_t>(),
+                                       (int64_t)X->rows * X->wpr, dnorm);
+    CKL("k_compare_final");
+  }
+  return C2F_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+C2F_API int c2f_compare_scars(c2f_ctx *ctx, int32_t sim_x, int32_t sim_y, double *mse, double *ssim,
+                              double *dnorm) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  auto X = find_sim(ctx, sim_x);
+  if (!X) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_x);
+  const size_t RH = (size_t)X->p.n_replicas * X->p.hours, R = (size_t)X->p.n_replicas;
+  cudaStream_t st = ctx->read_stream;
+  DevBuf dm, ds, dd;
+  int rc;
+  if (mse && (rc = dalloc_on(ctx, dm, RH * 8, st))) return rc;
+  if (ssim && (rc = dalloc_on(ctx, ds, RH * 8, st))) return rc;
+  if (dnorm && (rc = dalloc_on(ctx, dd, R * 8, st))) return rc;
+  if ((rc = compare_launch(ctx, sim_x, sim_y, dm.as<double>(), ds.as<double>(), dd.as<double>(), st)))
+    return rc;
+  if (mse) CK(cudaMemcpyAsync(mse, dm.p, RH * 8, cudaMemcpyDeviceToHost, st));
+  if (ssim) CK(cudaMemcpyAsync(ssim, ds.p, RH * 8, cudaMemcpyDeviceToHost, st));
+  if (dnorm) CK(cudaMemcpyAsync(dnorm, dd.p, R * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return C2F_OK;
+}
+
+C2F_API int c2f_compare_scars_device(c2f_ctx *ctx, int32_t sim_x, int32_t sim_y, double *mse_dev,
+                                     double *ssim_dev, double *dnorm_dev) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  return compare_launch(ctx, sim_x, sim_y, mse_dev, ssim_dev, dnorm_dev, ctx->stream);
 }
 
 C2F_API int c2f_get_counters(c2f_ctx *ctx, int32_t sim_id, int64_t *work, int32_t *ignited,
