@@ -715,85 +715,81 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         __syncwarp();
       }
 
-      // ---- hour boundary (i): drop Burned cells and cells with no open axis;
-      // prefetch the kept cells' table rows for (ii)
-      cnt = compact(cnt, baseh);
-      // ---- hour boundary (ii): the perturbation of every listed cell for this
-      // hour, one lane per cell, parked as a 32.32 multiplier in the cell's
-      // crossing-offset slot (rewritten below)
-      for (int32_t b0 = 0; b0 < cnt; b0 += 32) {
-        const int32_t e = b0 + lane;
-        if (lazy) {   // this hour's rows of the listed cells
-          const uint32_t rc = e < cnt ? erc[e] : 0u;
-          ensure(h, e < cnt, (int32_t)(rc >> 16), (int32_t)(rc & 0xFFFFu), 1u);
-        }
-        if (e < cnt) {
-          const uint32_t rc = erc[e];
-          const int64_t cell = (int64_t)(rc >> 16) * cols + (rc & 0xFFFFu);
-          const float f = noise_factor(seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, sigma);
-          *reinterpret_cast<uint64_t *>(ecofs + (size_t)e * 8) = noise_fixed(f);
-        }
-      }
-      __syncwarp();
-      if (status) break;
-      // ---- hour boundary (iii): crossing periods of this hour, a group per cell,
-      // four cells per group in flight
-      for (int32_t b0 = 0; b0 < cnt; b0 += 16) {
-        uint32_t rcu[4], mu[4], masku[4];
-        int64_t Pu[4], bku[4];
-        uint64_t Fu[4];
-        bool actu[4], openu[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int32_t e = b0 + 4 * u + grp;
-          actu[u] = e < cnt;
-          rcu[u] = actu[u] ? erc[e] : 0u;
-          mu[u] = actu[u] ? emask[e] : 0u;
-          Pu[u] = actu[u] ? eP[(size_t)e * 8 + k] : 0;
-          Fu[u] = actu[u] ? *reinterpret_cast<const uint64_t *>(ecofs + (size_t)e * 8) : 0ull;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int32_t cr = (int32_t)(rcu[u] >> 16), cc = (int32_t)(rcu[u] & 0xFFFFu);
-          bool open = actu[u] && ((mu[u] >> k) & 1u);
-          if (open) open = pl.avail(cr + axis_dr(k), cc + axis_dc(k));
-          openu[u] = open;
-          bku[u] = open ? __ldcg(baseh + ((int64_t)cr * cols + cc) * 8 + k) : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) masku[u] = group_bits(openu[u]);
-        __syncwarp();   // every lane has read its cell's multiplier before the slot is rewritten
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int32_t e = b0 + 4 * u + grp;
-          const int32_t cr = (int32_t)(rcu[u] >> 16), cc = (int32_t)(rcu[u] & 0xFFFFu);
+      // ---- hour boundary, one lane per listed cell, 32 cells at a time:
+      // (i) drop Burned cells and cells with no open axis (order kept);
+      // (ii) the cell's perturbation for this hour; (iii) on every open axis,
+      // the crossing period of this hour, or the progress carried to the next.
+      // The eight axes of a cell are independent chains in one lane.
+      {
+        int32_t out = 0;
+        for (int32_t b0 = 0; b0 < cnt; b0 += 32) {
+          const int32_t e = b0 + lane;
+          bool keep = false;
+          uint32_t rc = 0u, m = 0u;
+          if (e < cnt) {
+            rc = erc[e];
+            m = emask[e];
+            keep = m != 0u && !pl.burned((int32_t)(rc >> 16), (int32_t)(rc & 0xFFFFu));
+          }
+          const int32_t cr = (int32_t)(rc >> 16), cc = (int32_t)(rc & 0xFFFFu);
+          if (lazy) ensure(h, keep, cr, cc, 1u);   // this hour's row of the cell
           const int64_t cell = (int64_t)cr * cols + cc;
-          uint32_t cof = kNone;
-          int64_t P = Pu[u];
-          bool dying = false;
-          if (openu[u]) {
-            const int64_t inc = apply_noise(bku[u], Fu[u], dk);
-            const int64_t rem = dk - P;
-            if (inc > 0 && inc * sph >= rem) cof = (uint32_t)(ceil_div_small(rem, inc) - 1);
-            else P += inc * sph;
-          }
-          if (actu[u] && delta > 0.0) {
-            const double f = (double)Fu[u] * 0x1p-32;   // exact: F = f 2^32 for a binary32 f
-            if (__dmul_rn(__ldcg(hrosh + cell), f) < delta) {    // A5 (i)
-              if (k == 0) dying = pl.burn(cr, cc);
-              if (cof != 0) cof = kNone;   // still sends in period s0, Burned after it
+          int64_t P[8], bk[8];
+          if (keep) {   // progress and rate row: 64 bytes each, four 16-byte loads
+            const longlong2 *pp = reinterpret_cast<const longlong2 *>(eP + (size_t)e * 8);
+            const longlong2 *rw = reinterpret_cast<const longlong2 *>(baseh + cell * 8);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const longlong2 a = pp[j], b = __ldcg(rw + j);
+              P[2 * j] = a.x; P[2 * j + 1] = a.y;
+              bk[2 * j] = b.x; bk[2 * j + 1] = b.y;
             }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) P[q] = bk[q] = 0;
           }
-          const uint32_t nx = group_min(cof);
-          if (actu[u]) {
-            ecofs[(size_t)e * 8 + k] = (uint8_t)cof;
-            eP[(size_t)e * 8 + k] = P;
-            if (k == 0) { emask[e] = (uint8_t)masku[u]; enext[e] = (uint8_t)nx; }
+          const float f = keep ? noise_factor(seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, sigma) : 1.0f;
+          const uint64_t F = noise_fixed(f);
+          // A5 (i): a cell whose HROS * f is below delta still sends in the
+          // first period of the hour and is Burned after it
+          const bool dies = keep && delta > 0.0 && __dmul_rn(__ldcg(hrosh + cell), (double)f) < delta;
+          uint32_t mask = 0u;
+          uint64_t c8 = ~0ull;   // crossing offsets, one byte per axis (kNone: none this hour)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const bool open = keep && ((m >> q) & 1u) && pl.avail(cr + axis_dr(q), cc + axis_dc(q));
+            const int64_t dq = (q & 1) ? J.d_diag : J.d_orth;
+            uint32_t cof = kNone;
+            if (open) {
+              mask |= 1u << q;
+              const int64_t inc = apply_noise(bk[q], F, dq);
+              const int64_t rem = dq - P[q];
+              if (inc > 0 && inc * sph >= rem) cof = (uint32_t)(ceil_div_small(rem, inc) - 1);
+              else P[q] += inc * sph;
+            }
+            if (dies && cof != 0u) cof = kNone;
+            c8 = (c8 & ~(0xFFull << (8 * q))) | ((uint64_t)cof << (8 * q));
           }
+          const bool dying = dies && pl.burn(cr, cc);
+          const uint32_t bal = __ballot_sync(FULL, keep);
+          const int32_t pos = out + __popc(bal & lt);
+          __syncwarp();   // every lane has read its entry before any slot is rewritten
+          if (keep) {
+            erc[pos] = rc;
+            emask[pos] = (uint8_t)mask;
+            enext[pos] = (uint8_t)min_byte8(c8);
+            *reinterpret_cast<uint64_t *>(ecofs + (size_t)pos * 8) = c8;
+            longlong2 *pp = reinterpret_cast<longlong2 *>(eP + (size_t)pos * 8);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) pp[j] = make_longlong2(P[2 * j], P[2 * j + 1]);
+          }
+          out += __popc(bal);
           burned += __popc(__ballot_sync(FULL, dying));
+          __syncwarp();
         }
+        cnt = out;
       }
-      __syncwarp();
+      if (status) break;
 
       // ---- periods of this hour at which some axis reaches a centre
       int32_t s = s0;
