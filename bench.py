@@ -200,6 +200,14 @@ def run_ours(args, rank, world, local_rank):
     ctx = c2f.Context(local_rank)
     if args.frontier_threads:
         ctx.set_frontier_config(args.frontier_threads, args.smem_plane_bytes)
+    pipe_warps = None
+    if not args.frontier_threads and not args.serial:
+        # pipelined steps: size each warp's shared memory for one warp per SM
+        # more than a step's own replicas need, so that the next step's
+        # frontier starts beside the current one's last replicas
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        pipe_warps = -(-R // sms) + 1
+        ctx.set_frontier_config(32, pipe_warps)
     # the context issues its work (K1, K4, uploads) on this stream and the
     # timing events are recorded on it; frontier epochs run on the context's own
     # epoch streams and are waited for on the host before a step's K4
@@ -274,10 +282,14 @@ def run_ours(args, rank, world, local_rank):
         ctx.release(s)
     kt_alone = None
     if not args.serial:   # a few steps one at a time (outside the timing): each kernel alone
+        if pipe_warps:
+            ctx.set_frontier_config(32, 1)   # the default sizing for a launch that runs alone
         ctx.kernel_times()
         for _ in range(3):
             ctx.release(step())
         kt_alone = ctx.kernel_times()
+        if pipe_warps:
+            ctx.set_frontier_config(32, pipe_warps)
     ctx.profile(False)
 
     ms_max = max_over_ranks(ms, world, dev)
@@ -356,7 +368,10 @@ def run_ours(args, rank, world, local_rank):
                        "schedule": "serial" if args.serial else
                        f"pipelined, {max(2, args.depth)} steps in flight: the next steps' tables (K1) "
                        "overlap the current frontier (K3)",
-                       "tables": "on demand in K3" if args.lazy_tables else "K1, every row"},
+                       "tables": "on demand in K3" if args.lazy_tables else "K1, every row",
+                       "frontier_smem": (f"sized for {pipe_warps} warps per SM (one more than a step's "
+                                         "replicas need: the next step's frontier starts beside it)")
+                       if pipe_warps else "library default"},
             "replicas_per_s": R * world * args.steps / (ms_max / 1e3),
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in fam.items()},
             "roofline": roof,

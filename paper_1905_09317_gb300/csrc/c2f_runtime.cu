@@ -475,6 +475,8 @@ std::shared_ptr<Sim> find_sim(c2f_ctx *ctx, int32_t id) {
   return it == ctx->sims.end() ? nullptr : it->second;
 }
 
+constexpr int64_t kCoRunSmem = 12 * 1024;
+
 int64_t default_cap(const c2f_ctx *ctx, const Landscape &L) {
   if (ctx->cap_override > 0) return std::min<int64_t>(L.n, ctx->cap_override);
   const int64_t c = std::max<int64_t>(1024, 2 * (int64_t)(L.rows + L.cols));
@@ -603,19 +605,23 @@ int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, i
     const int64_t warps_per_sm =
         attempt == 0 ? (ctx->warps_per_sm > 0 ? (int64_t)ctx->warps_per_sm : std::min<int64_t>(want, 8))
                      : std::min<int64_t>(want, 2);
-    // per CTA: 1 KB reserved by the system and about 1 KB of static shared memory per warp
-    const int64_t per_warp = ((int64_t)ctx->smem_per_sm - (1024 * warps_per_sm) / wpc - 1024 * warps_per_sm) /
-                             warps_per_sm;
+    // per CTA: 1 KB reserved by the system and about 1.3 KB of static shared
+    // memory per warp; with the default sizing, kCoRunSmem per SM is left for
+    // kernels that run beside the frontier (the next step's or request's table
+    // build, burn counts), whose CTAs could not be placed on a full SM
+    const int64_t reserve = (attempt == 0 && ctx->warps_per_sm == 0) ? kCoRunSmem : 0;
+    const int64_t per_warp = ((int64_t)ctx->smem_per_sm - reserve - (1024 * warps_per_sm) / wpc -
+                              1300 * warps_per_sm) / warps_per_sm;
     const int64_t room = (per_warp - 2 * (int64_t)kWinRows * kWinWords * 4 - 512) / 14;
     win_cap = std::min<int64_t>(cap, std::max<int64_t>(256, room & ~int64_t(63)));
     if (attempt > 0) win_cap = std::max<int64_t>(256, room & ~int64_t(63));
   }
   const int64_t budget = (int64_t)ctx->smem_optin - 2048;
   const int64_t win_words = 2 * (int64_t)kWinRows * kWinWords + win_cap * 7 / 2;
-  // shared-memory lists only when they hold at least half the default capacity:
-  // smaller ones overflow on large fires and those replicas run twice
+  // shared-memory lists only when they hold at least 40 % of the default
+  // capacity: smaller ones overflow on large fires and those replicas run twice
   const bool use_win = ctx->window_smem && win_words * 4 * wpc <= budget &&
-                       (attempt == 0 ? (ctx->warps_per_sm > 0 || 2 * win_cap >= cap) : win_cap >= cap);
+                       (attempt == 0 ? (ctx->warps_per_sm > 0 || 5 * win_cap >= 2 * cap) : win_cap >= cap);
   if (use_win) cap = win_cap;
   const int64_t warp_words = use_win ? win_words : 0;
   F.kern = use_win ? (wpc == 1 ? k_frontier_w1 : wpc == 2 ? k_frontier_w2 : k_frontier_w4)
