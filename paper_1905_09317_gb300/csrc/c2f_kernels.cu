@@ -1105,13 +1105,27 @@ __device__ __forceinline__ void count_cell(int32_t sx, int32_t sy, int32_t sph, 
   if (hx >= 0 && hy >= 0 && max(hx, hy) < H) atomicAdd(&hist[2 * H + max(hx, hy)], 1u);
 }
 
+__device__ __forceinline__ void count_cells4(const int4 &a, const int4 &b, int32_t sph, int32_t H,
+                                             uint32_t *hist) {
+  // four cells that neither run ignites (the common case) cost one test
+  if ((a.x & a.y & a.z & a.w & b.x & b.y & b.z & b.w) < 0) return;
+  count_cell(a.x, b.x, sph, H, hist);
+  count_cell(a.y, b.y, sph, H, hist);
+  count_cell(a.z, b.z, sph, H, hist);
+  count_cell(a.w, b.w, sph, H, hist);
+}
+
 // One CTA per replica: histograms of the ignition hours of X, of Y and of the
 // later of the two (cells both runs ignite), then prefix sums over hours give
-// a, b, c of every hour's scars; one pass over the two ignition-step arrays
-// (streamed, 16-byte loads when the rows are aligned).  Dynamic shared
-// memory: 3 H counters.
-__global__ void k_compare_hours(const int32_t *__restrict__ step_x, const int32_t *__restrict__ step_y,
-                                int64_t n, int32_t sph, int32_t H, double *mse, double *ssim) {
+// a, b, c of every hour's scars; one pass over the two ignition-step arrays,
+// streamed with 16-byte loads (when the rows are aligned), four per array in
+// flight per thread.  128-thread CTAs so that every replica of a launch is
+// resident at once.  Dynamic shared memory: 3 H counters.  The final scars are
+// the scars of the last hour, so ||X - Y|| comes from the same counts.
+__global__ void __launch_bounds__(128) k_compare_hours(const int32_t *__restrict__ step_x,
+                                                       const int32_t *__restrict__ step_y, int64_t n,
+                                                       int32_t sph, int32_t H, double *mse, double *ssim,
+                                                       double *dnorm) {
   extern __shared__ uint32_t hist[];
   const int32_t r = blockIdx.x;
   for (int32_t i = threadIdx.x; i < 3 * H; i += blockDim.x) hist[i] = 0u;
@@ -1121,15 +1135,19 @@ __global__ void k_compare_hours(const int32_t *__restrict__ step_x, const int32_
   if ((n & 3) == 0 && ((reinterpret_cast<uintptr_t>(step_x) | reinterpret_cast<uintptr_t>(step_y)) & 15u) == 0) {
     const int4 *x4 = reinterpret_cast<const int4 *>(x);
     const int4 *y4 = reinterpret_cast<const int4 *>(y);
-    for (int64_t i = threadIdx.x; i < n / 4; i += blockDim.x) {
-      const int4 a = __ldcs(x4 + i), b = __ldcs(y4 + i);
-      // a cell that neither run ignites (the common case) costs two compares
-      if ((a.x & a.y & a.z & a.w & b.x & b.y & b.z & b.w) < 0) continue;
-      count_cell(a.x, b.x, sph, H, hist);
-      count_cell(a.y, b.y, sph, H, hist);
-      count_cell(a.z, b.z, sph, H, hist);
-      count_cell(a.w, b.w, sph, H, hist);
+    const int64_t n4 = n / 4, bd = blockDim.x;
+    int64_t i = threadIdx.x;
+    for (; i + 3 * bd < n4; i += 4 * bd) {
+      int4 a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = __ldcs(x4 + i + u * bd);
+        b[u] = __ldcs(y4 + i + u * bd);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) count_cells4(a[u], b[u], sph, H, hist);
     }
+    for (; i < n4; i += bd) count_cells4(__ldcs(x4 + i), __ldcs(y4 + i), sph, H, hist);
   } else {
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) count_cell(__ldcs(x + i), __ldcs(y + i), sph, H, hist);
   }
@@ -1146,6 +1164,8 @@ __global__ void k_compare_hours(const int32_t *__restrict__ step_x, const int32_
     if (mse) mse[(size_t)r * H + t] = m;
     if (ssim) ssim[(size_t)r * H + t] = q;
   }
+  if (dnorm && threadIdx.x == 0)   // |X xor Y| = a + b - 2c, exact in binary64
+    dnorm[r] = sqrt((double)hist[H - 1] + (double)hist[2 * H - 1] - 2.0 * (double)hist[3 * H - 1]);
 }
 
 // ||X - Y|| of the final scars from the bit planes: one CTA per replica

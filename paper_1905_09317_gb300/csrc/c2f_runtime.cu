@@ -65,7 +65,8 @@ __global__ void k_burn_prob(const uint32_t *, int32_t, int32_t, int32_t, int32_t
                             uint32_t *, int32_t);
 __global__ void k_scar_bytes(const uint32_t *, int32_t, int32_t, int32_t, int32_t, uint8_t *);
 __global__ void k_scar_at_step(const int32_t *, int64_t, int32_t, uint8_t *);
-__global__ void k_compare_hours(const int32_t *, const int32_t *, int64_t, int32_t, int32_t, double *, double *);
+__global__ void k_compare_hours(const int32_t *, const int32_t *, int64_t, int32_t, int32_t, double *, double *,
+                                double *);
 __global__ void k_compare_final(const uint32_t *, const uint32_t *, int64_t, double *);
 cudaError_t init_device_constants(int device);
 }  // namespace c2f
@@ -1646,11 +1647,10 @@ int compare_launch(c2f_ctx *ctx, int32_t sim_x, int32_t sim_y, double *mse, doub
     const size_t smem = sizeof(uint32_t) * 3 * (size_t)H;
     if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_compare_hours, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)smem));
-    k_compare_hours<<<R, 256, smem, st>>>(X->ign_step.as<int32_t>(), Y->ign_step.as<int32_t>(), X->n,
-                                          60 / X->p.minutes_per_step, H, mse, ssim);
+    k_compare_hours<<<R, 128, smem, st>>>(X->ign_step.as<int32_t>(), Y->ign_step.as<int32_t>(), X->n,
+                                          60 / X->p.minutes_per_step, H, mse, ssim, dnorm);
     CKL("k_compare_hours");
-  }
-  if (dnorm) {
+  } else if (dnorm) {   // no hourly metrics asked for: the final scars' bit planes
     k_compare_final<<<R, 256, 0, st>>>(X->ign_plane.as<uint32_t>(), Y->ign_plane.as<uint32_t>(),
                                        (int64_t)X->rows * X->wpr, dnorm);
     CKL("k_compare_final");
