@@ -61,6 +61,8 @@ class Params(C.Structure):
         ("o1_curing_pct", C.c_double),
         ("m1_pc", C.c_double),
         ("const_ros", C.c_double),
+        ("burn_hours_min", C.c_int32),
+        ("burn_hours_max", C.c_int32),
     ]
 
 
@@ -94,6 +96,7 @@ def _load():
         lib.or_base_inc.restype = None
         lib.or_base_inc.argtypes = [C.c_void_p, i32, i32, P(i64), P(d)]
         lib.or_ignition_cell.restype = i32; lib.or_ignition_cell.argtypes = [C.c_void_p, i32]
+        lib.or_burn_hours.restype = i32; lib.or_burn_hours.argtypes = [C.c_void_p, i32]
         lib.or_scenario_thresholds.restype = C.c_int
         lib.or_scenario_thresholds.argtypes = [i32, P(d), P(u64)]
         lib.or_scenario.restype = i32
@@ -151,11 +154,12 @@ def fbp_cell(fuel, slope_pct, aspect_deg, ws, wd_from, ffmc, bui, m1_pc=50.0,
 # ---------------------------------------------------------------- simulation
 def make_params(seed=0, hours=1, minutes_per_step=1, ignition_mode=0, ignition_cell=0,
                 ros_sigma=0.0, ros_threshold=0.0, burnout_delta=0.0, ellipse_mode=0,
-                o1_curing_pct=60.0, m1_pc=50.0, const_ros=0.0, **_ignored) -> Params:
+                o1_curing_pct=60.0, m1_pc=50.0, const_ros=0.0, burn_hours_min=0, burn_hours_max=0,
+                **_ignored) -> Params:
     return Params(int(seed), int(hours), int(minutes_per_step), int(ignition_mode),
                   int(ignition_cell), float(ros_sigma), float(ros_threshold),
                   float(burnout_delta), int(ellipse_mode), float(o1_curing_pct),
-                  float(m1_pc), float(const_ros))
+                  float(m1_pc), float(const_ros), int(burn_hours_min), int(burn_hours_max))
 
 
 class Oracle:
@@ -217,12 +221,18 @@ class Oracle:
     def ignition_cell(self, replica: int) -> int:
         return int(self.lib.or_ignition_cell(self._h, int(replica)))
 
+    def burn_hours(self, replica: int) -> int:
+        """Burning hours per day of this replica (24: no limit)."""
+        return int(self.lib.or_burn_hours(self._h, int(replica)))
+
     def _run(self, fn, replica):
         scar = np.zeros(self.n, dtype=np.uint8)
         ign = np.zeros(self.n, dtype=np.int32)
         w, ni, ic = C.c_int64(), C.c_int32(), C.c_int32()
-        fn(self._h, int(replica), scar.ctypes.data_as(C.c_void_p),
-           ign.ctypes.data_as(C.c_void_p), C.byref(w), C.byref(ni), C.byref(ic))
+        rc = fn(self._h, int(replica), scar.ctypes.data_as(C.c_void_p),
+                ign.ctypes.data_as(C.c_void_p), C.byref(w), C.byref(ni), C.byref(ic))
+        if rc == -2:
+            raise NotImplementedError("the event search (O2) has no burning-hours limit; use run_replica")
         return {"scar": scar.reshape(self.rows, self.cols),
                 "ign": ign.reshape(self.rows, self.cols),
                 "work": int(w.value), "n_ignited": int(ni.value), "ignition_cell": int(ic.value)}

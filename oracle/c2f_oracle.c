@@ -635,6 +635,8 @@ typedef struct {
   double o1_curing_pct;
   double m1_pc;
   double const_ros;       /* > 0: every burnable cell spreads at this rate on all axes */
+  int32_t burn_hours_min; /* burning hours per day drawn per replica from       */
+  int32_t burn_hours_max; /* {min..max}; 0, 0: no limit (A5 general cond. (1))  */
 } or_params;
 
 typedef struct {
@@ -761,6 +763,23 @@ OR_API int32_t or_ignition_cell(const or_ctx *c, int32_t replica) {
   return c->burnable_list[idx];
 }
 
+/* A5, general fire dynamics (1): a replica's fire burns for at most B hours of
+ * each day.  B is drawn per replica uniformly from {min..max} with one Philox
+ * block at counter (replica, 0, 0, 3): B = min + (x0 (max - min + 1)) >> 32
+ * (min = max: a constant).  Weather hour h is a burning hour iff h mod 24 < B;
+ * in the other hours the fire is dormant: no spread, no messages, no
+ * ignitions, no burn-out, no work counted, progress kept.  Returns 24 when
+ * there is no limit. */
+OR_API int32_t or_burn_hours(const or_ctx *c, int32_t replica) {
+  if (c->p.burn_hours_max <= 0) return 24;
+  uint32_t ctr[4] = {(uint32_t)replica, 0u, 0u, 3u};
+  uint32_t key[2] = {(uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32)};
+  uint32_t x[4];
+  or_philox4x32_10(ctr, key, x);
+  uint64_t span = (uint64_t)(c->p.burn_hours_max - c->p.burn_hours_min + 1);
+  return c->p.burn_hours_min + (int32_t)(((uint64_t)x[0] * span) >> 32);
+}
+
 static float noise_of(const or_ctx *c, int32_t replica, int32_t cell, int32_t hour) {
   return or_noise_factor(c->p.seed, (uint32_t)replica, (uint32_t)cell, (uint32_t)hour,
                          (float)c->p.ros_sigma);
@@ -813,9 +832,11 @@ OR_API int or_run_replica(or_ctx *c, int32_t replica, uint8_t *scar, int32_t *ig
 
   int64_t W = 0;
   int32_t dt = c->p.minutes_per_step;
+  int32_t B = or_burn_hours(c, replica);
   for (int32_t s = 1; s <= c->S; ++s) {
     int32_t h = ((s - 1) * dt) / 60;
     if (len == 0) break;
+    if (h % 24 >= B) continue;   /* dormant hour of the day */
     W += len;
     /* send: the state array is not modified until the receive stage */
     int32_t nmsg = 0;
@@ -958,6 +979,7 @@ static int32_t delta_death(or_ctx *c, int32_t r, int32_t cell, int32_t from) {
 
 OR_API int or_run_replica_event(or_ctx *c, int32_t replica, uint8_t *scar, int32_t *ign_out,
                                 int64_t *work_out, int32_t *n_ign_out, int32_t *ic_out) {
+  if (c->p.burn_hours_max > 0) return -2;   /* O2 has no dormant hours; use O1 */
   int32_t n = c->n;
   const int32_t INF = INT32_MAX;
   int32_t *t = (int32_t *)malloc((size_t)n * 4);
