@@ -85,11 +85,19 @@ typedef struct {
   double const_ros;         /* > 0: every burnable cell spreads at this rate (m/min) on
                                all 8 axes instead of FBP (deterministic test hook)      */
   uint32_t outputs;         /* C2F_OUT_* bits                                           */
+  int32_t burn_hours_min;   /* burning hours per day (A5, general fire dynamics (1)):   */
+  int32_t burn_hours_max;   /* each replica burns only in weather hours h with h mod 24
+                               < B, B drawn uniformly from {min..max} by one Philox4x32-10
+                               block at counter (replica, 0, 0, 3), B = min + (x0 (max -
+                               min + 1)) >> 32 (min = max: a constant); in the other
+                               hours the fire is dormant (no spread, ignition, burn-out
+                               or work; progress kept).  0, 0 = no limit; otherwise
+                               1 <= min <= max <= 24                                    */
 } c2f_sim_params;
 
 /* Fills *p with the defaults: seed 0, 1 replica, 1 hour, 1-minute steps,
  * fixed ignition at cell 0, sigma 0, threshold 0, delta 0, Eq. (1),
- * curing 60, PC 50, no constant ROS, scars + counters. */
+ * curing 60, PC 50, no constant ROS, scars + counters, no burning-hours limit. */
 C2F_API void c2f_default_params(c2f_sim_params *p);
 
 /* Creates a context on CUDA device `device`.  The context owns a stream,

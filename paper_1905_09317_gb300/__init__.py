@@ -42,6 +42,7 @@ class SimParams(C.Structure):
         ("ros_threshold", C.c_double), ("burnout_delta", C.c_double),
         ("ellipse_mode", C.c_int32), ("o1_curing_pct", C.c_double), ("m1_pc", C.c_double),
         ("const_ros", C.c_double), ("outputs", C.c_uint32),
+        ("burn_hours_min", C.c_int32), ("burn_hours_max", C.c_int32),
     ]
 
 

@@ -551,6 +551,12 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
     const int64_t n = (int64_t)rows * cols;
     const int32_t pw = rows * wpr;
     const int32_t sph = J.sph, H = J.hours;
+    // A5 general condition (1): burning hours per day, drawn per replica
+    int32_t bhours = 24;
+    if (J.burn_max > 0) {
+      const U4 x = philox4x32_10(U4{(uint32_t)r, 0u, 0u, 3u}, (uint32_t)J.seed, (uint32_t)(J.seed >> 32));
+      bhours = J.burn_min + (int32_t)(((uint64_t)x.x * (uint64_t)(J.burn_max - J.burn_min + 1)) >> 32);
+    }
     const bool lazy = LAZY && J.chunk_state != nullptr;
     const double delta = J.delta;
     const uint64_t seed = J.seed;
@@ -703,6 +709,10 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
 
     for (int32_t h = 0; h < H && live > 0 && status == 0; ++h) {
       const int32_t s0 = h * sph + 1, L = s0 + sph - 1;
+      if (h % 24 >= bhours) {   // a dormant hour: nothing moves, no work is counted
+        s_done = L;
+        continue;
+      }
       const int64_t *baseh = J.base + (size_t)h * n * 8;
       const double *hrosh = J.hros + (size_t)h * n;
       // receive tests can be skipped when the threshold is 0 and every HROS of

@@ -75,6 +75,7 @@ struct SimJob {
   int32_t ignition_mode, ignition_cell;
   double thr, delta;
   int32_t sph, hours;             // fire periods per hour, simulated hours
+  int32_t burn_min, burn_max;     // burning hours per day {min..max}; 0, 0: no limit
   int64_t d_orth, d_diag;         // axis lengths in fixed point
   int32_t n_replicas;
   // per-replica outputs

@@ -341,6 +341,9 @@ int validate_params(c2f_ctx *ctx, const Landscape &L, const c2f_sim_params *p) {
     return fail(ctx, C2F_EINVAL, "o1_curing_pct must lie in [0, 100]");
   if (!(p->m1_pc >= 0.0 && p->m1_pc <= 100.0)) return fail(ctx, C2F_EINVAL, "m1_pc must lie in [0, 100]");
   if (!(p->const_ros >= 0.0 && p->const_ros < 1e9)) return fail(ctx, C2F_EINVAL, "const_ros out of range");
+  if (!(p->burn_hours_min == 0 && p->burn_hours_max == 0) &&
+      !(p->burn_hours_min >= 1 && p->burn_hours_min <= p->burn_hours_max && p->burn_hours_max <= 24))
+    return fail(ctx, C2F_EINVAL, "burning hours per day: 0, 0 or 1 <= min <= max <= 24");
   if (p->ignition_mode == 0) {
     if (p->ignition_cell < 0 || p->ignition_cell >= L.n)
       return fail(ctx, C2F_EINVAL, "ignition_cell out of range");
@@ -566,6 +569,8 @@ SimJob job_of(const Sim &s) {
   j.delta = s.p.burnout_delta;
   j.sph = 60 / s.p.minutes_per_step;
   j.hours = s.p.hours;
+  j.burn_min = s.p.burn_hours_min;
+  j.burn_max = s.p.burn_hours_max;
   j.d_orth = (int64_t)std::llrint(L.cell_size * 4294967296.0);
   j.d_diag = (int64_t)std::llrint((L.cell_size * std::sqrt(2.0)) * 4294967296.0);
   j.n_replicas = s.p.n_replicas;
