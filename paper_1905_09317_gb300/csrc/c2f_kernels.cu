@@ -443,6 +443,21 @@ struct Planes {
   }
   // some neighbour of (r, c) is still Available
   __device__ __forceinline__ bool any_avail_nbr(int32_t rows, int32_t cols, int32_t r, int32_t c) const {
+    if constexpr (WIN) {
+      // the common case: the 3 x 3 block lies inside the grid and the window;
+      // a row's three bits come out of two adjacent window words by one funnel
+      // shift (bits past the last column are 0 in the plane)
+      const int32_t il = ((c - 1) >> 5) - w0, ih = ((c + 1) >> 5) - w0;
+      if (c >= 1 && r >= 1 && r + 1 < rows && (uint32_t)(r - 1 - r0) < (uint32_t)(kWinRows - 2) &&
+          (uint32_t)il < (uint32_t)kWinWords && (uint32_t)ih < (uint32_t)kWinWords) {
+        const uint32_t *p = sav + (r - 1 - r0) * kWinWords;
+        const uint32_t sh = (uint32_t)(c - 1) & 31u;
+        const uint32_t up = __funnelshift_r(p[il], p[ih], sh) & 7u;
+        const uint32_t mid = __funnelshift_r(p[kWinWords + il], p[kWinWords + ih], sh) & 5u;
+        const uint32_t dn = __funnelshift_r(p[2 * kWinWords + il], p[2 * kWinWords + ih], sh) & 7u;
+        return (up | mid | dn) != 0u;
+      }
+    }
     uint32_t words[3][2];
     const int32_t c0 = c > 0 ? c - 1 : 0, c1 = c + 1 < cols ? c + 1 : cols - 1;
 #pragma unroll
