@@ -311,6 +311,36 @@ __device__ inline float flog(float x) {
   return __fadd_rn(__fmul_rn(ef, kLn2HiF), __fmaf_rn(ef, kLn2LoF, lm));
 }
 
+// flog for u in [2^-25, 1) and fexp for |x| < 64 ln 2: the same arithmetic
+// without the special-value branches (NaN, sign, zero, infinity, subnormal,
+// overflow, underflow) that such arguments never take; the perturbation's
+// draws always lie in these ranges
+__device__ __forceinline__ float flog_unit(float x) {
+  const unsigned int b0 = (unsigned int)__float_as_int(x);
+  int e = (int)((b0 >> 23) & 0xff) - 127;
+  float m = __int_as_float((int)((b0 & 0x007fffffu) | 0x3f800000u));
+  if (m > kSqrt2F) { m = __fmul_rn(m, 0.5f); e += 1; }
+  const float f = __fsub_rn(m, 1.0f);
+  const float s = __fdiv_rn(f, __fadd_rn(2.0f, f));
+  const float z = __fmul_rn(s, s);
+  float q = g_mc.log_cf[5];
+#pragma unroll
+  for (int n = 4; n >= 1; --n) q = __fmaf_rn(q, z, g_mc.log_cf[n]);
+  const float s2 = __fadd_rn(s, s);
+  const float lm = __fmaf_rn(__fmul_rn(s2, z), q, s2);
+  const float ef = (float)e;
+  return __fadd_rn(__fmul_rn(ef, kLn2HiF), __fmaf_rn(ef, kLn2LoF, lm));
+}
+
+__device__ __forceinline__ float fexp_small(float x) {
+  const float kf = rintf(__fmul_rn(x, kInvLn2F));
+  const float r = __fsub_rn(__fsub_rn(x, __fmul_rn(kf, kLn2HiF)), __fmul_rn(kf, kLn2LoF));
+  float p = g_mc.inv_fact_f[7];
+#pragma unroll
+  for (int i = 6; i >= 0; --i) p = __fmaf_rn(p, r, g_mc.inv_fact_f[i]);
+  return __fmul_rn(p, pow2if((int)kf));
+}
+
 // cos(2 pi u)
 __device__ inline float fcos_turns(float u) {
   const float qf = rintf(__fmul_rn(u, 4.0f));
@@ -357,8 +387,9 @@ __device__ inline float noise_factor(uint64_t seed, uint32_t replica, uint32_t c
                              (uint32_t)(seed >> 32));
   const float u1 = __fmul_rn(__fadd_rn((float)(x.x >> 8), 0.5f), 0x1p-24f);
   const float u2 = __fmul_rn(__fadd_rn((float)(x.y >> 8), 0.5f), 0x1p-24f);
-  const float z = __fmul_rn(__fsqrt_rn(__fmul_rn(-2.0f, flog(u1))), fcos_turns(u2));
-  return fexp(__fmul_rn(sigma, z));
+  // u1 >= 2^-25, so |z| <= sqrt(50 ln 2) < 6 and |sigma z| < 6 for sigma <= 1
+  const float z = __fmul_rn(__fsqrt_rn(__fmul_rn(-2.0f, flog_unit(u1))), fcos_turns(u2));
+  return fexp_small(__fmul_rn(sigma, z));
 }
 
 // the perturbation as a 32.32 fixed-point multiplier f 2^32: exact, since
