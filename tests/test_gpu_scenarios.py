@@ -189,3 +189,52 @@ def test_bad_scenario_inputs_are_rejected(ctx):
         ctx.set_weather_scenarios(lid, np.repeat(big, 3, axis=0), [1, 1, 1])
     assert e.value.code == c2f.C2F_EINVAL
     ctx.release(lid)
+
+
+def test_full_size_scenarios_sampled():
+    """The scenario workload as the benchmark runs it: 512 x 512, 8 streams of
+    24 h, 1000 replicas; every replica's drawn scenario and a sample of
+    replicas (the first and last of two scenarios) replayed by the oracle."""
+    c2f.build()
+    w = S.config2()
+    weathers, probs = S.scenario_set(8, 24)
+    with c2f.Context(0) as ctx:
+        lid = _load(ctx, w, weathers, probs)
+        p = _params(**dict(w.params, outputs=c2f.OUT_SCARS | c2f.OUT_COUNTERS))
+        sid = ctx.simulate(lid, p)
+        scen = ctx.get_scenarios(sid, 1000)
+        work, nign, cell = ctx.get_counters(sid, 1000)
+        thr = oracle.scenario_thresholds(probs)
+        assert np.array_equal(scen, [oracle.scenario_of(w.params["seed"], r, thr) for r in range(1000)])
+        so = _oracle(w, weathers, probs)
+        picks = []
+        for s_ in (0, 7):
+            idx = np.flatnonzero(scen == s_)
+            picks += [int(idx[0]), int(idx[-1])]
+        for r in picks:
+            ref = so.run_replica(r)
+            scar, _ = ctx.get_replica_scar(sid, r, w.landscape.fuel.size)
+            assert ref["scenario"] == scen[r]
+            assert np.array_equal(scar, ref["scar"].ravel()), r
+            assert work[r] == ref["work"] and nign[r] == ref["n_ignited"] and cell[r] == ref["ignition_cell"], r
+        so.close()
+
+
+def test_scenarios_with_burning_hours(ctx):
+    """Weather scenarios and a drawn burning-hours limit together: every replica
+    equals the oracle (each draw has its own Philox counter)."""
+    probs = [0.4, 0.6]
+    w, weathers = _world(side=50, n_replicas=24, hours=30, n_scen=2, seed=35)
+    over = dict(burn_hours_min=2, burn_hours_max=9)
+    w.params.update(over)
+    ctx.set_table_mode(True)
+    lid = _load(ctx, w, weathers, probs)
+    _, got = _run(ctx, lid, w)
+    so = _oracle(w, weathers, probs)
+    for r in range(24):
+        ref = so.run_replica(r)
+        assert got["scen"][r] == ref["scenario"], r
+        assert np.array_equal(got["ign"][r], ref["ign"].ravel()), r
+        assert got["work"][r] == ref["work"], r
+    so.close()
+    ctx.release(lid)
