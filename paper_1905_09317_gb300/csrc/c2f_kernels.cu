@@ -331,9 +331,7 @@ __device__ __forceinline__ int64_t find_job(const int64_t *begin, int32_t n, int
 }
 
 __device__ __forceinline__ uint32_t warp_min(uint32_t v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
+  return __reduce_min_sync(0xffffffffu, v);   // one warp-wide reduction instruction
 }
 
 // min over the 8 lanes of this lane's group
