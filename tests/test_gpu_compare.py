@@ -142,3 +142,26 @@ def test_full_size_sampled():
         ref = _oracle_metrics(w, dict(ellipse_mode=0), dict(ellipse_mode=1), (0, 499, 999))
         for r in (0, 499, 999):
             _check(got, ref[r], r)
+
+
+def test_one_cell_grid_and_one_hour(ctx):
+    """A 1 x 1 grid has no SSIM (1/(N-1) statistics): hourly metrics are refused,
+    the final norm is 0; a 1-hour run compares its single hour."""
+    fuel = np.array([[2]], dtype=np.uint8)
+    lid = ctx.load_landscape(fuel, cell_size=100.0)
+    ctx.set_weather(lid, S.weather_stream(1, seed=3))
+    p = _params(n_replicas=3, hours=1, ignition_mode=0, ignition_cell=0)
+    sx, sy = ctx.simulate(lid, p), ctx.simulate(lid, p)
+    with pytest.raises(c2f.C2FError) as e:
+        ctx.compare_scars(sx, sy, 3, 1)
+    assert e.value.code == c2f.C2F_EINVAL
+    _, _, dn = ctx.compare_scars(sx, sy, 3, 1, hourly=False)
+    assert (dn == 0).all()
+    ctx.release(lid)
+    w = S.config2(side=20, n_replicas=4, hours=1)
+    lid, sx, sy = _run_pair(ctx, w, dict(ellipse_mode=0), dict(ellipse_mode=1))
+    got = ctx.compare_scars(sx, sy, 4, 1)
+    ref = _oracle_metrics(w, dict(ellipse_mode=0), dict(ellipse_mode=1), range(4))
+    for r in range(4):
+        _check(got, ref[r], r)
+    ctx.release(lid)

@@ -238,3 +238,27 @@ def test_scenarios_with_burning_hours(ctx):
         assert got["work"][r] == ref["work"], r
     so.close()
     ctx.release(lid)
+
+
+def test_single_scenario_and_null_probabilities(ctx):
+    """One scenario through the scenario call (probabilities may be NULL) is the
+    plain single-stream run; zero-weight scenarios are never drawn."""
+    w, weathers = _world(side=30, n_replicas=12, hours=2, seed=36)
+    L = w.landscape
+    ctx.set_table_mode(True)
+    lid = ctx.load_landscape(L.fuel, L.slope, L.aspect, L.unburnable, L.cell_size)
+    one = np.ascontiguousarray(weathers[:1], dtype=np.float64)
+    ctx._check(ctx.lib.c2f_set_weather_scenarios(ctx.h, lid, 1, one.shape[1],
+                                                  one.ctypes.data_as(c2f.C.c_void_p), None))
+    _, a = _run(ctx, lid, w)
+    ctx.set_weather(lid, weathers[0])
+    _, b = _run(ctx, lid, w)
+    for k in ("ign", "work", "n_ignited", "ign_cell"):
+        assert np.array_equal(a[k], b[k]), k
+    assert (a["scen"] == 0).all()
+    with pytest.raises(c2f.C2FError) as e:      # several scenarios need probabilities
+        ctx._check(ctx.lib.c2f_set_weather_scenarios(ctx.h, lid, 3, weathers.shape[1],
+                                                      np.ascontiguousarray(weathers).ctypes.data_as(c2f.C.c_void_p),
+                                                      None))
+    assert e.value.code == c2f.C2F_EINVAL
+    ctx.release(lid)
