@@ -299,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_e2e:
         host_counts = np.empty(n, dtype=np.uint32)
         h2d = L.fuel.nbytes + L.slope.nbytes + L.aspect.nbytes + w.weather.nbytes
-        e2e_steps = max(1, min(args.steps, 10))
+        e2e_steps = max(1, args.steps)   # as many steps as the device-resident timing
         # every step: the landscape and weather uploaded from host arrays, the
         # simulation submitted, the burn counts read back to the host; steps
         # pipelined like the device-resident ones (unless --serial)

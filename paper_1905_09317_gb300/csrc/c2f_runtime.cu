@@ -223,6 +223,7 @@ struct c2f_ctx {
   int64_t max_epoch_replicas = 1 << 16;
   int64_t hbm_reserve = int64_t(2) << 30;
   cudaStream_t read_stream = nullptr;   // result reads: not queued behind table builds
+  cudaStream_t load_stream = nullptr;   // landscape uploads: not queued behind table builds
   // kernel timing
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[C2F_KT_FAMILIES];
@@ -1118,6 +1119,7 @@ C2F_API int c2f_create_with_hooks(c2f_ctx **out, int device, const c2f_alloc_hoo
     CK(cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep));
   }
   CK(cudaStreamCreateWithFlags(&ctx->read_stream, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&ctx->load_stream, cudaStreamNonBlocking));
   int rc = ensure_device_constants(ctx);
   if (rc) return rc;
   *out = holder.release();
@@ -1147,8 +1149,9 @@ C2F_API void c2f_destroy(c2f_ctx *ctx) {
       for (auto &pr : ctx->prof_events[f]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     for (cudaStream_t s : ctx->stream_pool) cudaStreamDestroy(s);
-    if (ctx->read_stream) cudaStreamDestroy(ctx->read_stream);
     cudaDeviceSynchronize();
+    if (ctx->read_stream) cudaStreamDestroy(ctx->read_stream);
+    if (ctx->load_stream) cudaStreamDestroy(ctx->load_stream);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   }
@@ -1171,82 +1174,82 @@ C2F_API int c2f_load_landscape(c2f_ctx *ctx, int32_t rows, int32_t cols, double 
     return fail(ctx, C2F_EINVAL, "rows and cols must lie in [1, 65535] and rows*cols < 2^31");
   if (!(cell_size_m > 0.0 && cell_size_m <= 1e6)) return fail(ctx, C2F_EINVAL, "cell_size_m out of range");
   const int64_t n = (int64_t)rows * cols;
-  for (int64_t i = 0; i < n; ++i)
-    if (fuel[i] >= F_NCODES) return fail(ctx, C2F_EINVAL, "fuel code %d at cell %lld is not in the table",
-                                         (int)fuel[i], (long long)i);
-  if (slope_pct)
-    for (int64_t i = 0; i < n; ++i)
-      if (!(slope_pct[i] >= 0.0f && slope_pct[i] < 1e6f))
-        return fail(ctx, C2F_EINVAL, "slope at cell %lld is not a finite value >= 0", (long long)i);
-  if (aspect_deg)
-    for (int64_t i = 0; i < n; ++i)
-      if (!std::isfinite(aspect_deg[i]) || std::fabs(aspect_deg[i]) > 1e6f)
-        return fail(ctx, C2F_EINVAL, "aspect at cell %lld is not finite", (long long)i);
-  CK(cudaSetDevice(ctx->device));
   auto L = std::make_shared<Landscape>();
+  L->burnable_host.resize(n);
+  for (int64_t i = 0; i < n; ++i) {   // one pass: checks and the host copy of the burnable mask
+    if (fuel[i] >= F_NCODES)
+      return fail(ctx, C2F_EINVAL, "fuel code %d at cell %lld is not in the table", (int)fuel[i], (long long)i);
+    if (slope_pct && !(slope_pct[i] >= 0.0f && slope_pct[i] < 1e6f))
+      return fail(ctx, C2F_EINVAL, "slope at cell %lld is not a finite value >= 0", (long long)i);
+    if (aspect_deg && (!std::isfinite(aspect_deg[i]) || std::fabs(aspect_deg[i]) > 1e6f))
+      return fail(ctx, C2F_EINVAL, "aspect at cell %lld is not finite", (long long)i);
+    L->burnable_host[i] = (fuel[i] != 0 && !(unburnable && unburnable[i])) ? 1 : 0;
+  }
+  CK(cudaSetDevice(ctx->device));
+  // uploads and set-up kernels on the context's load stream: the waits below
+  // are for this landscape's work only, not for table builds queued before it
+  cudaStream_t st = ctx->load_stream;
   L->rows = rows; L->cols = cols; L->n = n; L->cell_size = cell_size_m;
   L->wpr = (cols + 31) / 32;
-  L->burnable_host.resize(n);
-  for (int64_t i = 0; i < n; ++i) L->burnable_host[i] = (fuel[i] != 0 && !(unburnable && unburnable[i])) ? 1 : 0;
   int rc;
-  if ((rc = dalloc(ctx, L->fuel, n))) return rc;
-  CK(cudaMemcpyAsync(L->fuel.p, fuel, n, cudaMemcpyHostToDevice, ctx->stream));
+  if ((rc = dalloc_on(ctx, L->fuel, n, st))) return rc;
+  CK(cudaMemcpyAsync(L->fuel.p, fuel, n, cudaMemcpyHostToDevice, st));
   L->has_slope = slope_pct != nullptr;
   if (slope_pct) {
-    if ((rc = dalloc(ctx, L->slope, n * 4))) return rc;
-    CK(cudaMemcpyAsync(L->slope.p, slope_pct, n * 4, cudaMemcpyHostToDevice, ctx->stream));
+    if ((rc = dalloc_on(ctx, L->slope, n * 4, st))) return rc;
+    CK(cudaMemcpyAsync(L->slope.p, slope_pct, n * 4, cudaMemcpyHostToDevice, st));
   }
   if (aspect_deg) {
-    if ((rc = dalloc(ctx, L->aspect, n * 4))) return rc;
-    CK(cudaMemcpyAsync(L->aspect.p, aspect_deg, n * 4, cudaMemcpyHostToDevice, ctx->stream));
+    if ((rc = dalloc_on(ctx, L->aspect, n * 4, st))) return rc;
+    CK(cudaMemcpyAsync(L->aspect.p, aspect_deg, n * 4, cudaMemcpyHostToDevice, st));
   }
   DevBuf unb;
   if (unburnable) {
-    if ((rc = dalloc(ctx, unb, n))) return rc;
-    CK(cudaMemcpyAsync(unb.p, unburnable, n, cudaMemcpyHostToDevice, ctx->stream));
+    if ((rc = dalloc_on(ctx, unb, n, st))) return rc;
+    CK(cudaMemcpyAsync(unb.p, unburnable, n, cudaMemcpyHostToDevice, st));
   }
   const int64_t words = (int64_t)rows * L->wpr;
   DevBuf wcount, woffs, total;
-  if ((rc = dalloc(ctx, L->burnable, words * 4))) return rc;
-  if ((rc = dalloc(ctx, wcount, words * 4))) return rc;
-  if ((rc = dalloc(ctx, woffs, words * 4))) return rc;
-  if ((rc = dalloc(ctx, total, 4))) return rc;
-  k_burnable_plane<<<grid1(words, 256), 256, 0, ctx->stream>>>(
+  if ((rc = dalloc_on(ctx, L->burnable, words * 4, st))) return rc;
+  if ((rc = dalloc_on(ctx, wcount, words * 4, st))) return rc;
+  if ((rc = dalloc_on(ctx, woffs, words * 4, st))) return rc;
+  if ((rc = dalloc_on(ctx, total, 4, st))) return rc;
+  k_burnable_plane<<<grid1(words, 256), 256, 0, st>>>(
       L->fuel.as<uint8_t>(), unb.as<uint8_t>(), rows, cols, L->wpr, L->burnable.as<uint32_t>(),
       wcount.as<int32_t>());
   CKL("k_burnable_plane");
-  k_scan_counts<<<1, 1024, 0, ctx->stream>>>(wcount.as<int32_t>(), words, woffs.as<int32_t>(),
+  k_scan_counts<<<1, 1024, 0, st>>>(wcount.as<int32_t>(), words, woffs.as<int32_t>(),
                                               total.as<int32_t>());
   CKL("k_scan_counts");
   int32_t nb = 0;
-  CK(cudaMemcpyAsync(&nb, total.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpyAsync(&nb, total.p, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   L->n_burnable = nb;
-  if ((rc = dalloc(ctx, L->burnable_list, (size_t)std::max(nb, 1) * 4))) return rc;
-  k_burnable_list<<<grid1(words, 256), 256, 0, ctx->stream>>>(
+  if ((rc = dalloc_on(ctx, L->burnable_list, (size_t)std::max(nb, 1) * 4, st))) return rc;
+  k_burnable_list<<<grid1(words, 256), 256, 0, st>>>(
       L->burnable.as<uint32_t>(), woffs.as<int32_t>(), rows, cols, L->wpr,
       L->burnable_list.as<int32_t>());
   CKL("k_burnable_list");
   {   // cells grouped by (fuel, sloped) for the ROS-table kernel
     DevBuf cursor;
-    if ((rc = dalloc(ctx, L->order, (size_t)n * 4))) return rc;
-    if ((rc = dalloc(ctx, cursor, kOrderBuckets * 4))) return rc;
-    CK(cudaMemsetAsync(cursor.p, 0, kOrderBuckets * 4, ctx->stream));
-    k_order_count<<<grid1(n, 256), 256, 0, ctx->stream>>>(L->fuel.as<uint8_t>(), L->slope.as<float>(),
+    if ((rc = dalloc_on(ctx, L->order, (size_t)n * 4, st))) return rc;
+    if ((rc = dalloc_on(ctx, cursor, kOrderBuckets * 4, st))) return rc;
+    CK(cudaMemsetAsync(cursor.p, 0, kOrderBuckets * 4, st));
+    k_order_count<<<grid1(n, 256), 256, 0, st>>>(L->fuel.as<uint8_t>(), L->slope.as<float>(),
         L->burnable.as<uint32_t>(), rows, cols, L->wpr, cursor.as<int32_t>());
     CKL("k_order_count");
-    k_order_scan<<<1, 32, 0, ctx->stream>>>(cursor.as<int32_t>());
+    k_order_scan<<<1, 32, 0, st>>>(cursor.as<int32_t>());
     CKL("k_order_scan");
-    k_order_scatter<<<grid1(n, 256), 256, 0, ctx->stream>>>(L->fuel.as<uint8_t>(), L->slope.as<float>(),
+    k_order_scatter<<<grid1(n, 256), 256, 0, st>>>(L->fuel.as<uint8_t>(), L->slope.as<float>(),
         L->burnable.as<uint32_t>(), rows, cols, L->wpr, cursor.as<int32_t>(), L->order.as<int32_t>());
     CKL("k_order_scatter");
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaStreamSynchronize(st));
   }
-  if ((rc = dalloc(ctx, L->cell_prep, sizeof(CellPrep) * n))) return rc;
-  k_cell_prep<<<grid1(n, 256), 256, 0, ctx->stream>>>(L->slope.as<float>(), L->aspect.as<float>(), n,
+  if ((rc = dalloc_on(ctx, L->cell_prep, sizeof(CellPrep) * n, st))) return rc;
+  k_cell_prep<<<grid1(n, 256), 256, 0, st>>>(L->slope.as<float>(), L->aspect.as<float>(), n,
                                                      L->cell_prep.as<CellPrep>());
   CKL("k_cell_prep");
-  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaStreamSynchronize(st));
   const int32_t id = ctx->next_id++;
   ctx->lands[id] = L;
   *landscape_id = id;
