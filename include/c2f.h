@@ -396,6 +396,13 @@ typedef struct {
 
 C2F_API int c2f_frontier_static(const c2f_frontier_io *io, const c2f_sim_params *p, void *stream);
 
+/* Calibration: the device's FP64 fused multiply-add rate (GFLOP/s, 2 flops per
+ * FMA), measured with CUDA events on the context stream by a kernel of eight
+ * independent FMA chains per thread over 8 CTAs of 256 threads per SM (best of
+ * three timed launches, about 0.1 s in all).  The roofline peak of the table
+ * kernel, which is FP64-bound.  Synchronous. */
+C2F_API int c2f_fp64_peak(c2f_ctx *ctx, double *gflops);
+
 /* Frees a landscape (and its tables) or a simulation result. */
 C2F_API int c2f_release(c2f_ctx *ctx, int32_t id);
 

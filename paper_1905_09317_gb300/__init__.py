@@ -127,6 +127,7 @@ _SIGS = [
                                 _P(C.c_int32), _P(C.c_int32), _P(C.c_double)]),
     ("c2f_profile", C.c_int, [C.c_void_p, C.c_int]),
     ("c2f_kernel_times", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("c2f_fp64_peak", C.c_int, [C.c_void_p, _P(C.c_double)]),
     ("c2f_release", C.c_int, [C.c_void_p, C.c_int32]),
     ("c2f_frontier_static", C.c_int, [C.c_void_p, _P(SimParams), C.c_void_p]),
 ]
@@ -376,6 +377,12 @@ class Context:
 
     def profile(self, enable: bool = True) -> None:
         self._check(self.lib.c2f_profile(self.h, int(bool(enable))))
+
+    def fp64_peak(self) -> float:
+        """Measured FP64 FMA rate of the device, GFLOP/s."""
+        g = C.c_double()
+        self._check(self.lib.c2f_fp64_peak(self.h, C.byref(g)))
+        return g.value
 
     def kernel_times(self) -> dict:
         ms = np.zeros(len(KERNEL_FAMILIES), dtype=np.float64)

@@ -1092,6 +1092,25 @@ __global__ void k_scar_bytes(const uint32_t *__restrict__ planes, int32_t R, int
   out[i] = (planes[(size_t)r * rows * wpr + (size_t)row * wpr + (col >> 5)] >> (col & 31)) & 1u;
 }
 
+// ------------------------------------------------------------------ calibration
+// FP64 fused multiply-add throughput of the device: eight independent chains
+// per thread, enough warps to cover the pipe's latency; the roofline peak of
+// the table kernel, which is FP64-bound.
+__global__ void k_dfma_peak(double *out, int32_t iters) {
+  const double m = 0.999999999, c = 1e-12;
+  double a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = 1.0 + 1e-3 * (threadIdx.x + j);
+  for (int32_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = __fma_rn(a[j], m, c);
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) t += a[j];
+  if (t == 12345.678) out[blockIdx.x] = t;   // never true; keeps the chains alive
+}
+
 // ------------------------------------------------------------------ scar comparison
 // Sec. 4.1 compares two runs' scars X^t, Y^t (0-1 grids, 1 = ignited by the
 // end of weather hour t) by MSE, SSIM and, for the final scars, ||X - Y||.

@@ -68,6 +68,7 @@ __global__ void k_scar_at_step(const int32_t *, int64_t, int32_t, uint8_t *);
 __global__ void k_compare_hours(const int32_t *, const int32_t *, int64_t, int32_t, int32_t, double *, double *,
                                 double *);
 __global__ void k_compare_final(const uint32_t *, const uint32_t *, int64_t, double *);
+__global__ void k_dfma_peak(double *, int32_t);
 cudaError_t init_device_constants(int device);
 }  // namespace c2f
 
@@ -1829,6 +1830,35 @@ C2F_API int c2f_profile(c2f_ctx *ctx, int enable) {
   if (!ctx) return C2F_EINVAL;
   LOCK;
   ctx->profiling = enable != 0;
+  return C2F_OK;
+}
+
+C2F_API int c2f_fp64_peak(c2f_ctx *ctx, double *gflops) {
+  if (!ctx || !gflops) return C2F_EINVAL;
+  LOCK;
+  CK(cudaSetDevice(ctx->device));
+  const int32_t iters = 4096;
+  const unsigned blocks = (unsigned)ctx->sm_count * 8, threads = 256;
+  DevBuf sink;
+  int rc;
+  if ((rc = dalloc(ctx, sink, sizeof(double) * blocks))) return rc;
+  cudaEvent_t a = get_event(ctx), b = get_event(ctx);
+  if (!a || !b) return fail(ctx, C2F_ECUDA, "no CUDA event");
+  double best = 0.0;
+  for (int rep = 0; rep < 4; ++rep) {   // the first launch warms up; the best of the rest counts
+    CK(cudaEventRecord(a, ctx->stream));
+    k_dfma_peak<<<blocks, threads, 0, ctx->stream>>>(sink.as<double>(), iters);
+    CKL("k_dfma_peak");
+    CK(cudaEventRecord(b, ctx->stream));
+    CK(cudaEventSynchronize(b));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    const double flop = 2.0 * 8.0 * iters * (double)blocks * threads;
+    if (rep > 0 && ms > 0.0f) best = std::max(best, flop / (ms * 1e-3) / 1e9);
+  }
+  ctx->event_pool.push_back(a);
+  ctx->event_pool.push_back(b);
+  *gflops = best;
   return C2F_OK;
 }
 
