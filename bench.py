@@ -73,6 +73,56 @@ def _oracle_chunk(args):
     return tot, len(replicas)
 
 
+def _workload_of(key):
+    """Workloads by name, rebuilt from their seeds inside a worker process."""
+    import c2f_synth as S2
+    if key[0] == "large":
+        return S2.config4()
+    if key[0] == "batch":
+        return S2.config3_workload(S2.config3_specs()[key[1]])
+    raise KeyError(key)
+
+
+def _oracle_sample_chunk(items):
+    """(spawned process) oracle replicas of named workloads: [(key, replica), ...]."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import oracle
+    tot, t_run = 0, 0.0
+    cur, o = None, None
+    for key, r in sorted(items):
+        if key != cur:   # one oracle at a time: large landscapes reserve much memory
+            if o is not None:
+                o.close()
+            w = _workload_of(key)
+            L = w.landscape
+            o = oracle.Oracle(L.fuel, L.slope, L.aspect, cell_size=L.cell_size, weather=w.weather,
+                              **w.params)
+            cur = key
+        t0 = time.perf_counter()
+        tot += o.run_replica(r)["work"]
+        t_run += time.perf_counter() - t0
+    if o is not None:
+        o.close()
+    return tot, t_run
+
+
+def cpu_oracle_sample_rate(items, procs: int):
+    """Oracle cell-updates/s on a sample of (workload, replica) items, one process per
+    core; inputs are built outside the timing, the rate is the sampled work over the
+    slowest process's replica time."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    chunks = [items[p::procs] for p in range(procs)]
+    chunks = [c for c in chunks if c]
+    with mp.get_context("spawn").Pool(len(chunks)) as pool:
+        res = pool.map(_oracle_sample_chunk, chunks)
+    work = sum(r[0] for r in res)
+    t = max(r[1] for r in res)
+    return work / t, work, t, len(chunks)
+
+
 def cpu_oracle_rate(n_replicas_sample: int, procs: int):
     """Oracle (single-threaded C, one process per core) on a replica sample."""
     import multiprocessing as mp
@@ -549,7 +599,19 @@ def run_batch(args):
             {"threads": tuned[0], "smem_lists": tuned[1], "sample_frontier_ms": tuned[2],
              "sample_replicas": args.tune_sample},
             "plain": out["plain"], "batched": out["batched"],
-            "batched_over_plain": out["plain"]["s_per_step"] / out["batched"]["s_per_step"]}
+            "batched_over_plain": out["plain"]["s_per_step"] / out["batched"]["s_per_step"],
+            "cpu_baseline": _batch_cpu_baseline(args, specs)}
+
+
+def _batch_cpu_baseline(args, specs):
+    """The oracle beside the GPU: replica 0 of every landscape of the batch."""
+    if args.no_cpu_baseline:
+        return None
+    procs = os.cpu_count() or 1
+    rate, work, t, used = cpu_oracle_sample_rate([(("batch", i), 0) for i in range(len(specs))], procs)
+    return {"value": rate, "unit": METRIC, "cores": used, "kind": "oracle",
+            "sample": f"replica 0 of each of the {len(specs)} landscapes ({work} cell-updates), "
+                      f"{used} single-threaded oracle processes, {t:.1f} s"}
 
 
 def run_serve(args):
@@ -687,7 +749,19 @@ def run_large(args):
                        "cell_updates_per_step": work},
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
             "roofline": roof, "fp64_peak_gflops_measured": fp64,
-            "replicas_per_s": p.n_replicas / dt}
+            "replicas_per_s": p.n_replicas / dt,
+            "cpu_baseline": _large_cpu_baseline(args)}
+
+
+def _large_cpu_baseline(args):
+    """The oracle beside the GPU: 8 of the 256 replicas (every 32nd)."""
+    if args.no_cpu_baseline:
+        return None
+    procs = min(os.cpu_count() or 1, 8)
+    rate, work, t, used = cpu_oracle_sample_rate([(("large",), r) for r in range(0, 256, 32)], procs)
+    return {"value": rate, "unit": METRIC, "cores": used, "kind": "oracle",
+            "sample": f"replicas 0, 32, .., 224 ({work} cell-updates), {used} single-threaded "
+                      f"oracle processes, {t:.1f} s"}
 
 
 def run_scenarios(args):
