@@ -681,8 +681,8 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
     };
 
     // drop Burned cells and cells with no open axis from the burning list
-    // (order kept); with a table pointer, prefetch the kept cells' rows
-    auto compact = [&](int32_t count, const int64_t *rows_tbl) -> int32_t {
+    // (order kept), within an hour when the list nears its capacity
+    auto compact = [&](int32_t count) -> int32_t {
       int32_t out = 0;
       for (int32_t b0 = 0; b0 < count; b0 += 32) {
         const int32_t e = b0 + lane;
@@ -696,7 +696,6 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           const int32_t cr = (int32_t)(rc >> 16), cc = (int32_t)(rc & 0xFFFFu);
           keep = m != 0 && !pl.burned(cr, cc);
           if (keep) {
-            if (rows_tbl) prefetch_l2(rows_tbl + ((int64_t)cr * cols + cc) * 8);
             nx = enext[e];
             c8 = *reinterpret_cast<const uint64_t *>(ecofs + (size_t)e * 8);
 #pragma unroll
@@ -819,7 +818,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       for (;;) {
         W += (long long)live * (long long)(s - s_done);
         s_done = s;
-        if (cnt > cap - cap / 4) cnt = compact(cnt, nullptr);   // keep room for new cells
+        if (cnt > cap - cap / 4) cnt = compact(cnt);   // keep room for new cells
         const uint32_t o = (uint32_t)(s - s0);
         uint32_t lmin = kNone;
         int32_t nnew = cnt;
