@@ -252,6 +252,12 @@ C2F_API int c2f_set_serving(c2f_ctx *ctx, int32_t max_inflight, int64_t max_epoc
  * of replicas in which cell c ignited, uint32, rows*cols entries, host memory. */
 C2F_API int c2f_burn_prob(c2f_ctx *ctx, int32_t sim_id, uint32_t *counts);
 
+/* Burn-probability counts of one weather scenario (Sec. 3.1 (3)): counts[c] =
+ * number of the replicas that drew `scenario` in which cell c ignited
+ * (rows*cols uint32, host memory).  A landscape with one weather stream has
+ * scenario 0 only; scenario outside [0, n_scenarios) is C2F_EINVAL. */
+C2F_API int c2f_burn_prob_scenario(c2f_ctx *ctx, int32_t sim_id, int32_t scenario, uint32_t *counts);
+
 /* Same into device memory (`counts_dev`, rows*cols uint32 on the context's
  * device); asynchronous on the context stream. */
 C2F_API int c2f_burn_prob_device(c2f_ctx *ctx, int32_t sim_id, uint32_t *counts_dev);

@@ -112,6 +112,7 @@ _SIGS = [
     ("c2f_set_table_mode", C.c_int, [C.c_void_p, C.c_int]),
     ("c2f_burn_prob", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_burn_prob_device", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    ("c2f_burn_prob_scenario", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     ("c2f_get_scars", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     ("c2f_get_replica_scar", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     ("c2f_get_scar_bits", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
@@ -303,6 +304,11 @@ class Context:
     def burn_prob(self, sim_id: int, n_cells: int) -> np.ndarray:
         out = np.empty(n_cells, dtype=np.uint32)
         self._check(self.lib.c2f_burn_prob(self.h, int(sim_id), _ptr(out)))
+        return out
+
+    def burn_prob_scenario(self, sim_id: int, scenario: int, n_cells: int) -> np.ndarray:
+        out = np.empty(n_cells, dtype=np.uint32)
+        self._check(self.lib.c2f_burn_prob_scenario(self.h, int(sim_id), int(scenario), _ptr(out)))
         return out
 
     def burn_prob_device(self, sim_id: int, dev_ptr: int) -> None:

@@ -1038,9 +1038,10 @@ __global__ void __launch_bounds__(32, 1) k_frontier_lw1(FrontierArgs A) { fronti
 // counts[c] = sum over replicas of the scar bit of c.  Each thread owns one
 // 32-cell word and adds the replicas' words into a bit-sliced (vertical)
 // counter: plane i holds bit i of the 32 per-cell counts.
+// With scen, only the replicas whose drawn weather scenario is `want` count.
 __global__ void k_burn_prob(const uint32_t *__restrict__ planes, int32_t R, int32_t rows,
                             int32_t cols, int32_t wpr, int32_t r_chunk, uint32_t *counts,
-                            int32_t accumulate) {
+                            int32_t accumulate, const int32_t *__restrict__ scen, int32_t want) {
   const int64_t pw = (int64_t)rows * wpr;
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= pw) return;
@@ -1050,6 +1051,7 @@ __global__ void k_burn_prob(const uint32_t *__restrict__ planes, int32_t R, int3
 #pragma unroll
   for (int i = 0; i < 16; ++i) c[i] = 0;
   for (int32_t r = r0; r < r1; ++r) {
+    if (scen && __ldg(&scen[r]) != want) continue;
     uint32_t carry = __ldg(&planes[(size_t)r * pw + w]);
 #pragma unroll
     for (int i = 0; i < 16; ++i) {

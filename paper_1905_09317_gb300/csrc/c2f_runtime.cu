@@ -62,7 +62,7 @@ __global__ void k_frontier_w4(FrontierArgs);
 __global__ void k_frontier_lg1(FrontierArgs);
 __global__ void k_frontier_lw1(FrontierArgs);
 __global__ void k_burn_prob(const uint32_t *, int32_t, int32_t, int32_t, int32_t, int32_t,
-                            uint32_t *, int32_t);
+                            uint32_t *, int32_t, const int32_t *, int32_t);
 __global__ void k_scar_bytes(const uint32_t *, int32_t, int32_t, int32_t, int32_t, uint8_t *);
 __global__ void k_scar_at_step(const int32_t *, int64_t, int32_t, uint8_t *);
 __global__ void k_compare_hours(const int32_t *, const int32_t *, int64_t, int32_t, int32_t, double *, double *,
@@ -1484,7 +1484,9 @@ C2F_API int c2f_cancel(c2f_ctx *ctx, int32_t sim_id) {
   return C2F_OK;
 }
 
-static int burn_prob_into(c2f_ctx *ctx, Sim &s, uint32_t *dst, cudaStream_t st) {
+// counts over all replicas, or (scen) over those that drew weather scenario `want`
+static int burn_prob_into(c2f_ctx *ctx, Sim &s, uint32_t *dst, cudaStream_t st,
+                          const int32_t *scen = nullptr, int32_t want = 0) {
   const int32_t R = s.p.n_replicas;
   const int64_t words = (int64_t)s.rows * s.wpr;
   const int64_t target = (int64_t)ctx->sm_count * 4 * 256;
@@ -1495,7 +1497,7 @@ static int burn_prob_into(c2f_ctx *ctx, Sim &s, uint32_t *dst, cudaStream_t st) 
   ProfScope prof(ctx, 3, st);
   if (chunks > 1) CK(cudaMemsetAsync(dst, 0, (size_t)s.n * 4, st));
   k_burn_prob<<<dim3(grid1(words, 256), (unsigned)chunks), 256, 0, st>>>(
-      s.ign_plane.as<uint32_t>(), R, s.rows, s.cols, s.wpr, per, dst, chunks > 1 ? 1 : 0);
+      s.ign_plane.as<uint32_t>(), R, s.rows, s.cols, s.wpr, per, dst, chunks > 1 ? 1 : 0, scen, want);
   CKL("k_burn_prob");
   return C2F_OK;
 }
@@ -1513,6 +1515,25 @@ C2F_API int c2f_burn_prob(c2f_ctx *ctx, int32_t sim_id, uint32_t *counts) {
   DevBuf tmp;
   if ((rc = dalloc_on(ctx, tmp, (size_t)s->n * 4, st))) return rc;
   if ((rc = burn_prob_into(ctx, *s, tmp.as<uint32_t>(), st))) return rc;
+  CK(cudaMemcpyAsync(counts, tmp.p, (size_t)s->n * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return C2F_OK;
+}
+
+C2F_API int c2f_burn_prob_scenario(c2f_ctx *ctx, int32_t sim_id, int32_t scenario, uint32_t *counts) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  auto s = find_sim(ctx, sim_id);
+  if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  if (!counts) return fail(ctx, C2F_EINVAL, "counts is NULL");
+  int rc = sim_ready(ctx, *s);
+  if (rc) return rc;
+  if (scenario < 0 || scenario >= s->table->n_scen) return fail(ctx, C2F_EINVAL, "scenario out of range");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->read_stream;
+  DevBuf tmp;
+  if ((rc = dalloc_on(ctx, tmp, (size_t)s->n * 4, st))) return rc;
+  if ((rc = burn_prob_into(ctx, *s, tmp.as<uint32_t>(), st, s->scen.as<int32_t>(), scenario))) return rc;
   CK(cudaMemcpyAsync(counts, tmp.p, (size_t)s->n * 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return C2F_OK;

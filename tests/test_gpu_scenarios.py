@@ -86,6 +86,17 @@ def test_every_replica_matches_the_oracle(ctx, eager):
         assert got["ign_cell"][r] == ref["ignition_cell"], r
     counts = ctx.burn_prob(sid, w.landscape.fuel.size)
     assert np.array_equal(counts, oracle.burn_prob(got["scars"]))
+    total = np.zeros_like(counts)
+    for sc in range(3):   # per-scenario maps: the oracle's scars of the replicas that drew sc
+        per = ctx.burn_prob_scenario(sid, sc, w.landscape.fuel.size)
+        ref = oracle.burn_prob(np.stack([so.run_replica(r)["scar"].ravel() for r in range(R)
+                                         if so.scenario(r) == sc]))
+        assert np.array_equal(per, ref), sc
+        total += per
+    assert np.array_equal(total, counts)
+    with pytest.raises(c2f.C2FError) as e:
+        ctx.burn_prob_scenario(sid, 3, w.landscape.fuel.size)
+    assert e.value.code == c2f.C2F_EINVAL
     so.close()
     ctx.release(lid)
 
