@@ -9,7 +9,9 @@ path never does.  It shares no code with the CUDA library.
 The arithmetic lives in ``c2f_oracle.c`` (plain C, binary64, contraction
 off); this module compiles it with gcc on first use and wraps it with
 ctypes.  ``burn_prob`` (the burn-probability count, Sec. 3.6 / 3.1 outputs)
-is a plain numpy sum over replica scars.
+is a plain numpy sum over replica scars; ``ScenarioOracle`` runs each replica
+under its drawn weather scenario (Sec. 3.1 (3)); ``scar_mse`` / ``scar_ssim``
+/ ``scar_dnorm`` are the Sec. 4.1 comparison metrics written out on the grids.
 
 Parity status: the FBP surface-spread equations (not printed in the paper)
 are "parity unpinned" against their publication; they are pinned only by
