@@ -93,6 +93,15 @@ typedef struct {
                                hours the fire is dormant (no spread, ignition, burn-out
                                or work; progress kept).  0, 0 = no limit; otherwise
                                1 <= min <= max <= 24                                    */
+  double const_bros;        /* with const_ros > 0 (test hook): BROS in m/min (0 = const_ros)
+                               and the length-to-breadth ratio LB (<= 1: 1); when
+                               const_bros > 0 or const_lb > 1 every burnable cell gets the
+                               ellipse of Sec. 3.7 (Eqs. 2-4) of HROS = const_ros, BROS and
+                               LB, its head along the hour's wind (toward WD + 180), and the
+                               8 axis rates of Eq. (1) (or of the ellipse_mode 1 ray);
+                               ignored when const_ros is 0.  0 <= const_bros < 1e9,
+                               0 <= const_lb <= 1000                                      */
+  double const_lb;
 } c2f_sim_params;
 
 /* Fills *p with the defaults: seed 0, 1 replica, 1 hour, 1-minute steps,

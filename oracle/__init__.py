@@ -65,6 +65,8 @@ class Params(C.Structure):
         ("const_ros", C.c_double),
         ("burn_hours_min", C.c_int32),
         ("burn_hours_max", C.c_int32),
+        ("const_bros", C.c_double),
+        ("const_lb", C.c_double),
     ]
 
 
@@ -157,11 +159,12 @@ def fbp_cell(fuel, slope_pct, aspect_deg, ws, wd_from, ffmc, bui, m1_pc=50.0,
 def make_params(seed=0, hours=1, minutes_per_step=1, ignition_mode=0, ignition_cell=0,
                 ros_sigma=0.0, ros_threshold=0.0, burnout_delta=0.0, ellipse_mode=0,
                 o1_curing_pct=60.0, m1_pc=50.0, const_ros=0.0, burn_hours_min=0, burn_hours_max=0,
-                **_ignored) -> Params:
+                const_bros=0.0, const_lb=0.0, **_ignored) -> Params:
     return Params(int(seed), int(hours), int(minutes_per_step), int(ignition_mode),
                   int(ignition_cell), float(ros_sigma), float(ros_threshold),
                   float(burnout_delta), int(ellipse_mode), float(o1_curing_pct),
-                  float(m1_pc), float(const_ros), int(burn_hours_min), int(burn_hours_max))
+                  float(m1_pc), float(const_ros), int(burn_hours_min), int(burn_hours_max),
+                  float(const_bros), float(const_lb))
 
 
 class Oracle:

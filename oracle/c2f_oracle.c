@@ -510,10 +510,63 @@ static void axis_dirs(double ct[8], double st[8]) {
   for (int k = 0; k < 8; ++k) { ct[k] = cx[k]; st[k] = sy[k]; }
 }
 
-/* Output row layout of or_fbp_cell:
- *  0 HROS  1 BROS  2 LB  3 FROS  4 a  5 e  6 ux  7 uy  8 WSV  9 RAZ-free slot (WSE)
+/* Output row layout of or_fbp_cell (and of ellipse_axes' part of it):
+ *  0 HROS  1 BROS  2 LB  3 FROS  4 a  5 e  6 ux  7 uy  8 WSV  9 WSE
  *  10..17 ros_k for k = 0..7                                                    */
 #define ROW_LEN 18
+
+/* Sec. 3.7, Eqs. (2)-(4): the ellipse of a cell from HROS, BROS and LB, and
+ * its rate along each of the 8 axes for a head direction (ux, uy) (unit
+ * vector, x east, y north): Eq. (1) (mode 0) or the ray from the ignition
+ * point (mode 1).  Fills out[2..7] and out[10..17]. */
+static void ellipse_axes(double hros, double bros, double lb, double ux, double uy,
+                         int ellipse_mode, double out[ROW_LEN]) {
+  double ilb = 1.0 / lb;   /* one reciprocal for FROS and e */
+  double fros = ((hros + bros) * ilb) * 0.5;
+  double a = (hros + bros) * 0.5;
+  double e = sqrt(1.0 - ilb * ilb);
+  out[2] = lb; out[3] = fros; out[4] = a; out[5] = e; out[6] = ux; out[7] = uy;
+  double ct[8], st[8];
+  axis_dirs(ct, st);
+  if (ellipse_mode == 0) {
+    /* Eq. (1): forward half (cos phi > 0) a(1-e^2)/(1-e cos phi), back half a(1-e^2) */
+    double A = a * (1.0 - e * e);
+    for (int k = 0; k < 8; ++k) {
+      double cphi = ct[k] * ux + st[k] * uy;
+      out[10 + k] = (cphi > 0.0) ? A / (1.0 - e * cphi) : A;
+    }
+  } else {
+    /* Centre-offset ellipse (Sec. 3.7, figure CellularHuygens): the ray from
+     * the ignition point, c = (HROS-BROS)/2 behind the centre, to the ellipse
+     * with semi-axes a (along the head) and b = FROS:
+     *   r = (b^2 c cos + a b sqrt(Q)) / (b^2 cos^2 + a^2 sin^2),
+     *   Q = b^2 cos^2 + (a^2 - c^2) sin^2,  a^2 - c^2 = HROS BROS.
+     * On the back half (cos < 0) the numerator is a difference of nearly
+     * equal terms when HROS >> BROS; multiplied out by its conjugate the
+     * same ray is r = b^2 HROS BROS / (a b sqrt(Q) - b^2 c cos), a sum of
+     * non-negative terms.  a^2 - c^2 is taken as the product HROS BROS. */
+    double b = fros;
+    double c = (hros - bros) * 0.5;
+    double hb = hros * bros;
+    for (int k = 0; k < 8; ++k) {
+      double cphi = ct[k] * ux + st[k] * uy;
+      double sphi2 = 1.0 - cphi * cphi;
+      if (sphi2 < 0.0) sphi2 = 0.0;
+      double bc = b * b * cphi * cphi;
+      double den = bc + a * a * sphi2;
+      double root = sqrt(bc + hb * sphi2);
+      double r = 0.0;
+      if (cphi >= 0.0) {
+        if (den > 0.0) r = (b * b * c * cphi + a * b * root) / den;
+      } else {
+        double q = a * b * root - b * b * c * cphi;
+        if (q > 0.0) r = (b * b * hb) / q;
+      }
+      out[10 + k] = r;
+    }
+  }
+}
+
 
 OR_API void or_fbp_cell(int fuel, double gs, double aspect_deg, double ws, double wd_from,
                         double ffmc, double bui, double m1_pc, double o1_curing,
@@ -566,38 +619,8 @@ OR_API void or_fbp_cell(int fuel, double gs, double aspect_deg, double ws, doubl
     lb = (wsv >= 1.0) ? 1.1 * or_pow(wsv, 0.464) : 1.0;
   else
     lb = 1.0 + 8.729 * or_pow(1.0 - or_exp(-0.030 * wsv), 2.155);
-  /* Eqs. (2)-(4) */
-  double ilb = 1.0 / lb;   /* one reciprocal for FROS and e */
-  double fros = ((hros + bros) * ilb) * 0.5;
-  double a = (hros + bros) * 0.5;
-  double e = sqrt(1.0 - ilb * ilb);
-  out[0] = hros; out[1] = bros; out[2] = lb; out[3] = fros;
-  out[4] = a; out[5] = e; out[6] = ux; out[7] = uy; out[8] = wsv; out[9] = wse;
-  double ct[8], st[8];
-  axis_dirs(ct, st);
-  if (ellipse_mode == 0) {
-    /* Eq. (1): forward half (cos phi > 0) a(1-e^2)/(1-e cos phi), back half a(1-e^2) */
-    double A = a * (1.0 - e * e);
-    for (int k = 0; k < 8; ++k) {
-      double cphi = ct[k] * ux + st[k] * uy;
-      out[10 + k] = (cphi > 0.0) ? A / (1.0 - e * cphi) : A;
-    }
-  } else {
-    /* Centre-offset ellipse (Sec. 3.7, figure CellularHuygens): the ray from
-     * the ignition point, c = (HROS-BROS)/2 behind the centre, to the ellipse
-     * with semi-axes a (along the head) and b = FROS. */
-    double b = fros;
-    double c = (hros - bros) * 0.5;
-    for (int k = 0; k < 8; ++k) {
-      double cphi = ct[k] * ux + st[k] * uy;
-      double sphi2 = 1.0 - cphi * cphi;
-      if (sphi2 < 0.0) sphi2 = 0.0;
-      double bc = b * b * cphi * cphi;
-      double den = bc + a * a * sphi2;
-      double root = sqrt(bc + (a * a - c * c) * sphi2);
-      out[10 + k] = (den > 0.0) ? (b * b * c * cphi + a * b * root) / den : 0.0;
-    }
-  }
+  out[0] = hros; out[1] = bros; out[8] = wsv; out[9] = wse;
+  ellipse_axes(hros, bros, lb, ux, uy, ellipse_mode, out);
 }
 
 /* ======================================================================
@@ -637,6 +660,8 @@ typedef struct {
   double const_ros;       /* > 0: every burnable cell spreads at this rate on all axes */
   int32_t burn_hours_min; /* burning hours per day drawn per replica from       */
   int32_t burn_hours_max; /* {min..max}; 0, 0: no limit (A5 general cond. (1))  */
+  double const_bros;      /* with const_ros > 0: BROS (0 = const_ros) and LB (<= 1:  */
+  double const_lb;        /* a circle); the head follows the hour's wind direction */
 } or_params;
 
 typedef struct {
@@ -715,6 +740,19 @@ OR_API void or_cell_row(const or_ctx *c, int32_t cell, int32_t hour, double out[
   }
   if (c->p.const_ros > 0.0) {
     for (int i = 0; i < ROW_LEN; ++i) out[i] = 0.0;
+    if (c->p.const_bros > 0.0 || c->p.const_lb > 1.0) {
+      /* test hook: the ellipse of Sec. 3.7 from given HROS, BROS and LB, its
+       * head along the hour's wind (toward WD + 180), rates by Eq. (1) or the
+       * ray of ellipse_mode 1 */
+      double hros = c->p.const_ros;
+      double bros = c->p.const_bros > 0.0 ? c->p.const_bros : hros;
+      double lb = c->p.const_lb > 1.0 ? c->p.const_lb : 1.0;
+      double sw, cw;
+      or_sincos_deg(w[1] + 180.0, &sw, &cw);
+      out[0] = hros; out[1] = bros;
+      ellipse_axes(hros, bros, lb, sw, cw, c->p.ellipse_mode, out);
+      return;
+    }
     out[0] = c->p.const_ros; out[1] = c->p.const_ros; out[2] = 1.0; out[3] = c->p.const_ros;
     out[4] = c->p.const_ros; out[6] = 1.0;
     for (int k = 0; k < 8; ++k) out[10 + k] = c->p.const_ros;

@@ -43,6 +43,7 @@ class SimParams(C.Structure):
         ("ellipse_mode", C.c_int32), ("o1_curing_pct", C.c_double), ("m1_pc", C.c_double),
         ("const_ros", C.c_double), ("outputs", C.c_uint32),
         ("burn_hours_min", C.c_int32), ("burn_hours_max", C.c_int32),
+        ("const_bros", C.c_double), ("const_lb", C.c_double),
     ]
 
 

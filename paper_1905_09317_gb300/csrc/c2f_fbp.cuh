@@ -178,6 +178,66 @@ __device__ inline void cell_prep(double gs, double aspect_deg, CellPrep *cp) {
 
 struct FbpOut { double hros, bros, lb, fros, a, e, ux, uy, wsv, wse; double ros[8]; };
 
+// Sec. 3.7, Eqs. (2)-(4): the ellipse of a cell from HROS, BROS and LB, and
+// its rate along each of the 8 axes for the head direction (ux, uy) (unit
+// vector, x east, y north) by Eq. (1) (ellipse_mode 0) or by the ray from the
+// ignition point (mode 1).  Sets o->lb, fros, a, e, ux, uy and ros[].
+__device__ __forceinline__ void ellipse_axes(double hros, double bros, double lb, double ux, double uy,
+                                             int ellipse_mode, FbpOut *o) {
+  const double hb = __dadd_rn(hros, bros);
+  const double ilb = __ddiv_rn(1.0, lb);   // one reciprocal for FROS and e
+  const double fros = __dmul_rn(__dmul_rn(hb, ilb), 0.5);
+  const double a = __dmul_rn(hb, 0.5);
+  const double e = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(ilb, ilb)));
+  o->lb = lb; o->fros = fros; o->a = a; o->e = e; o->ux = ux; o->uy = uy;
+  // cos(phi_k) = (cos theta_k) ux + (sin theta_k) uy for the 8 axes, whose
+  // cosines and sines are 0, +-1 and +-h (h = RN(sqrt(1/2))): products by 0 and
+  // +-1 are exact, so the sums are ux, uy, their negatives and +-(h ux) +- (h uy)
+  // -- the same values (up to the sign of a zero, which no test below sees)
+  const double h = 0x1.6a09e667f3bcdp-1;
+  const double hx = __dmul_rn(h, ux), hy = __dmul_rn(h, uy);
+  const double dpp = __dadd_rn(hx, hy), dmp = __dsub_rn(hy, hx);
+  const double cphk[8] = {ux, dpp, uy, dmp, -ux, -dpp, -uy, -dmp};
+  if (ellipse_mode == 0) {
+    const double A = __dmul_rn(a, __dsub_rn(1.0, __dmul_rn(e, e)));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double cphi = cphk[k];
+      // cphi > 0 as a sign test on the bits (cphi is never NaN)
+      o->ros[k] = (__double_as_longlong(cphi) > 0) ? __ddiv_rn(A, __dsub_rn(1.0, __dmul_rn(e, cphi))) : A;
+    }
+  } else {
+    // the ray from the ignition point, c = (HROS - BROS)/2 behind the centre,
+    // to the ellipse with semi-axes a and b = FROS:
+    //   r = (b^2 c cos + a b sqrt(Q)) / (b^2 cos^2 + a^2 sin^2),
+    //   Q = b^2 cos^2 + (a^2 - c^2) sin^2, a^2 - c^2 = HROS BROS;
+    // on the back half (cos < 0), the same ray multiplied out by the conjugate
+    // of its numerator, r = b^2 HROS BROS / (a b sqrt(Q) - b^2 c cos), so that
+    // no nearly equal terms are subtracted when HROS >> BROS
+    const double b = fros;
+    const double c = __dmul_rn(__dsub_rn(hros, bros), 0.5);
+    const double hbp = __dmul_rn(hros, bros);
+    const double bb = __dmul_rn(b, b), aa = __dmul_rn(a, a), ab = __dmul_rn(a, b);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double cphi = cphk[k];
+      double sphi2 = __dsub_rn(1.0, __dmul_rn(cphi, cphi));
+      if (sphi2 < 0.0) sphi2 = 0.0;
+      const double bc = __dmul_rn(__dmul_rn(bb, cphi), cphi);
+      const double den = __dadd_rn(bc, __dmul_rn(aa, sphi2));
+      const double root = __dsqrt_rn(__dadd_rn(bc, __dmul_rn(hbp, sphi2)));
+      double r = 0.0;
+      if (cphi >= 0.0) {
+        if (den > 0.0) r = __ddiv_rn(__dadd_rn(__dmul_rn(__dmul_rn(bb, c), cphi), __dmul_rn(ab, root)), den);
+      } else {
+        const double q = __dsub_rn(__dmul_rn(ab, root), __dmul_rn(__dmul_rn(bb, c), cphi));
+        if (q > 0.0) r = __ddiv_rn(__dmul_rn(bb, hbp), q);
+      }
+      o->ros[k] = r;
+    }
+  }
+}
+
 // per (cell, hour): FBP surface spread, Eqs. (2)-(4), then the 8 axis rates
 // by Eq. (1) (ellipse_mode 0) or by the centre-offset ellipse ray (mode 1).
 __device__ inline void fbp_row(int fuel, double gs, const CellPrep &cp, const HourPrep &hp,
@@ -216,46 +276,8 @@ __device__ inline void fbp_row(int fuel, double gs, const CellPrep &cp, const Ho
     lb = !lt_c(wsv, 1.0) ? __dmul_rn(1.1, dpow_n2(wsv, 0.464, 0)) : 1.0;
   else
     lb = __dadd_rn(1.0, __dmul_rn(8.729, dpow_n2(__dsub_rn(1.0, dexp(__dmul_rn(-0.030, wsv))), 2.155, 0)));
-  const double hb = __dadd_rn(hros, bros);
-  const double ilb = __ddiv_rn(1.0, lb);   // one reciprocal for FROS and e
-  const double fros = __dmul_rn(__dmul_rn(hb, ilb), 0.5);
-  const double a = __dmul_rn(hb, 0.5);
-  const double e = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(ilb, ilb)));
-  o->hros = hros; o->bros = bros; o->lb = lb; o->fros = fros; o->a = a; o->e = e;
-  o->ux = ux; o->uy = uy; o->wsv = wsv; o->wse = wse;
-  // cos(phi_k) = (cos theta_k) ux + (sin theta_k) uy for the 8 axes, whose
-  // cosines and sines are 0, +-1 and +-h (h = RN(sqrt(1/2))): products by 0 and
-  // +-1 are exact, so the sums are ux, uy, their negatives and +-(h ux) +- (h uy)
-  // -- the same values (up to the sign of a zero, which no test below sees)
-  const double h = 0x1.6a09e667f3bcdp-1;
-  const double hx = __dmul_rn(h, ux), hy = __dmul_rn(h, uy);
-  const double dpp = __dadd_rn(hx, hy), dmp = __dsub_rn(hy, hx);
-  const double cphk[8] = {ux, dpp, uy, dmp, -ux, -dpp, -uy, -dmp};
-  if (ellipse_mode == 0) {
-    const double A = __dmul_rn(a, __dsub_rn(1.0, __dmul_rn(e, e)));
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const double cphi = cphk[k];
-      // cphi > 0 as a sign test on the bits (cphi is never NaN)
-      o->ros[k] = (__double_as_longlong(cphi) > 0) ? __ddiv_rn(A, __dsub_rn(1.0, __dmul_rn(e, cphi))) : A;
-    }
-  } else {
-    const double b = fros;
-    const double c = __dmul_rn(__dsub_rn(hros, bros), 0.5);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const double cphi = cphk[k];
-      double sphi2 = __dsub_rn(1.0, __dmul_rn(cphi, cphi));
-      if (sphi2 < 0.0) sphi2 = 0.0;
-      const double bc = __dmul_rn(__dmul_rn(__dmul_rn(b, b), cphi), cphi);
-      const double den = __dadd_rn(bc, __dmul_rn(__dmul_rn(a, a), sphi2));
-      const double root = __dsqrt_rn(__dadd_rn(bc, __dmul_rn(__dsub_rn(__dmul_rn(a, a), __dmul_rn(c, c)), sphi2)));
-      o->ros[k] = (den > 0.0)
-                      ? __ddiv_rn(__dadd_rn(__dmul_rn(__dmul_rn(__dmul_rn(b, b), c), cphi),
-                                            __dmul_rn(__dmul_rn(a, b), root)), den)
-                      : 0.0;
-    }
-  }
+  o->hros = hros; o->bros = bros; o->wsv = wsv; o->wse = wse;
+  ellipse_axes(hros, bros, lb, ux, uy, ellipse_mode, o);
 }
 
 // 2^32 fixed point of a non-negative real: 0 for non-positive / NaN, capped at

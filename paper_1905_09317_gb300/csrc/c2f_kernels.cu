@@ -200,10 +200,22 @@ __global__ void k_order_scatter(const uint8_t *fuel, const float *slope, const u
 }
 
 // the 8 axis rates and HROS of one burnable cell at one hour
+// (const_ros > 0: the deterministic test rates -- all 8 axes at const_ros, or,
+// with const_bros > 0 or const_lb > 1, the ellipse of HROS = const_ros,
+// BROS = const_bros (0: const_ros), LB = const_lb headed along the hour's wind)
 __device__ __forceinline__ double row_rates(int fuel, const float *slope, int64_t cell,
                                             const CellPrep &cp, const HourPrep &hp, double pcf,
-                                            double const_ros, int ellipse_mode, double ros[8]) {
+                                            double const_ros, double const_bros, double const_lb,
+                                            int ellipse_mode, double ros[8]) {
   if (pos(const_ros)) {
+    if (pos(const_bros) || gt_c(const_lb, 1.0)) {
+      FbpOut o;
+      ellipse_axes(const_ros, pos(const_bros) ? const_bros : const_ros, gt_c(const_lb, 1.0) ? const_lb : 1.0,
+                   hp.sin_w, hp.cos_w, ellipse_mode, &o);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) ros[k] = o.ros[k];
+      return const_ros;
+    }
 #pragma unroll
     for (int k = 0; k < 8; ++k) ros[k] = const_ros;
     return const_ros;
@@ -242,7 +254,7 @@ __global__ void __launch_bounds__(128) k_ros_table(RosTableArgs a) {
     for (int k = 0; k < 8; ++k) ros[k] = 0.0;
   } else {
     hr = row_rates(a.fuel[cell], a.slope, cell, a.cell[cell], a.hour[h], a.pcf, a.const_ros,
-                   a.ellipse_mode, ros);
+                   a.const_bros, a.const_lb, a.ellipse_mode, ros);
   }
   const size_t idx = (size_t)h * n + cell;
   if (a.base) {
@@ -394,7 +406,7 @@ __device__ __forceinline__ void table_chunk(const SimJob &J, int32_t h, int32_t 
     const int64_t cell = (int64_t)row * J.cols + col;
     double ros[8];
     const double hr = row_rates(__ldg(&J.fuel[cell]), J.slope, cell, J.cell[cell], J.hour[h], J.pcf,
-                                J.const_ros, J.ellipse_mode, ros);
+                                J.const_ros, J.const_bros, J.const_lb, J.ellipse_mode, ros);
     const size_t idx = (size_t)h * n + cell;
     row_store(J.base + idx * 8, J.hros + idx, ros, hr, J.dt2p32);
   }

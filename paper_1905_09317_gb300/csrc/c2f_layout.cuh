@@ -60,7 +60,7 @@ struct SimJob {
   const uint8_t *fuel;            // FBP inputs of the on-demand rows
   const float *slope;             // nullable
   const CellPrep *cell;
-  double pcf, const_ros, dt2p32;
+  double pcf, const_ros, const_bros, const_lb, dt2p32;
   int32_t ellipse_mode;
   // weather scenarios (Sec. 3.1, uncertainty (3)): with n_scen > 1 the table
   // holds n_scen stacked tables ([n_scen][scen_hours] rows of base / hros /
@@ -115,7 +115,7 @@ struct RosTableArgs {
   const CellPrep *cell;
   const HourPrep *hour;    // indexed by absolute hour
   int32_t hour0;
-  double pcf, const_ros, dt2p32;
+  double pcf, const_ros, const_bros, const_lb, dt2p32;
   int32_t ellipse_mode;
   int64_t *base;           // [hour][N][8] (absolute hour), or nullptr
   double *hros;            // [hour][N], or nullptr

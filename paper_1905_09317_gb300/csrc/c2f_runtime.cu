@@ -101,10 +101,10 @@ struct DevBuf {
 
 struct TableKey {
   int32_t hours = 0, dt = 0, ellipse = 0;
-  double pc = 0, curing = 0, const_ros = 0;
+  double pc = 0, curing = 0, const_ros = 0, const_bros = 0, const_lb = 0;
   bool same_options(const TableKey &o) const {
     return dt == o.dt && ellipse == o.ellipse && pc == o.pc && curing == o.curing &&
-           const_ros == o.const_ros;
+           const_ros == o.const_ros && const_bros == o.const_bros && const_lb == o.const_lb;
   }
 };
 
@@ -343,6 +343,8 @@ int validate_params(c2f_ctx *ctx, const Landscape &L, const c2f_sim_params *p) {
     return fail(ctx, C2F_EINVAL, "o1_curing_pct must lie in [0, 100]");
   if (!(p->m1_pc >= 0.0 && p->m1_pc <= 100.0)) return fail(ctx, C2F_EINVAL, "m1_pc must lie in [0, 100]");
   if (!(p->const_ros >= 0.0 && p->const_ros < 1e9)) return fail(ctx, C2F_EINVAL, "const_ros out of range");
+  if (!(p->const_bros >= 0.0 && p->const_bros < 1e9) || !(p->const_lb >= 0.0 && p->const_lb <= 1e3))
+    return fail(ctx, C2F_EINVAL, "const_bros / const_lb out of range");
   if (!(p->burn_hours_min == 0 && p->burn_hours_max == 0) &&
       !(p->burn_hours_min >= 1 && p->burn_hours_min <= p->burn_hours_max && p->burn_hours_max <= 24))
     return fail(ctx, C2F_EINVAL, "burning hours per day: 0, 0 or 1 <= min <= max <= 24");
@@ -367,6 +369,8 @@ TableKey key_of(const c2f_sim_params *p) {
   k.pc = p->m1_pc;
   k.curing = p->o1_curing_pct;
   k.const_ros = p->const_ros;
+  k.const_bros = p->const_ros > 0.0 ? p->const_bros : 0.0;
+  k.const_lb = p->const_ros > 0.0 ? p->const_lb : 0.0;
   return k;
 }
 
@@ -410,6 +414,8 @@ int fill_table(c2f_ctx *ctx, Landscape &L, cudaStream_t st) {
   a.hour0 = 0;
   a.pcf = k.pc / 100.0;
   a.const_ros = k.const_ros;
+  a.const_bros = k.const_bros;
+  a.const_lb = k.const_lb;
   a.dt2p32 = (double)k.dt * 4294967296.0;
   a.ellipse_mode = k.ellipse;
   a.base = T.base.as<int64_t>();
@@ -554,6 +560,8 @@ SimJob job_of(const Sim &s) {
   j.cell = L.cell_prep.as<CellPrep>();
   j.pcf = T.key.pc / 100.0;
   j.const_ros = T.key.const_ros;
+  j.const_bros = T.key.const_bros;
+  j.const_lb = T.key.const_lb;
   j.dt2p32 = (double)T.key.dt * 4294967296.0;
   j.ellipse_mode = T.key.ellipse;
   j.n_scen = T.n_scen;
@@ -1388,6 +1396,8 @@ C2F_API int c2f_get_ros_scenario(c2f_ctx *ctx, int32_t landscape_id, const c2f_s
     a.hour0 = hour;
     a.pcf = p->m1_pc / 100.0;
     a.const_ros = p->const_ros;
+    a.const_bros = p->const_ros > 0.0 ? p->const_bros : 0.0;
+    a.const_lb = p->const_ros > 0.0 ? p->const_lb : 0.0;
     a.dt2p32 = (double)p->minutes_per_step * 4294967296.0;
     a.ellipse_mode = p->ellipse_mode;
     a.ros8 = tmp.as<double>();

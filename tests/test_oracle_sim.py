@@ -25,12 +25,19 @@ def homog(rows, cols, wd=270.0, ws=0.0, hours=1, **params):
     return oracle.Oracle(fuel, weather=weather, **p)
 
 
-@pytest.mark.parametrize("name", ["hand_3x3.txt", "hand_5x5.txt"])
+@pytest.mark.parametrize("name", ["hand_3x3.txt", "hand_5x5.txt", "hand_wind_eq1_5x5.txt",
+                                  "hand_wind_ray_5x5.txt"])
 @pytest.mark.parametrize("runner", ["run_replica", "run_replica_event"])
 def test_hand_enumeration(name, runner):
+    """Hand-enumerated ignition steps and work: constant rates on all axes, and
+    under wind the ellipse of chosen (H, B, LB) by Eq. (1) and by the ray of
+    ellipse_mode 1, each axis's rate derived by hand (tests/golden/)."""
     meta, grid = read_golden_grid(name)
     g = np.array(grid)
-    o = homog(g.shape[0], g.shape[1], hours=int(meta["hours"]), const_ros=float(meta["const_ros"]))
+    o = homog(g.shape[0], g.shape[1], hours=int(meta["hours"]), const_ros=float(meta["const_ros"]),
+              wd=float(meta.get("wd_from", 270.0)), ws=float(meta.get("ws", 0.0)),
+              const_bros=float(meta.get("const_bros", 0.0)), const_lb=float(meta.get("const_lb", 0.0)),
+              ellipse_mode=int(meta.get("ellipse_mode", 0)))
     r = getattr(o, runner)(0)
     assert np.array_equal(r["ign"], g)
     assert r["work"] == int(meta["work"])
