@@ -257,6 +257,14 @@ C2F_API int c2f_cancel(c2f_ctx *ctx, int32_t sim_id);
 C2F_API int c2f_set_serving(c2f_ctx *ctx, int32_t max_inflight, int64_t max_epoch_replicas,
                             int64_t hbm_reserve_bytes);
 
+/* Serving statistics since the context was created: epochs launched,
+ * admission waits (times queued work was held back because free device
+ * memory did not cover the epoch plus the reserve while other epochs ran),
+ * and the simulations queued and epochs running now.  Any pointer may be
+ * NULL.  Does not pump. */
+C2F_API int c2f_serving_stats(c2f_ctx *ctx, int64_t *epochs, int64_t *admission_waits, int32_t *queued,
+                              int32_t *running);
+
 /* Burn-probability counts (Sec. 3.6 (i), Sec. 3.1 outputs): counts[c] = number
  * of replicas in which cell c ignited, uint32, rows*cols entries, host memory. */
 C2F_API int c2f_burn_prob(c2f_ctx *ctx, int32_t sim_id, uint32_t *counts);
@@ -336,6 +344,24 @@ C2F_API int c2f_compare_scars_device(c2f_ctx *ctx, int32_t sim_x, int32_t sim_y,
  * results never depend on this value (a tuning and test knob). */
 C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap);
 
+/* Bounded waits inside the frontier kernel: a warp that needs a lazy-table
+ * chunk which another warp of the launch is computing polls for it (about
+ * 130 ns a poll) and gives up after `polls` polls (0 = the default, 2^23,
+ * about a second); the simulation then fails with C2F_ETIMEOUT and the
+ * context stays usable.  polls outside [0, 2^32) is C2F_EINVAL. */
+C2F_API int c2f_set_wait_limit(c2f_ctx *ctx, int64_t polls);
+
+/* Test hook for the bounded wait above; the paper has no counterpart.  Marks
+ * the chunk (32 cells of one row of the bit-plane layout) holding `cell` at
+ * weather hour `hour` of `scenario` in the landscape's lazy table as being
+ * computed by a warp that will never finish, so that a simulation that needs
+ * it waits until the wait limit and fails with C2F_ETIMEOUT.  The table is
+ * unusable afterwards: rebuild it (c2f_build_ros with force 1 or 2).
+ * C2F_EINVAL when the landscape has no lazy table or an index is out of
+ * range.  Synchronous. */
+C2F_API int c2f_test_hold_chunk(c2f_ctx *ctx, int32_t landscape_id, int32_t scenario, int32_t hour,
+                                int32_t cell);
+
 /* Frontier-kernel launch shape: CTA size `threads` (32, 64 or 128; each warp
  * simulates one replica) and whether a window of each replica's bit planes
  * and its burning list are staged in shared memory (`smem` != 0, the default)
@@ -368,34 +394,42 @@ C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free frontier step.  The paper has no counterpart: this entry
- * point exists for callers that cannot allocate device memory (code running
- * inside a CUDA-graph capture it does not own, a host application that has
- * handed all device memory to its own allocator, a plugin forbidden to
- * allocate after start-up).  It runs Step 2 of Alg. 1 for every replica --
- * the same kernel and the same results as c2f_simulate -- taking all scratch
- * from one fixed 16 MiB device array inside the library (every GPU that loads
- * the library holds it until exit).  It calls no cudaMalloc, cudaFree or
- * allocating library routine.
+ * point exists for callers that cannot allocate device memory (a host
+ * application that has handed all device memory to its own allocator and
+ * forbids others to take more, a plugin forbidden to allocate after
+ * start-up).  It runs Step 2 of Alg. 1 for every replica -- the same kernel
+ * and the same results as c2f_simulate -- taking all scratch from one fixed
+ * 16 MiB device array inside the library (every GPU that loads the library
+ * holds it until exit).  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.
  *
  * Inputs (device memory, caller-owned, not modified): the burnable bit plane
  * (rows * ceil(cols/32) 32-bit words, rows padded to whole words, bit = fuel
  * and not harvested), the rate-of-spread table `base` ([hours][rows*cols][8]
  * int64, the per-period fixed-point increments that c2f_get_ros exports for
  * the same minutes_per_step) and `hros` ([hours][rows*cols]), and the
- * ignition cell of every replica.  Outputs (device memory, caller-owned):
- * scars ([n_replicas][rows * ceil(cols/32)] words, same layout as the plane),
- * work and n_ignited per replica.  From *p it uses seed, n_replicas (at most
- * 65536), hours, minutes_per_step, ros_sigma, ros_threshold, burnout_delta.
+ * ignition cell of every replica: each must be a cell id in [0, rows*cols)
+ * whose burnable bit is set, else the call gives C2F_EINVAL (the kernel
+ * checks it and touches nothing for that replica).  Outputs (device memory,
+ * caller-owned): scars ([n_replicas][rows * ceil(cols/32)] words, same layout
+ * as the plane), work and n_ignited per replica.  From *p it uses seed,
+ * n_replicas (at most 65536), hours, minutes_per_step, ros_sigma,
+ * ros_threshold, burnout_delta, burn_hours_min and burn_hours_max, with the
+ * meaning and the checks of c2f_simulate.
  *
- * Limits: the two bit planes of one replica plus at least 256 burning-list
- * entries must fit the array (about 28 million cells); larger landscapes give
+ * Limits: the two bit planes of one replica (rows * ceil(cols/32) * 8 bytes)
+ * plus 256 burning-list entries of 78 bytes and a header of about 12 bytes
+ * per replica must fit the 16 MiB array: about 67 million cells (a square
+ * grid of up to 8,180 x 8,180 cells with one replica); larger landscapes give
  * C2F_EINVAL before any device work.  A replica whose burning list outgrows
  * the whole array gives C2F_ENOMEM.  Each call clears what must start at
  * zero; all calls share the array and it keeps the last call's contents, so
  * calls that overlap on the GPU (other streams, other host threads) race.
  * The first call on a device looks up the array's device address and loads
- * the library's constant tables (once per device, with that device current);
- * make that first call before any stream capture.  Synchronous: returns after the work on `stream` has finished.
+ * the library's constant tables (once per device, with that device current).
+ * Synchronous: the call waits for `stream`, reads the replicas' statuses on
+ * the host and re-runs replicas whose burning lists overflowed, so it must
+ * not be made on a stream that is being captured into a CUDA graph.
  * ------------------------------------------------------------------------- */
 typedef struct {
   int32_t rows, cols;

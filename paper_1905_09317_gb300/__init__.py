@@ -110,6 +110,8 @@ _SIGS = [
     ("c2f_wait", C.c_int, [C.c_void_p, C.c_int32]),
     ("c2f_cancel", C.c_int, [C.c_void_p, C.c_int32]),
     ("c2f_set_serving", C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_int64]),
+    ("c2f_serving_stats", C.c_int, [C.c_void_p, _P(C.c_int64), _P(C.c_int64), _P(C.c_int32),
+                                    _P(C.c_int32)]),
     ("c2f_set_table_mode", C.c_int, [C.c_void_p, C.c_int]),
     ("c2f_burn_prob", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_burn_prob_device", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
@@ -125,6 +127,8 @@ _SIGS = [
                                            C.c_void_p]),
     ("c2f_set_list_capacity", C.c_int, [C.c_void_p, C.c_int64]),
     ("c2f_set_frontier_config", C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
+    ("c2f_set_wait_limit", C.c_int, [C.c_void_p, C.c_int64]),
+    ("c2f_test_hold_chunk", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     ("c2f_autotune", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
                                 _P(C.c_int32), _P(C.c_int32), _P(C.c_double)]),
     ("c2f_profile", C.c_int, [C.c_void_p, C.c_int]),
@@ -178,13 +182,17 @@ def _ptr(a):
 class Context:
     """One c2f context on a CUDA device (owns a stream and all device memory)."""
 
-    def __init__(self, device: int = 0, allocator: str | None = None):
-        """allocator: None (the library's stream-ordered cudaMallocAsync) or
-        "torch" (device memory from PyTorch's caching allocator)."""
+    def __init__(self, device: int = 0, allocator=None):
+        """allocator: None (the library's stream-ordered cudaMallocAsync),
+        "torch" (device memory from PyTorch's caching allocator) or an
+        AllocHooks instance (kept alive by the context)."""
         self.lib = load_library()
         h = C.c_void_p()
         self._hooks = None
-        if allocator == "torch":
+        if isinstance(allocator, AllocHooks):
+            self._hooks = allocator
+            rc = self.lib.c2f_create_with_hooks(C.byref(h), int(device), C.byref(self._hooks))
+        elif allocator == "torch":
             self._hooks = torch_alloc_hooks(int(device))
             rc = self.lib.c2f_create_with_hooks(C.byref(h), int(device), C.byref(self._hooks))
         elif allocator is None:
@@ -301,6 +309,11 @@ class Context:
         self._check(self.lib.c2f_set_serving(self.h, int(max_inflight), int(max_epoch_replicas),
                                              int(hbm_reserve_bytes)))
 
+    def serving_stats(self) -> dict:
+        e, w, q, r = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int32()
+        self._check(self.lib.c2f_serving_stats(self.h, C.byref(e), C.byref(w), C.byref(q), C.byref(r)))
+        return dict(epochs=e.value, admission_waits=w.value, queued=q.value, running=r.value)
+
     # ---- outputs
     def burn_prob(self, sim_id: int, n_cells: int) -> np.ndarray:
         out = np.empty(n_cells, dtype=np.uint32)
@@ -368,6 +381,16 @@ class Context:
 
     def set_list_capacity(self, cap: int) -> None:
         self._check(self.lib.c2f_set_list_capacity(self.h, int(cap)))
+
+    def set_wait_limit(self, polls: int) -> None:
+        """Polls before a frontier wait for a lazy-table chunk gives up (0 = default)."""
+        self._check(self.lib.c2f_set_wait_limit(self.h, int(polls)))
+
+    def test_hold_chunk(self, landscape_id: int, hour: int, cell: int, scenario: int = 0) -> None:
+        """Test hook: mark the lazy-table chunk of `cell` at `hour` as held by a
+        computation that never finishes (exercises the bounded wait)."""
+        self._check(self.lib.c2f_test_hold_chunk(self.h, int(landscape_id), int(scenario), int(hour),
+                                                 int(cell)))
 
     def set_frontier_config(self, threads: int, smem_plane_bytes: int) -> None:
         self._check(self.lib.c2f_set_frontier_config(self.h, int(threads), int(smem_plane_bytes)))

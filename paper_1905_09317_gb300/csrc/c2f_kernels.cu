@@ -390,8 +390,9 @@ __device__ __forceinline__ uint32_t ld_state(const uint32_t *p) {
   return v;
 }
 
-// waits for a table chunk that another warp is computing give up after this
-// many polls (about a second); the replica then reports an internal error
+// waits for a table chunk that another warp is computing give up after
+// FrontierArgs::wait_limit polls (this many when it is 0: about a second);
+// the replica then stops with status 4 (a bounded wait ran out)
 constexpr uint32_t kChunkSpinLimit = 1u << 23;
 
 // On-demand table rows: the rows at hour h of the 32 cells of bit-plane word w
@@ -515,6 +516,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
   const uint32_t lt = (1u << lane) - 1u;
   const size_t slot = (size_t)blockIdx.x * WPC + wib;
   const int32_t cap = A.cap;
+  const uint32_t wait_limit = A.wait_limit ? A.wait_limit : kChunkSpinLimit;
   uint32_t *my = s_dyn + (size_t)wib * A.smem_warp_words;   // [Available win][Burned win][lists]
   uint32_t *erc;     // row << 16 | col
   uint8_t *emask, *enext, *ecofs;
@@ -590,6 +592,14 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
     int32_t *istep = J.ign_step ? J.ign_step + (size_t)r * n : nullptr;
     const int64_t dk = (k & 1) ? J.d_diag : J.d_orth;   // this lane's axis length
     const int32_t ic = J.ign_cell[r];
+    // an ignition cell outside the grid or not burnable (possible only for
+    // ignition cells a caller passes in): status 3, nothing else is written
+    if ((uint32_t)ic >= (uint32_t)n ||
+        !((__ldg(&burnable[(ic / cols) * wpr + ((ic % cols) >> 5)]) >> ((ic % cols) & 31)) & 1u)) {
+      if (lane == 0) J.status[r] = 3;
+      __syncwarp();
+      continue;
+    }
     const int32_t ir = ic / cols, icc = ic - ir * cols;
     // window of the done-chunk bitmap, centred on the ignition cell like the planes'
     const int32_t dr0 = min(max(ir - kWinRows / 2, 0), max(rows - kWinRows, 0));
@@ -648,6 +658,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
     // all lanes on one chunk), waited for when another warp is computing it --
     // that warp is running and never waits while it holds a claim.
     auto ensure = [&](int32_t h, bool valid, int32_t cr, int32_t cc, uint32_t slots) {
+      if (status != 0) return;   // the replica has stopped: no more claims or waits
       if (!valid) slots = 0;
       uint32_t todo = __reduce_or_sync(FULL, slots);
       uint32_t *sth = J.chunk_state + (size_t)h * pw;
@@ -681,15 +692,16 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         if (mine && inwin) atomicOr(&dbits[bi >> 5], 1u << (bi & 31));
         if (need) {
           uint32_t polls = 0;
+          bool gave_up = false;
           while (ld_state(sth + w) < 2u) {
-            if (++polls > kChunkSpinLimit) { status = 2; break; }
+            if (++polls > wait_limit) { status = 4; gave_up = true; break; }
             __nanosleep(128);
           }
-          if (polls <= kChunkSpinLimit && inwin) atomicOr(&dbits[bi >> 5], 1u << (bi & 31));
+          if (!gave_up && inwin) atomicOr(&dbits[bi >> 5], 1u << (bi & 31));
         }
         __syncwarp();
       }
-      if (__any_sync(FULL, status == 2)) status = 2;
+      status = (int32_t)__reduce_max_sync(FULL, (uint32_t)status);   // the warp's worst status
     };
 
     // drop Burned cells and cells with no open axis from the burning list

@@ -84,7 +84,9 @@ struct SimJob {
   int64_t *work;                  // [R]
   int32_t *n_ignited;             // [R]
   int32_t *ign_cell;              // [R]
-  int32_t *status;                // [R] 0 ok, 1 list capacity exceeded, 2 internal error
+  int32_t *status;                // [R] 0 ok, 1 list capacity exceeded, 2 internal error,
+                                  //     3 ignition cell outside the grid or not burnable,
+                                  //     4 a bounded wait (for a lazy table chunk) ran out
 };
 
 struct FrontierArgs {
@@ -104,6 +106,7 @@ struct FrontierArgs {
   uint32_t *brn_scratch;          // [slots][pw_max] Burned planes
   uint32_t *avail_scratch;        // [slots][pw_max] Available planes (global-plane variant)
   int64_t smem_warp_words;        // 32-bit words of dynamic shared memory per warp
+  uint32_t wait_limit;            // polls before a wait for a table chunk gives up; 0 = default
 };
 
 // K1 launch arguments: grid.y covers hours hour0 .. hour0 + gridDim.y - 1

@@ -120,6 +120,7 @@ struct Table {
   std::shared_ptr<DevBuf> weather;
   DevBuf hour_prep, base, hros, chunk_state;
   bool eager = false;
+  bool issued = false;   // its build (K1 or the cleared chunk states) has been issued
   cudaEvent_t ready = nullptr;   // recorded after the build; epochs on other streams wait on it
   Table() = default;
   Table(const Table &) = delete;
@@ -216,6 +217,7 @@ struct c2f_ctx {
   bool eager_tables = true;   // simulations build their tables with K1 up front
   int64_t cap_override = 0;
   int64_t graph_launches = 0;
+  uint32_t wait_limit = 0;     // frontier waits for table chunks: polls before giving up; 0 = default
   // serving
   std::vector<std::shared_ptr<Sim>> pending;
   std::list<std::unique_ptr<Epoch>> inflight;
@@ -223,6 +225,8 @@ struct c2f_ctx {
   int max_inflight = 3;
   int64_t max_epoch_replicas = 1 << 16;
   int64_t hbm_reserve = int64_t(2) << 30;
+  int64_t epochs_launched = 0;   // serving statistics
+  int64_t admission_waits = 0;   // times queued work was held back for device memory
   cudaStream_t read_stream = nullptr;   // result reads: not queued behind table builds
   cudaStream_t load_stream = nullptr;   // landscape uploads: not queued behind table builds
   // kernel timing
@@ -374,16 +378,21 @@ TableKey key_of(const c2f_sim_params *p) {
   return k;
 }
 
+// a table whose build was never issued (a later step of the call that
+// prepared it failed) is not reused: the next call prepares a new one
 bool table_ok(const Landscape &L, const TableKey &k) {
-  return L.table && L.table->key.same_options(k) && L.table->key.hours >= k.hours;
+  return L.table && L.table->issued && L.table->key.same_options(k) && L.table->key.hours >= k.hours;
 }
 
 // A new table object for the options in k (allocation only); the previous one
-// stays alive while simulations that ran on it still hold it.
-int prepare_table(c2f_ctx *ctx, Landscape &L, const TableKey &k) {
+// stays alive while simulations that ran on it still hold it.  `eager`: the
+// table will be filled by K1 (launch_table with eager), so frontiers planned
+// before that launch is issued read it as complete (they run after it).
+int prepare_table(c2f_ctx *ctx, Landscape &L, const TableKey &k, bool eager) {
   int rc;
   auto T = std::make_shared<Table>();
   T->key = k;
+  T->eager = eager;
   T->n_scen = L.n_scen;
   T->prep_hours = L.n_hours;
   T->weather = L.weather_dev;
@@ -459,6 +468,7 @@ int launch_table(c2f_ctx *ctx, Landscape &L, cudaStream_t st, bool eager) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   CK(cudaStreamIsCapturing(st, &cs));
   if (cs == cudaStreamCaptureStatusNone) CK(cudaEventRecord(T.ready, st));
+  T.issued = true;
   return C2F_OK;
 }
 
@@ -472,7 +482,7 @@ int ensure_table(c2f_ctx *ctx, Landscape &L, const TableKey &k, int mode) {
     CK(cudaEventRecord(L.table->ready, ctx->stream));
     return C2F_OK;
   }
-  int rc = prepare_table(ctx, L, k);
+  int rc = prepare_table(ctx, L, k, mode != 2);
   if (rc) return rc;
   return launch_table(ctx, L, ctx->stream, mode != 2);
 }
@@ -495,7 +505,10 @@ int64_t default_cap(const c2f_ctx *ctx, const Landscape &L) {
   return std::min<int64_t>(L.n, c);
 }
 
-int ensure_scratch(c2f_ctx *ctx, Scratch &S, cudaStream_t st, int64_t slots, int64_t cap, int64_t pw) {
+// (a failed allocation releases the whole scratch, so that no buffer is left
+// behind sizes that claim it is large enough)
+int ensure_scratch(c2f_ctx *ctx, Scratch &S, cudaStream_t st, int64_t slots, int64_t cap, int64_t pw);
+int ensure_scratch_once(c2f_ctx *ctx, Scratch &S, cudaStream_t st, int64_t slots, int64_t cap, int64_t pw) {
   int rc;
   if (!(slots <= S.slots && cap <= S.cap && S.ent_cell.p)) {
     slots = std::max(slots, S.slots);
@@ -519,6 +532,12 @@ int ensure_scratch(c2f_ctx *ctx, Scratch &S, cudaStream_t st, int64_t slots, int
     S.avail_words = S.slots * pw;
   }
   return C2F_OK;
+}
+
+int ensure_scratch(c2f_ctx *ctx, Scratch &S, cudaStream_t st, int64_t slots, int64_t cap, int64_t pw) {
+  const int rc = ensure_scratch_once(ctx, S, st, slots, cap, pw);
+  if (rc) S.reset();
+  return rc;
 }
 
 // output buffers of a simulation, allocated and initialised on stream st
@@ -676,6 +695,7 @@ int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, i
   A.brn_scratch = S.brn.as<uint32_t>();
   A.avail_scratch = S.avail.as<uint32_t>();
   A.smem_warp_words = warp_words;
+  A.wait_limit = ctx->wait_limit;
   F.cap = cap;
   return C2F_OK;
 }
@@ -739,7 +759,10 @@ int finish_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st) 
       CK(cudaMemcpyAsync(stv.data(), F.sims[i]->status.p, 4 * (size_t)R, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       for (int32_t r = 0; r < R; ++r) {
-        if (stv[r] == 2) return fail(ctx, C2F_ECUDA, "internal frontier error (replica %d)", r);
+        if (stv[r] == 4)
+          return fail(ctx, C2F_ETIMEOUT, "a wait for a table chunk ran out (replica %d)", r);
+        if (stv[r] == 3) return fail(ctx, C2F_EINVAL, "ignition cell not burnable (replica %d)", r);
+        if (stv[r] > 1) return fail(ctx, C2F_ECUDA, "internal frontier error (replica %d)", r);
         if (stv[r]) failed.push_back(F.begin[i] + r);
       }
     }
@@ -797,7 +820,7 @@ int make_sims(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_sim_params 
       if (ids[k] == ids[i]) want.hours = std::max(want.hours, params[k].hours);
     if (serving && !table_ok(*lands[i], want)) want.hours = std::max(want.hours, lands[i]->n_hours);
     if (!table_ok(*lands[i], want)) {
-      if ((rc = prepare_table(ctx, *lands[i], want))) return rc;
+      if ((rc = prepare_table(ctx, *lands[i], want, ctx->eager_tables))) return rc;
       if (built) built->push_back(lands[i].get());
       else if ((rc = launch_table(ctx, *lands[i], ctx->stream, ctx->eager_tables))) return rc;
     }
@@ -923,19 +946,21 @@ int simulate_many(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_sim_par
     return lrc;
   };
   if (graph) {
+    // the builds captured below run only if the graph is launched
+    auto unissue = [&]() { for (Landscape *L : builds) L->table->issued = false; };
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     const int lrc = issue();
     cudaGraph_t gr = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &gr);
-    if (lrc) { if (gr) cudaGraphDestroy(gr); cleanup(); return lrc; }
-    if (ce != cudaSuccess) { cleanup(); return cuda_fail(ctx, ce, "cudaStreamEndCapture"); }
+    if (lrc) { if (gr) cudaGraphDestroy(gr); unissue(); cleanup(); return lrc; }
+    if (ce != cudaSuccess) { unissue(); cleanup(); return cuda_fail(ctx, ce, "cudaStreamEndCapture"); }
     cudaGraphExec_t ge = nullptr;
     const cudaError_t ie = cudaGraphInstantiate(&ge, gr, 0);
     cudaGraphDestroy(gr);
-    if (ie != cudaSuccess) { cleanup(); return cuda_fail(ctx, ie, "cudaGraphInstantiate"); }
+    if (ie != cudaSuccess) { unissue(); cleanup(); return cuda_fail(ctx, ie, "cudaGraphInstantiate"); }
     const cudaError_t le = cudaGraphLaunch(ge, ctx->stream);
     cudaGraphExecDestroy(ge);
-    if (le != cudaSuccess) { cleanup(); return cuda_fail(ctx, le, "cudaGraphLaunch"); }
+    if (le != cudaSuccess) { unissue(); cleanup(); return cuda_fail(ctx, le, "cudaGraphLaunch"); }
     ++ctx->graph_launches;
   } else {
     if ((rc = issue())) { cudaStreamSynchronize(ctx->stream); cleanup(); return rc; }
@@ -1033,6 +1058,7 @@ int launch_pending(c2f_ctx *ctx) {
   }
   if (avail < epoch_bytes(ctx, batch) + ctx->hbm_reserve && !ctx->inflight.empty()) {
     ctx->pending.insert(ctx->pending.begin(), batch.begin(), batch.end());   // admission: wait for memory
+    ++ctx->admission_waits;
     return C2F_OK;
   }
   std::unique_ptr<Epoch> E(new Epoch());
@@ -1061,6 +1087,7 @@ int launch_pending(c2f_ctx *ctx) {
   }
   CK(cudaEventRecord(E->done, E->stream));
   ctx->inflight.push_back(std::move(E));
+  ++ctx->epochs_launched;
   return C2F_OK;
 }
 
@@ -1774,6 +1801,46 @@ C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap) {
   LOCK;
   if (cap < 0 || cap > (1LL << 31)) return fail(ctx, C2F_EINVAL, "capacity out of range");
   ctx->cap_override = cap;
+  return C2F_OK;
+}
+
+C2F_API int c2f_serving_stats(c2f_ctx *ctx, int64_t *epochs, int64_t *admission_waits, int32_t *queued,
+                              int32_t *running) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  if (epochs) *epochs = ctx->epochs_launched;
+  if (admission_waits) *admission_waits = ctx->admission_waits;
+  if (queued) *queued = (int32_t)ctx->pending.size();
+  if (running) *running = (int32_t)ctx->inflight.size();
+  return C2F_OK;
+}
+
+C2F_API int c2f_set_wait_limit(c2f_ctx *ctx, int64_t polls) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  if (polls < 0 || polls > 0xFFFFFFFFLL) return fail(ctx, C2F_EINVAL, "wait limit out of range");
+  ctx->wait_limit = (uint32_t)polls;
+  return C2F_OK;
+}
+
+C2F_API int c2f_test_hold_chunk(c2f_ctx *ctx, int32_t landscape_id, int32_t scenario, int32_t hour,
+                                int32_t cell) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  auto L = find_land(ctx, landscape_id);
+  if (!L) return fail(ctx, C2F_ENOTFOUND, "unknown landscape %d", landscape_id);
+  if (!L->table || L->table->eager) return fail(ctx, C2F_EINVAL, "the landscape has no lazy table");
+  const Table &T = *L->table;
+  if (scenario < 0 || scenario >= T.n_scen || hour < 0 || hour >= T.key.hours || cell < 0 || cell >= L->n)
+    return fail(ctx, C2F_EINVAL, "scenario, hour or cell out of range");
+  CK(cudaSetDevice(ctx->device));
+  const int32_t row = (int32_t)(cell / L->cols), col = (int32_t)(cell % L->cols);
+  const size_t idx = ((size_t)scenario * T.key.hours + (size_t)hour) * (size_t)L->rows * L->wpr +
+                     (size_t)row * L->wpr + (size_t)(col >> 5);
+  static const uint32_t kBeingComputed = 1u;
+  CK(cudaMemcpyAsync(T.chunk_state.as<uint32_t>() + idx, &kBeingComputed, 4, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return C2F_OK;
 }
 

@@ -1,15 +1,20 @@
 // c2f_static.cu -- c2f_frontier_static: the frontier kernel for callers that
 // cannot allocate device memory.
 //
-// Some callers of this library may not call cudaMalloc at all: code that runs
-// inside a CUDA-graph capture they do not own, a host with a fixed device
-// memory budget already carved up by another allocator, or a plugin whose
-// host application forbids new device allocations after start-up.  For them
-// this entry point runs the frontier step (ignited replicas -> scars, work
-// counts) with every byte of scratch taken from one file-scope device array
-// of fixed size, kStaticScratchBytes.  The caller passes the inputs (burnable
-// plane, rate-of-spread table, ignition cells) and the outputs in device
-// memory.  No cudaMalloc, cudaFree or allocating library routine is called.
+// Some callers of this library may not call cudaMalloc at all: a host
+// application that has handed all device memory to its own allocator and
+// forbids others to take more, or a plugin loaded into such a host that may
+// not allocate after start-up.  For them this entry point runs the frontier
+// step (ignited replicas -> scars, work counts) with every byte of scratch
+// taken from one file-scope device array of fixed size, kStaticScratchBytes.
+// The caller passes the inputs (burnable plane, rate-of-spread table,
+// ignition cells) and the outputs in device memory.  No cudaMalloc, cudaFree
+// or allocating library routine is called.
+//
+// The call is synchronous: it copies small arguments into the array, waits
+// for the stream, reads the per-replica statuses on the host and re-runs
+// replicas whose burning lists overflowed.  It must therefore not be issued
+// on a stream that is being captured into a CUDA graph.
 //
 // Every GPU that loads the library keeps this array until the process exits.
 // All calls share it and it keeps the last call's contents; the parts that
@@ -93,6 +98,9 @@ extern "C" C2F_API int c2f_frontier_static(const c2f_frontier_io *io, const c2f_
   if (!(p->ros_sigma >= 0.0 && p->ros_sigma <= 1.0)) return C2F_EINVAL;
   if (!std::isfinite(p->ros_threshold) || !std::isfinite(p->burnout_delta) || p->burnout_delta < 0.0)
     return C2F_EINVAL;
+  if (!(p->burn_hours_min == 0 && p->burn_hours_max == 0) &&
+      !(p->burn_hours_min >= 1 && p->burn_hours_min <= p->burn_hours_max && p->burn_hours_max <= 24))
+    return C2F_EINVAL;
   cudaStream_t st = (cudaStream_t)stream_ptr;
   const int32_t R = p->n_replicas;
   const int32_t wpr = (io->cols + 31) / 32;
@@ -133,6 +141,8 @@ extern "C" C2F_API int c2f_frontier_static(const c2f_frontier_io *io, const c2f_
   job.delta = p->burnout_delta;
   job.sph = 60 / p->minutes_per_step;
   job.hours = p->hours;
+  job.burn_min = p->burn_hours_min;   // A5 general condition (1), as in c2f_simulate
+  job.burn_max = p->burn_hours_max;
   job.d_orth = (int64_t)std::llrint(io->cell_size_m * 4294967296.0);
   job.d_diag = (int64_t)std::llrint((io->cell_size_m * std::sqrt(2.0)) * 4294967296.0);
   job.n_replicas = R;
@@ -206,7 +216,8 @@ extern "C" C2F_API int c2f_frontier_static(const c2f_frontier_io *io, const c2f_
     if (e != cudaSuccess) { cudaGetLastError(); return C2F_ECUDA; }
     items.clear();
     for (int32_t r = 0; r < R; ++r) {
-      if (status[r] == 2) return C2F_ECUDA;
+      if (status[r] == 3) return C2F_EINVAL;   // ignition cell outside the grid or not burnable
+      if (status[r] > 1) return C2F_ECUDA;
       if (status[r] == 1) items.push_back(r);
     }
     if (items.empty()) return C2F_OK;
