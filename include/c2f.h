@@ -392,6 +392,18 @@ C2F_API int c2f_autotune(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
 C2F_API int c2f_profile(c2f_ctx *ctx, int enable);
 C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches);
 
+/* Per-replica frontier profile of a simulation run while profiling was on
+ * (c2f_profile): counters[r*16 + i] for replica r (SM clock cycles, counts),
+ * i = 0 cycles of the replica's whole frontier run (its last attempt),
+ * 1 cycles at hour boundaries, 2 cycles finding and sending crossings and
+ * receiving (A), 3 cycles setting up newly ignited cells (C), 4 fire periods
+ * visited, 5 burning cells with a crossing processed, 6 cells ignited,
+ * 7 longest burning list, 8 cycles of (A) spent scanning the list for
+ * crossings, 9 scan steps, 10 rounds of crossing cells, 11 new-cell set-up
+ * iterations, 12-15 zero.  Host memory, n_replicas*16 int64.  C2F_EINVAL if
+ * the simulation ran without profiling. */
+C2F_API int c2f_get_replica_profile(c2f_ctx *ctx, int32_t sim_id, int64_t *counters);
+
 /* ---------------------------------------------------------------------------
  * Allocation-free frontier step.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory (a host
@@ -418,7 +430,7 @@ C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches);
  * meaning and the checks of c2f_simulate.
  *
  * Limits: the two bit planes of one replica (rows * ceil(cols/32) * 8 bytes)
- * plus 256 burning-list entries of 78 bytes and a header of about 12 bytes
+ * plus 256 burning-list entries of 80 bytes and a header of about 12 bytes
  * per replica must fit the 16 MiB array: about 67 million cells (a square
  * grid of up to 8,180 x 8,180 cells with one replica); larger landscapes give
  * C2F_EINVAL before any device work.  A replica whose burning list outgrows

@@ -133,6 +133,7 @@ _SIGS = [
                                 _P(C.c_int32), _P(C.c_int32), _P(C.c_double)]),
     ("c2f_profile", C.c_int, [C.c_void_p, C.c_int]),
     ("c2f_kernel_times", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("c2f_get_replica_profile", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_fp64_peak", C.c_int, [C.c_void_p, _P(C.c_double)]),
     ("c2f_release", C.c_int, [C.c_void_p, C.c_int32]),
     ("c2f_frontier_static", C.c_int, [C.c_void_p, _P(SimParams), C.c_void_p]),
@@ -419,6 +420,15 @@ class Context:
         n = np.zeros(len(KERNEL_FAMILIES), dtype=np.int64)
         self._check(self.lib.c2f_kernel_times(self.h, _ptr(ms), _ptr(n)))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_FAMILIES)}
+
+    def replica_profile(self, sim_id: int, n_replicas: int) -> np.ndarray:
+        """(n_replicas, 16) frontier counters of a simulation run with profiling on
+        (include/c2f.h, c2f_get_replica_profile): total, boundary, send and
+        new-cell cycles, visited periods, hit cells, ignited cells, longest
+        burning list, scan cycles, scan steps, hit rounds, new-cell iterations."""
+        out = np.empty((n_replicas, 16), dtype=np.int64)
+        self._check(self.lib.c2f_get_replica_profile(self.h, int(sim_id), _ptr(out)))
+        return out
 
     def release(self, id_: int) -> None:
         self._check(self.lib.c2f_release(self.h, int(id_)))

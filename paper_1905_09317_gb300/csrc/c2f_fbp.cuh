@@ -20,10 +20,6 @@
 
 namespace c2f {
 
-
-
-
-
 // FBP fuel-type coefficients (a, b, c of the RSI curve; q and BUI0 of the
 // build-up effect).  Table 1 of the paper maps grid code 1 -> C-1, 2 -> C-2,
 // 3 -> C-3; the remaining codes continue through the FBP fuel types.
@@ -59,10 +55,6 @@ inline void make_fuel_table(FuelCoef t[F_NCODES]) {
 
 __device__ __forceinline__ bool is_o1(int f) { return f == F_O1A || f == F_O1B; }
 
-
-
-
-
 __device__ __forceinline__ double rsi_curve(const FuelCoef &k, double isi) {
   const double x = __dsub_rn(1.0, dexp(__dmul_rn(-k.b, isi)));
   return __dmul_rn(k.a, dpow_n2(x, k.c, k.c2));
@@ -95,7 +87,6 @@ __device__ inline double isf_curve(const FuelCoef &k, double inv_am, double rsf)
 }
 
 __device__ inline double isf_of(int fuel, const HourPrep &hp, double sf, double pcf) {
-  const double cf = hp.cf;
   if (fuel == F_M1) {
     const double rsf_c2 = __dmul_rn(hp.rszf[F_C2], sf);
     const double rsf_d1 = __dmul_rn(hp.rszf[F_D1], sf);

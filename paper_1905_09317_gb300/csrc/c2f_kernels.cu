@@ -30,6 +30,7 @@
 // ones the period-by-period loop produces.
 #include <cstdint>
 #include <mutex>
+#include <type_traits>
 
 #include "c2f_fbp.cuh"
 
@@ -61,11 +62,16 @@ cudaError_t init_device_constants(int device) {
 }
 
 // axis k = 0..7 at 45 k degrees counter-clockwise from east: (row, col) offsets
-// E (0,+1), NE (-1,+1), N (-1,0), NW (-1,-1), W (0,-1), SW (+1,-1), S (+1,0), SE (+1,+1)
-__device__ __constant__ int kDR[8] = {0, -1, -1, -1, 0, 1, 1, 1};
-__device__ __constant__ int kDC[8] = {1, 1, 0, -1, -1, -1, 0, 1};
-__device__ __forceinline__ int axis_dr(int k) { return kDR[k]; }
-__device__ __forceinline__ int axis_dc(int k) { return kDC[k]; }
+// E (0,+1), NE (-1,+1), N (-1,0), NW (-1,-1), W (0,-1), SW (+1,-1), S (+1,0), SE (+1,+1),
+// kept as offset + 1 in the nibbles of one immediate: lanes index them with
+// different k, which a __constant__ table would serve one address at a time
+__device__ __forceinline__ int axis_dr(int k) { return (int)((0x22210001u >> (4 * k)) & 0xFu) - 1; }
+__device__ __forceinline__ int axis_dc(int k) { return (int)((0x21000122u >> (4 * k)) & 0xFu) - 1; }
+
+// bit 0 of each byte of x, gathered into bits 0..3 (byte 0 -> bit 0)
+__device__ __forceinline__ uint32_t byte_lsbs(uint32_t x) {
+  return (((x & 0x01010101u) * 0x00204081u) >> 21) & 0xFu;
+}
 
 // ------------------------------------------------------------------ set-up
 // burnable plane (bit per cell, rows padded to 32-bit words) and per-word counts
@@ -363,20 +369,16 @@ __device__ __forceinline__ uint32_t rc_pack(int32_t r, int32_t c) {
   return ((uint32_t)r << 16) | (uint32_t)c;
 }
 
-// One warp per replica; replicas come from a work list of (simulation,
-// replica) items that every warp pulls from.  The four 8-lane groups of the
-// warp each take one burning cell at a time, lane k owning axis k, so the
-// per-axis work of a cell (crossing tests, increments, crossing periods, the
-// burn-out test of the neighbour on that axis) runs side by side.  There is
-// no CTA barrier: the warp's own counters stay in registers, appends to the
-// burning list are placed by ballot + popc, and phases are ordered with
-// __syncwarp.  State per replica: one Available bit plane (burnable, not
-// harvested, not yet ignited -- an ignition is one atomicAnd, whose old value
-// also picks the single winner), in shared memory when it fits (SMEM) and in
-// per-warp global scratch otherwise, and a Burned plane in global scratch;
-// the scar plane (burnable and no longer Available) is written at the end.
+// a table row into L2 ahead of its use
 __device__ __forceinline__ void prefetch_l2(const void *p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// a 64-byte table row into this SM's L1 ahead of its use (both 32-byte
+// sectors); only for tables that no warp writes while the frontier runs
+__device__ __forceinline__ void prefetch_row_l1(const int64_t *row) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(row));
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(row + 4));
 }
 
 // chunk state, read at device scope from L2.  A relaxed load suffices: a warp
@@ -417,6 +419,26 @@ __device__ __forceinline__ void table_chunk(const SimJob &J, int32_t h, int32_t 
   __syncwarp();
 }
 
+// 32-bit atomics on words known to lie in shared memory
+__device__ __forceinline__ uint32_t atom_and_shared(uint32_t *p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.shared.and.b32 %0, [%1], %2;"
+               : "=r"(old) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ uint32_t atom_or_shared(uint32_t *p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.shared.or.b32 %0, [%1], %2;"
+               : "=r"(old) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ int32_t atom_exch_shared(int32_t *p, int32_t v) {
+  int32_t old;
+  asm volatile("atom.shared.exch.b32 %0, [%1], %2;"
+               : "=r"(old) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+  return old;
+}
+
 // The replica's Available and Burned bit planes.  With WIN, a window of
 // kWinRows x (32 kWinWords) cells around the ignition cell lives in shared
 // memory and the rest of the grid in global memory; without it, all in global
@@ -443,14 +465,45 @@ struct Planes {
   __device__ __forceinline__ bool avail(int32_t r, int32_t c) const { return (*avw(r, c) >> (c & 31)) & 1u; }
   __device__ __forceinline__ bool burned(int32_t r, int32_t c) const { return (*brw(r, c) >> (c & 31)) & 1u; }
   // ignition: clears the Available bit; true for the one caller that cleared it
+  // (a word of the window is changed with a shared-memory atomic, the others
+  // in global memory: an atomic on a generic address costs more than either)
   __device__ __forceinline__ bool take(int32_t r, int32_t c) const {
     const uint32_t bit = 1u << (c & 31);
-    return (atomicAnd(avw(r, c), ~bit) & bit) != 0;
+    const int32_t w = c >> 5;
+    if (in_win(r, w)) return (atom_and_shared(sav + (r - r0) * kWinWords + (w - w0), ~bit) & bit) != 0;
+    return (atomicAnd(gav + r * wpr + w, ~bit) & bit) != 0;
   }
   // burn-out: sets the Burned bit; true for the one caller that set it
   __device__ __forceinline__ bool burn(int32_t r, int32_t c) const {
     const uint32_t bit = 1u << (c & 31);
-    return (atomicOr(brw(r, c), bit) & bit) == 0;
+    const int32_t w = c >> 5;
+    if (in_win(r, w)) return (atom_or_shared(sbr + (r - r0) * kWinWords + (w - w0), bit) & bit) == 0;
+    return (atomicOr(gbr + r * wpr + w, bit) & bit) == 0;
+  }
+  // the Available neighbours of (r, c) as an 8-bit mask, bit k = axis k
+  // (neighbours outside the grid are not Available)
+  __device__ __forceinline__ uint32_t avail_mask(int32_t rows, int32_t cols, int32_t r, int32_t c) const {
+    if constexpr (WIN) {
+      // the common case, as in any_avail_nbr: three window rows, funnel shifts
+      const int32_t il = ((c - 1) >> 5) - w0, ih = ((c + 1) >> 5) - w0;
+      if (c >= 1 && r >= 1 && r + 1 < rows && (uint32_t)(r - 1 - r0) < (uint32_t)(kWinRows - 2) &&
+          (uint32_t)il < (uint32_t)kWinWords && (uint32_t)ih < (uint32_t)kWinWords) {
+        const uint32_t *p = sav + (r - 1 - r0) * kWinWords;
+        const uint32_t sh = (uint32_t)(c - 1) & 31u;
+        const uint32_t up = __funnelshift_r(p[il], p[ih], sh) & 7u;                  // NW N NE
+        const uint32_t mid = __funnelshift_r(p[kWinWords + il], p[kWinWords + ih], sh) & 7u;   // W . E
+        const uint32_t dn = __funnelshift_r(p[2 * kWinWords + il], p[2 * kWinWords + ih], sh) & 7u;  // SW S SE
+        return ((mid >> 2) & 1u) | (((up >> 2) & 1u) << 1) | (((up >> 1) & 1u) << 2) | ((up & 1u) << 3) |
+               ((mid & 1u) << 4) | ((dn & 1u) << 5) | (((dn >> 1) & 1u) << 6) | (((dn >> 2) & 1u) << 7);
+      }
+    }
+    uint32_t m = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int32_t nr = r + axis_dr(q), nc = c + axis_dc(q);
+      if (nr >= 0 && nr < rows && nc >= 0 && nc < cols && avail(nr, nc)) m |= 1u << q;
+    }
+    return m;
   }
   // some neighbour of (r, c) is still Available
   __device__ __forceinline__ bool any_avail_nbr(int32_t rows, int32_t cols, int32_t r, int32_t c) const {
@@ -494,32 +547,61 @@ struct Planes {
   }
 };
 
+// The bytes of an entry's crossing offsets: 0..sph-1 the offset in the hour
+// at which that axis reaches its neighbour's centre, kOpen an open axis with
+// no crossing this hour, kNone a closed axis (message sent, or the neighbour
+// was not Available when the axis was set up)
+constexpr uint32_t kOpen = 0xFEu;
+
+// the open axes of an entry (bytes that are not kNone) as an 8-bit mask
+__device__ __forceinline__ uint32_t open_axes(uint64_t c8) {
+  const uint32_t closed = byte_lsbs(__vcmpeq4((uint32_t)c8, 0xFFFFFFFFu)) |
+                          (byte_lsbs(__vcmpeq4((uint32_t)(c8 >> 32), 0xFFFFFFFFu)) << 4);
+  return ~closed & 0xFFu;
+}
+
+// the axes of an entry crossing at offset o as an 8-bit mask (bytewise compares)
+__device__ __forceinline__ uint32_t axes_at(uint64_t c8, uint32_t o) {
+  const uint32_t oo = o * 0x01010101u;
+  return byte_lsbs(__vcmpeq4((uint32_t)c8, oo)) | (byte_lsbs(__vcmpeq4((uint32_t)(c8 >> 32), oo)) << 4);
+}
+
 // One warp per replica; replicas come from a work list of (simulation,
-// replica) items that every warp pulls from.  The four 8-lane groups of the
-// warp each take one burning cell at a time, lane k owning axis k, so the
-// per-axis work of a cell (crossing tests, increments, crossing periods, the
-// burn-out test of the neighbour on that axis) runs side by side.  There is
-// no CTA barrier: the warp's counters stay in registers, appends to the
-// burning list are placed by ballot + popc, and phases are ordered with
-// __syncwarp.  Per replica: an Available plane (burnable, not harvested, not
-// yet ignited -- an ignition is one atomicAnd, whose old value also picks the
-// single winner) and a Burned plane; with WIN their window around the
-// ignition cell and the burning-list arrays sit in shared memory.  The scar
-// plane (burnable and no longer Available) is written at the end.
+// replica) items that every warp pulls from.  There is no CTA barrier: the
+// warp's counters stay in registers, appends to the burning list are placed
+// by ballot + popc, and phases are ordered with __syncwarp.  Per replica: an
+// Available plane (burnable, not harvested, not yet ignited -- an ignition is
+// one atomicAnd, whose old value also picks the single winner) and a Burned
+// plane; with WIN their window around the ignition cell and the burning-list
+// arrays sit in shared memory.  The scar plane (burnable and no longer
+// Available) is written at the end.
+//
+// Each hour the burning cells' crossings are kept in a calendar: one linked
+// list of list entries per crossing offset (an entry sits in the list of its
+// earliest crossing) and a 64-bit mask of the offsets whose lists are not
+// empty.  The next fire period to visit is the mask's lowest bit, and a
+// visited period walks only the entries that cross in it.  Work is laid out
+// one lane per cell, the 8 axes of a cell as independent chains in its lane:
+// at the hour boundary (every listed cell) and for the cells ignited in a
+// visited period.
 template <int WPC, bool WIN, bool LAZY>
 __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
+  // list links: 16 bits in shared memory (capacities there stay far below 2^16)
+  using Link = typename std::conditional<WIN, uint16_t, int32_t>::type;
+  constexpr int32_t kNil = -1;
   extern __shared__ __align__(16) uint32_t s_dyn[];
   __shared__ SimJob s_job[WPC];
   constexpr uint32_t FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int k = lane & 7, grp = lane >> 3;
+  const int k = lane & 7, grp = lane >> 3;   // new-cell set-up: lane k of group grp owns axis k
   const uint32_t lt = (1u << lane) - 1u;
   const size_t slot = (size_t)blockIdx.x * WPC + wib;
   const int32_t cap = A.cap;
   const uint32_t wait_limit = A.wait_limit ? A.wait_limit : kChunkSpinLimit;
   uint32_t *my = s_dyn + (size_t)wib * A.smem_warp_words;   // [Available win][Burned win][lists]
   uint32_t *erc;     // row << 16 | col
-  uint8_t *emask, *enext, *ecofs;
+  uint8_t *ecofs;    // 8 crossing-offset bytes per entry
+  Link *elink;       // next entry in the same calendar list
   Planes<WIN> pl;
   pl.gav = A.avail_scratch + slot * (size_t)A.pw_max;
   pl.gbr = A.brn_scratch + slot * (size_t)A.pw_max;
@@ -529,23 +611,21 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
     uint32_t *ls = my + 2 * kWinRows * kWinWords;
     erc = ls;
     ecofs = reinterpret_cast<uint8_t *>(ls + cap);
-    emask = reinterpret_cast<uint8_t *>(ls + 3 * (size_t)cap);
-    enext = emask + cap;
+    elink = reinterpret_cast<Link *>(ls + 3 * (size_t)cap);
   } else {
     pl.sav = pl.sbr = nullptr;
     erc = reinterpret_cast<uint32_t *>(A.ent_cell) + slot * cap;
-    emask = A.ent_mask + slot * cap;
-    enext = A.ent_next + slot * cap;
     ecofs = A.ent_cofs + slot * (size_t)cap * 8;
+    elink = reinterpret_cast<Link *>(A.ent_link) + slot * cap;
   }
   int64_t *eP = A.ent_P + slot * (size_t)cap * 8;
-  // next-event bytes are scanned four at a time when the list is word-aligned
-  // and its capacity a multiple of 4 (the runtime's lists are)
-  const bool words4 = (cap & 3) == 0 && (reinterpret_cast<uintptr_t>(enext) & 3u) == 0;
-  __shared__ int32_t s_hits[WPC][160];   // < 32 carried over + 128 gathered
+  __shared__ int32_t s_hits[WPC][32];                  // one round of crossing entries
+  __shared__ int32_t s_head[WPC][64];                  // calendar: first entry per offset
   __shared__ uint32_t s_dbits[WPC][LAZY ? kWinRows * kWinWords / 32 : 1];   // chunks known done this hour
   __shared__ int32_t s_claim[WPC][LAZY ? 32 : 1];
+  __shared__ long long s_prof[WPC][kProfCounters];
   int32_t *hitbuf = s_hits[wib];
+  int32_t *head = s_head[wib];
   uint32_t *dbits = s_dbits[wib];
   int32_t *claim = s_claim[wib];
   SimJob &J = s_job[wib];
@@ -625,6 +705,22 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       }
     __syncwarp();
 
+    // per-replica profile (J.prof, off unless the caller asked for it; the
+    // layout of c2f_get_replica_profile): cycles in all, at hour boundaries,
+    // finding + sending crossings and receiving (A), new-cell set-up (C);
+    // visited periods, crossing entries, new cells, longest list; cycles of
+    // (A) spent walking the period's calendar list, compactions within an
+    // hour, rounds of crossing entries, new-cell passes (32 cells each)
+    // (kept in shared memory, lane 0 only, so that they cost no registers)
+    const bool prof = J.prof != nullptr;
+    long long pc_t = 0;
+    long long *pq = s_prof[wib];
+    if (prof && lane == 0) {
+#pragma unroll
+      for (int i = 0; i < kProfCounters; ++i) pq[i] = 0;
+      pq[0] = clock64();
+    }
+
     // Step 1 of Alg. 1: the ignition cell burns from period 0
     int32_t live = 1, nign = 1, cnt = 1, status = 0;
     long long W = 0, s_done = 0;
@@ -634,15 +730,13 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         if (istep) istep[ic] = 0;
       }
       __syncwarp();
-      bool open = false;
+      const uint32_t am = pl.avail_mask(rows, cols, ir, icc);
       if (lane < 8) {
-        const int32_t nr = ir + axis_dr(k), nc = icc + axis_dc(k);
-        open = nr >= 0 && nr < rows && nc >= 0 && nc < cols && pl.avail(nr, nc);
+        eP[lane] = 0;
+        ecofs[lane] = (uint8_t)(((am >> lane) & 1u) ? kOpen : kNone);
       }
-      const uint32_t mask0 = __ballot_sync(FULL, open) & 0xFFu;
-      if (lane < 8) { eP[k] = 0; ecofs[k] = kNone; }
-      if (lane == 0) { erc[0] = rc_pack(ir, icc); emask[0] = (uint8_t)mask0; enext[0] = kNone; }
-      if (mask0 == 0) {   // no Available neighbour: Burned at the end of period 1
+      if (lane == 0) erc[0] = rc_pack(ir, icc);
+      if (am == 0) {   // no Available neighbour: Burned at the end of period 1
         if (lane == 0) pl.burn(ir, icc);
         live = 0;
         W = (H * sph >= 1) ? 1 : 0;
@@ -704,24 +798,37 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       status = (int32_t)__reduce_max_sync(FULL, (uint32_t)status);   // the warp's worst status
     };
 
+    // calendar: puts entry e into the list of offset nx; returns nx's bit
+    // (0 when the entry has no crossing left this hour)
+    auto push = [&](int32_t e, uint32_t nx) -> uint64_t {
+      if (nx >= (uint32_t)sph) return 0ull;
+      elink[e] = (Link)atom_exch_shared(&head[nx], e);
+      return 1ull << nx;
+    };
+    auto cal_or = [&](uint64_t bits) -> uint64_t {   // OR of the lanes' calendar bits
+      return ((uint64_t)__reduce_or_sync(FULL, (uint32_t)(bits >> 32)) << 32) |
+             (uint64_t)__reduce_or_sync(FULL, (uint32_t)bits);
+    };
+
     // drop Burned cells and cells with no open axis from the burning list
-    // (order kept), within an hour when the list nears its capacity
-    auto compact = [&](int32_t count) -> int32_t {
+    // (order kept) when it nears its capacity within an hour, and rebuild the
+    // calendar lists of the offsets from o on; returns the new calendar mask
+    auto compact = [&](int32_t &count, uint32_t o) -> uint64_t {
+      for (int32_t i = lane; i < 64; i += 32) head[i] = kNil;
+      __syncwarp();
       int32_t out = 0;
+      uint64_t cal = 0;
       for (int32_t b0 = 0; b0 < count; b0 += 32) {
         const int32_t e = b0 + lane;
         bool keep = false;
-        uint32_t rc = 0, m = 0, nx = kNone;
-        uint64_t c8 = 0;
+        uint32_t rc = 0;
+        uint64_t c8 = ~0ull;
         int64_t P[8];
         if (e < count) {
           rc = erc[e];
-          m = emask[e];
-          const int32_t cr = (int32_t)(rc >> 16), cc = (int32_t)(rc & 0xFFFFu);
-          keep = m != 0 && !pl.burned(cr, cc);
+          c8 = *reinterpret_cast<const uint64_t *>(ecofs + (size_t)e * 8);
+          keep = open_axes(c8) != 0 && !pl.burned((int32_t)(rc >> 16), (int32_t)(rc & 0xFFFFu));
           if (keep) {
-            nx = enext[e];
-            c8 = *reinterpret_cast<const uint64_t *>(ecofs + (size_t)e * 8);
 #pragma unroll
             for (int q = 0; q < 8; ++q) P[q] = eP[(size_t)e * 8 + q];
           }
@@ -729,18 +836,21 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         const uint32_t bal = __ballot_sync(FULL, keep);
         const int32_t pos = out + __popc(bal & lt);
         __syncwarp();
+        uint64_t bit = 0;
         if (keep) {
           erc[pos] = rc;
-          emask[pos] = (uint8_t)m;
-          enext[pos] = (uint8_t)nx;
           *reinterpret_cast<uint64_t *>(ecofs + (size_t)pos * 8) = c8;
 #pragma unroll
           for (int q = 0; q < 8; ++q) eP[(size_t)pos * 8 + q] = P[q];
+          const uint32_t nx = min_byte8(c8);
+          if (nx >= o) bit = push(pos, nx);
         }
+        cal |= cal_or(bit);
         out += __popc(bal);
         __syncwarp();
       }
-      return out;
+      count = out;
+      return cal;
     };
 
     for (int32_t h = 0; h < H && live > 0 && status == 0; ++h) {
@@ -758,14 +868,17 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       int32_t burned = 0;   // cells Burned at the end of the period being visited
       if (lazy) {
         for (int32_t i = lane; i < kWinRows * kWinWords / 32; i += 32) dbits[i] = 0u;
-        __syncwarp();
       }
+      for (int32_t i = lane; i < 64; i += 32) head[i] = kNil;
+      __syncwarp();
+      uint64_t cal = 0;   // offsets of this hour whose calendar list is not empty
 
+      if (prof && lane == 0) pc_t = clock64();
       // ---- hour boundary, one lane per listed cell, 32 cells at a time:
       // (i) drop Burned cells and cells with no open axis (order kept);
       // (ii) the cell's perturbation for this hour; (iii) on every open axis,
-      // the crossing period of this hour, or the progress carried to the next.
-      // The eight axes of a cell are independent chains in one lane.
+      // the crossing period of this hour, or the progress carried to the next;
+      // (iv) the cell into the calendar list of its first crossing.
       {
         int32_t out = 0;
         for (int32_t b0 = 0; b0 < cnt; b0 += 32) {
@@ -774,7 +887,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           uint32_t rc = 0u, m = 0u;
           if (e < cnt) {
             rc = erc[e];
-            m = emask[e];
+            m = open_axes(*reinterpret_cast<const uint64_t *>(ecofs + (size_t)e * 8));
             keep = m != 0u && !pl.burned((int32_t)(rc >> 16), (int32_t)(rc & 0xFFFFu));
           }
           const int32_t cr = (int32_t)(rc >> 16), cc = (int32_t)(rc & 0xFFFFu);
@@ -790,6 +903,8 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
               P[2 * j] = a.x; P[2 * j + 1] = a.y;
               bk[2 * j] = b.x; bk[2 * j + 1] = b.y;
             }
+            // the cell's row of the next hour into L2, for the next boundary
+            if (!LAZY && h + 1 < H) prefetch_l2(baseh + n * 8 + cell * 8);
           } else {
 #pragma unroll
             for (int q = 0; q < 8; ++q) P[q] = bk[q] = 0;
@@ -799,94 +914,89 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           // A5 (i): a cell whose HROS * f is below delta still sends in the
           // first period of the hour and is Burned after it
           const bool dies = keep && delta > 0.0 && __dmul_rn(__ldcg(hrosh + cell), (double)f) < delta;
-          uint32_t mask = 0u;
-          uint64_t c8 = ~0ull;   // crossing offsets, one byte per axis (kNone: none this hour)
+          uint64_t c8 = ~0ull;   // crossing-offset bytes
+          const uint32_t am = keep ? (m & pl.avail_mask(rows, cols, cr, cc)) : 0u;   // open axes toward Available cells
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            const bool open = keep && ((m >> q) & 1u) && pl.avail(cr + axis_dr(q), cc + axis_dc(q));
-            const int64_t dq = (q & 1) ? J.d_diag : J.d_orth;
             uint32_t cof = kNone;
-            if (open) {
-              mask |= 1u << q;
+            if ((am >> q) & 1u) {
+              const int64_t dq = (q & 1) ? J.d_diag : J.d_orth;
               const int64_t inc = apply_noise(bk[q], F, dq);
               const int64_t rem = dq - P[q];
-              if (inc > 0 && inc * sph >= rem) cof = (uint32_t)(ceil_div_small(rem, inc) - 1);
-              else P[q] += inc * sph;
+              if (inc > 0 && inc * sph >= rem) {
+                cof = (uint32_t)(ceil_div_small(rem, inc) - 1);
+              } else {
+                P[q] += inc * sph;
+                cof = kOpen;
+              }
+              if (dies && cof != 0u) cof = kNone;
             }
-            if (dies && cof != 0u) cof = kNone;
             c8 = (c8 & ~(0xFFull << (8 * q))) | ((uint64_t)cof << (8 * q));
           }
           const bool dying = dies && pl.burn(cr, cc);
           const uint32_t bal = __ballot_sync(FULL, keep);
           const int32_t pos = out + __popc(bal & lt);
           __syncwarp();   // every lane has read its entry before any slot is rewritten
+          uint64_t bit = 0;
           if (keep) {
             erc[pos] = rc;
-            emask[pos] = (uint8_t)mask;
-            enext[pos] = (uint8_t)min_byte8(c8);
             *reinterpret_cast<uint64_t *>(ecofs + (size_t)pos * 8) = c8;
             longlong2 *pp = reinterpret_cast<longlong2 *>(eP + (size_t)pos * 8);
 #pragma unroll
             for (int j = 0; j < 4; ++j) pp[j] = make_longlong2(P[2 * j], P[2 * j + 1]);
+            bit = push(pos, min_byte8(c8));
           }
+          cal |= cal_or(bit);
           out += __popc(bal);
           burned += __popc(__ballot_sync(FULL, dying));
           __syncwarp();
         }
         cnt = out;
       }
+      if (prof && lane == 0) pq[1] += clock64() - pc_t;
       if (status) break;
+      // cells that die this hour (A5 (i)) are Burned at the end of its first
+      // period: that period is visited even if no axis crosses in it
+      if (burned) cal |= 1ull;
 
       // ---- periods of this hour at which some axis reaches a centre
-      int32_t s = s0;
-      for (;;) {
+      while (cal != 0ull) {
+        const uint32_t o = (uint32_t)(__ffsll((long long)cal) - 1);
+        const int32_t s = s0 + (int32_t)o;
         W += (long long)live * (long long)(s - s_done);
         s_done = s;
-        if (cnt > cap - cap / 4) cnt = compact(cnt);   // keep room for new cells
-        const uint32_t o = (uint32_t)(s - s0);
-        uint32_t lmin = kNone;
+        if (prof && lane == 0) { pc_t = clock64(); pq[4] += 1; pq[7] = max(pq[7], (long long)cnt); }
+        if (cnt > cap - cap / 4) {   // keep room for new cells
+          cal = compact(cnt, o);
+          if (prof && lane == 0) pq[9] += 1;
+        }
+        cal &= ~(1ull << o);
         int32_t nnew = cnt;
         bool ovf = false;
-        // (A) send and receive: cells with a crossing at offset o.  Hits are
-        // gathered across the whole list, four next-event bytes per lane (one
-        // 32-bit load, bytewise compares), then each lane takes one hit cell:
-        // its 8 crossing offsets in one load, every axis crossing at o handled
-        // in turn (targets tested, ignited, appended by ballot + popc).
-        int32_t hbase = 0;      // hits gathered so far in the buffer
-        uint32_t lmin4 = ~0u;   // bytewise minimum of the next offsets that are not hits
-        int32_t b0 = 0;
-        while (b0 < cnt || hbase > 0) {
-          if (b0 < cnt && hbase < 32) {
-            const int32_t e0 = b0 + 4 * lane;
-            uint32_t nx4 = ~0u;
-            if (e0 < cnt) {
-              if (words4) {   // the word lies inside the list
-                nx4 = *reinterpret_cast<const uint32_t *>(enext + e0);
-              } else {
-                nx4 = 0u;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) nx4 |= (e0 + q < cnt ? (uint32_t)enext[e0 + q] : 0xFFu) << (8 * q);
-              }
-              if (cnt - e0 < 4) nx4 |= ~0u << (8 * (cnt - e0));   // entries past the end: none
+        // (A) send and receive: the entries of offset o's calendar list, 32 at
+        // a time (lane 0 walks the list); each lane takes one entry: every
+        // axis crossing at o is handled in turn (target tested, ignited,
+        // appended by ballot + popc), then the entry goes into the list of its
+        // next crossing
+        int32_t cur = head[o];
+        int32_t walked = 0;   // a list holds each entry at most once: never more than cnt
+        while (cur != kNil) {
+          long long pw0 = 0;
+          if (prof && lane == 0) pw0 = clock64();
+          int32_t take_n = 0;
+          if (lane == 0) {
+            while (cur != kNil && take_n < 32) {
+              hitbuf[take_n++] = cur;
+              cur = elink[cur];
+              if (cur == (int32_t)(Link)kNil) cur = kNil;
             }
-            const uint32_t eq = __vcmpeq4(nx4, o * 0x01010101u);   // 0xFF where the offset is o
-            lmin4 = __vminu4(lmin4, nx4 | eq);
-            const uint32_t hb = eq & 0x01010101u;
-            const uint32_t h4 = (hb | (hb >> 7) | (hb >> 14) | (hb >> 21)) & 0xFu;
-            if (__any_sync(FULL, h4 != 0u)) {
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const bool hit = (h4 >> q) & 1u;
-                const uint32_t hits = __ballot_sync(FULL, hit);
-                if (hit) hitbuf[hbase + __popc(hits & lt)] = e0 + q;
-                hbase += __popc(hits);
-              }
-            }
-            __syncwarp();
-            b0 += 128;
-            if (hbase < 32 && b0 < cnt) continue;   // gather a full round first
           }
-          const int32_t take_n = min(hbase, 32);
+          take_n = __shfl_sync(FULL, take_n, 0);
+          cur = __shfl_sync(FULL, cur, 0);
+          __syncwarp();
+          walked += take_n;
+          if (walked > cnt) { status = 2; break; }   // cannot happen; a broken list stops here
+          if (prof && lane == 0) { pq[8] += clock64() - pw0; pq[5] += take_n; pq[10] += 1; }
           const int32_t ent = lane < take_n ? hitbuf[lane] : -1;
           uint64_t cof8 = ~0ull;
           uint32_t rc = 0;
@@ -894,10 +1004,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
             cof8 = *reinterpret_cast<const uint64_t *>(ecofs + (size_t)ent * 8);
             rc = erc[ent];
           }
-          // crossing axes of this lane's cell as an 8-bit mask
-          uint32_t cm = 0;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) cm |= (((cof8 >> (8 * q)) & 0xFFull) == o ? 1u : 0u) << q;
+          const uint32_t cm = ent >= 0 ? axes_at(cof8, o) : 0u;   // axes crossing at o
           const int32_t cr = (int32_t)(rc >> 16), cc = (int32_t)(rc & 0xFFFFu);
           if (lazy && !gate_free) ensure(h, ent >= 0, cr, cc, cm << 1);   // receivers' HROS
           uint32_t todo = cm;
@@ -923,40 +1030,37 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
               const int32_t idx = nnew + __popc(wins & lt);
               if (idx < cap) erc[idx] = wrc; else ovf = true;
               if (istep) istep[jc] = s;
-              prefetch_l2(baseh + jc * 8);   // the new cell's table row, read when it is set up
+              // the new cell's table row, read when it is set up: into L1 when
+              // the table is complete (read-only here), else into L2
+              if (LAZY) prefetch_l2(baseh + jc * 8);
+              else prefetch_row_l1(baseh + jc * 8);
             }
             nnew += __popc(wins);
           }
-          if (ent >= 0) {
+          uint64_t bit = 0;
+          if (ent >= 0) {   // the axes that crossed close; the entry moves to its next crossing
             uint64_t nc8 = cof8;
 #pragma unroll
             for (int q = 0; q < 8; ++q)
               if ((cm >> q) & 1u) nc8 |= 0xFFull << (8 * q);
             *reinterpret_cast<uint64_t *>(ecofs + (size_t)ent * 8) = nc8;
-            const uint32_t nx2 = min_byte8(nc8);
-            emask[ent] = (uint8_t)(emask[ent] & ~cm);
-            enext[ent] = (uint8_t)nx2;
-            lmin = min(lmin, nx2);
+            bit = push(ent, min_byte8(nc8));
           }
-          // drop the processed round from the buffer
+          cal |= cal_or(bit);
           __syncwarp();
-          const int32_t rest = hbase - take_n;
-          for (int32_t i0 = 0; i0 < rest; i0 += 32) {
-            const int32_t v = (i0 + lane < rest) ? hitbuf[take_n + i0 + lane] : 0;
-            __syncwarp();
-            if (i0 + lane < rest) hitbuf[i0 + lane] = v;
-            __syncwarp();
-          }
-          hbase = rest;
         }
-        {
-          uint32_t m = __vminu4(lmin4, lmin4 >> 16);
-          m = __vminu4(m, m >> 8);
-          lmin = min(lmin, m & 0xFFu);
+        if (prof && lane == 0) {
+          const long long t1 = clock64();
+          pq[2] += t1 - pc_t;
+          pc_t = t1;
+          pq[6] += nnew - cnt;
         }
+        if (status) break;
         if (__any_sync(FULL, ovf)) { status = 1; break; }
         __syncwarp();
-        // (C) cells ignited in period s: open axes, first crossings, burn-out tests
+        // (C) cells ignited in period s, four at a time, lane k of each 8-lane
+        // group owning axis k: open axes, first crossings, progress to the end
+        // of the hour, burn-out tests, and the cell into the calendar
         if (lazy) {   // this hour's rows of the new cells
           for (int32_t b0 = cnt; b0 < nnew; b0 += 32) {
             const int32_t e = b0 + lane;
@@ -966,6 +1070,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           if (status) break;
         }
         for (int32_t b0 = cnt; b0 < nnew; b0 += 4) {
+          if (prof && lane == 0) pq[11] += 1;
           const int32_t e = b0 + grp;
           const bool act = e < nnew;
           const uint32_t rc = act ? erc[e] : 0u;
@@ -973,7 +1078,9 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           const int64_t cell = (int64_t)cr * cols + cc;
           const int32_t nr = cr + axis_dr(k), nc = cc + axis_dc(k);
           const bool ingrid = act && nr >= 0 && nr < rows && nc >= 0 && nc < cols;
-          const int64_t bk = act ? __ldcg(baseh + cell * 8 + k) : 0;   // issue the table load early
+          // the table load issued early; through L1 (the row was prefetched
+          // there) unless other warps may be writing the table (lazy rows)
+          const int64_t bk = act ? (LAZY ? __ldcg(baseh + cell * 8 + k) : __ldca(baseh + cell * 8 + k)) : 0;
           const bool open = ingrid && pl.avail(nr, nc);
           // the perturbation does not depend on the loads above: computed while they are in flight
           const float f = act ? noise_factor(seed, (uint32_t)r, (uint32_t)cell, (uint32_t)h, sigma) : 1.0f;
@@ -984,45 +1091,42 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           if (act && delta > 0.0) {
             if (__dmul_rn(__ldcg(hrosh + cell), (double)f) < delta) { dies = true; mask = 0; }   // A5 (i)
           }
-          uint32_t cof = kNone;
+          uint32_t cof = ((mask >> k) & 1u) ? kOpen : kNone;
           int64_t P = 0;
-          if (act && mask != 0 && s < L) {
-            if ((mask >> k) & 1u) {
-              const int32_t nmax = L - s;
-              const int64_t inc = apply_noise(bk, noise_fixed(f), dk);
-              if (inc > 0 && inc * nmax >= dk) cof = o + (uint32_t)ceil_div_small(dk, inc);
-              else P = inc * nmax;
-            }
+          if (act && ((mask >> k) & 1u) && s < L) {
+            const int32_t nmax = L - s;   // periods left in the hour
+            const int64_t inc = apply_noise(bk, noise_fixed(f), dk);
+            if (inc > 0 && inc * nmax >= dk) cof = o + (uint32_t)ceil_div_small(dk, inc);
+            else P = inc * nmax;
           }
           const uint32_t nx = group_min(cof);
           uint32_t newly = 0;   // cells this lane turned Burned (its own cell, its axis neighbour)
+          uint64_t bit = 0;
           if (act) {
             ecofs[(size_t)e * 8 + k] = (uint8_t)cof;
             eP[(size_t)e * 8 + k] = P;
             if (k == 0) {
-              emask[e] = (uint8_t)mask;
-              enext[e] = (uint8_t)nx;
-              lmin = min(lmin, nx);
+              bit = push(e, nx);
               if (omask == 0 || dies)   // this cell: A5 (ii) no Available neighbour, or (i)
                 newly += pl.burn(cr, cc) ? 1u : 0u;
             }
             // A5 (ii) for the ignited neighbour on this lane's axis
             if (ignq && !pl.any_avail_nbr(rows, cols, nr, nc)) newly += pl.burn(nr, nc) ? 1u : 0u;
           }
+          cal |= cal_or(bit);
           burned += (int32_t)__reduce_add_sync(FULL, newly);
         }
-        lmin = warp_min(lmin);
         __syncwarp();
+        if (prof && lane == 0) pq[3] += clock64() - pc_t;
+        // every crossing pushed in this period lies after it; a bit at or
+        // before o cannot happen and would revisit a period
+        if (cal & ((2ull << o) - 1ull)) { status = 2; break; }
         const int32_t added = nnew - cnt;
         nign += added;
         live += added - burned;
         burned = 0;
         cnt = nnew;
-        const int32_t next = (lmin == kNone) ? L + 1 : s0 + (int32_t)lmin;
-        if (next <= s) { status = 2; break; }   // cannot happen; never visit a period twice
         if (live == 0) break;
-        s = next;
-        if (s > L) break;
       }
       if (status == 0) { W += (long long)live * (long long)(L - s_done); s_done = L; }
     }
@@ -1040,6 +1144,12 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       J.work[r] = W;
       J.n_ignited[r] = nign;
       J.status[r] = status;
+      if (prof) {
+        long long *q = J.prof + (size_t)r * kProfCounters;
+        q[0] = clock64() - pq[0];
+#pragma unroll
+        for (int i = 1; i < kProfCounters; ++i) q[i] = pq[i];
+      }
     }
     __syncwarp();
   }
@@ -1047,11 +1157,15 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
 
 // Variants: warps per CTA (1, 2, 4); planes windowed and lists in shared
 // memory (w), or everything in global memory (g); l: tables filled on demand.
-__global__ void __launch_bounds__(32) k_frontier_g1(FrontierArgs A) { frontier_warp<1, false, false>(A); }
-__global__ void __launch_bounds__(64) k_frontier_g2(FrontierArgs A) { frontier_warp<2, false, false>(A); }
+// Register budgets: one-warp CTAs sized so that 11 fit on an SM (the
+// pipelined steps run the next table build beside the frontier, which more
+// registers a thread would crowd out; fewer would spill); two-warp CTAs so
+// that 5 fit
+__global__ void __launch_bounds__(32, 11) k_frontier_g1(FrontierArgs A) { frontier_warp<1, false, false>(A); }
+__global__ void __launch_bounds__(64, 5) k_frontier_g2(FrontierArgs A) { frontier_warp<2, false, false>(A); }
 __global__ void __launch_bounds__(128) k_frontier_g4(FrontierArgs A) { frontier_warp<4, false, false>(A); }
-__global__ void __launch_bounds__(32) k_frontier_w1(FrontierArgs A) { frontier_warp<1, true, false>(A); }
-__global__ void __launch_bounds__(64) k_frontier_w2(FrontierArgs A) { frontier_warp<2, true, false>(A); }
+__global__ void __launch_bounds__(32, 11) k_frontier_w1(FrontierArgs A) { frontier_warp<1, true, false>(A); }
+__global__ void __launch_bounds__(64, 5) k_frontier_w2(FrontierArgs A) { frontier_warp<2, true, false>(A); }
 __global__ void __launch_bounds__(128) k_frontier_w4(FrontierArgs A) { frontier_warp<4, true, false>(A); }
 // on-demand table rows: one warp per CTA; the FBP code inlined into the
 // frontier needs the whole register budget of a one-warp CTA

@@ -84,6 +84,7 @@ struct SimJob {
   int64_t *work;                  // [R]
   int32_t *n_ignited;             // [R]
   int32_t *ign_cell;              // [R]
+  long long *prof;                // [R][kProfCounters] per-replica profile counters, or nullptr (off)
   int32_t *status;                // [R] 0 ok, 1 list capacity exceeded, 2 internal error,
                                   //     3 ignition cell outside the grid or not burnable,
                                   //     4 a bounded wait (for a lazy table chunk) ran out
@@ -98,9 +99,9 @@ struct FrontierArgs {
   unsigned long long *counter;    // work-list cursor (zeroed before the launch)
   int32_t cap;                    // burning-list capacity per slot
   int32_t *ent_cell;              // [slots][cap] cell as row << 16 | col
-  uint8_t *ent_mask;              // [slots][cap] open axes
-  uint8_t *ent_next;              // [slots][cap] next event offset in the hour (0xFF none)
-  uint8_t *ent_cofs;              // [slots][cap][8] per-axis crossing offsets (0xFF none)
+  int32_t *ent_link;              // [slots][cap] next entry in the same calendar list (-1 none)
+  uint8_t *ent_cofs;              // [slots][cap][8] per-axis crossing offsets this hour
+                                  //   (0xFE open axis, no crossing this hour; 0xFF closed)
   int64_t *ent_P;                 // [slots][cap][8] progress at the start of the next hour
   int64_t pw_max;                 // words per bit plane of the largest landscape
   uint32_t *brn_scratch;          // [slots][pw_max] Burned planes
@@ -129,6 +130,7 @@ struct RosTableArgs {
 constexpr int kOrderBuckets = 2 * 16;   // (fuel code, slope > 0); code 0 = not burnable
 
 constexpr uint8_t kNone = 0xFF;
+constexpr int kProfCounters = 16;   // per-replica frontier profile counters (c2f_get_replica_profile)
 // shared-memory window of the per-replica bit planes: kWinRows x (32 kWinWords) cells
 constexpr int kWinRows = 256;
 constexpr int kWinWords = 8;

@@ -151,17 +151,17 @@ struct Sim {
   std::shared_ptr<Table> table;
   int32_t rows = 0, cols = 0, wpr = 0;
   int64_t n = 0;
-  DevBuf ign_plane, ign_step, work, n_ignited, ign_cell, status, scen;
+  DevBuf ign_plane, ign_step, work, n_ignited, ign_cell, status, scen, prof;
   int state = S_PENDING;
   int rc = C2F_OK;
   bool cancel_requested = false;
 };
 
 struct Scratch {
-  DevBuf ent_cell, ent_mask, ent_next, ent_cofs, ent_P, counter, brn, avail;
+  DevBuf ent_cell, ent_link, ent_cofs, ent_P, counter, brn, avail;
   int64_t slots = 0, cap = 0, brn_words = 0, avail_words = 0;
   void reset() {
-    ent_cell.reset(); ent_mask.reset(); ent_next.reset(); ent_cofs.reset(); ent_P.reset();
+    ent_cell.reset(); ent_link.reset(); ent_cofs.reset(); ent_P.reset();
     counter.reset(); brn.reset(); avail.reset();
     slots = cap = brn_words = avail_words = 0;
   }
@@ -515,8 +515,7 @@ int ensure_scratch_once(c2f_ctx *ctx, Scratch &S, cudaStream_t st, int64_t slots
     cap = std::max(cap, S.cap);
     const size_t sc = (size_t)slots * cap;
     if ((rc = dalloc_on(ctx, S.ent_cell, sc * 4, st))) return rc;
-    if ((rc = dalloc_on(ctx, S.ent_mask, sc, st))) return rc;
-    if ((rc = dalloc_on(ctx, S.ent_next, sc, st))) return rc;
+    if ((rc = dalloc_on(ctx, S.ent_link, sc * 4, st))) return rc;
     if ((rc = dalloc_on(ctx, S.ent_cofs, sc * 8, st))) return rc;
     if ((rc = dalloc_on(ctx, S.ent_P, sc * 64, st))) return rc;
     S.slots = slots;
@@ -558,6 +557,10 @@ int alloc_sim(c2f_ctx *ctx, Sim &s, cudaStream_t st) {
   CK(cudaMemsetAsync(s.status.p, 0, 4 * R, st));
   if (s.table->n_scen > 1) {
     if ((rc = dalloc_on(ctx, s.scen, 4 * R, st))) return rc;
+  }
+  if (ctx->profiling) {   // per-replica profile counters of the frontier
+    if ((rc = dalloc_on(ctx, s.prof, 8 * kProfCounters * R, st))) return rc;
+    CK(cudaMemsetAsync(s.prof.p, 0, 8 * kProfCounters * R, st));
   }
   return C2F_OK;
 }
@@ -609,6 +612,7 @@ SimJob job_of(const Sim &s) {
   j.n_ignited = s.n_ignited.as<int32_t>();
   j.ign_cell = s.ign_cell.as<int32_t>();
   j.status = s.status.as<int32_t>();
+  j.prof = s.prof.as<long long>();
   return j;
 }
 
@@ -650,6 +654,7 @@ int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, i
     const int64_t room = (per_warp - 2 * (int64_t)kWinRows * kWinWords * 4 - 512) / 14;
     win_cap = std::min<int64_t>(cap, std::max<int64_t>(256, room & ~int64_t(63)));
     if (attempt > 0) win_cap = std::max<int64_t>(256, room & ~int64_t(63));
+    win_cap = std::min<int64_t>(win_cap, 65532);   // shared-memory lists link entries with 16 bits
   }
   const int64_t budget = (int64_t)ctx->smem_optin - 2048;
   const int64_t win_words = 2 * (int64_t)kWinRows * kWinWords + win_cap * 7 / 2;
@@ -687,8 +692,7 @@ int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, i
   A.counter = S.counter.as<unsigned long long>();
   A.cap = (int32_t)cap;
   A.ent_cell = S.ent_cell.as<int32_t>();
-  A.ent_mask = S.ent_mask.as<uint8_t>();
-  A.ent_next = S.ent_next.as<uint8_t>();
+  A.ent_link = S.ent_link.as<int32_t>();
   A.ent_cofs = S.ent_cofs.as<uint8_t>();
   A.ent_P = S.ent_P.as<int64_t>();
   A.pw_max = F.pw_max;
@@ -1006,7 +1010,7 @@ int64_t epoch_bytes(c2f_ctx *ctx, const std::vector<std::shared_ptr<Sim>> &sims)
     if (s->p.outputs & C2F_OUT_IGN_STEPS) outputs += r * s->n * 4;
   }
   const int64_t slots = std::min<int64_t>(R, (int64_t)ctx->sm_count * 8);
-  return outputs + slots * (cap * 78 + pw * 8) + 4096;
+  return outputs + slots * (cap * 80 + pw * 8) + 4096;
 }
 
 // finish the epochs whose work is done (all of them, when `block`)
@@ -1801,6 +1805,22 @@ C2F_API int c2f_set_list_capacity(c2f_ctx *ctx, int64_t cap) {
   LOCK;
   if (cap < 0 || cap > (1LL << 31)) return fail(ctx, C2F_EINVAL, "capacity out of range");
   ctx->cap_override = cap;
+  return C2F_OK;
+}
+
+C2F_API int c2f_get_replica_profile(c2f_ctx *ctx, int32_t sim_id, int64_t *counters) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  auto s = find_sim(ctx, sim_id);
+  if (!s) return fail(ctx, C2F_ENOTFOUND, "unknown simulation %d", sim_id);
+  if (!counters) return fail(ctx, C2F_EINVAL, "counters is NULL");
+  int rc = sim_ready(ctx, *s);
+  if (rc) return rc;
+  if (!s->prof.p) return fail(ctx, C2F_EINVAL, "the simulation ran without profiling");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaMemcpyAsync(counters, s->prof.p, 8 * kProfCounters * (size_t)s->p.n_replicas, cudaMemcpyDeviceToHost,
+                     ctx->read_stream));
+  CK(cudaStreamSynchronize(ctx->read_stream));
   return C2F_OK;
 }
 

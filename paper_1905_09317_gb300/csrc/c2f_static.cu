@@ -58,7 +58,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Carve {
   size_t off_counter, off_job, off_begin, off_list, off_status, off_slots;
   size_t per_slot;
-  size_t off_cell, off_mask, off_next, off_cofs, off_P, off_avail, off_brn;   // within the slot area
+  size_t off_cell, off_link, off_cofs, off_P, off_avail, off_brn;   // within the slot area
 };
 
 Carve carve(int64_t slots, int64_t cap, int64_t pw, int32_t R) {
@@ -73,8 +73,7 @@ Carve carve(int64_t slots, int64_t cap, int64_t pw, int32_t R) {
   // slot-major arrays, each sized for all slots (the kernel indexes slot * cap)
   size_t p = 0;
   c.off_cell = p; p = align256(p + (size_t)slots * cap * 4);
-  c.off_mask = p; p = align256(p + (size_t)slots * cap);
-  c.off_next = p; p = align256(p + (size_t)slots * cap);
+  c.off_link = p; p = align256(p + (size_t)slots * cap * 4);
   c.off_cofs = p; p = align256(p + (size_t)slots * cap * 8);
   c.off_P = p; p = align256(p + (size_t)slots * cap * 64);
   c.off_avail = p; p = align256(p + (size_t)slots * pw * 4);
@@ -111,7 +110,7 @@ extern "C" C2F_API int c2f_frontier_static(const c2f_frontier_io *io, const c2f_
   const int64_t header = (int64_t)carve(0, 0, 0, R).off_slots;
   const int64_t avail_bytes = (int64_t)kStaticScratchBytes - header - 8 * 256;
   const int64_t fixed_per_slot = pw * 8;          // Available + Burned planes
-  const int64_t per_entry = 4 + 1 + 1 + 8 + 64;
+  const int64_t per_entry = 4 + 4 + 8 + 64;   // cell, calendar link, crossing offsets, progress
   const int64_t cap_max = std::min<int64_t>(n, (avail_bytes - fixed_per_slot) / per_entry);
   if (cap_max < std::min<int64_t>(n, kStaticMinCap)) return C2F_EINVAL;   // landscape too large
 
@@ -188,8 +187,7 @@ extern "C" C2F_API int c2f_frontier_static(const c2f_frontier_io *io, const c2f_
     A.counter = reinterpret_cast<unsigned long long *>(base_ptr + c.off_counter);
     A.cap = (int32_t)cap;
     A.ent_cell = reinterpret_cast<int32_t *>(sl + c.off_cell);
-    A.ent_mask = sl + c.off_mask;
-    A.ent_next = sl + c.off_next;
+    A.ent_link = reinterpret_cast<int32_t *>(sl + c.off_link);
     A.ent_cofs = sl + c.off_cofs;
     A.ent_P = reinterpret_cast<int64_t *>(sl + c.off_P);
     A.pw_max = pw;
