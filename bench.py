@@ -1,27 +1,35 @@
 """Benchmark: Monte-Carlo fire growth on one GB300 (or N, replica-sharded).
 
-Workload (one "step" = one pass of the whole path): the 512x512 heterogeneous
+Headline (one "step" = one pass of the whole path): the 512x512 heterogeneous
 landscape, 24 h hourly weather, 1000 replicas with random ignitions and
 lognormal(0, 0.1) ROS noise -- ROS table (K1), ignition (K2), frontier (K3)
 and burn-probability counts (K4).  Metric: cell-updates/s, the number of
 (burning cell, fire period) pairs of Algorithm 1 per second, summed over
-replicas; replicas/s is reported beside it.
+replicas; replicas/s is reported beside it.  Steps are pipelined (the next
+steps' tables overlap the current frontier).
+
+The same JSON line also carries, each with its own timing and clock record:
+  plain    the same step as one synchronous c2f_simulate at a time (one
+           request per launch); its per-kernel times feed the roofline entries;
+  batched  64 landscapes of 64^2..2048^2 cells, 16..4096 replicas, 48 h: one
+           call per landscape vs one batched call (tables and frontiers in one
+           CUDA graph);
+  served   Poisson arrivals (50/s; a 10 s window, --serve-window) over a pool
+           of 16 landscapes, served with submit/poll (continuous batching):
+           throughput and p50/p99 latency, and a capacity comparison with the
+           first requests all waiting (served vs one synchronous call each);
+  large    4096^2 cells, 72 h with a 90-degree wind shift, 256 replicas.
+Their inputs are generated in spawned host processes while the GPU works.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs its own 1000 replicas (replica ids offset by
 rank), so per-GPU work is fixed (weak scaling) and no collective touches the
-data path; the timing is max-over-ranks.
+data path; the timing is max-over-ranks.  --gpus must equal the number of
+processes launched (it is refused otherwise).
 
 Other workloads (one GPU; each prints its own JSON line):
-  --workload batch   64 landscapes of 64^2..2048^2 cells, 16..4096 replicas,
-                     48 h: one request per call ("plain") vs one batched call
-                     (tables and frontier in one CUDA graph) ("batched").
-  --workload serve   Poisson arrivals (50/s for 60 s) over a pool of 16
-                     landscapes of 128^2..2048^2 cells, 32..2048 replicas,
-                     12..72 h, served with submit/poll (continuous batching):
-                     throughput and p50/p99 latency from arrival to the burn
-                     counts on the host.
-  --workload large   4096^2 cells, 72 h with a 90-degree wind shift, 256 replicas.
+  --workload batch | serve | large   the sections above on their own (serve
+                     with 60 s of arrivals, --duration)
   --workload scenarios  the 512^2 landscape under 8 weather scenarios x 24 h with
                      probabilities; each of 1000 replicas draws its scenario.
   --workload compare the Sec. 4.1 scar comparison (hourly MSE / SSIM, final
@@ -156,7 +164,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
@@ -223,6 +231,18 @@ def whole_job_rate(units_per_rank_step: int, world: int, steps: int, seconds: fl
     return units_per_rank_step * world * steps / seconds
 
 
+def gpus_mismatch(gpus: int, world: int):
+    """--gpus N must be what the launcher started: one process per GPU under
+    torchrun (WORLD_SIZE = N), or a single process for N = 1.  A mismatch would
+    time a different number of GPUs than the line claims, so it is refused."""
+    if gpus < 1:
+        return f"--gpus must be >= 1 (got {gpus})"
+    if gpus != world:
+        return (f"--gpus {gpus} but {world} process(es) were launched (WORLD_SIZE={world}); run "
+                f"N > 1 as: python -m torch.distributed.run --nproc-per-node {gpus} bench.py --gpus {gpus} ...")
+    return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -231,14 +251,71 @@ def measured_peaks():
         return {}
 
 
+# ------------------------------------------------------------------ workload generation
+def _gen_batch(i):
+    """(spawned process) landscape i of the 64-landscape batch."""
+    return S.config3_workload(S.config3_specs()[i])
+
+
+def _gen_large():
+    """(spawned process) the 4096^2 workload."""
+    return S.config4()
+
+
+def _gen_serve_land(side, seed):
+    """(spawned process) one landscape of the request stream's pool."""
+    return S.heterogeneous_landscape(side, seed=seed)
+
+
+class WorkloadPool:
+    """The batch, request-stream and 4096^2 inputs, generated in spawned
+    processes (host numpy only) while the GPU runs the headline measurement."""
+
+    def __init__(self, serve_rate, serve_window):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.ex = cf.ProcessPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1)),
+                                         mp_context=mp.get_context("spawn"))
+        self.f_large = self.ex.submit(_gen_large)
+        self.specs = S.config3_specs()
+        self.f_batch = [self.ex.submit(_gen_batch, i) for i in range(len(self.specs))]
+        self.sides, self.reqs = S.serving_requests(rate=serve_rate, duration_s=serve_window)
+        self.f_serve = [self.ex.submit(_gen_serve_land, side, 500 + i) for i, side in enumerate(self.sides)]
+
+    def batch(self):
+        return [f.result() for f in self.f_batch]
+
+    def large(self):
+        return self.f_large.result()
+
+    def serve(self):
+        return self.sides, self.reqs, [f.result() for f in self.f_serve]
+
+    def close(self):
+        self.ex.shutdown(wait=True, cancel_futures=True)
+
+
+def _section(fn, *a):
+    """One extra section of the default line; a failure is reported, not hidden."""
+    try:
+        return fn(*a)
+    except Exception as e:   # the headline line is still printed, with the error beside it
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
+    extras_on = world == 1 and not args.no_extras
+    # the extra sections' inputs are generated on the host cores while the GPU works
+    # (spawned processes, started before the first GPU call)
+    pool = WorkloadPool(args.rate, args.serve_window) if extras_on else None
     import torch
     import paper_1905_09317_gb300 as c2f
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     c2f.build()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     w = S.config2(n_replicas=args.replicas)
     L = w.landscape
     n = L.fuel.size
@@ -255,7 +332,6 @@ def run_ours(args, rank, world, local_rank):
         # pipelined steps: size each warp's shared memory for one warp per SM
         # more than a step's own replicas need, so that the next step's
         # frontier starts beside the current one's last replicas
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
         pipe_warps = -(-R // sms) + 1
         ctx.set_frontier_config(32, pipe_warps)
     # the context issues its work (K1, K4, uploads) on this stream and the
@@ -326,23 +402,11 @@ def run_ours(args, rank, world, local_rank):
         barrier()
     ms = ev0.elapsed_time(ev1)
     kt = ctx.kernel_times()
+    ctx.profile(False)
     last_work, _, _ = ctx.get_counters(sids[-1], R)
     assert int(last_work.sum()) == work_per_step, "work count changed between steps"
     for s in sids:
         ctx.release(s)
-    kt_alone = None
-    if not args.serial:   # a few steps one at a time (outside the timing): each kernel alone
-        if pipe_warps:
-            ctx.set_frontier_config(32, 1)   # the default sizing for a launch that runs alone
-        ctx.kernel_times()
-        for _ in range(3):
-            ctx.release(step())
-        kt_alone = ctx.kernel_times()
-        if pipe_warps:
-            ctx.set_frontier_config(32, pipe_warps)
-    ctx.profile(False)
-    fp64_peak = ctx.fp64_peak()   # outside the timed region: the table kernel's FP64 roofline
-
     ms_max = max_over_ranks(ms, world, dev)
 
     # e2e: host buffers through the C ABI, copies inside the timed region
@@ -386,22 +450,57 @@ def run_ours(args, rank, world, local_rank):
                    h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(host_counts.nbytes),
                    steps=e2e_steps)
 
+    # plain: the same step as one synchronous c2f_simulate at a time (one
+    # request per launch, nothing overlapped), timed with CUDA events; then a
+    # few such steps with per-kernel events: each kernel's duration when it runs
+    # by itself (the roofline's timing)
+    if pipe_warps:
+        ctx.set_frontier_config(32, 1)   # the default sizing for a launch that runs alone
+    plain_steps = max(3, args.plain_steps)
+    sampler_plain = ClockSampler(local_rank)
+    barrier()
+    with sampler_plain:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(plain_steps):
+            ctx.release(step())
+        ev1.record(stream)
+        barrier()
+    ms_plain = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+    ctx.profile(True)
+    ctx.kernel_times()
+    for _ in range(3):
+        ctx.release(step())
+    kt_alone = ctx.kernel_times()
+    ctx.profile(False)
+    fp64_peak = ctx.fp64_peak()   # outside the timed regions: the table kernel's FP64 roofline
+    ctx.release(lid)
+    ctx.close()
+
     out = None
     if rank == 0:
         value = whole_job_rate(work_per_step, world, args.steps, ms_max / 1e3)
         peaks = measured_peaks()
-        fam = {k: v for k, v in kt.items()}
-        dom = max(fam, key=lambda k: fam[k][0])
-        roof = roofline(dom, fam, w, work_per_step, peaks)
-        if roof is not None and kt_alone is not None and dom in kt_alone:
-            alone = roofline(dom, kt_alone, w, work_per_step, peaks)
-            if alone is not None:   # the same kernel when a step runs by itself
-                roof["alone"] = {"achieved": alone["achieved"], "frac": alone["frac"],
-                                 "ms_per_launch": kt_alone[dom][0] / max(kt_alone[dom][1], 1)}
-            roof["ms_per_launch"] = fam[dom][0] / max(fam[dom][1], 1)
-        # the FP64-bound table kernel (K1) against the FP64 rate measured in this run
-        roof_k1 = roofline("ros_table", kt_alone if kt_alone else fam, w, work_per_step, peaks, fp64_peak)
-        launches = int(sum(v[1] for v in fam.values()))   # every kernel of the timed steps
+        clocks = sampler.summary()
+        plain = {"value": whole_job_rate(work_per_step, world, plain_steps, ms_plain / 1e3), "unit": METRIC,
+                 "ms_per_step": ms_plain / plain_steps, "steps": plain_steps,
+                 "replicas_per_s": R * world * plain_steps / (ms_plain / 1e3),
+                 "schedule": "one synchronous c2f_simulate per step (one request per launch), the table "
+                             "rebuilt every step, nothing overlapped",
+                 "kernel_ms_alone": {k: v[0] / max(v[1], 1) * (2 if k == "ros_table" else 1)
+                                     for k, v in kt_alone.items()},
+                 "clocks": sampler_plain.summary()}
+        roof = frontier_roofline(kt_alone, w, work_per_step, peaks, sms,
+                                 plain["clocks"].get("sm_mhz") or clocks.get("sm_mhz"))
+        roof_k1 = roofline_table(kt_alone, w, fp64_peak)
+        launches = int(sum(v[1] for v in kt.values()))   # every kernel of the timed steps
+        extras = {}
+        if extras_on:
+            extras["batched"] = _section(batch_measure, args, pool.batch(), pool.specs, 2, 1, local_rank)
+            extras["served"] = _section(serve_measure, args, *pool.serve(), local_rank)
+            extras["large"] = _section(large_measure, args, pool.large(), 2, local_rank)
+            pool.close()
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             procs = os.cpu_count() or 1
@@ -426,66 +525,89 @@ def run_ours(args, rank, world, local_rank):
                                          "replicas need: the next step's frontier starts beside it)")
                        if pipe_warps else "library default"},
             "replicas_per_s": R * world * args.steps / (ms_max / 1e3),
-            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in fam.items()},
+            "kernel_event_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+            "kernel_event_note": "sums of each family's event brackets in the pipelined steps; the "
+                                 "brackets of overlapping steps overlap, so these are not durations "
+                                 "(plain.kernel_ms_alone are)",
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
             "roofline_table_kernel": roof_k1,
-            "clocks": sampler.summary(),
+            "clocks": clocks,
+            "plain": plain,
+            **extras,
         }
-    ctx.release(lid)
-    ctx.close()
+        if extras_on and "error" not in extras.get("batched", {}) and "error" not in extras.get("served", {}):
+            out["batched_over_plain"] = extras["batched"]["batched_over_plain"]
+            out["served_over_plain"] = extras["served"]["capacity"]["served_over_plain"]
     return out
 
 
-def roofline(dom, fam, w, work_per_step, peaks, fp64_peak=None):
-    """Roofline entry of the dominant kernel family (algorithmic bytes / flops per launch)."""
-    ms, launches = fam[dom]
+def frontier_roofline(kt_alone, w, work_per_step, peaks, sms, sm_mhz):
+    """K3 against what bounds it, from its duration when a step runs by itself.
+
+    The event-driven frontier moves about 2 B of DRAM per cell-update (ncu), so
+    HBM is far from its limit; it is bound by the latency of one warp per
+    replica.  achieved / frac: DRAM bytes per launch (ncu, scaled by the
+    replicas) over the launch's duration, against the measured copy bandwidth.
+    issue: warp instructions per launch (ncu, per cell-update) over the
+    duration, against every scheduler issuing every cycle.  The period-by-
+    period method's 194 B per cell-update is kept as period_method_equiv_gbs:
+    the bandwidth that method would need for this throughput."""
+    ms, launches = kt_alone["frontier"]
+    if launches == 0:
+        return None
+    per_launch_s = ms / launches / 1e3
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    R = w.params["n_replicas"]
+    traffic = FRONTIER_DRAM_BYTES_PER_REPLICA * R
+    ach = traffic / per_launch_s / 1e9
+    mhz = float(sm_mhz or peaks.get("sm_max_mhz", 2070.0))
+    inst = FRONTIER_WARP_INST_PER_UPDATE * work_per_step
+    issue_peak = sms * 4 * mhz * 1e6          # warp instructions per second, 4 schedulers per SM
+    return {"kernel": "k_frontier_w1", "bound": "latency", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "traffic": traffic, "ms_per_launch": per_launch_s * 1e3,
+            "timing": "K3 launches of plain steps (one step at a time), CUDA events",
+            "traffic_source": FRONTIER_PROFILE_NOTE,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+            "issue": {"warp_inst_per_launch": inst, "achieved_ginst_per_s": inst / per_launch_s / 1e9,
+                      "peak_ginst_per_s": issue_peak / 1e9, "frac": inst / per_launch_s / issue_peak,
+                      "peak_source": f"{sms} SMs x 4 schedulers x {mhz:.0f} MHz (SM clock sampled under load)"},
+            "period_method_equiv_gbs": FRONTIER_BYTES_PER_UPDATE * work_per_step / per_launch_s / 1e9,
+            "period_method_note": "194 B per cell-update (8 x 8 B progress read and written, 8 x 8 B rates, "
+                                  "neighbour bits) is what the period-by-period method would move; the "
+                                  "event-driven kernel does not move it"}
+
+
+def roofline_table(kt, w, fp64_peak):
+    """K1 against the device's FP64 rate (binary64 flops per cell-hour, ncu)."""
+    ms, launches = kt["ros_table"]
     if launches == 0:
         return None
     n = w.landscape.fuel.size
     H = w.params["hours"]
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    per_launch_s = ms / launches / 1e3
-    if dom == "ros_table":
-        # FP64-ALU bound: binary64 flops per cell-hour, counted by ncu on this kernel.
-        # The family brackets two launches per table build (hour prep, then the table
-        # kernel), so a build takes ms / (launches / 2).
-        flops = FP64_OPS_PER_CELL_HOUR * n * H
-        peak = fp64_peak or FP64_PEAK_GFLOPS
-        ach = flops / (ms / max(launches // 2, 1) / 1e3) / 1e9
-        return {"kernel": "k_ros_table", "bound": "alu", "achieved": ach, "peak": peak,
-                "unit": "GFLOP/s (fp64)", "frac": ach / peak, "traffic": None,
-                "peak_source": "measured: c2f_fp64_peak (FP64 FMA chains, this run)" if fp64_peak else
-                               "derived: 152 SMs x 2 DFMA/clk x 2 flop x SM clock"}
-    if dom == "frontier":
-        by = FRONTIER_BYTES_PER_UPDATE * work_per_step
-        ach = by / per_launch_s / 1e9
-        traffic = FRONTIER_DRAM_BYTES_PER_REPLICA * w.params["n_replicas"]
-        return {"kernel": "k_frontier", "bound": "hbm", "achieved": ach, "peak": hbm,
-                "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
-                "algorithmic": "194 B per cell-update of the period-by-period method; the "
-                               "event-driven kernel moves about 2 B per update (ncu traffic), "
-                               "so the fraction can exceed 1; the kernel is bound by "
-                               "instruction latency, not by HBM",
-                "traffic_source": "ncu dram__bytes_read+write of a 200-replica launch, "
-                                  "scaled by replicas",
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    by = w.params["n_replicas"] * ((w.landscape.fuel.shape[1] + 31) // 32) * 4 * \
-        w.landscape.fuel.shape[0] + 4 * n
-    ach = by / per_launch_s / 1e9
-    return {"kernel": "k_" + dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-            "frac": ach / hbm, "traffic": None}
+    flops = FP64_OPS_PER_CELL_HOUR * n * H
+    peak = fp64_peak or FP64_PEAK_GFLOPS
+    # the family brackets two launches per table build (hour prep, then the table kernel)
+    ach = flops / (ms / max(launches // 2, 1) / 1e3) / 1e9
+    return {"kernel": "k_ros_table", "bound": "alu", "achieved": ach, "peak": peak,
+            "unit": "GFLOP/s (fp64)", "frac": ach / peak, "traffic": None,
+            "peak_source": "measured: c2f_fp64_peak (FP64 FMA chains, this run)" if fp64_peak else
+                           "derived: 152 SMs x 2 DFMA/clk x 2 flop x SM clock"}
 
 
-# Algorithmic figures.  Frontier: bytes per cell-update of the period-by-period
-# method (8 x 8 B progress read and written, 8 x 8 B rates read, ~2 B of
-# neighbour state).  ROS table: binary64 flops per cell-hour (2 x DFMA + DMUL +
-# DADD from ncu's instruction counts over cells x hours).  FP64 peak: 152 SMs x 2
-# DFMA per clock x 2 flop x 2.07 GHz.
+# Algorithmic and measured figures.  Frontier: bytes per cell-update of the
+# period-by-period method (8 x 8 B progress read and written, 8 x 8 B rates
+# read, ~2 B of neighbour state); DRAM bytes per replica and warp instructions
+# per cell-update from ncu on the 512^2 x 24 h workload.  ROS table: binary64
+# flops per cell-hour (2 x DFMA + DMUL + DADD from ncu's instruction counts over
+# cells x hours).  FP64 peak: 152 SMs x 2 DFMA per clock x 2 flop x 2.07 GHz.
 FRONTIER_BYTES_PER_UPDATE = 194.0
-FRONTIER_DRAM_BYTES_PER_REPLICA = 94.59e6 / 200   # ncu, 512^2 x 24 h, 200 replicas
+FRONTIER_DRAM_BYTES_PER_REPLICA = 94.59e6 / 200
+FRONTIER_WARP_INST_PER_UPDATE = 5.9
+FRONTIER_PROFILE_NOTE = "ncu dram__bytes_read+write and smsp__inst_executed of a 200-replica launch, " \
+                        "scaled by replicas / cell-updates"
 FP64_OPS_PER_CELL_HOUR = 364.0      # ncu: (2 x DFMA + DMUL + DADD) / (cells x hours)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x DFMA/clk x flop/DFMA x GHz
 
@@ -524,14 +646,13 @@ def _params_of(c2f, w, **over):
     return c2f.default_params(**d)
 
 
-def run_batch(args):
-    """64-landscape batch: plain (one simulate per landscape) vs batched (one call)."""
+def batch_measure(args, ws, specs, steps, warmup, device=0):
+    """64-landscape batch: plain (one c2f_simulate per landscape) vs batched (one
+    c2f_simulate_batch), tables rebuilt every pass, the same autotuned launch shape."""
     import torch
     import paper_1905_09317_gb300 as c2f
     c2f.build()
-    specs = S.config3_specs()
-    ws = [S.config3_workload(sp) for sp in specs]
-    ctx = c2f.Context(0)
+    ctx = c2f.Context(device)
     ctx.set_table_mode(not args.lazy_tables)
     if args.frontier_threads:
         ctx.set_frontier_config(args.frontier_threads, args.smem_plane_bytes)
@@ -562,21 +683,23 @@ def run_batch(args):
     out = {}
     work = None
     for name, fn in (("plain", plain), ("batched", batched)):
-        for _ in range(max(args.warmup, 1)):
+        for _ in range(max(warmup, 1)):
             for sid in fn():
                 ctx.release(sid)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            sids = fn()
-            for sid, n in zip(sids, ns):
-                ctx.burn_prob(sid, n)
-            wk = sum(int(ctx.get_counters(sid, p.n_replicas)[0].sum()) for sid, p in zip(sids, ps))
-            for sid in sids:
-                ctx.release(sid)
-            assert work is None or wk == work, "work count differs between plain and batched"
-            work = wk
-        dt = (time.perf_counter() - t0) / args.steps
+        sampler = ClockSampler(device)
+        with sampler:
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                sids = fn()
+                for sid, n in zip(sids, ns):
+                    ctx.burn_prob(sid, n)
+                wk = sum(int(ctx.get_counters(sid, p.n_replicas)[0].sum()) for sid, p in zip(sids, ps))
+                for sid in sids:
+                    ctx.release(sid)
+                assert work is None or wk == work, "work count differs between plain and batched"
+                work = wk
+            dt = (time.perf_counter() - t0) / steps
         # one more pass, outside the timing, with per-kernel device times
         ctx.profile(True)
         ctx.kernel_times()
@@ -587,46 +710,33 @@ def run_batch(args):
         out[name] = dict(s_per_step=dt, cell_updates_per_s=work / dt,
                          replicas_per_s=sum(p.n_replicas for p in ps) / dt,
                          kernel_ms={k: v[0] for k, v in kt.items()},
-                         kernel_launches={k: v[1] for k, v in kt.items()})
+                         kernel_launches={k: v[1] for k, v in kt.items()},
+                         clocks=sampler.summary())
     ctx.close()
-    return {"metric": METRIC, "value": out["batched"]["cell_updates_per_s"], "unit": METRIC,
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * out["batched"]["s_per_step"], "higher_is_better": True,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batch of 64 landscapes, sides log-uniform 64..2048 cells, "
-                                   "replicas log-uniform 16..4096, 48 h weather, random ignitions, "
-                                   "lognormal(0,0.1) noise", "cells": int(sum(ns)),
-                       "replicas": int(sum(p.n_replicas for p in ps)),
+    return {"value": out["batched"]["cell_updates_per_s"], "unit": METRIC, "steps": steps, "warmup": warmup,
+            "config": {"workload": "batch of 64 landscapes, sides log-uniform 64..2048 cells, replicas "
+                                   "log-uniform 16..4096, 48 h weather, random ignitions, lognormal(0,0.1) "
+                                   "noise", "cells": int(sum(ns)), "replicas": int(sum(p.n_replicas for p in ps)),
                        "cell_updates_per_step": work,
-                       "timing": "host wall clock per step incl. table builds, burn counts to host"},
+                       "timing": "host wall clock per pass incl. table builds (tables are rebuilt every "
+                                 "pass, 64 x 48 h, larger than L2) and burn counts to the host"},
             "autotuned": None if tuned is None else
-            {"threads": tuned[0], "smem_lists": tuned[1], "sample_frontier_ms": tuned[2],
+            {"threads": tuned[0], "smem": tuned[1], "sample_frontier_ms": tuned[2],
              "sample_replicas": args.tune_sample},
             "plain": out["plain"], "batched": out["batched"],
-            "batched_over_plain": out["plain"]["s_per_step"] / out["batched"]["s_per_step"],
-            "cpu_baseline": _batch_cpu_baseline(args, specs)}
+            "batched_over_plain": out["plain"]["s_per_step"] / out["batched"]["s_per_step"]}
 
 
-def _batch_cpu_baseline(args, specs):
-    """The oracle beside the GPU: replica 0 of every landscape of the batch."""
-    if args.no_cpu_baseline:
-        return None
-    procs = os.cpu_count() or 1
-    rate, work, t, used = cpu_oracle_sample_rate([(("batch", i), 0) for i in range(len(specs))], procs)
-    return {"value": rate, "unit": METRIC, "cores": used, "kind": "oracle",
-            "sample": f"replica 0 of each of the {len(specs)} landscapes ({work} cell-updates), "
-                      f"{used} single-threaded oracle processes, {t:.1f} s"}
-
-
-def run_serve(args):
-    """Poisson request stream served with submit/poll; latency = arrival -> counts on host."""
+def serve_measure(args, sides, reqs, lands, device=0):
+    """Request stream: (i) Poisson arrivals served with submit/poll (continuous
+    batching), latency from arrival to counts on the host; (ii) capacity: the
+    first requests all waiting at once, served vs plain (one synchronous
+    c2f_simulate per request), landscapes and tables resident in both."""
     import torch
     import paper_1905_09317_gb300 as c2f
     c2f.build()
-    sides, reqs = S.serving_requests(rate=args.rate, duration_s=args.duration)
-    lands = [S.heterogeneous_landscape(side, seed=500 + i) for i, side in enumerate(sides)]
     weathers = [S.weather_stream(72, seed=600 + i) for i in range(len(sides))]
-    ctx = c2f.Context(0)
+    ctx = c2f.Context(device)
     ctx.set_table_mode(not args.lazy_tables)
     ctx.set_serving(max_inflight=args.max_inflight)
     lids = [None] * len(sides)
@@ -641,7 +751,7 @@ def run_serve(args):
         ctx.set_weather(lid, weathers[k])
         return lid
 
-    def serve(mode):
+    def stream(mode):
         for k in range(len(lids)):
             if lids[k] is not None:
                 ctx.release(lids[k])
@@ -649,77 +759,115 @@ def run_serve(args):
         torch.cuda.synchronize()
         lat, work, i = [], 0, 0
         outstanding = {}
-        t0 = time.perf_counter()
-        while i < len(reqs) or outstanding:
-            now = time.perf_counter() - t0
-            busy = False
-            while i < len(reqs) and reqs[i]["arrival_s"] <= now:
-                r = reqs[i]
-                k = r["pool_index"]
-                if lids[k] is None:
-                    lids[k] = load(k)                 # a new load: inside the request's latency
-                n = lands[k].fuel.size
-                if mode == "served":
-                    outstanding[ctx.submit(lids[k], params(r))] = (i, n)
-                else:                                 # plain: one synchronous call per request
-                    sid = ctx.simulate(lids[k], params(r))
-                    ctx.burn_prob(sid, n)
-                    work += int(ctx.get_counters(sid, r["n_replicas"])[0].sum())
-                    lat.append(time.perf_counter() - t0 - r["arrival_s"])
-                    ctx.release(sid)
-                i += 1
-                busy = True
-            if mode == "served" and outstanding:
-                for sid in [s for s in outstanding if ctx.poll(s)]:
-                    j, n = outstanding.pop(sid)
-                    ctx.burn_prob(sid, n)
-                    work += int(ctx.get_counters(sid, reqs[j]["n_replicas"])[0].sum())
-                    lat.append(time.perf_counter() - t0 - reqs[j]["arrival_s"])
-                    ctx.release(sid)
+        sampler = ClockSampler(device)
+        with sampler:
+            t0 = time.perf_counter()
+            while i < len(reqs) or outstanding:
+                now = time.perf_counter() - t0
+                busy = False
+                while i < len(reqs) and reqs[i]["arrival_s"] <= now:
+                    r = reqs[i]
+                    k = r["pool_index"]
+                    if lids[k] is None:
+                        lids[k] = load(k)                 # a new load: inside the request's latency
+                    n = lands[k].fuel.size
+                    if mode == "served":
+                        outstanding[ctx.submit(lids[k], params(r))] = (i, n)
+                    else:                                 # plain: one synchronous call per request
+                        sid = ctx.simulate(lids[k], params(r))
+                        ctx.burn_prob(sid, n)
+                        work += int(ctx.get_counters(sid, r["n_replicas"])[0].sum())
+                        lat.append(time.perf_counter() - t0 - r["arrival_s"])
+                        ctx.release(sid)
+                    i += 1
                     busy = True
-            if not busy:
-                nxt = reqs[i]["arrival_s"] - (time.perf_counter() - t0) if i < len(reqs) else 0.0
-                time.sleep(min(max(nxt, 0.0), 0.0005) if outstanding else max(min(nxt, 0.01), 0.0))
-        wall = time.perf_counter() - t0
+                if mode == "served" and outstanding:
+                    for sid in [s for s in outstanding if ctx.poll(s)]:
+                        j, n = outstanding.pop(sid)
+                        ctx.burn_prob(sid, n)
+                        work += int(ctx.get_counters(sid, reqs[j]["n_replicas"])[0].sum())
+                        lat.append(time.perf_counter() - t0 - reqs[j]["arrival_s"])
+                        ctx.release(sid)
+                        busy = True
+                if not busy:
+                    nxt = reqs[i]["arrival_s"] - (time.perf_counter() - t0) if i < len(reqs) else 0.0
+                    time.sleep(min(max(nxt, 0.0), 0.0005) if outstanding else max(min(nxt, 0.01), 0.0))
+            wall = time.perf_counter() - t0
         lat = np.array(lat)
         return dict(wall_s=wall, requests=len(lat), cell_updates_per_s=work / wall,
                     replicas_per_s=sum(r["n_replicas"] for r in reqs) / wall,
                     p50_latency_s=float(np.percentile(lat, 50)),
                     p99_latency_s=float(np.percentile(lat, 99)),
-                    mean_latency_s=float(lat.mean()), cell_updates=work)
+                    mean_latency_s=float(lat.mean()), cell_updates=work, clocks=sampler.summary())
 
-    out = {"served": serve("served")}
+    def capacity(reqs_c):
+        """the requests all waiting at t = 0, landscapes and tables resident"""
+        for k in range(len(lids)):
+            if lids[k] is None:
+                lids[k] = load(k)
+            ctx.build_ros(lids[k], c2f.default_params(hours=72, ros_sigma=0.1, ignition_mode=1), force=0)
+        torch.cuda.synchronize()
+        res = {}
+        for mode in ("plain", "served"):
+            for _ in range(2):   # the first pass warms the allocator pools; the second is timed
+                work = 0
+                sampler = ClockSampler(device)
+                with sampler:
+                    t0 = time.perf_counter()
+                    if mode == "plain":
+                        for r in reqs_c:
+                            k = r["pool_index"]
+                            sid = ctx.simulate(lids[k], params(r))
+                            ctx.burn_prob(sid, lands[k].fuel.size)
+                            work += int(ctx.get_counters(sid, r["n_replicas"])[0].sum())
+                            ctx.release(sid)
+                    else:
+                        sids = [ctx.submit(lids[r["pool_index"]], params(r)) for r in reqs_c]
+                        for sid, r in zip(sids, reqs_c):
+                            ctx.wait(sid)
+                            ctx.burn_prob(sid, lands[r["pool_index"]].fuel.size)
+                            work += int(ctx.get_counters(sid, r["n_replicas"])[0].sum())
+                            ctx.release(sid)
+                    wall = time.perf_counter() - t0
+            res[mode] = dict(wall_s=wall, cell_updates_per_s=work / wall, cell_updates=work,
+                             replicas_per_s=sum(r["n_replicas"] for r in reqs_c) / wall,
+                             clocks=sampler.summary())
+        res["served_over_plain"] = res["plain"]["wall_s"] / res["served"]["wall_s"]
+        res["requests"] = len(reqs_c)
+        return res
+
+    out = {"served": stream("served")}
     if args.serve_plain:
-        out["plain"] = serve("plain")
+        out["plain_stream"] = stream("plain")
+    out["capacity"] = capacity(reqs[:args.capacity_requests])
     ctx.close()
     sv = out["served"]
-    return {"metric": METRIC, "value": sv["cell_updates_per_s"], "unit": METRIC, "n_gpus": 1,
-            "steps": 1, "warmup": 0, "ms_per_step": 1e3 * sv["wall_s"], "higher_is_better": True,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"Poisson arrivals {args.rate}/s for {args.duration} s, pool of "
-                                   f"{len(sides)} landscapes (sides {min(sides)}..{max(sides)}), "
+    return {"value": sv["cell_updates_per_s"], "unit": METRIC,
+            "p50_latency_s": sv["p50_latency_s"], "p99_latency_s": sv["p99_latency_s"],
+            "config": {"workload": f"Poisson arrivals {args.rate}/s for {max(r['arrival_s'] for r in reqs):.0f} s, "
+                                   f"pool of {len(sides)} landscapes (sides {min(sides)}..{max(sides)}), "
                                    "replicas 32..2048, 12..72 h", "requests": len(reqs),
                        "max_inflight_epochs": args.max_inflight,
-                       "timing": "host wall clock from the first arrival to the last result; "
-                                 "latency from arrival to burn counts on the host"},
+                       "timing": "host wall clock; stream: latency from arrival to burn counts on the host "
+                                 "(new landscape loads inside it); capacity: the first "
+                                 f"{min(len(reqs), args.capacity_requests)} requests waiting at once"},
             **out}
 
 
-def run_large(args):
+def large_measure(args, w, steps, device=0):
     """4096^2 cells, 72 h, 256 replicas: table build + frontier + burn counts."""
     import torch
     import paper_1905_09317_gb300 as c2f
     c2f.build()
-    w = S.config4()
     L = w.landscape
     n = L.fuel.size
     p = _params_of(c2f, w)
-    ctx = c2f.Context(0)
+    ctx = c2f.Context(device)
     lid = ctx.load_landscape(L.fuel, L.slope, L.aspect, cell_size=L.cell_size)
     ctx.set_weather(lid, w.weather)
     counts = torch.empty(n, dtype=torch.int32, device="cuda")
-    ctx.set_stream(torch.cuda.current_stream().cuda_stream)
-
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream.cuda_stream)
     ctx.set_table_mode(not args.lazy_tables)
 
     def step():
@@ -735,26 +883,64 @@ def run_large(args):
     ctx.profile(True)
     ctx.kernel_times()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ctx.release(step())
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / args.steps
+    sampler = ClockSampler(device)
+    with sampler:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            ctx.release(step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    dt = ev0.elapsed_time(ev1) / 1e3 / steps
     kt = ctx.kernel_times()
     ctx.close()
-    roof = None
-    if not args.lazy_tables:   # the table kernel dominates: FP64-bound
-        roof = roofline("ros_table", kt, w, work, measured_peaks(), fp64)
-    return {"metric": METRIC, "value": work / dt, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
-            "warmup": 1, "ms_per_step": 1e3 * dt, "higher_is_better": True, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "4096x4096 heterogeneous landscape, 72 h weather with a +90 deg "
-                                   "wind shift at hour 36, 256 replicas", "cells": int(n),
-                       "cell_updates_per_step": work},
-            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+    roof = None if args.lazy_tables else roofline_table(kt, w, fp64)   # the table kernel dominates
+    return {"value": work / dt, "unit": METRIC, "steps": steps, "ms_per_step": 1e3 * dt,
+            "config": {"workload": "4096x4096 heterogeneous landscape, 72 h weather with a +90 deg wind "
+                                   "shift at hour 36, 256 replicas", "cells": int(n),
+                       "cell_updates_per_step": work,
+                       "timing": "CUDA events on the context stream; the 87 GB table is rebuilt every step"},
+            "kernel_ms_per_step": {k: v[0] / steps for k, v in kt.items()},
             "roofline": roof, "fp64_peak_gflops_measured": fp64,
-            "replicas_per_s": p.n_replicas / dt,
-            "cpu_baseline": _large_cpu_baseline(args)}
+            "replicas_per_s": p.n_replicas / dt, "clocks": sampler.summary()}
+
+
+def run_batch(args):
+    """--workload batch: the 64-landscape batch on its own line."""
+    specs = S.config3_specs()
+    ws = [S.config3_workload(sp) for sp in specs]
+    r = batch_measure(args, ws, specs, args.steps, args.warmup)
+    return {"metric": METRIC, "n_gpus": 1, "ms_per_step": 1e3 * r["batched"]["s_per_step"],
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic", **r,
+            "cpu_baseline": _batch_cpu_baseline(args, specs)}
+
+
+def _batch_cpu_baseline(args, specs):
+    """The oracle beside the GPU: replica 0 of every landscape of the batch."""
+    if args.no_cpu_baseline:
+        return None
+    procs = os.cpu_count() or 1
+    rate, work, t, used = cpu_oracle_sample_rate([(("batch", i), 0) for i in range(len(specs))], procs)
+    return {"value": rate, "unit": METRIC, "cores": used, "kind": "oracle",
+            "sample": f"replica 0 of each of the {len(specs)} landscapes ({work} cell-updates), "
+                      f"{used} single-threaded oracle processes, {t:.1f} s"}
+
+
+def run_serve(args):
+    """--workload serve: the request stream on its own line."""
+    sides, reqs = S.serving_requests(rate=args.rate, duration_s=args.duration)
+    lands = [S.heterogeneous_landscape(side, seed=500 + i) for i, side in enumerate(sides)]
+    r = serve_measure(args, sides, reqs, lands)
+    return {"metric": METRIC, "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 * r["served"]["wall_s"], "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", **r}
+
+
+def run_large(args):
+    """--workload large: 4096^2 cells on its own line."""
+    r = large_measure(args, S.config4(), args.steps)
+    return {"metric": METRIC, "n_gpus": 1, "warmup": 1, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", **r, "cpu_baseline": _large_cpu_baseline(args)}
 
 
 def _large_cpu_baseline(args):
@@ -918,7 +1104,20 @@ def main():
     ap.add_argument("--max-inflight", type=int, default=3, help="serve: concurrent epochs")
     ap.add_argument("--serve-plain", action="store_true",
                     help="serve: also replay the stream with one synchronous call per request")
+    ap.add_argument("--serve-window", type=float, default=10.0,
+                    help="default line: seconds of Poisson arrivals in its request-stream section")
+    ap.add_argument("--capacity-requests", type=int, default=200,
+                    help="request stream: requests waiting at once in the capacity comparison")
+    ap.add_argument("--plain-steps", type=int, default=10,
+                    help="default line: steps of the plain (one synchronous call per step) timing")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line without its batch, request-stream and 4096^2 sections")
     args = ap.parse_args()
+    world_env = int(os.environ.get("WORLD_SIZE", "1"))
+    err = gpus_mismatch(args.gpus, world_env)
+    if err:
+        print(err, file=sys.stderr, flush=True)
+        sys.exit(2)
     if args.workload != "landscape" and args.impl == "ours":
         fn = {"batch": run_batch, "serve": run_serve, "large": run_large,
               "scenarios": run_scenarios, "compare": run_compare}[args.workload]

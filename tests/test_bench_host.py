@@ -35,3 +35,14 @@ def test_reference_arm_prints_one_json_line():
     d = json.loads(lines[-1])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_gpus_must_match_the_launched_processes():
+    """--gpus N with N processes launched is accepted; anything else is refused
+    before any device work, so that a line never claims GPUs it did not time."""
+    assert bench.gpus_mismatch(1, 1) is None and bench.gpus_mismatch(8, 8) is None
+    assert bench.gpus_mismatch(2, 1) and bench.gpus_mismatch(1, 4) and bench.gpus_mismatch(0, 1)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2", "--steps", "1"],
+                         capture_output=True, text=True, timeout=300, cwd=ROOT,
+                         env={k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK")})
+    assert out.returncode == 2 and "--gpus 2" in out.stderr and not out.stdout.strip()
