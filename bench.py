@@ -665,8 +665,11 @@ def batch_measure(args, ws, specs, steps, warmup, device=0):
     ps = [_params_of(c2f, w) for w in ws]
     ns = [w.landscape.fuel.size for w in ws]
     tuned = None
-    if not args.frontier_threads:   # launch shape chosen by the autotuner on a scaled-down copy
-        tuned = ctx.autotune(lids, ps, sample_replicas=args.tune_sample)
+    if not args.frontier_threads:   # frontier settings chosen by the autotuner on a scaled-down copy
+        t0 = time.perf_counter()
+        tuned = ctx.autotune_full(lids, ps, sample_replicas=args.tune_sample)
+        tuned["tuning_s"] = time.perf_counter() - t0
+        tuned["sample_replicas"] = args.tune_sample
 
     def plain():
         sids = []
@@ -720,9 +723,7 @@ def batch_measure(args, ws, specs, steps, warmup, device=0):
                        "cell_updates_per_step": work,
                        "timing": "host wall clock per pass incl. table builds (tables are rebuilt every "
                                  "pass, 64 x 48 h, larger than L2) and burn counts to the host"},
-            "autotuned": None if tuned is None else
-            {"threads": tuned[0], "smem": tuned[1], "sample_frontier_ms": tuned[2],
-             "sample_replicas": args.tune_sample},
+            "autotuned": tuned,
             "plain": out["plain"], "batched": out["batched"],
             "batched_over_plain": out["plain"]["s_per_step"] / out["batched"]["s_per_step"]}
 

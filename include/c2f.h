@@ -373,11 +373,40 @@ C2F_API int c2f_test_hold_chunk(c2f_ctx *ctx, int32_t landscape_id, int32_t scen
  * knobs.  smem outside [0, 16] is C2F_EINVAL. */
 C2F_API int c2f_set_frontier_config(c2f_ctx *ctx, int threads, int64_t smem);
 
+/* Compaction trigger of the frontier's burning lists: within a weather hour
+ * a list is compacted (Burned cells and cells with no open axis dropped) once
+ * it holds more than eighths/8 of its capacity (2..7, default 6).  Results do
+ * not depend on it (a tuning knob); outside [2, 7] is C2F_EINVAL. */
+C2F_API int c2f_set_compaction(c2f_ctx *ctx, int32_t eighths);
+
+/* Autotuner result: the frontier settings it kept on the context. */
+typedef struct {
+  int32_t threads;          /* CTA size: 32, 64 or 128 (one replica per warp)                */
+  int32_t smem_lists;       /* 1: plane windows and lists in shared memory; 0: global memory */
+  int32_t warps_per_sm;     /* shared-memory sizing target (0: the launch's own replicas)    */
+  int32_t compact_eighths;  /* compaction trigger, eighths of the list capacity              */
+  int64_t list_capacity;    /* initial burning-list capacity (0: automatic)                  */
+  double frontier_ms;       /* the winner's frontier time on the sample                      */
+  int32_t candidates;       /* settings timed                                                */
+} c2f_tuning;
+
 /* Launch-shape autotuner for a batch: runs the same mix of simulations,
- * scaled down to about `sample_replicas` replicas, under each candidate
- * frontier launch shape (warps per CTA x shared-memory staging), keeps the
- * fastest on the context and reports it.  Results of later runs are the same
- * under any shape; only their speed changes.  Outputs may be NULL. */
+ * scaled down to about `sample_replicas` replicas, under candidate frontier
+ * settings and keeps the fastest on the context.  Coordinate descent, each
+ * stage keeping its best for the next: (1) warps per CTA x shared / global
+ * lists; (2) the shared-memory sizing (warps per SM: the launch's own, 4, 6,
+ * 8, 11) when lists are in shared memory; (3) the compaction trigger (4, 6,
+ * 7 eighths of capacity); (4) the initial list capacity (automatic, 2x, 4x)
+ * when lists are in global memory.  Candidates are timed by the frontier's
+ * kernel events.  Results of later runs are the same under any setting; only
+ * their speed changes.  `out` may be NULL. */
+C2F_API int c2f_autotune_full(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
+                              const c2f_sim_params *params, int32_t sample_replicas, c2f_tuning *out);
+
+/* c2f_autotune_full reporting the CTA size, the shared-memory setting (0:
+ * global lists; 1: shared, sized for the launch; N >= 2: shared, sized for N
+ * warps per SM, as c2f_set_frontier_config takes it) and the frontier time.
+ * Outputs may be NULL. */
 C2F_API int c2f_autotune(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
                          const c2f_sim_params *params, int32_t sample_replicas, int32_t *best_threads,
                          int32_t *best_smem, double *best_ms);

@@ -47,6 +47,13 @@ class SimParams(C.Structure):
     ]
 
 
+class Tuning(C.Structure):
+    """c2f_tuning: the frontier settings the autotuner kept."""
+    _fields_ = [("threads", C.c_int32), ("smem_lists", C.c_int32), ("warps_per_sm", C.c_int32),
+                ("compact_eighths", C.c_int32), ("list_capacity", C.c_int64), ("frontier_ms", C.c_double),
+                ("candidates", C.c_int32)]
+
+
 class FrontierIO(C.Structure):
     """Device-pointer arguments of c2f_frontier_static (allocation-free frontier step)."""
     _fields_ = [("rows", C.c_int32), ("cols", C.c_int32), ("cell_size_m", C.c_double),
@@ -131,6 +138,9 @@ _SIGS = [
     ("c2f_test_hold_chunk", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     ("c2f_autotune", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
                                 _P(C.c_int32), _P(C.c_int32), _P(C.c_double)]),
+    ("c2f_autotune_full", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                                     _P(Tuning)]),
+    ("c2f_set_compaction", C.c_int, [C.c_void_p, C.c_int32]),
     ("c2f_profile", C.c_int, [C.c_void_p, C.c_int]),
     ("c2f_kernel_times", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("c2f_get_replica_profile", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
@@ -405,6 +415,18 @@ class Context:
         self._check(self.lib.c2f_autotune(self.h, n, ids, ps, int(sample_replicas), C.byref(t),
                                           C.byref(sm), C.byref(ms)))
         return t.value, sm.value, ms.value
+
+    def autotune_full(self, landscape_ids, params_list, sample_replicas=256) -> dict:
+        """All the frontier knobs the autotuner turns, kept on the context; returns them."""
+        n = len(landscape_ids)
+        ids = (C.c_int32 * n)(*landscape_ids)
+        ps = (SimParams * n)(*params_list)
+        t = Tuning()
+        self._check(self.lib.c2f_autotune_full(self.h, n, ids, ps, int(sample_replicas), C.byref(t)))
+        return {f[0]: getattr(t, f[0]) for f in Tuning._fields_}
+
+    def set_compaction(self, eighths: int) -> None:
+        self._check(self.lib.c2f_set_compaction(self.h, int(eighths)))
 
     def profile(self, enable: bool = True) -> None:
         self._check(self.lib.c2f_profile(self.h, int(bool(enable))))

@@ -597,6 +597,8 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
   const uint32_t lt = (1u << lane) - 1u;
   const size_t slot = (size_t)blockIdx.x * WPC + wib;
   const int32_t cap = A.cap;
+  // compact the list within an hour once it holds more than this many entries
+  const int32_t compact_at = (A.compact_at > 0 && A.compact_at < cap) ? A.compact_at : cap - cap / 4;
   const uint32_t wait_limit = A.wait_limit ? A.wait_limit : kChunkSpinLimit;
   uint32_t *my = s_dyn + (size_t)wib * A.smem_warp_words;   // [Available win][Burned win][lists]
   uint32_t *erc;     // row << 16 | col
@@ -966,7 +968,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
         W += (long long)live * (long long)(s - s_done);
         s_done = s;
         if (prof && lane == 0) { pc_t = clock64(); pq[4] += 1; pq[7] = max(pq[7], (long long)cnt); }
-        if (cnt > cap - cap / 4) {   // keep room for new cells
+        if (cnt > compact_at) {   // keep room for new cells
           cal = compact(cnt, o);
           if (prof && lane == 0) pq[9] += 1;
         }

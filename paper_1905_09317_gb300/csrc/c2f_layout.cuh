@@ -108,6 +108,8 @@ struct FrontierArgs {
   uint32_t *avail_scratch;        // [slots][pw_max] Available planes (global-plane variant)
   int64_t smem_warp_words;        // 32-bit words of dynamic shared memory per warp
   uint32_t wait_limit;            // polls before a wait for a table chunk gives up; 0 = default
+  int32_t compact_at;             // list entries above which the list is compacted within an
+                                  //   hour (0 = three quarters of cap)
 };
 
 // K1 launch arguments: grid.y covers hours hour0 .. hour0 + gridDim.y - 1

@@ -216,6 +216,7 @@ struct c2f_ctx {
   int warps_per_sm = 0;        // shared-memory sizing target; 0: this launch's own replicas
   bool eager_tables = true;   // simulations build their tables with K1 up front
   int64_t cap_override = 0;
+  int compact_eighths = 6;     // compaction trigger within an hour: eighths of the list capacity
   int64_t graph_launches = 0;
   uint32_t wait_limit = 0;     // frontier waits for table chunks: polls before giving up; 0 = default
   // serving
@@ -700,6 +701,7 @@ int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, i
   A.avail_scratch = S.avail.as<uint32_t>();
   A.smem_warp_words = warp_words;
   A.wait_limit = ctx->wait_limit;
+  A.compact_at = (int32_t)std::max<int64_t>(1, std::min<int64_t>(cap - 1, cap * ctx->compact_eighths / 8));
   F.cap = cap;
   return C2F_OK;
 }
@@ -1897,9 +1899,28 @@ C2F_API int c2f_set_serving(c2f_ctx *ctx, int32_t max_inflight, int64_t max_epoc
 
 C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches);
 
-C2F_API int c2f_autotune(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
-                         const c2f_sim_params *params, int32_t sample_replicas, int32_t *best_threads,
-                         int32_t *best_smem, double *best_ms) {
+C2F_API int c2f_set_compaction(c2f_ctx *ctx, int32_t eighths) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  if (eighths < 2 || eighths > 7) return fail(ctx, C2F_EINVAL, "compaction trigger must be 2..7 eighths");
+  ctx->compact_eighths = eighths;
+  return C2F_OK;
+}
+
+// Launch-shape autotuner: coordinate descent over the frontier's knobs on a
+// scaled-down copy of the mix (the same landscapes and options, replicas cut
+// in proportion), each candidate timed by the frontier's kernel events:
+//   1. warps per CTA x shared / global lists (threads 32, 64, 128 with
+//      windowed shared-memory lists; 32, 128 with global lists);
+//   2. shared-memory sizing (warps per SM the per-warp share is cut for:
+//      the launch's own, 4, 6, 8, 11), with shared-memory lists only;
+//   3. the compaction trigger (4, 6, 7 eighths of the list capacity);
+//   4. the initial list capacity (automatic, 2x, 4x: fewer overflow re-runs
+//      against more memory), with global lists only.
+// The best setting of each stage is kept for the next; the winner stays on
+// the context.  Results never depend on any of these.
+C2F_API int c2f_autotune_full(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
+                              const c2f_sim_params *params, int32_t sample_replicas, c2f_tuning *out) {
   if (!ctx) return C2F_EINVAL;
   LOCK;
   if (n < 1 || !landscape_ids || !params || sample_replicas < 1)
@@ -1907,40 +1928,105 @@ C2F_API int c2f_autotune(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
   int64_t total = 0;
   for (int32_t i = 0; i < n; ++i) total += std::max(params[i].n_replicas, 1);
   std::vector<c2f_sim_params> q(params, params + n);
+  int64_t auto_cap = 0;
   for (int32_t i = 0; i < n; ++i) {   // the same mix of simulations, scaled down
     const int64_t r = (int64_t)params[i].n_replicas * sample_replicas / std::max<int64_t>(total, 1);
     q[i].n_replicas = (int32_t)std::max<int64_t>(1, std::min<int64_t>(r, params[i].n_replicas));
     q[i].outputs = C2F_OUT_SCARS | C2F_OUT_COUNTERS;
+    auto L = find_land(ctx, landscape_ids[i]);
+    if (!L) return fail(ctx, C2F_ENOTFOUND, "unknown landscape %d", landscape_ids[i]);
+    auto_cap = std::max(auto_cap, std::max<int64_t>(1024, 2 * (int64_t)(L->rows + L->cols)));
   }
-  const int cand_threads[5] = {32, 64, 128, 32, 128};
-  const int cand_smem[5] = {1, 1, 1, 0, 0};
-  const int keep_threads = ctx->frontier_threads;
-  const bool keep_win = ctx->window_smem, keep_prof = ctx->profiling;
-  double best = 1e300;
-  int bi = 0;
+  struct Knobs { int threads; bool win; int warps_per_sm; int eighths; int64_t cap; };
+  const Knobs keep{ctx->frontier_threads, ctx->window_smem, ctx->warps_per_sm, ctx->compact_eighths,
+                   ctx->cap_override};
+  const bool keep_prof = ctx->profiling;
+  auto apply = [&](const Knobs &k) {
+    ctx->frontier_threads = k.threads; ctx->window_smem = k.win; ctx->warps_per_sm = k.warps_per_sm;
+    ctx->compact_eighths = k.eighths; ctx->cap_override = k.cap;
+  };
   std::vector<int32_t> sids(n);
-  for (int c = 0; c < 5; ++c) {
-    ctx->frontier_threads = cand_threads[c];
-    ctx->window_smem = cand_smem[c] != 0;
+  int32_t tried = 0;
+  auto time_of = [&](const Knobs &k, double *ms_out) -> int {
+    apply(k);
     ctx->profiling = true;
     double ms[C2F_KT_FAMILIES];
     int64_t cnt[C2F_KT_FAMILIES];
     int rc = c2f_kernel_times(ctx, ms, cnt);   // reset
     if (!rc) rc = simulate_many(ctx, n, landscape_ids, q.data(), sids.data());
     if (!rc) rc = c2f_kernel_times(ctx, ms, cnt);
-    if (rc) {
-      ctx->frontier_threads = keep_threads; ctx->window_smem = keep_win; ctx->profiling = keep_prof;
-      return rc;
-    }
-    for (int32_t i = 0; i < n; ++i) ctx->sims.erase(sids[i]);
-    if (ms[2] < best) { best = ms[2]; bi = c; }
+    if (!rc) for (int32_t i = 0; i < n; ++i) ctx->sims.erase(sids[i]);
+    ++tried;
+    *ms_out = ms[2];
+    return rc;
+  };
+  auto restore = [&]() { apply(keep); ctx->profiling = keep_prof; };
+  Knobs best{32, true, 0, 6, 0};
+  double best_ms = 1e300;
+  // 1. warps per CTA x shared / global lists
+  const Knobs shapes[5] = {{32, true, 0, 6, 0}, {64, true, 0, 6, 0}, {128, true, 0, 6, 0},
+                           {32, false, 0, 6, 0}, {128, false, 0, 6, 0}};
+  for (const Knobs &k : shapes) {
+    double ms;
+    if (int rc = time_of(k, &ms)) { restore(); return rc; }
+    if (ms < best_ms) { best_ms = ms; best = k; }
   }
-  ctx->frontier_threads = cand_threads[bi];
-  ctx->window_smem = cand_smem[bi] != 0;
+  // 2. shared-memory sizing (shared-memory lists only)
+  if (best.win) {
+    const Knobs base = best;
+    for (int wps : {4, 6, 8, 11}) {
+      Knobs k = base;
+      k.warps_per_sm = wps;
+      double ms;
+      if (int rc = time_of(k, &ms)) { restore(); return rc; }
+      if (ms < best_ms) { best_ms = ms; best = k; }
+    }
+  }
+  // 3. compaction trigger
+  {
+    const Knobs base = best;
+    for (int e : {4, 7}) {
+      Knobs k = base;
+      k.eighths = e;
+      double ms;
+      if (int rc = time_of(k, &ms)) { restore(); return rc; }
+      if (ms < best_ms) { best_ms = ms; best = k; }
+    }
+  }
+  // 4. initial list capacity (global lists only; shared lists are sized by stage 2)
+  if (!best.win) {
+    const Knobs base = best;
+    for (int64_t mult : {2, 4}) {
+      Knobs k = base;
+      k.cap = auto_cap * mult;
+      double ms;
+      if (int rc = time_of(k, &ms)) { restore(); return rc; }
+      if (ms < best_ms) { best_ms = ms; best = k; }
+    }
+  }
+  apply(best);
   ctx->profiling = keep_prof;
-  if (best_threads) *best_threads = cand_threads[bi];
-  if (best_smem) *best_smem = cand_smem[bi];
-  if (best_ms) *best_ms = best;
+  if (out) {
+    out->threads = best.threads;
+    out->smem_lists = best.win ? 1 : 0;
+    out->warps_per_sm = best.warps_per_sm;
+    out->compact_eighths = best.eighths;
+    out->list_capacity = best.cap;
+    out->frontier_ms = best_ms;
+    out->candidates = tried;
+  }
+  return C2F_OK;
+}
+
+C2F_API int c2f_autotune(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
+                         const c2f_sim_params *params, int32_t sample_replicas, int32_t *best_threads,
+                         int32_t *best_smem, double *best_ms) {
+  c2f_tuning t{};
+  const int rc = c2f_autotune_full(ctx, n, landscape_ids, params, sample_replicas, &t);
+  if (rc) return rc;
+  if (best_threads) *best_threads = t.threads;
+  if (best_smem) *best_smem = t.smem_lists ? (t.warps_per_sm >= 2 ? t.warps_per_sm : 1) : 0;
+  if (best_ms) *best_ms = t.frontier_ms;
   return C2F_OK;
 }
 

@@ -258,15 +258,37 @@ def test_errors(ctx):
 
 
 def test_autotune_keeps_results(ctx):
+    """Every knob the autotuner turns (warps per CTA, shared / global lists,
+    shared-memory sizing, compaction trigger, list capacity) changes speed
+    only: the ignition steps are the same under each setting it tries and
+    under the one it keeps."""
     ws = [S.config2(side=s, n_replicas=r, hours=3) for s, r in ((60, 30), (90, 12))]
     lids = [load(ctx, w) for w in ws]
     ps = [gpu_params(**w.params) for w in ws]
-    before = [ctx.get_scars(sid, p.n_replicas, w.landscape.fuel.size, ign_steps=True)[1]
-              for sid, p, w in zip(ctx.simulate_batch(lids, ps), ps, ws)]
-    threads, smem, ms = ctx.autotune(lids, ps, sample_replicas=16)
-    assert threads in (32, 64, 128) and smem in (0, 1) and ms > 0
-    after = [ctx.get_scars(sid, p.n_replicas, w.landscape.fuel.size, ign_steps=True)[1]
-             for sid, p, w in zip(ctx.simulate_batch(lids, ps), ps, ws)]
-    for a, b in zip(before, after):
+
+    def steps():
+        return [ctx.get_scars(sid, p.n_replicas, w.landscape.fuel.size, ign_steps=True)[1]
+                for sid, p, w in zip(ctx.simulate_batch(lids, ps), ps, ws)]
+
+    before = steps()
+    t = ctx.autotune_full(lids, ps, sample_replicas=16)
+    assert t["threads"] in (32, 64, 128) and t["smem_lists"] in (0, 1) and t["frontier_ms"] > 0
+    assert t["compact_eighths"] in (4, 6, 7) and t["warps_per_sm"] in (0, 4, 6, 8, 11)
+    assert t["list_capacity"] >= 0 and t["candidates"] >= 7
+    for a, b in zip(before, steps()):
         assert np.array_equal(a, b)
+    # each knob on its own, including settings that force list overflows and re-runs
+    settings = [dict(threads=64, smem=1), dict(threads=32, smem=0), dict(threads=128, smem=11),
+                dict(threads=32, smem=4, eighths=2), dict(threads=32, smem=1, eighths=7),
+                dict(threads=32, smem=0, cap=64), dict(threads=128, smem=0, cap=16, eighths=4)]
+    for st in settings:
+        ctx.set_frontier_config(st["threads"], st["smem"])
+        ctx.set_compaction(st.get("eighths", 6))
+        ctx.set_list_capacity(st.get("cap", 0))
+        for a, b in zip(before, steps()):
+            assert np.array_equal(a, b), st
+    threads, smem, ms = ctx.autotune(lids, ps, sample_replicas=16)
+    assert threads in (32, 64, 128) and smem in (0, 1, 4, 6, 8, 11) and ms > 0
     ctx.set_frontier_config(32, 1)
+    ctx.set_compaction(6)
+    ctx.set_list_capacity(0)
