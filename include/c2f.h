@@ -427,10 +427,11 @@ C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches);
  * 1 cycles at hour boundaries, 2 cycles finding and sending crossings and
  * receiving (A), 3 cycles setting up newly ignited cells (C), 4 fire periods
  * visited, 5 burning cells with a crossing processed, 6 cells ignited,
- * 7 longest burning list, 8 cycles of (A) spent scanning the list for
- * crossings, 9 scan steps, 10 rounds of crossing cells, 11 new-cell set-up
- * iterations, 12-15 zero.  Host memory, n_replicas*16 int64.  C2F_EINVAL if
- * the simulation ran without profiling. */
+ * 7 longest burning list, 8 cycles of (A) spent walking the visited period's
+ * calendar list, 9 list compactions within an hour, 10 rounds of crossing
+ * cells (up to 32 each), 11 new-cell set-up iterations (up to 4 cells each),
+ * 12-15 zero.  Host memory, n_replicas*16 int64.  C2F_EINVAL if the
+ * simulation ran without profiling. */
 C2F_API int c2f_get_replica_profile(c2f_ctx *ctx, int32_t sim_id, int64_t *counters);
 
 /* ---------------------------------------------------------------------------

@@ -446,8 +446,9 @@ class Context:
     def replica_profile(self, sim_id: int, n_replicas: int) -> np.ndarray:
         """(n_replicas, 16) frontier counters of a simulation run with profiling on
         (include/c2f.h, c2f_get_replica_profile): total, boundary, send and
-        new-cell cycles, visited periods, hit cells, ignited cells, longest
-        burning list, scan cycles, scan steps, hit rounds, new-cell iterations."""
+        new-cell cycles, visited periods, crossing cells, ignited cells, longest
+        burning list, calendar-walk cycles, compactions, crossing rounds,
+        new-cell iterations."""
         out = np.empty((n_replicas, 16), dtype=np.int64)
         self._check(self.lib.c2f_get_replica_profile(self.h, int(sim_id), _ptr(out)))
         return out
