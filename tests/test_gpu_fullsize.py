@@ -116,3 +116,57 @@ def test_served_request_stream_sampled():
             _check_replica(ctx, sids[j], w, q["n_replicas"] - 1 - j % q["n_replicas"], work, nign, ign_cell)
         for s in sids:
             ctx.wait(s)
+
+
+def test_headline_pipelined_steps_sampled():
+    """The benchmark's headline configuration exactly: the 512x512 landscape,
+    1000 replicas, 24 h; the frontier's shared memory sized for 8 warps per SM
+    (one more than a step's replicas need), three steps in flight through
+    submit / wait, each step's table rebuilt (K1) while the previous step's
+    frontier runs, burn counts into device memory.  Every step's counts equal
+    the sum of its scars, the steps agree with each other (same seed, same
+    replicas), and replicas 0, 333, 666, 999 of each are replayed by the oracle."""
+    torch = pytest.importorskip("torch")
+    c2f.build()
+    w = S.config2()
+    L = w.landscape
+    n = L.fuel.size
+    p = _params(w)
+    R = p.n_replicas
+    with c2f.Context(0) as ctx:
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        ctx.set_frontier_config(32, -(-R // sms) + 1)
+        stream = torch.cuda.Stream()
+        ctx.set_stream(stream.cuda_stream)
+        lid = ctx.load_landscape(L.fuel, L.slope, L.aspect, cell_size=L.cell_size)
+        ctx.set_weather(lid, w.weather)
+        ctx.set_serving(max_inflight=3, max_epoch_replicas=R, hbm_reserve_bytes=0)
+        counts_dev = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(5)]
+        inflight, done = [], []
+        for i in range(5):
+            ctx.build_ros(lid, p, force=1)
+            inflight.append((i, ctx.submit(lid, p)))
+            if len(inflight) >= 3:
+                j, sid = inflight.pop(0)
+                ctx.wait(sid)
+                ctx.burn_prob_device(sid, counts_dev[j].data_ptr())
+                done.append((j, sid))
+        while inflight:
+            j, sid = inflight.pop(0)
+            ctx.wait(sid)
+            ctx.burn_prob_device(sid, counts_dev[j].data_ptr())
+            done.append((j, sid))
+        torch.cuda.synchronize()
+        first = None
+        for j, sid in done:
+            work, nign, ign_cell = ctx.get_counters(sid, R)
+            scars, _ = ctx.get_scars(sid, R, n)
+            counts = counts_dev[j].cpu().numpy().view(np.uint32)
+            assert np.array_equal(counts, scars.sum(0, dtype=np.uint32)), j
+            if first is None:
+                first = (work, nign, ign_cell, counts)
+                for r in (0, 333, 666, 999):
+                    _check_replica(ctx, sid, w, r, work, nign, ign_cell)
+            else:
+                for a, b in zip(first, (work, nign, ign_cell, counts)):
+                    assert np.array_equal(a, b), j

@@ -219,8 +219,9 @@ def test_batch_equals_separate_runs(ctx):
 
 
 def test_config2_full_size_sampled_replicas(ctx):
-    """512x512, 1000 replicas, 24 h in the benchmark's launch configuration;
-    every 125th replica is replayed by the oracle."""
+    """512x512, 1000 replicas, 24 h, one c2f_simulate (the library's default
+    launch sizing, the benchmark's plain steps); every 125th replica is
+    replayed by the oracle, ignition steps included."""
     w = S.config2()
     g = run_gpu(ctx, w)
     compare_replicas(w, g, range(0, 1000, 125))
