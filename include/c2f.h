@@ -411,7 +411,16 @@ C2F_API int c2f_autotune(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
                          const c2f_sim_params *params, int32_t sample_replicas, int32_t *best_threads,
                          int32_t *best_smem, double *best_ms);
 
-/* Kernel timing: with profiling on, the context brackets each launch of its
+/* Profiling switches, flags of c2f_profile's `enable` (0 turns both off; other
+ * bits give C2F_EINVAL).  C2F_PROFILE_KERNELS: kernel timing as below.
+ * C2F_PROFILE_REPLICAS: per-replica frontier counters (c2f_get_replica_profile);
+ * they cost the frontier a few clock reads and shared-memory adds per visited
+ * period, so a timing run should leave them off.  Either switch makes
+ * c2f_simulate_batch launch its groups directly instead of through a graph. */
+#define C2F_PROFILE_KERNELS 1
+#define C2F_PROFILE_REPLICAS 2
+
+/* Kernel timing: with C2F_PROFILE_KERNELS on, the context brackets each launch of its
  * kernel families with CUDA events on its stream.  c2f_kernel_times waits for
  * the stream, writes per family the summed milliseconds and the launch count
  * since the last call, and resets them.  Families (index): 0 ROS table (K1,
@@ -421,8 +430,8 @@ C2F_API int c2f_autotune(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
 C2F_API int c2f_profile(c2f_ctx *ctx, int enable);
 C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches);
 
-/* Per-replica frontier profile of a simulation run while profiling was on
- * (c2f_profile): counters[r*16 + i] for replica r (SM clock cycles, counts),
+/* Per-replica frontier profile of a simulation run while C2F_PROFILE_REPLICAS
+ * was on (c2f_profile): counters[r*16 + i] for replica r (SM clock cycles, counts),
  * i = 0 cycles of the replica's whole frontier run (its last attempt),
  * 1 cycles at hour boundaries, 2 cycles finding and sending crossings and
  * receiving (A), 3 cycles setting up newly ignited cells (C), 4 fire periods
@@ -431,7 +440,7 @@ C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches);
  * calendar list, 9 list compactions within an hour, 10 rounds of crossing
  * cells (up to 32 each), 11 new-cell set-up iterations (up to 4 cells each),
  * 12-15 zero.  Host memory, n_replicas*16 int64.  C2F_EINVAL if the
- * simulation ran without profiling. */
+ * simulation ran without per-replica counters. */
 C2F_API int c2f_get_replica_profile(c2f_ctx *ctx, int32_t sim_id, int64_t *counters);
 
 /* ---------------------------------------------------------------------------

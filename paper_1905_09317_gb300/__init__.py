@@ -19,6 +19,7 @@ from .build import LIB as LIB_PATH, build  # noqa: F401
 C2F_OK, C2F_EINVAL, C2F_ENOMEM, C2F_ECUDA, C2F_ETIMEOUT = 0, -1, -2, -3, -4
 C2F_ENOTFOUND, C2F_EBUSY, C2F_ECANCELED = -5, -6, -7
 OUT_SCARS, OUT_IGN_STEPS, OUT_COUNTERS = 1, 2, 8
+PROFILE_KERNELS, PROFILE_REPLICAS = 1, 2
 _ERR = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ENOTFOUND",
         -6: "EBUSY", -7: "ECANCELED"}
 
@@ -428,8 +429,11 @@ class Context:
     def set_compaction(self, eighths: int) -> None:
         self._check(self.lib.c2f_set_compaction(self.h, int(eighths)))
 
-    def profile(self, enable: bool = True) -> None:
-        self._check(self.lib.c2f_profile(self.h, int(bool(enable))))
+    def profile(self, enable: bool = True, replicas: bool = False) -> None:
+        """Kernel-family timing on or off; with `replicas` also the per-replica
+        frontier counters (replica_profile)."""
+        flags = (PROFILE_KERNELS if enable else 0) | (PROFILE_REPLICAS if replicas else 0)
+        self._check(self.lib.c2f_profile(self.h, flags))
 
     def fp64_peak(self) -> float:
         """Measured FP64 FMA rate of the device, GFLOP/s."""

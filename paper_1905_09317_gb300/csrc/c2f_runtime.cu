@@ -231,7 +231,8 @@ struct c2f_ctx {
   cudaStream_t read_stream = nullptr;   // result reads: not queued behind table builds
   cudaStream_t load_stream = nullptr;   // landscape uploads: not queued behind table builds
   // kernel timing
-  bool profiling = false;
+  bool profiling = false;          // kernel-family events (C2F_PROFILE_KERNELS)
+  bool replica_counters = false;   // per-replica frontier counters (C2F_PROFILE_REPLICAS)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[C2F_KT_FAMILIES];
   std::vector<cudaEvent_t> event_pool;
 };
@@ -559,7 +560,7 @@ int alloc_sim(c2f_ctx *ctx, Sim &s, cudaStream_t st) {
   if (s.table->n_scen > 1) {
     if ((rc = dalloc_on(ctx, s.scen, 4 * R, st))) return rc;
   }
-  if (ctx->profiling) {   // per-replica profile counters of the frontier
+  if (ctx->replica_counters) {   // per-replica profile counters of the frontier
     if ((rc = dalloc_on(ctx, s.prof, 8 * kProfCounters * R, st))) return rc;
     CK(cudaMemsetAsync(s.prof.p, 0, 8 * kProfCounters * R, st));
   }
@@ -865,7 +866,7 @@ int simulate_many(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_sim_par
   if (n < 1 || !ids || !params || !sim_ids) return fail(ctx, C2F_EINVAL, "bad batch arguments");
   CK(cudaSetDevice(ctx->device));
   int rc;
-  const bool graph = n > 1 && !ctx->profiling;
+  const bool graph = n > 1 && !ctx->profiling && !ctx->replica_counters;
   std::vector<Landscape *> builds;
   std::vector<std::shared_ptr<Sim>> sims;
   if ((rc = make_sims(ctx, n, ids, params, sims, &builds))) return rc;
@@ -1818,7 +1819,7 @@ C2F_API int c2f_get_replica_profile(c2f_ctx *ctx, int32_t sim_id, int64_t *count
   if (!counters) return fail(ctx, C2F_EINVAL, "counters is NULL");
   int rc = sim_ready(ctx, *s);
   if (rc) return rc;
-  if (!s->prof.p) return fail(ctx, C2F_EINVAL, "the simulation ran without profiling");
+  if (!s->prof.p) return fail(ctx, C2F_EINVAL, "the simulation ran without per-replica counters");
   CK(cudaSetDevice(ctx->device));
   CK(cudaMemcpyAsync(counters, s->prof.p, 8 * kProfCounters * (size_t)s->p.n_replicas, cudaMemcpyDeviceToHost,
                      ctx->read_stream));
@@ -1940,7 +1941,7 @@ C2F_API int c2f_autotune_full(c2f_ctx *ctx, int32_t n, const int32_t *landscape_
   struct Knobs { int threads; bool win; int warps_per_sm; int eighths; int64_t cap; };
   const Knobs keep{ctx->frontier_threads, ctx->window_smem, ctx->warps_per_sm, ctx->compact_eighths,
                    ctx->cap_override};
-  const bool keep_prof = ctx->profiling;
+  const bool keep_prof = ctx->profiling, keep_rc = ctx->replica_counters;
   auto apply = [&](const Knobs &k) {
     ctx->frontier_threads = k.threads; ctx->window_smem = k.win; ctx->warps_per_sm = k.warps_per_sm;
     ctx->compact_eighths = k.eighths; ctx->cap_override = k.cap;
@@ -1950,6 +1951,7 @@ C2F_API int c2f_autotune_full(c2f_ctx *ctx, int32_t n, const int32_t *landscape_
   auto time_of = [&](const Knobs &k, double *ms_out) -> int {
     apply(k);
     ctx->profiling = true;
+    ctx->replica_counters = false;
     double ms[C2F_KT_FAMILIES];
     int64_t cnt[C2F_KT_FAMILIES];
     int rc = c2f_kernel_times(ctx, ms, cnt);   // reset
@@ -1960,7 +1962,7 @@ C2F_API int c2f_autotune_full(c2f_ctx *ctx, int32_t n, const int32_t *landscape_
     *ms_out = ms[2];
     return rc;
   };
-  auto restore = [&]() { apply(keep); ctx->profiling = keep_prof; };
+  auto restore = [&]() { apply(keep); ctx->profiling = keep_prof; ctx->replica_counters = keep_rc; };
   Knobs best{32, true, 0, 6, 0};
   double best_ms = 1e300;
   // 1. warps per CTA x shared / global lists
@@ -2006,6 +2008,7 @@ C2F_API int c2f_autotune_full(c2f_ctx *ctx, int32_t n, const int32_t *landscape_
   }
   apply(best);
   ctx->profiling = keep_prof;
+  ctx->replica_counters = keep_rc;
   if (out) {
     out->threads = best.threads;
     out->smem_lists = best.win ? 1 : 0;
@@ -2032,8 +2035,10 @@ C2F_API int c2f_autotune(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
 
 C2F_API int c2f_profile(c2f_ctx *ctx, int enable) {
   if (!ctx) return C2F_EINVAL;
+  if (enable & ~(C2F_PROFILE_KERNELS | C2F_PROFILE_REPLICAS)) return C2F_EINVAL;
   LOCK;
-  ctx->profiling = enable != 0;
+  ctx->profiling = (enable & C2F_PROFILE_KERNELS) != 0;
+  ctx->replica_counters = (enable & C2F_PROFILE_REPLICAS) != 0;
   return C2F_OK;
 }
 
