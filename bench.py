@@ -360,13 +360,25 @@ def run_ours(args, rank, world, local_rank):
 
     def run_steps(k):
         if args.serial:
-            return [step() for _ in range(k)]
+            done = []
+            for _ in range(k):
+                sid = step()
+                if done:
+                    ctx.release(done.pop())   # as in the pipelined form: the last step is kept
+                done.append(sid)
+            return done
         done, inflight = [], []
 
         def retire():
             sid = inflight.pop(0)
             ctx.wait(sid)
             ctx.burn_prob_device(sid, counts_dev.data_ptr())    # a9 (K4)
+            # a step's result is its counts: the simulation (and the table only it
+            # still holds) is released at once, as a serving caller would, so the
+            # next builds reuse that memory (freed after K4 has read the scars);
+            # the last step is kept for its work counters
+            if done:
+                ctx.release(done.pop())
             done.append(sid)
 
         for _ in range(k):
@@ -475,6 +487,12 @@ def run_ours(args, rank, world, local_rank):
     kt_alone = ctx.kernel_times()
     ctx.profile(False)
     fp64_peak = ctx.fp64_peak()   # outside the timed regions: the table kernel's FP64 roofline
+    trace = None
+    if world == 1 and not args.serial and not args.lazy_tables and args.trace_steps > 0:
+        # outside the timed regions: how K1 and K3 share the device, one step alone
+        # and then pipelined steps (launch trace, c2f_trace)
+        trace = _section(pipeline_trace, ctx, torch, dev, step, run_steps, sms, args.trace_steps,
+                         args.trace_out)
     ctx.release(lid)
     ctx.close()
 
@@ -536,12 +554,99 @@ def run_ours(args, rank, world, local_rank):
             "roofline_table_kernel": roof_k1,
             "clocks": clocks,
             "plain": plain,
+            "pipeline_trace": trace,
             **extras,
         }
         if extras_on and "error" not in extras.get("batched", {}) and "error" not in extras.get("served", {}):
             out["batched_over_plain"] = extras["batched"]["batched_over_plain"]
             out["served_over_plain"] = extras["served"]["capacity"]["served_over_plain"]
     return out
+
+
+def timeline(rec, sms):
+    """Per-build and per-simulation spans of a launch trace (c2f_trace records:
+    kind | SM << 8 | aux << 32, tag, start ns, end ns), the K1 builds' resident
+    CTAs per SM, the replicas resident beside them, and replica durations."""
+    import numpy as np
+    kind = (rec[:, 0] & 0xFF).astype(np.int64)
+    tag = rec[:, 1].astype(np.int64)
+    t0 = rec[:, 2].astype(np.float64)
+    t1 = rec[:, 3].astype(np.float64)
+    base = t0.min()
+    t0 = (t0 - base) / 1e6                      # ms
+    t1 = (t1 - base) / 1e6
+    tab, rep = kind == 1, kind == 2
+    builds = []
+    for tg in np.unique(tag[tab]):
+        m = tab & (tag == tg)
+        builds.append((t0[m].min(), t1[m].max(), float((t1[m] - t0[m]).sum())))
+    builds.sort()
+    sims = []
+    for tg in np.unique(tag[rep]):
+        m = rep & (tag == tg)
+        d = t1[m] - t0[m]
+        sims.append((t0[m].min(), t1[m].max(), float(np.median(d)), float(d.max())))
+    sims.sort()
+    out = {"builds": len(builds), "simulations": len(sims)}
+    if builds:
+        spans = [b[1] - b[0] for b in builds]
+        busy = sum(b[2] for b in builds)
+        out["k1_ms"] = float(np.median(spans))
+        out["k1_ctas_per_sm"] = busy / sum(spans) / sms
+        if len(builds) > 1:
+            out["k1_gap_ms"] = float(np.median([builds[i + 1][0] - builds[i][1] for i in range(len(builds) - 1)]))
+            out["build_period_ms"] = (builds[-1][0] - builds[0][0]) / (len(builds) - 1)
+        # replica-time inside the build windows, per SM
+        inside = 0.0
+        rs, re_ = t0[rep], t1[rep]
+        for b0, b1, _ in builds:
+            inside += float(np.clip(np.minimum(re_, b1) - np.maximum(rs, b0), 0, None).sum())
+        out["replicas_per_sm_during_k1"] = inside / sum(spans) / sms
+    if sims:
+        out["replica_ms_median"] = float(np.median([x[2] for x in sims]))
+        out["replica_ms_max"] = float(max(x[3] for x in sims))
+        out["frontier_span_ms"] = float(np.median([x[1] - x[0] for x in sims]))
+    lines = []
+    for b in builds:
+        lines.append((b[0], f"K1 build   {b[0]:9.3f} .. {b[1]:9.3f} ms  span {b[1] - b[0]:6.3f} ms  "
+                            f"{b[2] / (b[1] - b[0]) / sms:5.2f} CTAs/SM"))
+    for x in sims:
+        lines.append((x[0], f"frontier   {x[0]:9.3f} .. {x[1]:9.3f} ms  span {x[1] - x[0]:6.3f} ms  "
+                            f"replica median {x[2]:6.3f} max {x[3]:6.3f} ms"))
+    return out, [t for _, t in sorted(lines, key=lambda x: x[0])]
+
+
+def pipeline_trace(ctx, torch, dev, step, run_steps, sms, k, out_path):
+    """One step alone, then k pipelined steps, under the launch trace."""
+    import numpy as np
+    cap = 1 << 21
+    buf = torch.empty(cap * 4, dtype=torch.int64, device=dev)
+
+    def traced(fn):
+        torch.cuda.synchronize(dev)
+        ctx.trace(buf.data_ptr(), cap)
+        sids = fn()
+        torch.cuda.synchronize(dev)
+        cnt = ctx.trace_count()
+        ctx.trace(None)
+        for s in sids:
+            ctx.release(s)
+        return buf.view(-1, 4)[:min(cnt, cap)].cpu().numpy().view(np.uint64), cnt
+
+    rec_a, na = traced(lambda: [step()])
+    rec_p, npp = traced(lambda: run_steps(k))
+    alone, lines_a = timeline(rec_a, sms)
+    piped, lines_p = timeline(rec_p, sms)
+    if out_path:
+        with open(out_path, "w") as f:
+            f.write(f"# launch trace: one step alone ({na} records)\n")
+            f.write("\n".join(lines_a) + "\n")
+            f.write(f"# {k} pipelined steps ({npp} records)\n")
+            f.write("\n".join(lines_p) + "\n")
+            f.write(json.dumps({"alone": alone, "pipelined": piped}) + "\n")
+    return {"steps": k, "alone": alone, "pipelined": piped,
+            "note": "c2f_trace records (globaltimer), outside the timed regions: K1 build spans and "
+                    "gaps, resident K1 CTAs and replicas per SM while builds run, replica durations"}
 
 
 def frontier_roofline(kt_alone, w, work_per_step, peaks, sms, sm_mhz):
@@ -1113,6 +1218,9 @@ def main():
                     help="default line: steps of the plain (one synchronous call per step) timing")
     ap.add_argument("--no-extras", action="store_true",
                     help="default line without its batch, request-stream and 4096^2 sections")
+    ap.add_argument("--trace-steps", type=int, default=8,
+                    help="pipelined steps under the launch trace after the timed regions (0: none)")
+    ap.add_argument("--trace-out", default=None, help="write the launch-trace summary to this file")
     args = ap.parse_args()
     world_env = int(os.environ.get("WORLD_SIZE", "1"))
     err = gpus_mismatch(args.gpus, world_env)

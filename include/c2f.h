@@ -430,6 +430,29 @@ C2F_API int c2f_autotune(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
 C2F_API int c2f_profile(c2f_ctx *ctx, int enable);
 C2F_API int c2f_kernel_times(c2f_ctx *ctx, double *ms, int64_t *launches);
 
+/* Launch trace: how the table builds (K1) and the frontier's replicas (K3)
+ * share the device over time, e.g. when steps are pipelined.  With tracing on,
+ * every K1 CTA and every frontier replica that runs appends one record of
+ * four uint64 to records_dev (device memory of the context's device, owned by
+ * the caller, at least 32*capacity bytes):
+ *   [0] kind | SM id << 8 | aux << 32, kind C2F_TRACE_TABLE (aux = weather
+ *       hour of the CTA, which is timed by its first thread) or
+ *       C2F_TRACE_REPLICA (aux = replica index; a replica re-run after a list
+ *       overflow appends again);
+ *   [1] tag: the table's build number / the simulation's creation number,
+ *       both counted from 1 per context;
+ *   [2], [3] start and end, nanoseconds of the GPU's global timer.
+ * Records go in no particular order; once `capacity` are written the rest are
+ * counted but dropped.  c2f_trace waits for the context stream and resets the
+ * count; NULL with capacity 0 turns tracing off (launches already issued keep
+ * their setting).  c2f_trace_count gives the records claimed since, written or
+ * not; call it after the traced work has finished.  Other arguments:
+ * C2F_EINVAL.  The allocation-free entry point does not trace. */
+#define C2F_TRACE_TABLE 1
+#define C2F_TRACE_REPLICA 2
+C2F_API int c2f_trace(c2f_ctx *ctx, uint64_t *records_dev, int64_t capacity);
+C2F_API int c2f_trace_count(c2f_ctx *ctx, int64_t *count);
+
 /* Per-replica frontier profile of a simulation run while C2F_PROFILE_REPLICAS
  * was on (c2f_profile): counters[r*16 + i] for replica r (SM clock cycles, counts),
  * i = 0 cycles of the replica's whole frontier run (its last attempt),
@@ -503,7 +526,11 @@ C2F_API int c2f_frontier_static(const c2f_frontier_io *io, const c2f_sim_params 
  * kernel, which is FP64-bound.  Synchronous. */
 C2F_API int c2f_fp64_peak(c2f_ctx *ctx, double *gflops);
 
-/* Frees a landscape (and its tables) or a simulation result. */
+/* Frees a landscape (and its tables) or a simulation result.  A simulation
+ * may be released right after an asynchronous read of it (c2f_burn_prob_device,
+ * c2f_compare_scars_device): its device memory is returned only after those
+ * reads, in the order of the streams they were issued on.  A running
+ * simulation is cancelled (its epoch keeps it until the epoch ends). */
 C2F_API int c2f_release(c2f_ctx *ctx, int32_t id);
 
 #ifdef __cplusplus

@@ -20,6 +20,7 @@ C2F_OK, C2F_EINVAL, C2F_ENOMEM, C2F_ECUDA, C2F_ETIMEOUT = 0, -1, -2, -3, -4
 C2F_ENOTFOUND, C2F_EBUSY, C2F_ECANCELED = -5, -6, -7
 OUT_SCARS, OUT_IGN_STEPS, OUT_COUNTERS = 1, 2, 8
 PROFILE_KERNELS, PROFILE_REPLICAS = 1, 2
+TRACE_TABLE, TRACE_REPLICA = 1, 2
 _ERR = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ENOTFOUND",
         -6: "EBUSY", -7: "ECANCELED"}
 
@@ -144,6 +145,8 @@ _SIGS = [
     ("c2f_set_compaction", C.c_int, [C.c_void_p, C.c_int32]),
     ("c2f_profile", C.c_int, [C.c_void_p, C.c_int]),
     ("c2f_kernel_times", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("c2f_trace", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    ("c2f_trace_count", C.c_int, [C.c_void_p, _P(C.c_int64)]),
     ("c2f_get_replica_profile", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("c2f_fp64_peak", C.c_int, [C.c_void_p, _P(C.c_double)]),
     ("c2f_release", C.c_int, [C.c_void_p, C.c_int32]),
@@ -440,6 +443,16 @@ class Context:
         g = C.c_double()
         self._check(self.lib.c2f_fp64_peak(self.h, C.byref(g)))
         return g.value
+
+    def trace(self, records_dev_ptr: int | None, capacity: int = 0) -> None:
+        """Launch trace into caller device memory (c2f_trace); None turns it off."""
+        self._check(self.lib.c2f_trace(self.h, C.c_void_p(records_dev_ptr) if records_dev_ptr else None,
+                                       int(capacity)))
+
+    def trace_count(self) -> int:
+        n = C.c_int64()
+        self._check(self.lib.c2f_trace_count(self.h, C.byref(n)))
+        return n.value
 
     def kernel_times(self) -> dict:
         ms = np.zeros(len(KERNEL_FAMILIES), dtype=np.float64)

@@ -245,9 +245,33 @@ __device__ __forceinline__ void row_store(int64_t *row, double *hros_at, const d
   *hros_at = hr;
 }
 
+// nanoseconds of the GPU's global timer
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// one launch-trace record (c2f_trace); records past the capacity are counted, not written
+__device__ __forceinline__ void trace_record(const TraceArgs &tr, uint32_t kind, uint32_t aux, long long tag,
+                                             unsigned long long t0, unsigned long long t1) {
+  const unsigned long long i = atomicAdd(tr.cursor, 1ull);
+  if (i < (unsigned long long)tr.cap) {
+    uint32_t smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    unsigned long long *p = tr.rec + 4 * i;
+    p[0] = (unsigned long long)kind | ((unsigned long long)smid << 8) | ((unsigned long long)aux << 32);
+    p[1] = (unsigned long long)tag;
+    p[2] = t0;
+    p[3] = t1;
+  }
+}
+
 __global__ void __launch_bounds__(128) k_ros_table(RosTableArgs a) {
   const int64_t n = (int64_t)a.rows * a.cols;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool traced = a.trace.rec != nullptr && threadIdx.x == 0;   // thread 0 stands for its CTA
+  const unsigned long long t_start = traced ? global_ns() : 0ull;
   if (t >= n) return;
   const int64_t cell = a.order ? (int64_t)a.order[t] : t;
   const int h = a.hour0 + blockIdx.y;
@@ -273,6 +297,7 @@ __global__ void __launch_bounds__(128) k_ros_table(RosTableArgs a) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) a.ros8[(size_t)cell * 8 + k] = ros[k];
   }
+  if (traced) trace_record(a.trace, kTraceTable, (uint32_t)h, a.trace.tag, t_start, global_ns());
 }
 
 // ------------------------------------------------------------------ K2
@@ -655,6 +680,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
     jidx = __shfl_sync(FULL, jidx, 0);
     __syncwarp();
     if (item < 0) return;
+    const unsigned long long t_start = A.trace.rec ? global_ns() : 0ull;
     const int32_t r = (int32_t)(item - A.item_begin[jidx]);
     const int32_t rows = J.rows, cols = J.cols, wpr = J.wpr;
     const int64_t n = (int64_t)rows * cols;
@@ -1143,6 +1169,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       }
     }
     if (lane == 0) {
+      if (A.trace.rec) trace_record(A.trace, kTraceReplica, (uint32_t)r, J.trace_tag, t_start, global_ns());
       J.work[r] = W;
       J.n_ignited[r] = nign;
       J.status[r] = status;

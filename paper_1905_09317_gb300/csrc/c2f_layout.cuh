@@ -43,6 +43,17 @@ struct HourPrep {
 struct CellPrep { double sf, sin_s, cos_s; };
 
 // One simulation inside a frontier launch (several for a batch).
+// Launch trace (c2f_trace): one record per K1 CTA and per frontier replica,
+// four u64 each: kind | SM id << 8 | aux << 32, tag, start and end in
+// nanoseconds of the global timer.  rec == nullptr: off.
+struct TraceArgs {
+  unsigned long long *rec;      // [cap][4]
+  unsigned long long *cursor;   // records claimed so far (only the first cap are written)
+  long long cap;
+  long long tag;                // K1: the table's build number (frontier jobs carry their own)
+};
+constexpr uint32_t kTraceTable = 1, kTraceReplica = 2;
+
 struct SimJob {
   // landscape
   int32_t rows, cols, wpr;        // wpr: 32-bit words per row of a bit plane
@@ -85,6 +96,7 @@ struct SimJob {
   int32_t *n_ignited;             // [R]
   int32_t *ign_cell;              // [R]
   long long *prof;                // [R][kProfCounters] per-replica profile counters, or nullptr (off)
+  long long trace_tag;            // the simulation's creation number, for trace records
   int32_t *status;                // [R] 0 ok, 1 list capacity exceeded, 2 internal error,
                                   //     3 ignition cell outside the grid or not burnable,
                                   //     4 a bounded wait (for a lazy table chunk) ran out
@@ -110,6 +122,7 @@ struct FrontierArgs {
   uint32_t wait_limit;            // polls before a wait for a table chunk gives up; 0 = default
   int32_t compact_at;             // list entries above which the list is compacted within an
                                   //   hour (0 = three quarters of cap)
+  TraceArgs trace;                // one record per replica when on
 };
 
 // K1 launch arguments: grid.y covers hours hour0 .. hour0 + gridDim.y - 1
@@ -127,6 +140,7 @@ struct RosTableArgs {
   double *hros;            // [hour][N], or nullptr
   double *ros8;            // export: [N][8] of hour0 only, or nullptr
   const int32_t *order;    // cells grouped by (fuel code, sloped); nullptr = identity
+  TraceArgs trace;         // one record per CTA when on
 };
 
 constexpr int kOrderBuckets = 2 * 16;   // (fuel code, slope > 0); code 0 = not burnable

@@ -121,6 +121,7 @@ struct Table {
   DevBuf hour_prep, base, hros, chunk_state;
   bool eager = false;
   bool issued = false;   // its build (K1 or the cleared chunk states) has been issued
+  int64_t serial = 0;    // build number within the context (trace tag)
   cudaEvent_t ready = nullptr;   // recorded after the build; epochs on other streams wait on it
   Table() = default;
   Table(const Table &) = delete;
@@ -155,6 +156,21 @@ struct Sim {
   int state = S_PENDING;
   int rc = C2F_OK;
   bool cancel_requested = false;
+  int64_t serial = 0;   // creation number within the context (trace tag)
+  // asynchronous reads of the buffers on caller streams (burn counts, scar
+  // comparison into device memory), one event per stream: the buffers' frees,
+  // issued on the streams that allocated them, wait for these reads
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> reads;
+  Sim() = default;
+  Sim(const Sim &) = delete;
+  Sim &operator=(const Sim &) = delete;
+  ~Sim() {
+    for (auto &r : reads) {
+      for (DevBuf *b : {&ign_plane, &ign_step, &work, &n_ignited, &ign_cell, &status, &scen, &prof})
+        if (b->p) cudaStreamWaitEvent(b->st, r.second, 0);
+      cudaEventDestroy(r.second);   // released once recorded work completes
+    }
+  }
 };
 
 struct Scratch {
@@ -233,6 +249,11 @@ struct c2f_ctx {
   // kernel timing
   bool profiling = false;          // kernel-family events (C2F_PROFILE_KERNELS)
   bool replica_counters = false;   // per-replica frontier counters (C2F_PROFILE_REPLICAS)
+  // launch trace (c2f_trace): records in caller memory, cursor in the context's
+  unsigned long long *trace_rec = nullptr;
+  int64_t trace_cap = 0;
+  DevBuf trace_cursor;
+  int64_t table_serial = 0, sim_serial = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[C2F_KT_FAMILIES];
   std::vector<cudaEvent_t> event_pool;
 };
@@ -395,6 +416,7 @@ int prepare_table(c2f_ctx *ctx, Landscape &L, const TableKey &k, bool eager) {
   auto T = std::make_shared<Table>();
   T->key = k;
   T->eager = eager;
+  T->serial = ++ctx->table_serial;
   T->n_scen = L.n_scen;
   T->prep_hours = L.n_hours;
   T->weather = L.weather_dev;
@@ -407,6 +429,18 @@ int prepare_table(c2f_ctx *ctx, Landscape &L, const TableKey &k, bool eager) {
     return rc;
   L.table = T;
   return C2F_OK;
+}
+
+// the context's trace setting as launch arguments (off: rec == nullptr)
+TraceArgs trace_args(const c2f_ctx *ctx, int64_t tag) {
+  TraceArgs t{};
+  if (ctx->trace_rec && ctx->trace_cursor.p) {
+    t.rec = ctx->trace_rec;
+    t.cursor = ctx->trace_cursor.as<unsigned long long>();
+    t.cap = ctx->trace_cap;
+    t.tag = tag;
+  }
+  return t;
 }
 
 // K1 over every row of L.table (one launch per weather scenario), then every
@@ -433,6 +467,7 @@ int fill_table(c2f_ctx *ctx, Landscape &L, cudaStream_t st) {
   a.hros = T.hros.as<double>();
   a.ros8 = nullptr;
   a.order = L.order.as<int32_t>();
+  a.trace = trace_args(ctx, T.serial);
   dim3 grid(grid1(L.n, 128), (unsigned)k.hours);
   for (int32_t sc = 0; sc < T.n_scen; ++sc) {
     const size_t rows_off = (size_t)sc * k.hours * (size_t)L.n;
@@ -615,6 +650,7 @@ SimJob job_of(const Sim &s) {
   j.ign_cell = s.ign_cell.as<int32_t>();
   j.status = s.status.as<int32_t>();
   j.prof = s.prof.as<long long>();
+  j.trace_tag = s.serial;
   return j;
 }
 
@@ -703,6 +739,7 @@ int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, i
   A.smem_warp_words = warp_words;
   A.wait_limit = ctx->wait_limit;
   A.compact_at = (int32_t)std::max<int64_t>(1, std::min<int64_t>(cap - 1, cap * ctx->compact_eighths / 8));
+  A.trace = trace_args(ctx, 0);
   F.cap = cap;
   return C2F_OK;
 }
@@ -835,6 +872,7 @@ int make_sims(c2f_ctx *ctx, int32_t n, const int32_t *ids, const c2f_sim_params 
   out.resize(n);
   for (int32_t i = 0; i < n; ++i) {
     auto s = std::make_shared<Sim>();
+    s->serial = ++ctx->sim_serial;
     s->p = params[i];
     s->land = lands[i];
     s->table = lands[i]->table;
@@ -1187,6 +1225,7 @@ C2F_API void c2f_destroy(c2f_ctx *ctx) {
     ctx->sims.clear();
     ctx->lands.clear();
     ctx->scratch.reset();
+    ctx->trace_cursor.reset();
     cudaStreamSynchronize(ctx->stream);
     for (int f = 0; f < C2F_KT_FAMILIES; ++f)
       for (auto &pr : ctx->prof_events[f]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
@@ -1529,6 +1568,20 @@ C2F_API int c2f_cancel(c2f_ctx *ctx, int32_t sim_id) {
 }
 
 // counts over all replicas, or (scen) over those that drew weather scenario `want`
+// an asynchronous read of s's buffers issued on stream st
+static int note_read(c2f_ctx *ctx, Sim &s, cudaStream_t st) {
+  for (auto &r : s.reads)
+    if (r.first == st) {
+      CK(cudaEventRecord(r.second, st));
+      return C2F_OK;
+    }
+  cudaEvent_t e = nullptr;
+  CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  s.reads.emplace_back(st, e);
+  CK(cudaEventRecord(e, st));
+  return C2F_OK;
+}
+
 static int burn_prob_into(c2f_ctx *ctx, Sim &s, uint32_t *dst, cudaStream_t st,
                           const int32_t *scen = nullptr, int32_t want = 0) {
   const int32_t R = s.p.n_replicas;
@@ -1592,7 +1645,8 @@ C2F_API int c2f_burn_prob_device(c2f_ctx *ctx, int32_t sim_id, uint32_t *counts_
   int rc = sim_ready(ctx, *s);
   if (rc) return rc;
   CK(cudaSetDevice(ctx->device));
-  return burn_prob_into(ctx, *s, counts_dev, ctx->stream);
+  if ((rc = burn_prob_into(ctx, *s, counts_dev, ctx->stream))) return rc;
+  return note_read(ctx, *s, ctx->stream);
 }
 
 C2F_API int c2f_get_scars(c2f_ctx *ctx, int32_t sim_id, uint8_t *scars, int32_t *ign_step) {
@@ -1729,7 +1783,8 @@ int compare_launch(c2f_ctx *ctx, int32_t sim_x, int32_t sim_y, double *mse, doub
                                        (int64_t)X->rows * X->wpr, dnorm);
     CKL("k_compare_final");
   }
-  return C2F_OK;
+  if ((rc = note_read(ctx, *X, st))) return rc;
+  return note_read(ctx, *Y, st);
 }
 
 }  // namespace
@@ -2039,6 +2094,38 @@ C2F_API int c2f_profile(c2f_ctx *ctx, int enable) {
   LOCK;
   ctx->profiling = (enable & C2F_PROFILE_KERNELS) != 0;
   ctx->replica_counters = (enable & C2F_PROFILE_REPLICAS) != 0;
+  return C2F_OK;
+}
+
+C2F_API int c2f_trace(c2f_ctx *ctx, uint64_t *records_dev, int64_t capacity) {
+  if (!ctx) return C2F_EINVAL;
+  LOCK;
+  if (records_dev && capacity <= 0) return fail(ctx, C2F_EINVAL, "trace capacity must be positive");
+  if (!records_dev && capacity != 0) return fail(ctx, C2F_EINVAL, "no trace buffer but a capacity");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (records_dev) {
+    int rc;
+    // the cursor lives on the context's own stream, which outlives any caller stream
+    if (!ctx->trace_cursor.p && (rc = dalloc_on(ctx, ctx->trace_cursor, 8, ctx->own_stream))) return rc;
+    CK(cudaMemsetAsync(ctx->trace_cursor.p, 0, 8, ctx->own_stream));
+    CK(cudaStreamSynchronize(ctx->own_stream));
+  }
+  ctx->trace_rec = reinterpret_cast<unsigned long long *>(records_dev);
+  ctx->trace_cap = records_dev ? capacity : 0;
+  return C2F_OK;
+}
+
+C2F_API int c2f_trace_count(c2f_ctx *ctx, int64_t *count) {
+  if (!ctx || !count) return C2F_EINVAL;
+  LOCK;
+  *count = 0;
+  if (!ctx->trace_cursor.p) return C2F_OK;
+  CK(cudaSetDevice(ctx->device));
+  unsigned long long v = 0;
+  CK(cudaMemcpyAsync(&v, ctx->trace_cursor.p, 8, cudaMemcpyDeviceToHost, ctx->read_stream));
+  CK(cudaStreamSynchronize(ctx->read_stream));
+  *count = (int64_t)v;
   return C2F_OK;
 }
 

@@ -46,3 +46,30 @@ def test_gpus_must_match_the_launched_processes():
                          capture_output=True, text=True, timeout=300, cwd=ROOT,
                          env={k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK")})
     assert out.returncode == 2 and "--gpus 2" in out.stderr and not out.stdout.strip()
+
+
+def test_timeline_summary_of_trace_records():
+    """bench.timeline on hand-made c2f_trace records: two builds of 2 CTAs on a
+    2-SM device, each followed by a simulation of two replicas."""
+    ms = 1_000_000   # ns
+
+    def rec(kind, sm, aux, tag, t0, t1):
+        return [kind | (sm << 8) | (aux << 32), tag, int(t0 * ms), int(t1 * ms)]
+
+    r = np.array([
+        rec(1, 0, 0, 1, 0.0, 2.0), rec(1, 1, 0, 1, 0.0, 1.0),          # build 1: 0..2 ms, 3 CTA-ms
+        rec(2, 0, 0, 1, 2.0, 5.0), rec(2, 1, 1, 1, 2.0, 4.0),          # sim 1 replicas: 3 and 2 ms
+        rec(1, 0, 0, 2, 3.0, 4.0), rec(1, 1, 0, 2, 3.0, 4.0),          # build 2: 3..4 ms, 2 CTA-ms
+        rec(2, 0, 0, 2, 4.0, 8.0), rec(2, 1, 1, 2, 4.0, 5.0),          # sim 2 replicas: 4 and 1 ms
+    ], dtype=np.uint64)
+    out, lines = bench.timeline(r, sms=2)
+    assert out["builds"] == 2 and out["simulations"] == 2
+    assert out["k1_ms"] == 1.5                                         # median of spans 2 and 1
+    assert abs(out["k1_ctas_per_sm"] - (3 + 2) / (2 + 1) / 2) < 1e-12
+    assert out["k1_gap_ms"] == 1.0 and out["build_period_ms"] == 3.0
+    # replica time inside the build windows: build 2 (3..4 ms) overlaps both of sim 1's
+    # replicas (2..5 and 2..4 ms) for 1 ms each; build 1 (0..2 ms) overlaps none
+    assert abs(out["replicas_per_sm_during_k1"] - 2.0 / 3.0 / 2) < 1e-12
+    assert out["replica_ms_median"] == 2.5 and out["replica_ms_max"] == 4.0
+    assert out["frontier_span_ms"] == 3.5                              # spans 3 and 4
+    assert len(lines) == 4 and lines[0].startswith("K1 build")

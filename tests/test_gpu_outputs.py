@@ -111,3 +111,52 @@ def test_last_error_is_per_thread():
         t.join()
         assert "unknown landscape" in msgs["worker_after"]
         assert lib.c2f_last_error(ctx.h).decode() == mine and "fuel code" in mine
+
+
+def test_release_right_after_asynchronous_reads():
+    """Burn counts into device memory on a caller stream, the simulation released
+    at once, and new simulations (whose allocations may reuse the freed memory)
+    submitted on the context's epoch streams while the counts are being read: every
+    step's counts equal a clean run's.  The same with the scar comparison."""
+    torch = pytest.importorskip("torch")
+    c2f.build()
+    w = S.config2(side=192, n_replicas=200, hours=6)
+    L = w.landscape
+    n = L.fuel.size
+    p = _params(**w.params)
+    with c2f.Context(0) as ctx:
+        lid = ctx.load_landscape(L.fuel, L.slope, L.aspect, cell_size=L.cell_size)
+        ctx.set_weather(lid, w.weather)
+        sid = ctx.simulate(lid, p)
+        ref = ctx.burn_prob(sid, n)
+        ctx.release(sid)
+        stream = torch.cuda.Stream()
+        ctx.set_stream(stream.cuda_stream)
+        ctx.set_serving(max_inflight=3, max_epoch_replicas=p.n_replicas, hbm_reserve_bytes=0)
+        outs = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(12)]
+        pending = [ctx.submit(lid, p)]
+        for i in range(12):
+            pending.append(ctx.submit(lid, p))          # more work, more allocations
+            sid = pending.pop(0)
+            ctx.wait(sid)
+            ctx.burn_prob_device(sid, outs[i].data_ptr())
+            ctx.release(sid)                             # K4 may still be reading its scars
+        for sid in pending:
+            ctx.wait(sid)
+            ctx.release(sid)
+        torch.cuda.synchronize()
+        for i, o in enumerate(outs):
+            assert np.array_equal(o.cpu().numpy().view(np.uint32), ref), i
+        # the scar comparison into device memory, both simulations released at once
+        a, b = ctx.submit(lid, p), ctx.submit(lid, p)
+        ctx.wait(a)
+        ctx.wait(b)
+        dn = torch.full((p.n_replicas,), -1.0, dtype=torch.float64, device="cuda")
+        ctx.compare_scars_device(a, b, 0, 0, dn.data_ptr())
+        ctx.release(a)
+        ctx.release(b)
+        c = ctx.submit(lid, p)
+        ctx.wait(c)
+        torch.cuda.synchronize()
+        assert np.all(dn.cpu().numpy() == 0.0)          # identical runs
+        ctx.release(c)
