@@ -96,3 +96,50 @@ def test_trace_records_every_table_cta_and_replica():
         assert ctx.trace_count() == before
         assert ctx.lib.c2f_trace(ctx.h, C.c_void_p(buf.data_ptr()), 0) == c2f.C2F_EINVAL
         assert ctx.lib.c2f_trace(ctx.h, None, 5) == c2f.C2F_EINVAL
+
+
+def test_trace_covers_batched_and_served_simulations():
+    """A batch of two landscapes (one CUDA graph) and two served requests: every
+    table build and every replica is recorded once, one tag per simulation."""
+    torch = pytest.importorskip("torch")
+    c2f.build()
+    wa = S.config2(side=96, n_replicas=24, hours=2)
+    wb = S.config2(side=130, n_replicas=16, hours=3)
+    pa, pb = _params(wa), _params(wb)
+    with c2f.Context(0) as ctx:
+        lids = []
+        for w in (wa, wb):
+            L = w.landscape
+            lid = ctx.load_landscape(L.fuel, L.slope, L.aspect, cell_size=L.cell_size)
+            ctx.set_weather(lid, w.weather)
+            lids.append(lid)
+        cap = 20_000
+        buf = torch.full((cap * 4,), -1, dtype=torch.int64, device="cuda")
+        ctx.trace(buf.data_ptr(), cap)
+        sids = ctx.simulate_batch(lids, [pa, pb])
+        cnt = ctx.trace_count()
+        na, nb = wa.landscape.fuel.size, wb.landscape.fuel.size
+        blocks = (-(-na // 128)) * pa.hours + (-(-nb // 128)) * pb.hours
+        assert cnt == blocks + pa.n_replicas + pb.n_replicas
+        kind, _, aux, tag, t0, t1 = _records(buf, cnt)
+        rep = kind == c2f.TRACE_REPLICA
+        tags = np.unique(tag[rep])
+        assert tags.size == 2
+        assert sorted(np.bincount(np.searchsorted(tags, tag[rep]))) == sorted([pa.n_replicas, pb.n_replicas])
+        assert np.unique(tag[kind == c2f.TRACE_TABLE]).size == 2 and np.all(t1 >= t0)
+        for s in sids:
+            ctx.release(s)
+
+        # served: the tables are built, so only replicas are recorded
+        ctx.trace(buf.data_ptr(), cap)
+        ctx.set_serving(max_inflight=2)
+        s1, s2 = ctx.submit(lids[0], pa), ctx.submit(lids[1], pb)
+        ctx.wait(s1)
+        ctx.wait(s2)
+        cnt = ctx.trace_count()
+        assert cnt == pa.n_replicas + pb.n_replicas
+        kind, _, aux, tag, _, _ = _records(buf, cnt)
+        assert np.all(kind == c2f.TRACE_REPLICA) and np.unique(tag).size == 2
+        ctx.trace(None)
+        ctx.release(s1)
+        ctx.release(s2)
