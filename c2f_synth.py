@@ -227,3 +227,26 @@ def random_small_case(seed, max_side=24):
     if rng.random() < 0.3:
         land.unburnable = (rng.random(land.fuel.shape) < 0.1).astype(np.uint8)
     return Workload(land, weather, params)
+
+
+def digest(*arrays) -> str:
+    """sha256 over arrays' dtype, shape and bytes (None counts as absent): a
+    checksum of generated inputs, for the manifest in tests/golden."""
+    import hashlib
+    h = hashlib.sha256()
+    for a in arrays:
+        if a is None:
+            h.update(b"none")
+            continue
+        a = np.ascontiguousarray(a)
+        h.update(str(a.dtype).encode() + str(a.shape).encode())
+        h.update(a.tobytes())
+    return h.hexdigest()
+
+
+def workload_digest(w: Workload) -> dict:
+    """Checksums of one workload's arrays and its parameters."""
+    L = w.landscape
+    return {"fuel": digest(L.fuel), "slope": digest(L.slope), "aspect": digest(L.aspect),
+            "unburnable": digest(L.unburnable), "weather": digest(w.weather),
+            "cell_size": L.cell_size, "params": {k: w.params[k] for k in sorted(w.params)}}
