@@ -413,9 +413,10 @@ C2F_API int c2f_autotune(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
 
 /* Profiling switches, flags of c2f_profile's `enable` (0 turns both off; other
  * bits give C2F_EINVAL).  C2F_PROFILE_KERNELS: kernel timing as below.
- * C2F_PROFILE_REPLICAS: per-replica frontier counters (c2f_get_replica_profile);
- * they cost the frontier a few clock reads and shared-memory adds per visited
- * period, so a timing run should leave them off.  Either switch makes
+ * C2F_PROFILE_REPLICAS: per-replica frontier counters (c2f_get_replica_profile),
+ * recorded by a profiling build of the frontier kernel (one-warp CTAs, the
+ * counter code compiled in: a few clock reads and shared-memory adds per
+ * visited period), so a timing run should leave them off.  Either switch makes
  * c2f_simulate_batch launch its groups directly instead of through a graph. */
 #define C2F_PROFILE_KERNELS 1
 #define C2F_PROFILE_REPLICAS 2

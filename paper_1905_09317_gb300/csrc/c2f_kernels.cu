@@ -609,7 +609,7 @@ __device__ __forceinline__ uint32_t axes_at(uint64_t c8, uint32_t o) {
 // one lane per cell, the 8 axes of a cell as independent chains in its lane:
 // at the hour boundary (every listed cell) and for the cells ignited in a
 // visited period.
-template <int WPC, bool WIN, bool LAZY>
+template <int WPC, bool WIN, bool LAZY, bool PROF>
 __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
   // list links: 16 bits in shared memory (capacities there stay far below 2^16)
   using Link = typename std::conditional<WIN, uint16_t, int32_t>::type;
@@ -650,7 +650,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
   __shared__ int32_t s_head[WPC][64];                  // calendar: first entry per offset
   __shared__ uint32_t s_dbits[WPC][LAZY ? kWinRows * kWinWords / 32 : 1];   // chunks known done this hour
   __shared__ int32_t s_claim[WPC][LAZY ? 32 : 1];
-  __shared__ long long s_prof[WPC][kProfCounters];
+  __shared__ long long s_prof[WPC][PROF ? kProfCounters : 1];
   int32_t *hitbuf = s_hits[wib];
   int32_t *head = s_head[wib];
   uint32_t *dbits = s_dbits[wib];
@@ -740,7 +740,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
     // (A) spent walking the period's calendar list, compactions within an
     // hour, rounds of crossing entries, new-cell passes (32 cells each)
     // (kept in shared memory, lane 0 only, so that they cost no registers)
-    const bool prof = J.prof != nullptr;
+    const bool prof = PROF && J.prof != nullptr;   // compiled out of the production kernels
     long long pc_t = 0;
     long long *pq = s_prof[wib];
     if (prof && lane == 0) {
@@ -1185,21 +1185,27 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
 }
 
 // Variants: warps per CTA (1, 2, 4); planes windowed and lists in shared
-// memory (w), or everything in global memory (g); l: tables filled on demand.
+// memory (w), or everything in global memory (g); l: tables filled on demand;
+// p: the per-replica profile counters compiled in (one-warp CTAs; the
+// production kernels leave that code out, which makes them about 4 % faster).
 // Register budgets: one-warp CTAs sized so that 11 fit on an SM (the
 // pipelined steps run the next table build beside the frontier, which more
 // registers a thread would crowd out; fewer would spill); two-warp CTAs so
 // that 5 fit
-__global__ void __launch_bounds__(32, 11) k_frontier_g1(FrontierArgs A) { frontier_warp<1, false, false>(A); }
-__global__ void __launch_bounds__(64, 5) k_frontier_g2(FrontierArgs A) { frontier_warp<2, false, false>(A); }
-__global__ void __launch_bounds__(128) k_frontier_g4(FrontierArgs A) { frontier_warp<4, false, false>(A); }
-__global__ void __launch_bounds__(32, 11) k_frontier_w1(FrontierArgs A) { frontier_warp<1, true, false>(A); }
-__global__ void __launch_bounds__(64, 5) k_frontier_w2(FrontierArgs A) { frontier_warp<2, true, false>(A); }
-__global__ void __launch_bounds__(128) k_frontier_w4(FrontierArgs A) { frontier_warp<4, true, false>(A); }
+__global__ void __launch_bounds__(32, 11) k_frontier_g1(FrontierArgs A) { frontier_warp<1, false, false, false>(A); }
+__global__ void __launch_bounds__(64, 5) k_frontier_g2(FrontierArgs A) { frontier_warp<2, false, false, false>(A); }
+__global__ void __launch_bounds__(128) k_frontier_g4(FrontierArgs A) { frontier_warp<4, false, false, false>(A); }
+__global__ void __launch_bounds__(32, 11) k_frontier_w1(FrontierArgs A) { frontier_warp<1, true, false, false>(A); }
+__global__ void __launch_bounds__(64, 5) k_frontier_w2(FrontierArgs A) { frontier_warp<2, true, false, false>(A); }
+__global__ void __launch_bounds__(128) k_frontier_w4(FrontierArgs A) { frontier_warp<4, true, false, false>(A); }
+__global__ void __launch_bounds__(32, 11) k_frontier_pg1(FrontierArgs A) { frontier_warp<1, false, false, true>(A); }
+__global__ void __launch_bounds__(32, 11) k_frontier_pw1(FrontierArgs A) { frontier_warp<1, true, false, true>(A); }
 // on-demand table rows: one warp per CTA; the FBP code inlined into the
 // frontier needs the whole register budget of a one-warp CTA
-__global__ void __launch_bounds__(32, 1) k_frontier_lg1(FrontierArgs A) { frontier_warp<1, false, true>(A); }
-__global__ void __launch_bounds__(32, 1) k_frontier_lw1(FrontierArgs A) { frontier_warp<1, true, true>(A); }
+__global__ void __launch_bounds__(32, 1) k_frontier_lg1(FrontierArgs A) { frontier_warp<1, false, true, false>(A); }
+__global__ void __launch_bounds__(32, 1) k_frontier_lw1(FrontierArgs A) { frontier_warp<1, true, true, false>(A); }
+__global__ void __launch_bounds__(32, 1) k_frontier_plg1(FrontierArgs A) { frontier_warp<1, false, true, true>(A); }
+__global__ void __launch_bounds__(32, 1) k_frontier_plw1(FrontierArgs A) { frontier_warp<1, true, true, true>(A); }
 
 // ------------------------------------------------------------------ K4
 // counts[c] = sum over replicas of the scar bit of c.  Each thread owns one

@@ -61,6 +61,10 @@ __global__ void k_frontier_w2(FrontierArgs);
 __global__ void k_frontier_w4(FrontierArgs);
 __global__ void k_frontier_lg1(FrontierArgs);
 __global__ void k_frontier_lw1(FrontierArgs);
+__global__ void k_frontier_pg1(FrontierArgs);
+__global__ void k_frontier_pw1(FrontierArgs);
+__global__ void k_frontier_plg1(FrontierArgs);
+__global__ void k_frontier_plw1(FrontierArgs);
 __global__ void k_burn_prob(const uint32_t *, int32_t, int32_t, int32_t, int32_t, int32_t,
                             uint32_t *, int32_t, const int32_t *, int32_t);
 __global__ void k_scar_bytes(const uint32_t *, int32_t, int32_t, int32_t, int32_t, uint8_t *);
@@ -673,7 +677,9 @@ int64_t replica_cost(const Landscape &L, const Sim &s) {
 int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, int64_t todo,
                    int64_t cap_in, int attempt) {
   int rc;
-  const int threads = F.lazy ? 32 : ctx->frontier_threads;   // 32, 64 or 128: one replica per warp
+  // 32, 64 or 128: one replica per warp; the profiling kernels (per-replica
+  // counters) are one-warp CTAs
+  const int threads = (F.lazy || ctx->replica_counters) ? 32 : ctx->frontier_threads;
   const int wpc = threads / 32;
   int64_t cap = (cap_in + 3) & ~int64_t(3);
   int64_t win_cap = cap;
@@ -705,6 +711,8 @@ int shape_frontier(c2f_ctx *ctx, FrontierPlan &F, Scratch &S, cudaStream_t st, i
   F.kern = use_win ? (wpc == 1 ? k_frontier_w1 : wpc == 2 ? k_frontier_w2 : k_frontier_w4)
                    : (wpc == 1 ? k_frontier_g1 : wpc == 2 ? k_frontier_g2 : k_frontier_g4);
   if (F.lazy) F.kern = use_win ? k_frontier_lw1 : k_frontier_lg1;
+  if (ctx->replica_counters)
+    F.kern = F.lazy ? (use_win ? k_frontier_plw1 : k_frontier_plg1) : (use_win ? k_frontier_pw1 : k_frontier_pg1);
   F.dyn_smem = (size_t)warp_words * 4 * wpc;
   F.threads = threads;
   if (F.dyn_smem > 0) {   // only ever raised: plans made earlier may still be launched
