@@ -352,8 +352,14 @@ __device__ __forceinline__ int32_t ceil_div_small(int64_t rem, int64_t inc) {
   return n + 1;
 }
 
+// The frontier's two binary64 tests are kept out of line: inlined, the
+// compiler issues their FP64 instructions (predicated off) in every round and
+// set-up pass even when no threshold or delta is set, and each of them waits
+// for the FP64 pipe, which a table build running beside the frontier keeps
+// busy.  Called only when a threshold (receive) or a delta (burn-out) is set.
+
 // receive test of a messaged Available cell (Sec. 3.1): HROS * f > threshold
-__device__ inline bool receive_ok(const SimJob &J, int32_t r, int64_t j, int32_t h, int64_t n) {
+__device__ __noinline__ bool receive_ok(const SimJob &J, int32_t r, int64_t j, int32_t h, int64_t n) {
   if (J.thr < 0.0) return true;
   const double hr = __ldcg(J.hros + (size_t)h * n + j);
   if (J.thr == 0.0) {
@@ -362,6 +368,11 @@ __device__ inline bool receive_ok(const SimJob &J, int32_t r, int64_t j, int32_t
   }
   const float f = noise_factor(J.seed, (uint32_t)r, (uint32_t)j, (uint32_t)h, J.sigma);
   return __dmul_rn(hr, (double)f) > J.thr;
+}
+
+// A5 (i): the cell's HROS * f this hour is below delta
+__device__ __noinline__ bool below_delta(const double *hrosh, int64_t cell, float f, double delta) {
+  return __dmul_rn(__ldcg(hrosh + cell), (double)f) < delta;
 }
 
 __device__ __forceinline__ int64_t find_job(const int64_t *begin, int32_t n, int64_t item) {
@@ -694,6 +705,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
     }
     const bool lazy = LAZY && J.chunk_state != nullptr;
     const double delta = J.delta;
+    const bool use_delta = delta > 0.0;   // A5 (i) burn-out on
     const uint64_t seed = J.seed;
     const float sigma = J.sigma;
     const uint32_t *burnable = J.burnable;
@@ -941,7 +953,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           const uint64_t F = noise_fixed(f);
           // A5 (i): a cell whose HROS * f is below delta still sends in the
           // first period of the hour and is Burned after it
-          const bool dies = keep && delta > 0.0 && __dmul_rn(__ldcg(hrosh + cell), (double)f) < delta;
+          const bool dies = keep && use_delta && below_delta(hrosh, cell, f, delta);
           uint64_t c8 = ~0ull;   // crossing-offset bytes
           const uint32_t am = keep ? (m & pl.avail_mask(rows, cols, cr, cc)) : 0u;   // open axes toward Available cells
 #pragma unroll
@@ -1116,8 +1128,8 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
           const uint32_t omask = group_bits(open);
           uint32_t mask = omask;
           bool dies = false;
-          if (act && delta > 0.0) {
-            if (__dmul_rn(__ldcg(hrosh + cell), (double)f) < delta) { dies = true; mask = 0; }   // A5 (i)
+          if (act && use_delta) {
+            if (below_delta(hrosh, cell, f, delta)) { dies = true; mask = 0; }   // A5 (i)
           }
           uint32_t cof = ((mask >> k) & 1u) ? kOpen : kNone;
           int64_t P = 0;
