@@ -19,9 +19,9 @@ The same JSON line also carries, each with its own timing and clock record:
            throughput and p50/p99 latency, and a capacity comparison with the
            first requests all waiting (served vs one synchronous call each);
   large    4096^2 cells, 72 h with a 90-degree wind shift, 256 replicas.
-Their inputs are generated in spawned host processes at the lowest CPU
-priority, started after the headline and e2e timed regions (so that the
-thread issuing the pipelined steps has the host to itself while they run).
+Their inputs are generated in spawned host processes once the headline
+workload's timings are done, and all of them before the first section is
+timed: the thread that issues GPU work must not wait for a host core.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs its own 1000 replicas (replica ids offset by
@@ -270,8 +270,8 @@ def _gen_serve_land(side, seed):
 
 
 def _low_priority():
-    """(spawned process initializer) the lowest CPU priority: the thread that
-    issues GPU work keeps its core when the host is busy."""
+    """(spawned process initializer) the lowest CPU priority, so that the thread
+    that issues GPU work keeps its core when the host is busy."""
     try:
         os.nice(19)
     except OSError:
@@ -280,13 +280,15 @@ def _low_priority():
 
 class WorkloadPool:
     """The batch, request-stream and 4096^2 inputs, generated in spawned
-    processes (host numpy only, lowest priority, two cores left free) while
-    the GPU runs the plain steps and the launch trace."""
+    processes (host numpy only, one thread each, lowest priority, two cores
+    left free)."""
 
     def __init__(self, serve_rate, serve_window):
         import concurrent.futures as cf
         import multiprocessing as mp
         workers = max(1, min(16, (os.cpu_count() or 1) - 2))
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(v, "1")   # one thread per generating process
         self.ex = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"),
                                          initializer=_low_priority)
         self.f_large = self.ex.submit(_gen_large)
@@ -473,12 +475,6 @@ def run_ours(args, rank, world, local_rank):
                    h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(host_counts.nbytes),
                    steps=e2e_steps)
 
-    # the extra sections' inputs: generated on the host cores from here on, while
-    # the GPU runs the plain steps and the trace (after the pipelined timings,
-    # whose host thread must not wait for a core)
-    if extras_on:
-        pool = WorkloadPool(args.rate, args.serve_window)
-
     # plain: the same step as one synchronous c2f_simulate at a time (one
     # request per launch, nothing overlapped), timed with CUDA events; then a
     # few such steps with per-kernel events: each kernel's duration when it runs
@@ -513,6 +509,15 @@ def run_ours(args, rank, world, local_rank):
     ctx.release(lid)
     ctx.close()
 
+    # the extra sections' inputs: generated on the host cores only now, after every
+    # timing of the headline workload (the thread that issues its steps must not
+    # wait for a core), and all of them before the first section is timed
+    sections_in = None
+    if extras_on and rank == 0:
+        pool = WorkloadPool(args.rate, args.serve_window)
+        sections_in = (pool.batch(), pool.serve(), pool.large())
+        pool.close()
+
     out = None
     if rank == 0:
         value = whole_job_rate(work_per_step, world, args.steps, ms_max / 1e3)
@@ -532,10 +537,10 @@ def run_ours(args, rank, world, local_rank):
         launches = int(sum(v[1] for v in kt.values()))   # every kernel of the timed steps
         extras = {}
         if extras_on:
-            extras["batched"] = _section(batch_measure, args, pool.batch(), pool.specs, 2, 1, local_rank)
-            extras["served"] = _section(serve_measure, args, *pool.serve(), local_rank)
-            extras["large"] = _section(large_measure, args, pool.large(), 2, local_rank)
-            pool.close()
+            batch_in, serve_in, large_in = sections_in
+            extras["batched"] = _section(batch_measure, args, batch_in, pool.specs, 2, 1, local_rank)
+            extras["served"] = _section(serve_measure, args, *serve_in, local_rank)
+            extras["large"] = _section(large_measure, args, large_in, 2, local_rank)
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             procs = os.cpu_count() or 1

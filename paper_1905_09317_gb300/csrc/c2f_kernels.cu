@@ -903,8 +903,7 @@ __device__ __forceinline__ void frontier_warp(const FrontierArgs &A) {
       const double *hrosh = J.hros + (size_t)h * n;
       // receive tests can be skipped when the threshold is 0 and every HROS of
       // the hour is positive (then HROS * f > 0), or when the threshold is < 0
-      const bool gate_free = (J.thr < 0.0) ||
-                             (J.thr == 0.0 && (J.const_ros > 0.0 || (J.hour && J.hour[h].pos)));
+      const bool gate_free = J.recv_gate <= 1 || (J.recv_gate == 2 && J.hour && J.hour[h].pos);
       int32_t burned = 0;   // cells Burned at the end of the period being visited
       if (lazy) {
         for (int32_t i = lane; i < kWinRows * kWinWords / 32; i += 32) dbits[i] = 0u;

@@ -85,6 +85,7 @@ struct SimJob {
   float sigma;
   int32_t ignition_mode, ignition_cell;
   double thr, delta;
+  int32_t recv_gate;              // receive_gate(thr, const_ros): when receive tests are needed
   int32_t sph, hours;             // fire periods per hour, simulated hours
   int32_t burn_min, burn_max;     // burning hours per day {min..max}; 0, 0: no limit
   int64_t d_orth, d_diag;         // axis lengths in fixed point
@@ -142,6 +143,18 @@ struct RosTableArgs {
   const int32_t *order;    // cells grouped by (fuel code, sloped); nullptr = identity
   TraceArgs trace;         // one record per CTA when on
 };
+
+// When the frontier needs the receive test of Sec. 3.1 (HROS * f > threshold),
+// decided on the host from the threshold and the constant-ROS setting so that
+// the frontier's loops hold no binary64 compare: 0 never (threshold < 0: every
+// message to an Available cell ignites it), 1 never (threshold 0 with a
+// positive constant ROS), 2 only in hours whose lower bound on every fuel's
+// HROS is not positive (threshold 0), 3 always (threshold > 0, or NaN)
+inline int32_t receive_gate(double thr, double const_ros) {
+  if (thr < 0.0) return 0;
+  if (thr == 0.0) return const_ros > 0.0 ? 1 : 2;
+  return 3;
+}
 
 constexpr int kOrderBuckets = 2 * 16;   // (fuel code, slope > 0); code 0 = not burnable
 

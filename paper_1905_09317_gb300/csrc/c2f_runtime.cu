@@ -640,6 +640,7 @@ SimJob job_of(const Sim &s) {
   j.ignition_cell = s.p.ignition_cell;
   j.thr = s.p.ros_threshold;
   j.delta = s.p.burnout_delta;
+  j.recv_gate = receive_gate(j.thr, j.const_ros);
   j.sph = 60 / s.p.minutes_per_step;
   j.hours = s.p.hours;
   j.burn_min = s.p.burn_hours_min;

@@ -138,6 +138,7 @@ extern "C" C2F_API int c2f_frontier_static(const c2f_frontier_io *io, const c2f_
   job.ignition_mode = 0;
   job.thr = p->ros_threshold;
   job.delta = p->burnout_delta;
+  job.recv_gate = receive_gate(job.thr, job.const_ros);
   job.sph = 60 / p->minutes_per_step;
   job.hours = p->hours;
   job.burn_min = p->burn_hours_min;   // A5 general condition (1), as in c2f_simulate
