@@ -731,8 +731,8 @@ def roofline_table(kt, w, fp64_peak):
 # flops per cell-hour (2 x DFMA + DMUL + DADD from ncu's instruction counts over
 # cells x hours).  FP64 peak: 152 SMs x 2 DFMA per clock x 2 flop x 2.07 GHz.
 FRONTIER_BYTES_PER_UPDATE = 194.0
-FRONTIER_DRAM_BYTES_PER_REPLICA = (96.547e6 + 14.949e6) / 200   # 200-replica launch: read + write
-FRONTIER_WARP_INST_PER_UPDATE = 218.406e6 / 43484764             # warp instructions / cell-updates
+FRONTIER_DRAM_BYTES_PER_REPLICA = (96.998e6 + 14.878e6) / 200   # 200-replica launch: read + write
+FRONTIER_WARP_INST_PER_UPDATE = 214.105e6 / 43484764             # warp instructions / cell-updates
 FRONTIER_PROFILE_NOTE = "ncu dram__bytes_read+write and smsp__inst_executed of a 200-replica launch, " \
                         "scaled by replicas / cell-updates"
 FP64_OPS_PER_CELL_HOUR = 364.0      # ncu: (2 x DFMA + DMUL + DADD) / (cells x hours)
