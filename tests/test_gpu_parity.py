@@ -171,6 +171,29 @@ def test_edges_corners_and_strips(ctx):
         compare_replicas(w, g, range(3))
 
 
+def test_maximum_side_strips(ctx):
+    """Strips at the largest side the boundary accepts (65,535 cells): cell ids,
+    packed (row, col) coordinates and plane words at their limits, with most of
+    the grid outside the shared-memory window of the bit planes, which the fire
+    leaves; ignition in the last row or column.  A side of 65,536 is rejected."""
+    # wind from the far end of each strip (east of the row strip, south of the
+    # column strip): the head fire runs back along it from its last cells
+    for rows, cols, cell, wd_from in [(3, 65535, 2 * 65535 - 1, 90.0), (65535, 3, 3 * 65535 - 2, 180.0)]:
+        fuel = np.full((rows, cols), 2, np.uint8)           # C2
+        zeros = np.zeros_like(fuel, np.float32)
+        w = S.Workload(S.Landscape(fuel, zeros, zeros),
+                       S.constant_weather(12, ws=30.0, wd_from=wd_from, ffmc=93.0, bui=100.0),
+                       dict(hours=12, ignition_cell=cell, ros_sigma=0.1, seed=13))
+        g = run_gpu(ctx, w, n_replicas=2)
+        # the fire runs about 300 cells along the strip: past the 256-cell window
+        assert g["n_ignited"].min() > 800
+        compare_replicas(w, g, range(2))
+    for shape in [(1, 65536), (65536, 1)]:
+        with pytest.raises(c2f.C2FError) as e:
+            ctx.load_landscape(np.full(shape, 2, np.uint8))
+        assert e.value.code == c2f.C2F_EINVAL
+
+
 def test_clock_lengths_and_options(ctx):
     w = S.config2(side=48, n_replicas=24, hours=4)
     for over in (dict(minutes_per_step=60), dict(minutes_per_step=5), dict(ros_threshold=3.0),
