@@ -118,11 +118,13 @@ def test_config1_full(ctx):
 
 
 @pytest.mark.parametrize("name", ["hand_3x3.txt", "hand_5x5.txt", "hand_wind_eq1_5x5.txt",
-                                  "hand_wind_ray_5x5.txt"])
+                                  "hand_wind_ray_5x5.txt", "hand_delta_5x5.txt",
+                                  "hand_threshold_5x5.txt"])
 def test_hand_enumeration(ctx, name):
     """Ignition steps and work count of hand-enumerated grids: constant rates
-    on all axes, and an ellipse (H, B, LB) under wind by Eq. (1) and by the
-    ray of ellipse_mode 1 (tests/golden/)."""
+    on all axes, an ellipse (H, B, LB) under wind by Eq. (1) and by the ray of
+    ellipse_mode 1, burn-out below delta and rejected messages under a receive
+    threshold (tests/golden/)."""
     from conftest import read_golden_grid
     meta, grid = read_golden_grid(name)
     gr = np.array(grid)
@@ -135,10 +137,13 @@ def test_hand_enumeration(ctx, name):
                         const_ros=float(meta["const_ros"]),
                         const_bros=float(meta.get("const_bros", 0.0)),
                         const_lb=float(meta.get("const_lb", 0.0)),
-                        ellipse_mode=int(meta.get("ellipse_mode", 0))))
+                        ellipse_mode=int(meta.get("ellipse_mode", 0)),
+                        burnout_delta=float(meta.get("burnout_delta", 0.0)),
+                        ros_threshold=float(meta.get("ros_threshold", 0.0))))
     g = run_gpu(ctx, w)
     assert np.array_equal(g["ign"][0].reshape(rows, cols), gr)
     assert g["work"][0] == int(meta["work"])
+    assert g["n_ignited"][0] == int((gr >= 0).sum())
 
 
 @pytest.mark.parametrize("seed", range(16))
