@@ -119,12 +119,12 @@ def test_config1_full(ctx):
 
 @pytest.mark.parametrize("name", ["hand_3x3.txt", "hand_5x5.txt", "hand_wind_eq1_5x5.txt",
                                   "hand_wind_ray_5x5.txt", "hand_delta_5x5.txt",
-                                  "hand_threshold_5x5.txt"])
+                                  "hand_threshold_5x5.txt", "hand_burnhours_3x3.txt"])
 def test_hand_enumeration(ctx, name):
     """Ignition steps and work count of hand-enumerated grids: constant rates
     on all axes, an ellipse (H, B, LB) under wind by Eq. (1) and by the ray of
-    ellipse_mode 1, burn-out below delta and rejected messages under a receive
-    threshold (tests/golden/)."""
+    ellipse_mode 1, burn-out below delta, rejected messages under a receive
+    threshold, and a fire that burns one hour a day (tests/golden/)."""
     from conftest import read_golden_grid
     meta, grid = read_golden_grid(name)
     gr = np.array(grid)
@@ -139,7 +139,9 @@ def test_hand_enumeration(ctx, name):
                         const_lb=float(meta.get("const_lb", 0.0)),
                         ellipse_mode=int(meta.get("ellipse_mode", 0)),
                         burnout_delta=float(meta.get("burnout_delta", 0.0)),
-                        ros_threshold=float(meta.get("ros_threshold", 0.0))))
+                        ros_threshold=float(meta.get("ros_threshold", 0.0)),
+                        burn_hours_min=int(meta.get("burn_hours_min", 0)),
+                        burn_hours_max=int(meta.get("burn_hours_max", 0))))
     g = run_gpu(ctx, w)
     assert np.array_equal(g["ign"][0].reshape(rows, cols), gr)
     assert g["work"][0] == int(meta["work"])
