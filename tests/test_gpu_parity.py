@@ -119,7 +119,8 @@ def test_config1_full(ctx):
 
 @pytest.mark.parametrize("name", ["hand_3x3.txt", "hand_5x5.txt", "hand_wind_eq1_5x5.txt",
                                   "hand_wind_ray_5x5.txt", "hand_delta_5x5.txt",
-                                  "hand_threshold_5x5.txt", "hand_burnhours_3x3.txt"])
+                                  "hand_threshold_5x5.txt", "hand_burnhours_3x3.txt",
+                                  "hand_clock5_3x3.txt"])
 def test_hand_enumeration(ctx, name):
     """Ignition steps and work count of hand-enumerated grids: constant rates
     on all axes, an ellipse (H, B, LB) under wind by Eq. (1) and by the ray of
@@ -141,7 +142,8 @@ def test_hand_enumeration(ctx, name):
                         burnout_delta=float(meta.get("burnout_delta", 0.0)),
                         ros_threshold=float(meta.get("ros_threshold", 0.0)),
                         burn_hours_min=int(meta.get("burn_hours_min", 0)),
-                        burn_hours_max=int(meta.get("burn_hours_max", 0))))
+                        burn_hours_max=int(meta.get("burn_hours_max", 0)),
+                        minutes_per_step=int(meta.get("minutes_per_step", 1))))
     g = run_gpu(ctx, w)
     assert np.array_equal(g["ign"][0].reshape(rows, cols), gr)
     assert g["work"][0] == int(meta["work"])

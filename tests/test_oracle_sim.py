@@ -27,7 +27,8 @@ def homog(rows, cols, wd=270.0, ws=0.0, hours=1, **params):
 
 @pytest.mark.parametrize("name", ["hand_3x3.txt", "hand_5x5.txt", "hand_wind_eq1_5x5.txt",
                                   "hand_wind_ray_5x5.txt", "hand_delta_5x5.txt",
-                                  "hand_threshold_5x5.txt", "hand_burnhours_3x3.txt"])
+                                  "hand_threshold_5x5.txt", "hand_burnhours_3x3.txt",
+                                  "hand_clock5_3x3.txt"])
 @pytest.mark.parametrize("runner", ["run_replica", "run_replica_event"])
 def test_hand_enumeration(name, runner):
     """Hand-enumerated ignition steps and work: constant rates on all axes, and
@@ -46,7 +47,8 @@ def test_hand_enumeration(name, runner):
               ellipse_mode=int(meta.get("ellipse_mode", 0)),
               burnout_delta=float(meta.get("burnout_delta", 0.0)),
               ros_threshold=float(meta.get("ros_threshold", 0.0)),
-              burn_hours_min=bh[0], burn_hours_max=bh[1])
+              burn_hours_min=bh[0], burn_hours_max=bh[1],
+              minutes_per_step=int(meta.get("minutes_per_step", 1)))
     r = getattr(o, runner)(0)
     assert np.array_equal(r["ign"], g)
     assert r["work"] == int(meta["work"])
