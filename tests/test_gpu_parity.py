@@ -120,18 +120,23 @@ def test_config1_full(ctx):
 @pytest.mark.parametrize("name", ["hand_3x3.txt", "hand_5x5.txt", "hand_wind_eq1_5x5.txt",
                                   "hand_wind_ray_5x5.txt", "hand_delta_5x5.txt",
                                   "hand_threshold_5x5.txt", "hand_burnhours_3x3.txt",
-                                  "hand_clock5_3x3.txt"])
+                                  "hand_clock5_3x3.txt", "hand_harvested_5x5.txt"])
 def test_hand_enumeration(ctx, name):
     """Ignition steps and work count of hand-enumerated grids: constant rates
     on all axes, an ellipse (H, B, LB) under wind by Eq. (1) and by the ray of
     ellipse_mode 1, burn-out below delta, rejected messages under a receive
-    threshold, and a fire that burns one hour a day (tests/golden/)."""
+    threshold, a fire that burns one hour a day, a 5-minute clock and a
+    harvested column (tests/golden/)."""
     from conftest import read_golden_grid
     meta, grid = read_golden_grid(name)
     gr = np.array(grid)
     rows, cols = gr.shape
+    unb = None
+    if "harvested_col" in meta:
+        unb = np.zeros((rows, cols), np.uint8)
+        unb[:, int(meta["harvested_col"])] = 1
     w = S.Workload(S.Landscape(np.ones((rows, cols), np.uint8), np.zeros((rows, cols), np.float32),
-                               np.zeros((rows, cols), np.float32)),
+                               np.zeros((rows, cols), np.float32), unburnable=unb),
                    S.constant_weather(int(meta["hours"]), ws=0.0,
                                       wd_from=float(meta.get("wd_from", 270.0))),
                    dict(hours=int(meta["hours"]), ignition_cell=(rows // 2) * cols + cols // 2,

@@ -17,31 +17,42 @@ import oracle
 from conftest import read_golden_grid
 
 
-def homog(rows, cols, wd=270.0, ws=0.0, hours=1, **params):
+def homog(rows, cols, wd=270.0, ws=0.0, hours=1, unburnable=None, **params):
     fuel = np.full((rows, cols), 1, dtype=np.uint8)
     weather = S.constant_weather(hours, ws=ws, wd_from=wd)
     p = dict(hours=hours, ignition_mode=0, ignition_cell=(rows // 2) * cols + cols // 2)
     p.update(params)
-    return oracle.Oracle(fuel, weather=weather, **p)
+    return oracle.Oracle(fuel, unburnable=unburnable, weather=weather, **p)
+
+
+def harvested_mask(meta, shape):
+    """The golden's harvested cells (key harvested_col: one whole column), or None."""
+    if "harvested_col" not in meta:
+        return None
+    unb = np.zeros(shape, np.uint8)
+    unb[:, int(meta["harvested_col"])] = 1
+    return unb
 
 
 @pytest.mark.parametrize("name", ["hand_3x3.txt", "hand_5x5.txt", "hand_wind_eq1_5x5.txt",
                                   "hand_wind_ray_5x5.txt", "hand_delta_5x5.txt",
                                   "hand_threshold_5x5.txt", "hand_burnhours_3x3.txt",
-                                  "hand_clock5_3x3.txt"])
+                                  "hand_clock5_3x3.txt", "hand_harvested_5x5.txt"])
 @pytest.mark.parametrize("runner", ["run_replica", "run_replica_event"])
 def test_hand_enumeration(name, runner):
     """Hand-enumerated ignition steps and work: constant rates on all axes, and
     under wind the ellipse of chosen (H, B, LB) by Eq. (1) and by the ray of
     ellipse_mode 1, each axis's rate derived by hand; burn-out below delta
-    (A5 (i)), rejected messages under a receive threshold, and a fire that
-    burns one hour a day (A5, condition (1)) (tests/golden/)."""
+    (A5 (i)), rejected messages under a receive threshold, a fire that burns
+    one hour a day (A5, condition (1)), a 5-minute clock and a harvested
+    column (tests/golden/)."""
     meta, grid = read_golden_grid(name)
     g = np.array(grid)
     bh = (int(meta.get("burn_hours_min", 0)), int(meta.get("burn_hours_max", 0)))
     if bh != (0, 0) and runner == "run_replica_event":
         pytest.skip("the event search (O2) has no burning-hours limit")
     o = homog(g.shape[0], g.shape[1], hours=int(meta["hours"]), const_ros=float(meta["const_ros"]),
+              unburnable=harvested_mask(meta, g.shape),
               wd=float(meta.get("wd_from", 270.0)), ws=float(meta.get("ws", 0.0)),
               const_bros=float(meta.get("const_bros", 0.0)), const_lb=float(meta.get("const_lb", 0.0)),
               ellipse_mode=int(meta.get("ellipse_mode", 0)),
