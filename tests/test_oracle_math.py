@@ -12,6 +12,7 @@ import mpmath
 import numpy as np
 import pytest
 
+import c2f_synth as S
 import oracle
 from conftest import ROOT
 
@@ -118,3 +119,43 @@ def test_noise_factor_distribution():
     # one draw per (replica, cell, hour): changing any coordinate changes it
     a = oracle.noise_factor(7, 1, 2, 3, sig)
     assert a != oracle.noise_factor(7, 1, 2, 4, sig) and a != oracle.noise_factor(7, 2, 2, 3, sig)
+
+
+def test_noise_factor_equals_a_plain_box_muller():
+    """The perturbation of (replica, cell, hour): f = exp(sigma z), z by Box-Muller
+    from the Philox block at counter (replica, cell, hour, 0) under the key
+    (seed low word, seed high word), u = ((x >> 8) + 1/2) 2^-24 from its first two
+    words, z = sqrt(-2 ln u1) cos(2 pi u2).  The oracle's binary32 value against
+    the same mapping evaluated with float64 libm functions on the known-answer-
+    pinned Philox block: within 2^-17 relative (binary32 rounding of u, log, sqrt,
+    cos and exp, amplified by |sigma z| < 6)."""
+    rng = np.random.default_rng(5)
+    for _ in range(3000):
+        seed = int(rng.integers(0, 2 ** 63))
+        r, c, h = (int(v) for v in rng.integers(0, 2 ** 20, 3))
+        sig = float(np.float32(rng.choice([0.05, 0.1, 0.5, 1.0])))
+        x = oracle.philox4x32_10([r, c, h, 0], [seed & 0xFFFFFFFF, seed >> 32])
+        u1 = ((x[0] >> 8) + 0.5) * 2.0 ** -24
+        u2 = ((x[1] >> 8) + 0.5) * 2.0 ** -24
+        z = math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
+        f_plain = math.exp(sig * z)
+        f = float(oracle.noise_factor(seed, r, c, h, sig))
+        assert abs(f - f_plain) <= 2.0 ** -17 * f_plain, (seed, r, c, h, sig, f, f_plain)
+
+
+def test_ignition_draw_equals_its_integer_mapping():
+    """A random ignition cell (ignition_mode 1): the Philox block at counter
+    (replica, 0, 0, 1) under the run key, index (x0 * n_burnable) >> 32 into the
+    burnable cells in row-major order -- exact integer arithmetic on the
+    known-answer-pinned Philox block."""
+    rng = np.random.default_rng(9)
+    fuel = rng.integers(0, 3, (23, 37)).astype(np.uint8)
+    unb = (rng.random((23, 37)) < 0.1).astype(np.uint8)
+    burnable = np.flatnonzero(((fuel != 0) & (unb == 0)).ravel())
+    for seed in (1, 1002, 2 ** 40 + 17):
+        o = oracle.Oracle(fuel, unburnable=unb, weather=S.constant_weather(1), hours=1,
+                          ignition_mode=1, seed=seed, n_replicas=64)
+        for r in range(64):
+            x = oracle.philox4x32_10([r, 0, 0, 1], [seed & 0xFFFFFFFF, seed >> 32])
+            assert o.ignition_cell(r) == burnable[(x[0] * len(burnable)) >> 32]
+        o.close()
