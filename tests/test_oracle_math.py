@@ -159,3 +159,28 @@ def test_ignition_draw_equals_its_integer_mapping():
             x = oracle.philox4x32_10([r, 0, 0, 1], [seed & 0xFFFFFFFF, seed >> 32])
             assert o.ignition_cell(r) == burnable[(x[0] * len(burnable)) >> 32]
         o.close()
+
+
+def test_burning_hours_and_scenario_draws_equal_their_integer_mappings():
+    """The per-replica draws of the burning-hours limit (counter (replica, 0, 0,
+    3): B = min + (x0 (max - min + 1)) >> 32) and of the weather scenario
+    (counter (replica, 0, 0, 2): the first s with x0 < T_s, T_s = floor(2^32
+    cum_s / total), T_last = 2^32) against exact integer arithmetic on the
+    known-answer-pinned Philox blocks."""
+    fuel = np.ones((5, 5), np.uint8)
+    probs = [1.0, 2.0, 3.0, 4.0, 0.0, 5.0]
+    total = sum(probs)
+    cum = np.cumsum(probs)
+    thr = [int((c / total) * 2.0 ** 32) for c in cum[:-1]] + [2 ** 32]
+    assert list(oracle.scenario_thresholds(probs)) == thr
+    for seed in (3, 2 ** 35 + 1):
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        o = oracle.Oracle(fuel, weather=S.constant_weather(1), hours=1, seed=seed,
+                          burn_hours_min=3, burn_hours_max=17)
+        for r in range(200):
+            x = oracle.philox4x32_10([r, 0, 0, 3], key)
+            assert o.burn_hours(r) == 3 + ((x[0] * 15) >> 32)
+            x = oracle.philox4x32_10([r, 0, 0, 2], key)
+            want = next(s for s, t in enumerate(thr) if x[0] < t)
+            assert oracle.scenario_of(seed, r, thr) == want
+        o.close()
