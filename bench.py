@@ -701,6 +701,10 @@ def frontier_roofline(kt_alone, w, work_per_step, peaks, sms, sm_mhz):
             "issue": {"warp_inst_per_launch": inst, "achieved_ginst_per_s": inst / per_launch_s / 1e9,
                       "peak_ginst_per_s": issue_peak / 1e9, "frac": inst / per_launch_s / issue_peak,
                       "peak_source": f"{sms} SMs x 4 schedulers x {mhz:.0f} MHz (SM clock sampled under load)"},
+            "l2": {"bytes_per_launch": FRONTIER_L2_BYTES_PER_REPLICA * R,
+                   "achieved_gbs": FRONTIER_L2_BYTES_PER_REPLICA * R / per_launch_s / 1e9,
+                   "pct_of_peak_in_capture": FRONTIER_L2_PCT_IN_CAPTURE,
+                   "source": "ncu lts__t_sectors of the same 200-replica launch, scaled by replicas"},
             "period_method_equiv_gbs": FRONTIER_BYTES_PER_UPDATE * work_per_step / per_launch_s / 1e9,
             "period_method_note": "194 B per cell-update (8 x 8 B progress read and written, 8 x 8 B rates, "
                                   "neighbour bits) is what the period-by-period method would move; the "
@@ -733,6 +737,8 @@ def roofline_table(kt, w, fp64_peak):
 FRONTIER_BYTES_PER_UPDATE = 194.0
 FRONTIER_DRAM_BYTES_PER_REPLICA = (96.998e6 + 14.878e6) / 200   # 200-replica launch: read + write
 FRONTIER_WARP_INST_PER_UPDATE = 214.105e6 / 43484764             # warp instructions / cell-updates
+FRONTIER_L2_BYTES_PER_REPLICA = 20432252 * 32 / 200                 # lts__t_sectors x 32 B / replicas
+FRONTIER_L2_PCT_IN_CAPTURE = 0.43                                   # lts__t_sectors % of peak, same capture
 FRONTIER_PROFILE_NOTE = "ncu dram__bytes_read+write and smsp__inst_executed of a 200-replica launch, " \
                         "scaled by replicas / cell-updates"
 FP64_OPS_PER_CELL_HOUR = 364.0      # ncu: (2 x DFMA + DMUL + DADD) / (cells x hours)
