@@ -22,6 +22,7 @@
 // list outgrows its capacity is re-run with a larger one, so results never
 // depend on launch shapes or capacities.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>   // header-only; the ranges cost a pointer test unless a tool is attached
 
 #include <algorithm>
 #include <cmath>
@@ -335,15 +336,22 @@ cudaEvent_t get_event(c2f_ctx *ctx) {
 }
 
 // brackets the launches of one kernel family with events when profiling
+// One kernel family's launches: an NVTX range on the host timeline (named for
+// the step of the method, for profilers that show or filter by ranges) and,
+// with profiling on, a pair of events on the launching stream.
+constexpr const char *kFamilyRange[4] = {"c2f K1 rate-of-spread table", "c2f K2 ignition",
+                                         "c2f K3 frontier", "c2f K4 burn counts"};
 struct ProfScope {
   c2f_ctx *ctx;
   int fam;
   cudaStream_t st;
   cudaEvent_t a = nullptr;
   ProfScope(c2f_ctx *c, int f, cudaStream_t s) : ctx(c), fam(f), st(s) {
+    nvtxRangePushA(kFamilyRange[f & 3]);
     if (ctx->profiling && (a = get_event(ctx))) cudaEventRecord(a, st);
   }
   ~ProfScope() {
+    nvtxRangePop();
     if (!a) return;
     cudaEvent_t b = get_event(ctx);
     if (!b) { ctx->event_pool.push_back(a); return; }
