@@ -398,7 +398,9 @@ typedef struct {
  * 8, 11) when lists are in shared memory; (3) the compaction trigger (4, 6,
  * 7 eighths of capacity); (4) the initial list capacity (automatic, 2x, 4x)
  * when lists are in global memory.  Candidates are timed by the frontier's
- * kernel events.  Results of later runs are the same under any setting; only
+ * kernel events; in stages 2-4 a candidate replaces the incumbent only when
+ * it is at least 3 % faster (smaller differences are timing noise, and
+ * repeated tunings of one mix then agree).  Results of later runs are the same under any setting; only
  * their speed changes.  `out` may be NULL. */
 C2F_API int c2f_autotune_full(c2f_ctx *ctx, int32_t n, const int32_t *landscape_ids,
                               const c2f_sim_params *params, int32_t sample_replicas, c2f_tuning *out);
