@@ -73,3 +73,23 @@ def test_timeline_summary_of_trace_records():
     assert out["replica_ms_median"] == 2.5 and out["replica_ms_max"] == 4.0
     assert out["frontier_span_ms"] == 3.5                              # spans 3 and 4
     assert len(lines) == 4 and lines[0].startswith("K1 build")
+
+
+def test_frontier_roofline_entry_follows_its_inputs():
+    """The K3 roofline entry from a launch time: every figure is the profile's
+    per-replica or per-update constant scaled by the workload and divided by
+    the same duration; none of the measured fractions exceeds 1."""
+    w = S.config2()
+    work = 219342267
+    r = bench.frontier_roofline({"frontier": (44.0, 10)}, w, work, {"hbm_gbs": 6800.0}, 152, 2070.0)
+    s = 4.4e-3
+    R = w.params["n_replicas"]
+    assert r["bound"] == "latency" and abs(r["ms_per_launch"] - 4.4) < 1e-12
+    assert abs(r["traffic"] - bench.FRONTIER_DRAM_BYTES_PER_REPLICA * R) < 1
+    assert abs(r["achieved"] - r["traffic"] / s / 1e9) < 1e-9 and 0 < r["frac"] < 1
+    inst = bench.FRONTIER_WARP_INST_PER_UPDATE * work
+    assert abs(r["issue"]["warp_inst_per_launch"] - inst) < 1
+    assert abs(r["issue"]["frac"] - inst / s / (152 * 4 * 2070e6)) < 1e-12 and r["issue"]["frac"] < 1
+    assert abs(r["l2"]["achieved_gbs"] - bench.FRONTIER_L2_BYTES_PER_REPLICA * R / s / 1e9) < 1e-9
+    assert abs(r["period_method_equiv_gbs"] - 194.0 * work / s / 1e9) < 1e-6
+    assert bench.frontier_roofline({"frontier": (0.0, 0)}, w, work, {}, 152, 2070.0) is None
