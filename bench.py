@@ -36,6 +36,9 @@ Other workloads (one GPU; each prints its own JSON line):
                      probabilities; each of 1000 replicas draws its scenario.
   --workload compare the Sec. 4.1 scar comparison (hourly MSE / SSIM, final
                      norm) of two 1000-replica runs of the 512^2 workload.
+  --workload burnhours  the 512^2 landscape over 48 h with fires that burn only
+                     6-12 hours a day (drawn per replica), beside the same
+                     replicas with no limit.
 """
 from __future__ import annotations
 
@@ -1201,6 +1204,58 @@ def run_scenarios(args):
             "pipelined": pipelined}
 
 
+def run_burnhours(args):
+    """512^2 landscape, 48 h weather, 1000 replicas whose fires burn only the first B
+    hours of each day, B drawn per replica from {6..12} (A5, condition (1)), against
+    the same replicas with no limit.  A step: table (K1) + K2 + K3 + K4, one at a time."""
+    import torch
+    import paper_1905_09317_gb300 as c2f
+    c2f.build()
+    w = S.config2(hours=48)
+    L = w.landscape
+    n = L.fuel.size
+    ctx = c2f.Context(0)
+    lid = ctx.load_landscape(L.fuel, L.slope, L.aspect, cell_size=L.cell_size)
+    ctx.set_weather(lid, w.weather)
+    counts = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx.set_stream(torch.cuda.current_stream().cuda_stream)
+    out = {}
+    for name, over in (("limited", dict(burn_hours_min=6, burn_hours_max=12)), ("unlimited", {})):
+        p = _params_of(c2f, w, **over)
+
+        def step():
+            ctx.build_ros(lid, p, force=1)
+            sid = ctx.simulate(lid, p)
+            ctx.burn_prob_device(sid, counts.data_ptr())
+            return sid
+
+        sid = step()
+        work = int(ctx.get_counters(sid, p.n_replicas)[0].sum())
+        ctx.release(sid)
+        ctx.profile(True)
+        ctx.kernel_times()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.release(step())
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        kt = ctx.kernel_times()
+        ctx.profile(False)
+        out[name] = {"value": work / dt, "unit": METRIC, "ms_per_step": 1e3 * dt, "cell_updates_per_step": work,
+                     "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()}}
+    ctx.close()
+    lim = out["limited"]
+    return {"metric": METRIC, "value": lim["value"], "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "ms_per_step": lim["ms_per_step"], "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "512x512 heterogeneous landscape, 48 h hourly weather, 1000 replicas "
+                                   "burning the first B hours of each day, B uniform in {6..12} per "
+                                   "replica, random ignitions, lognormal(0,0.1) ROS noise",
+                       "timing": "host wall clock, one step at a time (table rebuilt every step)"},
+            "limited": lim, "unlimited": out["unlimited"]}
+
+
 def run_compare(args):
     """Sec. 4.1 scar comparison: the 512^2 workload run with Eq. (1) and with the
     centre-offset ellipse ray (1000 replicas each, ignition steps kept), then
@@ -1281,7 +1336,7 @@ def main():
     ap.add_argument("--serial", action="store_true",
                     help="one synchronous step at a time (no overlap of K1 with the previous frontier)")
     ap.add_argument("--workload", default="landscape",
-                    choices=["landscape", "batch", "serve", "large", "scenarios", "compare"])
+                    choices=["landscape", "batch", "serve", "large", "scenarios", "compare", "burnhours"])
     ap.add_argument("--tune-sample", type=int, default=4096, help="batch: autotuner replica sample")
     ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
@@ -1307,7 +1362,7 @@ def main():
         sys.exit(2)
     if args.workload != "landscape" and args.impl == "ours":
         fn = {"batch": run_batch, "serve": run_serve, "large": run_large,
-              "scenarios": run_scenarios, "compare": run_compare}[args.workload]
+              "scenarios": run_scenarios, "compare": run_compare, "burnhours": run_burnhours}[args.workload]
         print(json.dumps(fn(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
