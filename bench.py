@@ -39,6 +39,8 @@ Other workloads (one GPU; each prints its own JSON line):
   --workload burnhours  the 512^2 landscape over 48 h with fires that burn only
                      6-12 hours a day (drawn per replica), beside the same
                      replicas with no limit.
+  --workload replica-profile  the headline workload's frontier once with the
+                     per-replica counters on: cycles per visited period by phase.
 """
 from __future__ import annotations
 
@@ -1256,6 +1258,40 @@ def run_burnhours(args):
             "limited": lim, "unlimited": out["unlimited"]}
 
 
+def run_replica_profile(args):
+    """The 512^2 x 1000-replica frontier, one launch alone with the per-replica
+    counters on (the profiling build of the kernel): where a visited period's
+    cycles go, averaged over every visited period of every replica."""
+    import paper_1905_09317_gb300 as c2f
+    c2f.build()
+    w = S.config2(n_replicas=args.replicas)
+    L = w.landscape
+    p = _params_of(c2f, w)
+    R = p.n_replicas
+    with c2f.Context(0) as ctx:
+        lid = ctx.load_landscape(L.fuel, L.slope, L.aspect, cell_size=L.cell_size)
+        ctx.set_weather(lid, w.weather)
+        ctx.release(ctx.simulate(lid, p))                       # tables built, warm-up
+        ctx.profile(True, replicas=True)
+        sid = ctx.simulate(lid, p)
+        pr = ctx.replica_profile(sid, R).astype(np.float64)
+        ctx.profile(False)
+        ctx.release(sid)
+    total, bound, send, new, periods, hits, newc, longest, walk, comp, rounds, newit = pr[:, :12].T
+    v = periods.sum()
+    per = lambda x: float(x.sum() / v)   # noqa: E731
+    return {"workload": WORKLOAD, "replicas": R, "counters": "c2f_get_replica_profile, profiling build",
+            "visited_periods_per_replica": float(periods.mean()),
+            "cycles_per_visited_period": {"all": per(total), "hour_boundary": per(bound),
+                                          "calendar_walk": per(walk), "crossing_rounds": per(send - walk),
+                                          "new_cell_setup": per(new)},
+            "per_visited_period": {"crossing_cells": per(hits), "rounds": per(rounds), "new_cells": per(newc),
+                                   "setup_passes": per(newit)},
+            "setup_pass_cycles": float(new.sum() / max(newit.sum(), 1)),
+            "replica_cycles": {"median": float(np.median(total)), "max": float(total.max())},
+            "longest_list_median": float(np.median(longest)), "compactions": float(comp.sum())}
+
+
 def run_compare(args):
     """Sec. 4.1 scar comparison: the 512^2 workload run with Eq. (1) and with the
     centre-offset ellipse ray (1000 replicas each, ignition steps kept), then
@@ -1336,7 +1372,8 @@ def main():
     ap.add_argument("--serial", action="store_true",
                     help="one synchronous step at a time (no overlap of K1 with the previous frontier)")
     ap.add_argument("--workload", default="landscape",
-                    choices=["landscape", "batch", "serve", "large", "scenarios", "compare", "burnhours"])
+                    choices=["landscape", "batch", "serve", "large", "scenarios", "compare", "burnhours",
+                             "replica-profile"])
     ap.add_argument("--tune-sample", type=int, default=4096, help="batch: autotuner replica sample")
     ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
@@ -1362,7 +1399,8 @@ def main():
         sys.exit(2)
     if args.workload != "landscape" and args.impl == "ours":
         fn = {"batch": run_batch, "serve": run_serve, "large": run_large,
-              "scenarios": run_scenarios, "compare": run_compare, "burnhours": run_burnhours}[args.workload]
+              "scenarios": run_scenarios, "compare": run_compare, "burnhours": run_burnhours,
+              "replica-profile": run_replica_profile}[args.workload]
         print(json.dumps(fn(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
