@@ -99,6 +99,8 @@ def _load():
         lib.or_cell_row.restype = None; lib.or_cell_row.argtypes = [C.c_void_p, i32, i32, P(d)]
         lib.or_base_inc.restype = None
         lib.or_base_inc.argtypes = [C.c_void_p, i32, i32, P(i64), P(d)]
+        lib.or_set_row.restype = None
+        lib.or_set_row.argtypes = [C.c_void_p, i32, i32, P(d), d]
         lib.or_ignition_cell.restype = i32; lib.or_ignition_cell.argtypes = [C.c_void_p, i32]
         lib.or_burn_hours.restype = i32; lib.or_burn_hours.argtypes = [C.c_void_p, i32]
         lib.or_scenario_thresholds.restype = C.c_int
@@ -222,6 +224,12 @@ class Oracle:
         hr = C.c_double()
         self.lib.or_base_inc(self._h, int(cell), int(hour), b, C.byref(hr))
         return np.array(list(b), dtype=np.int64), hr.value
+
+    def set_row(self, cell: int, hour: int, ros8, hros: float) -> None:
+        """Test hook: use the given 8 axis rates (m/min) and HROS as the table row
+        of (cell, hour) instead of the oracle's own FBP evaluation."""
+        r = (C.c_double * 8)(*[float(v) for v in ros8])
+        self.lib.or_set_row(self._h, int(cell), int(hour), r, float(hros))
 
     def ignition_cell(self, replica: int) -> int:
         return int(self.lib.or_ignition_cell(self._h, int(replica)))

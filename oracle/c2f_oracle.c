@@ -773,6 +773,17 @@ static void ensure_row(or_ctx *c, int32_t cell, int32_t hour) {
   c->have[idx] = 1;
 }
 
+/* test hook: the table row of (cell, hour) from given rates -- the 8 axis rates
+ * (m/min) and HROS -- instead of the oracle's own FBP evaluation; the
+ * fixed-point increments follow from them as for computed rows ([R2]) */
+OR_API void or_set_row(or_ctx *c, int32_t cell, int32_t hour, const double ros8[8], double hros) {
+  size_t idx = (size_t)hour * c->n + cell;
+  double dt2p32 = (double)c->p.minutes_per_step * FP_ONE;
+  for (int k = 0; k < 8; ++k) c->base[idx * 8 + k] = fixed_of(ros8[k] * dt2p32);
+  c->hros[idx] = hros;
+  c->have[idx] = 1;
+}
+
 /* base fixed-point increments B_k = fixed(ros_k * dt * 2^32) of (cell, hour) */
 OR_API void or_base_inc(or_ctx *c, int32_t cell, int32_t hour, int64_t out[8], double *hros) {
   ensure_row(c, cell, hour);
