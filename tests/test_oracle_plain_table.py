@@ -12,14 +12,18 @@ in all but at most one row in a thousand (in every row, on the machines this
 ran on): the rounding-order choices stay below the increments' resolution.
 """
 import numpy as np
+import pytest
 
 import c2f_synth as S
 import fbp_plain as P
 import oracle
 
 
-def test_plain_libm_table_gives_the_same_fires():
+@pytest.mark.parametrize("ellipse_mode", [0, 1])
+def test_plain_libm_table_gives_the_same_fires(ellipse_mode):
     w = S.config2(side=64, n_replicas=24, hours=6)
+    w.weather[3, 0] = 55.0                          # an hour on the high-wind branch
+    w.params["ellipse_mode"] = ellipse_mode
     L = w.landscape
     own = oracle.Oracle(L.fuel, L.slope, L.aspect, cell_size=L.cell_size, weather=w.weather, **w.params)
     plain = oracle.Oracle(L.fuel, L.slope, L.aspect, cell_size=L.cell_size, weather=w.weather, **w.params)
@@ -31,7 +35,7 @@ def test_plain_libm_table_gives_the_same_fires():
         ws, wd, ffmc, bui = w.weather[h]
         for cell in np.flatnonzero(fuel):
             row = P.fbp_row(P.LIBM, int(fuel[cell]), float(slope[cell]), float(aspect[cell]),
-                            ws, wd, ffmc, bui, 50.0, 60.0, 0, conjugate_back=True)
+                            ws, wd, ffmc, bui, 50.0, 60.0, ellipse_mode, conjugate_back=True)
             plain.set_row(int(cell), h, row["ros8"], row["hros"])
             a, ha = own.base_inc(int(cell), h)
             b, hb = plain.base_inc(int(cell), h)
