@@ -166,3 +166,64 @@ def test_smaller_steps_change_the_scar_little():
     b = oracle.Oracle(L.fuel, weather=w.weather, **dict(w.params, minutes_per_step=2)).run_replica(0)
     diff = (a["scar"] != b["scar"]).sum()
     assert diff <= 0.1 * a["scar"].sum()
+
+
+def _strip_by_integers(seed, sigma, ros, n, hours):
+    """Ignition steps and work of a 1 x n strip (centre ignition, constant rate
+    `ros` on every axis, 1-minute clock) by exact integer arithmetic: per step s
+    (weather hour (s - 1) // 60) a burning cell i advances by
+    inc = min((B F + 2^31) >> 32, D), B = ros 2^32, F = f 2^32 with f the
+    perturbation of (replica 0, i, hour), D = 100 m in 2^-32 m units; its
+    neighbour is reached at the first step where the sum of its increments since
+    it ignited reaches D; a cell burns until its last neighbour has ignited."""
+    D = 100 * 2 ** 32
+    B = int(round(ros * 2 ** 32))
+    steps = 60 * hours
+    incs = {}
+
+    def inc(i, h):
+        if (i, h) not in incs:
+            f = float(oracle.noise_factor(seed, 0, i, h, sigma))
+            F = int(f * 2 ** 32)
+            assert F == f * 2 ** 32                              # f 2^32 is an integer
+            incs[i, h] = min((B * F + 2 ** 31) >> 32, D)
+        return incs[i, h]
+
+    c = n // 2
+    ign = [-1] * n
+    ign[c] = 0
+    for d in (1, -1):
+        i = c
+        while 0 <= i + d < n:
+            p, s = 0, ign[i]
+            while p < D and s < steps:
+                s += 1
+                p += inc(i, (s - 1) // 60)
+            if p < D:
+                break
+            ign[i + d] = s
+            i += d
+    work = 0
+    for i in range(n):
+        if ign[i] >= 0:
+            nb = [ign[j] for j in (i - 1, i + 1) if 0 <= j < n]
+            work += (max(nb) if min(nb) >= 0 else steps) - ign[i]
+    return np.array(ign), work
+
+
+@pytest.mark.parametrize("seed,sigma", [(1, 0.1), (7, 0.5), (12345, 1.0)])
+@pytest.mark.parametrize("runner", ["run_replica", "run_replica_event"])
+def test_noisy_strip_equals_its_integer_model(seed, sigma, runner):
+    """[R2] with the perturbation applied in integers, and progress carried across
+    weather hours (Alg. 1): a noisy 3-hour strip against exact big-integer
+    arithmetic on the perturbations (pinned against a float64 Box-Muller in
+    test_oracle_math.py)."""
+    n, hours = 101, 3
+    fuel = np.ones((1, n), np.uint8)
+    o = oracle.Oracle(fuel, weather=S.constant_weather(hours, ws=0.0), hours=hours, ignition_mode=0,
+                      ignition_cell=n // 2, const_ros=30.0, ros_sigma=sigma, seed=seed)
+    ign, work = _strip_by_integers(seed, sigma, 30.0, n, hours)
+    r = getattr(o, runner)(0)
+    assert np.array_equal(r["ign"][0], ign)
+    assert r["work"] == work
+    assert (ign > 60).any()                                      # crossings after the first hour
