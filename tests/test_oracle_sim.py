@@ -168,14 +168,16 @@ def test_smaller_steps_change_the_scar_little():
     assert diff <= 0.1 * a["scar"].sum()
 
 
-def _strip_by_integers(seed, sigma, ros, n, hours):
+def _strip_by_integers(seed, sigma, ros, n, hours, thr=0.0):
     """Ignition steps and work of a 1 x n strip (centre ignition, constant rate
     `ros` on every axis, 1-minute clock) by exact integer arithmetic: per step s
     (weather hour (s - 1) // 60) a burning cell i advances by
     inc = min((B F + 2^31) >> 32, D), B = ros 2^32, F = f 2^32 with f the
     perturbation of (replica 0, i, hour), D = 100 m in 2^-32 m units; its
     neighbour is reached at the first step where the sum of its increments since
-    it ignited reaches D; a cell burns until its last neighbour has ignited."""
+    it ignited reaches D, and ignites if ros f > thr (binary64 product, its own
+    perturbation at that hour; a rejected message is consumed, so a strip's
+    fire stops there); a cell burns until its last neighbour has ignited."""
     D = 100 * 2 ** 32
     B = int(round(ros * 2 ** 32))
     steps = 60 * hours
@@ -200,6 +202,9 @@ def _strip_by_integers(seed, sigma, ros, n, hours):
                 s += 1
                 p += inc(i, (s - 1) // 60)
             if p < D:
+                break
+            f_next = float(oracle.noise_factor(seed, 0, i + d, (s - 1) // 60, sigma))
+            if not ros * f_next > thr:
                 break
             ign[i + d] = s
             i += d
@@ -227,3 +232,21 @@ def test_noisy_strip_equals_its_integer_model(seed, sigma, runner):
     assert np.array_equal(r["ign"][0], ign)
     assert r["work"] == work
     assert (ign > 60).any()                                      # crossings after the first hour
+
+
+@pytest.mark.parametrize("seed", [11, 21, 42])
+def test_noisy_strip_with_a_receive_threshold(seed):
+    """Sec. 3.1 receive test with noise: a messaged cell ignites only if
+    HROS f > threshold; here HROS = 30 m/min and the threshold 25 m/min, so a
+    cell whose perturbation is below 5/6 rejects its message and stops the
+    strip's fire on that side; the integer model decides each test in binary64
+    like the oracle."""
+    n, hours = 101, 3
+    fuel = np.ones((1, n), np.uint8)
+    o = oracle.Oracle(fuel, weather=S.constant_weather(hours, ws=0.0), hours=hours, ignition_mode=0,
+                      ignition_cell=n // 2, const_ros=30.0, ros_sigma=0.2, seed=seed, ros_threshold=25.0)
+    ign, work = _strip_by_integers(seed, 0.2, 30.0, n, hours, thr=25.0)
+    free, _ = _strip_by_integers(seed, 0.2, 30.0, n, hours)
+    r = o.run_replica(0)
+    assert np.array_equal(r["ign"][0], ign) and r["work"] == work
+    assert 1 < (ign >= 0).sum() < (free >= 0).sum()              # accepted, then rejected messages
