@@ -250,3 +250,78 @@ def test_noisy_strip_with_a_receive_threshold(seed):
     r = o.run_replica(0)
     assert np.array_equal(r["ign"][0], ign) and r["work"] == work
     assert 1 < (ign >= 0).sum() < (free >= 0).sum()              # accepted, then rejected messages
+
+
+def _strip_with_delta(seed, sigma, ros, n, hours, delta):
+    """A 1 x n noisy strip under the delta burn-out of A5 (i), by exact integer
+    arithmetic: a cell whose ros f is below delta in the hour it ignites is
+    Burned at the end of its ignition period and sends nothing; a burning cell
+    whose ros f falls below delta at a later hour boundary (the ignition cell:
+    at hour 0) still advances in that hour's first period and is Burned after
+    it; otherwise as _strip_by_integers, and a cell also burns out once its last
+    neighbour has ignited (A5 (ii))."""
+    D = 100 * 2 ** 32
+    B = int(round(ros * 2 ** 32))
+    steps = 60 * hours
+
+    def f(i, h):
+        return float(oracle.noise_factor(seed, 0, i, h, sigma))
+
+    def inc(i, h):
+        return min((B * int(f(i, h) * 2 ** 32) + 2 ** 31) >> 32, D)
+
+    def dies(i, h):
+        return ros * f(i, h) < delta
+
+    def timeline(i, t):
+        """(step at which cell i, ignited at t, reaches its outward neighbour or
+        None, step at whose end A5 (i) burns it or None)."""
+        h_t = (t - 1) // 60 if t >= 1 else 0
+        if t >= 1 and dies(i, h_t):
+            return None, t
+        p, cross = 0, None
+        for s in range(t + 1, steps + 1):
+            h = (s - 1) // 60
+            boundary = s == 60 * h + 1 and (t == 0 or h > h_t)
+            if cross is None:
+                p += inc(i, h)
+                if p >= D:
+                    cross = s
+            if boundary and dies(i, h):
+                return cross, s
+        return cross, None
+
+    c = n // 2
+    ign = [-1] * n
+    ign[c] = 0
+    for d in (1, -1):
+        i = c
+        while 0 <= i + d < n:
+            cross, _ = timeline(i, ign[i])
+            if cross is None:
+                break
+            ign[i + d] = cross
+            i += d
+    work = 0
+    for i in range(n):
+        if ign[i] < 0:
+            continue
+        nb = [ign[j] for j in (i - 1, i + 1) if 0 <= j < n]
+        ends = [x for x in (timeline(i, ign[i])[1], max(nb) if min(nb) >= 0 else None) if x is not None]
+        work += (min(ends) if ends else steps) - ign[i]
+    return np.array(ign), work
+
+
+@pytest.mark.parametrize("seed", [2, 5, 13])
+def test_noisy_strip_with_delta_burnout(seed):
+    """A5 (i) with noise over 4 hours: cells die when their perturbed HROS is
+    below delta = 22 m/min (HROS 30, sigma 0.2), at ignition or at a later hour
+    boundary; ignition steps and work against the integer model."""
+    n, hours = 201, 4
+    fuel = np.ones((1, n), np.uint8)
+    o = oracle.Oracle(fuel, weather=S.constant_weather(hours, ws=0.0), hours=hours, ignition_mode=0,
+                      ignition_cell=n // 2, const_ros=30.0, ros_sigma=0.2, seed=seed, burnout_delta=22.0)
+    ign, work = _strip_with_delta(seed, 0.2, 30.0, n, hours, 22.0)
+    r = o.run_replica(0)
+    assert np.array_equal(r["ign"][0], ign) and r["work"] == work
+    assert (ign >= 0).sum() > 5                                  # the fire runs, then dies out
