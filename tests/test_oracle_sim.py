@@ -168,7 +168,7 @@ def test_smaller_steps_change_the_scar_little():
     assert diff <= 0.1 * a["scar"].sum()
 
 
-def _strip_by_integers(seed, sigma, ros, n, hours, thr=0.0):
+def _strip_by_integers(seed, sigma, ros, n, hours, thr=0.0, burn_hours=24):
     """Ignition steps and work of a 1 x n strip (centre ignition, constant rate
     `ros` on every axis, 1-minute clock) by exact integer arithmetic: per step s
     (weather hour (s - 1) // 60) a burning cell i advances by
@@ -177,7 +177,9 @@ def _strip_by_integers(seed, sigma, ros, n, hours, thr=0.0):
     neighbour is reached at the first step where the sum of its increments since
     it ignited reaches D, and ignites if ros f > thr (binary64 product, its own
     perturbation at that hour; a rejected message is consumed, so a strip's
-    fire stops there); a cell burns until its last neighbour has ignited."""
+    fire stops there); a cell burns until its last neighbour has ignited.  With
+    burn_hours B < 24 the steps of weather hours h with h mod 24 >= B are dormant:
+    no progress and no work (A5, condition (1))."""
     D = 100 * 2 ** 32
     B = int(round(ros * 2 ** 32))
     steps = 60 * hours
@@ -200,7 +202,8 @@ def _strip_by_integers(seed, sigma, ros, n, hours, thr=0.0):
             p, s = 0, ign[i]
             while p < D and s < steps:
                 s += 1
-                p += inc(i, (s - 1) // 60)
+                if ((s - 1) // 60) % 24 < burn_hours:
+                    p += inc(i, (s - 1) // 60)
             if p < D:
                 break
             f_next = float(oracle.noise_factor(seed, 0, i + d, (s - 1) // 60, sigma))
@@ -208,11 +211,14 @@ def _strip_by_integers(seed, sigma, ros, n, hours, thr=0.0):
                 break
             ign[i + d] = s
             i += d
+    def burning_steps(a, b):         # steps a+1..b outside dormant hours
+        return sum(1 for s in range(a + 1, b + 1) if ((s - 1) // 60) % 24 < burn_hours)
+
     work = 0
     for i in range(n):
         if ign[i] >= 0:
             nb = [ign[j] for j in (i - 1, i + 1) if 0 <= j < n]
-            work += (max(nb) if min(nb) >= 0 else steps) - ign[i]
+            work += burning_steps(ign[i], max(nb) if min(nb) >= 0 else steps)
     return np.array(ign), work
 
 
@@ -325,3 +331,19 @@ def test_noisy_strip_with_delta_burnout(seed):
     r = o.run_replica(0)
     assert np.array_equal(r["ign"][0], ign) and r["work"] == work
     assert (ign >= 0).sum() > 5                                  # the fire runs, then dies out
+
+
+@pytest.mark.parametrize("seed", [4, 9])
+def test_noisy_strip_burning_three_hours_a_day(seed):
+    """A5 condition (1) with noise: over 30 hours a fire that burns only the first
+    3 hours of each day (hours 0-2 and 24-26) against the integer model with the
+    other hours dormant (the event search O2 has no burning-hours limit)."""
+    n, hours = 201, 30
+    fuel = np.ones((1, n), np.uint8)
+    o = oracle.Oracle(fuel, weather=S.constant_weather(hours, ws=0.0), hours=hours, ignition_mode=0,
+                      ignition_cell=n // 2, const_ros=30.0, ros_sigma=0.3, seed=seed,
+                      burn_hours_min=3, burn_hours_max=3)
+    ign, work = _strip_by_integers(seed, 0.3, 30.0, n, hours, burn_hours=3)
+    r = o.run_replica(0)
+    assert np.array_equal(r["ign"][0], ign) and r["work"] == work
+    assert (ign > 24 * 60).any()                                 # it burns again on the second day
