@@ -244,8 +244,6 @@ class Oracle:
         w, ni, ic = C.c_int64(), C.c_int32(), C.c_int32()
         rc = fn(self._h, int(replica), scar.ctypes.data_as(C.c_void_p),
                 ign.ctypes.data_as(C.c_void_p), C.byref(w), C.byref(ni), C.byref(ic))
-        if rc == -2:
-            raise NotImplementedError("the event search (O2) has no burning-hours limit; use run_replica")
         return {"scar": scar.reshape(self.rows, self.cols),
                 "ign": ign.reshape(self.rows, self.cols),
                 "work": int(w.value), "n_ignited": int(ni.value), "ignition_cell": int(ic.value)}

@@ -978,6 +978,8 @@ OR_API int or_run_replica(or_ctx *c, int32_t replica, uint8_t *scar, int32_t *ig
  * step alone; the neighbour's ignition step is the earliest such crossing
  * whose receive test passes.  The work count follows from the ignition
  * steps: cell i is burning at the start of steps t_i+1 .. min(death_i, S).
+ * With a burning-hours limit the dormant hours add no progress, burn
+ * nothing out and count no work.
  * ---------------------------------------------------------------------- */
 typedef struct { int32_t t, cell; } heap_item;
 
@@ -1015,21 +1017,38 @@ static double ros_times_noise(or_ctx *c, int32_t r, int32_t cell, int32_t hour) 
 }
 
 /* first step s >= from at which the delta burn-out fires, or INT32_MAX */
-static int32_t delta_death(or_ctx *c, int32_t r, int32_t cell, int32_t from) {
+/* the step at whose end A5 (i) burns the cell out, tested from step `from` on
+ * in the burning hours only (B = burning hours per day; dormant hours burn
+ * nothing out) */
+static int32_t delta_death(or_ctx *c, int32_t r, int32_t cell, int32_t from, int32_t B) {
   if (!(c->p.burnout_delta > 0.0)) return INT32_MAX;
   int32_t dt = c->p.minutes_per_step;
   for (int32_t s = from; s <= c->S;) {
     int32_t h = ((s - 1) * dt) / 60;
-    if (ros_times_noise(c, r, cell, h) < c->p.burnout_delta) return s;
+    if (h % 24 < B && ros_times_noise(c, r, cell, h) < c->p.burnout_delta) return s;
     s = (h + 1) * c->sph + 1;
   }
   return INT32_MAX;
 }
 
+/* steps a+1 .. b that fall in burning hours (the others count no work) */
+static int64_t burning_steps(const or_ctx *c, int32_t a, int32_t b, int32_t B) {
+  if (B >= 24) return b > a ? (int64_t)(b - a) : 0;
+  int64_t w = 0;
+  for (int32_t s = a + 1; s <= b;) {
+    int32_t h = ((s - 1) * c->p.minutes_per_step) / 60;
+    int32_t L = (h + 1) * c->sph;
+    if (L > b) L = b;
+    if (h % 24 < B) w += (int64_t)(L - s + 1);
+    s = L + 1;
+  }
+  return w;
+}
+
 OR_API int or_run_replica_event(or_ctx *c, int32_t replica, uint8_t *scar, int32_t *ign_out,
                                 int64_t *work_out, int32_t *n_ign_out, int32_t *ic_out) {
-  if (c->p.burn_hours_max > 0) return -2;   /* O2 has no dormant hours; use O1 */
   int32_t n = c->n;
+  const int32_t B = or_burn_hours(c, replica);   /* 24: no dormant hours */
   const int32_t INF = INT32_MAX;
   int32_t *t = (int32_t *)malloc((size_t)n * 4);
   uint8_t *done = (uint8_t *)calloc((size_t)n, 1);
@@ -1048,7 +1067,7 @@ OR_API int or_run_replica_event(or_ctx *c, int32_t replica, uint8_t *scar, int32
     done[i] = 1;
     int32_t ti = t[i];
     int32_t first = ti > 1 ? ti : 1;
-    death[i] = delta_death(c, replica, i, first);
+    death[i] = delta_death(c, replica, i, first, B);
     int32_t limit = death[i] < c->S ? death[i] : c->S;
     for (int k = 0; k < 8; ++k) {
       int32_t j = nbr_of(c, i, k);
@@ -1060,6 +1079,7 @@ OR_API int or_run_replica_event(or_ctx *c, int32_t replica, uint8_t *scar, int32
         int32_t h = ((s - 1) * dt) / 60;
         int32_t L = (h + 1) * c->sph;
         if (L > limit) L = limit;
+        if (h % 24 >= B) { s = L + 1; continue; }   /* dormant hour: no progress */
         int64_t b[8];
         or_base_inc(c, i, h, b, NULL);
         int64_t inc = apply_noise(b[k], noise_fixed(noise_of(c, replica, i, h)), c->D[k]);
@@ -1093,7 +1113,7 @@ OR_API int or_run_replica_event(or_ctx *c, int32_t replica, uint8_t *scar, int32
     }
     int32_t d = death[i] < b ? death[i] : b;
     if (d > c->S) d = c->S;
-    if (d > t[i]) W += (int64_t)(d - t[i]);
+    W += burning_steps(c, t[i], d, B);
   }
   for (int32_t i = 0; i < n; ++i) {
     if (scar) scar[i] = (t[i] != INF) ? 1 : 0;

@@ -6,7 +6,8 @@ drawn per replica uniformly from {min..max} (Philox counter (replica, 0, 0, 3)).
 Pinned by: B = 24 equals no limit; with no perturbation, a run with dormant
 hours equals the unlimited run on the stream of its burning hours alone (same
 scar and work, ignition steps shifted by the dormant periods before them);
-the draw's range and frequencies; the event search refusing the option.
+the draw's range and frequencies; and the event search (O2), a different
+algorithm over ignition steps, equal to the stepped loop (O1) with the limit.
 """
 import math
 
@@ -81,9 +82,24 @@ def test_draw_range_and_frequencies():
         assert o.burn_hours(r) == 3 + (x0 * 6 >> 32)
 
 
-def test_no_limit_reports_24_and_event_search_refuses():
+def test_no_limit_reports_24():
     w = _world(hours=2)
     assert _mk(w).burn_hours(0) == 24
-    o = _mk(w, burn_hours_min=4, burn_hours_max=4)
-    with pytest.raises(NotImplementedError):
-        o.run_replica_event(0)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_event_search_equals_stepped_loop_with_dormant_hours(seed):
+    """O2 = O1 under a burning-hours limit: noise, drawn B in {2..9}, a delta
+    burn-out or a threshold on alternate seeds, 1- and 5-minute clocks."""
+    w = _world(hours=50, seed=seed)
+    over = dict(burn_hours_min=2, burn_hours_max=9, ros_sigma=0.3,
+                minutes_per_step=5 if seed % 3 == 2 else 1)
+    if seed % 2:
+        over["burnout_delta"] = 1.0
+    else:
+        over["ros_threshold"] = 0.5
+    o = _mk(w, **over)
+    for r in range(4):
+        a, b = o.run_replica(r), o.run_replica_event(r)
+        assert np.array_equal(a["ign"], b["ign"]), r
+        assert a["work"] == b["work"] and a["n_ignited"] == b["n_ignited"], r

@@ -49,8 +49,6 @@ def test_hand_enumeration(name, runner):
     meta, grid = read_golden_grid(name)
     g = np.array(grid)
     bh = (int(meta.get("burn_hours_min", 0)), int(meta.get("burn_hours_max", 0)))
-    if bh != (0, 0) and runner == "run_replica_event":
-        pytest.skip("the event search (O2) has no burning-hours limit")
     o = homog(g.shape[0], g.shape[1], hours=int(meta["hours"]), const_ros=float(meta["const_ros"]),
               unburnable=harvested_mask(meta, g.shape),
               wd=float(meta.get("wd_from", 270.0)), ws=float(meta.get("ws", 0.0)),
@@ -334,16 +332,17 @@ def test_noisy_strip_with_delta_burnout(seed):
 
 
 @pytest.mark.parametrize("seed", [4, 9])
-def test_noisy_strip_burning_three_hours_a_day(seed):
+@pytest.mark.parametrize("runner", ["run_replica", "run_replica_event"])
+def test_noisy_strip_burning_three_hours_a_day(seed, runner):
     """A5 condition (1) with noise: over 30 hours a fire that burns only the first
     3 hours of each day (hours 0-2 and 24-26) against the integer model with the
-    other hours dormant (the event search O2 has no burning-hours limit)."""
+    other hours dormant; the stepped loop (O1) and the event search (O2)."""
     n, hours = 201, 30
     fuel = np.ones((1, n), np.uint8)
     o = oracle.Oracle(fuel, weather=S.constant_weather(hours, ws=0.0), hours=hours, ignition_mode=0,
                       ignition_cell=n // 2, const_ros=30.0, ros_sigma=0.3, seed=seed,
                       burn_hours_min=3, burn_hours_max=3)
     ign, work = _strip_by_integers(seed, 0.3, 30.0, n, hours, burn_hours=3)
-    r = o.run_replica(0)
+    r = getattr(o, runner)(0)
     assert np.array_equal(r["ign"][0], ign) and r["work"] == work
     assert (ign > 24 * 60).any()                                 # it burns again on the second day
